@@ -1,0 +1,888 @@
+/*
+ * CPU oracle for the dipolar Barnes-Hut ferrofluid step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+ * CUDA path is checked against.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header or
+ * constant table with the CUDA library.
+ *
+ * Everything here follows the paper (Polyakov et al., "Large-scale Ferrofluid
+ * Simulations on Graphics Processing Units"), Sections 2-3 and 5:
+ *   - reduced dipolar field and force of a pair: Sec. 2, Eqs. (h_dip_red) and
+ *     (f_dip) in reduced units;
+ *   - Lennard-Jones short-range force: Sec. 2, Eq. (LJ) / reduced f_sr;
+ *   - all-pairs sum: Sec. 3.1, Algorithm 1 (plain double loop, self skipped);
+ *   - Barnes-Hut octree, pseudo-particle (Eq. magCenter) and traversal:
+ *     Sec. 3.2;
+ *   - Euler-Maruyama step with dt = 1e-3: Sec. 4;
+ *   - magnetisation observables: Sec. 5.
+ *
+ * Readings where the paper is silent or garbled (opening rule, rotational
+ * dynamics in vector form, noise strength 2 kT Gamma_r, wall potential,
+ * Philox counter layout, Morton quantisation, aggregation order) are listed
+ * with the CUDA design notes; they are restated at each function below.
+ *
+ * Floating point: all sums are FP64.  The Barnes-Hut *tree* (Morton
+ * quantisation, cell centres used for the opening test, the opening decision
+ * itself) is computed in the tree precision `prec` (0 = IEEE single, 1 = IEEE
+ * double) because these floating-point values decide discrete outcomes
+ * (which cell a particle falls in, whether a cell is accepted); the paper ran
+ * in single precision.  Build with -ffp-contract=off and without fast-math so
+ * every single operation is rounded exactly once in the written order.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+#define ORA_MAXLEVEL 21               /* 21 bits per axis -> 63-bit keys */
+#define ORA_QMAX ((1u << 21) - 1u)
+
+/* ------------------------------------------------------------------------ */
+/* threads                                                                   */
+/* ------------------------------------------------------------------------ */
+void ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int ora_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* pair terms                                                                */
+/* ------------------------------------------------------------------------ */
+static double dot3(const double *a, const double *b)
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/*
+ * Reduced dipolar field of particle j at particle k and the reduced dipolar
+ * force on k (Sec. 2, reduced Eqs. h_dip and f_dip):
+ *   h = [3 r (u_j.r) - u_j r^2] / r^5
+ *   f = 3 [r (u_j.u_k) + u_k (u_j.r) + u_j (u_k.r)] / r^5
+ *       - 15 r (u_k.r)(u_j.r) / r^7
+ * with r = rho_k - rho_j.  The force expression is written so that swapping
+ * (k, j) negates it bit for bit (every product and the inner sum commute).
+ * Coincident particles (r = 0) have no defined pair term; the caller skips
+ * them.
+ */
+void ora_pair_dipole(const double r[3], const double uk[3], const double uj[3],
+                     double h[3], double f[3])
+{
+    double r2 = dot3(r, r);
+    double ir = 1.0 / sqrt(r2);
+    double ir2 = ir * ir;
+    double ir3 = ir2 * ir;
+    double ir5 = ir3 * ir2;
+    double ir7 = ir5 * ir2;
+    double bj = dot3(uj, r);
+    double bk = dot3(uk, r);
+    double a = dot3(uj, uk);
+    for (int c = 0; c < 3; ++c) {
+        h[c] = (3.0 * r[c] * bj - uj[c] * r2) * ir5;
+        f[c] = 3.0 * (r[c] * a + (uk[c] * bj + uj[c] * bk)) * ir5
+             - 15.0 * r[c] * (bk * bj) * ir7;
+    }
+}
+
+/*
+ * Reduced Lennard-Jones force as printed (Sec. 2, Eq. LJ / reduced f_sr):
+ *   f = 24 eps r / r^2 [(sigma/r)^12 - (sigma/r)^6],   |r| < rcut, else 0.
+ * Its pair energy is 2 eps (sigma/r)^12 - 4 eps (sigma/r)^6, shifted to zero
+ * at rcut (the printed force is minus the derivative of that energy).
+ * Returns the shifted pair energy.
+ */
+double ora_pair_lj(const double r[3], double eps, double sigma, double rcut,
+                   double f[3])
+{
+    double r2 = dot3(r, r);
+    f[0] = f[1] = f[2] = 0.0;
+    if (!(r2 < rcut * rcut) || r2 == 0.0) return 0.0;
+    double s2 = sigma * sigma / r2;
+    double s6 = s2 * s2 * s2;
+    double s12 = s6 * s6;
+    double coef = 24.0 * eps * (s12 - s6) / r2;
+    for (int c = 0; c < 3; ++c) f[c] = coef * r[c];
+    double sc2 = sigma * sigma / (rcut * rcut);
+    double sc6 = sc2 * sc2 * sc2;
+    double shift = 2.0 * eps * sc6 * sc6 - 4.0 * eps * sc6;
+    return 2.0 * eps * s12 - 4.0 * eps * s6 - shift;
+}
+
+/* ------------------------------------------------------------------------ */
+/* all pairs (Sec. 3.1, Algorithm 1)                                         */
+/* ------------------------------------------------------------------------ */
+/*
+ * For every particle k: h_k = dip_scale * sum_{j != k} h_kj,
+ * f_k = dip_scale * sum_{j != k} f_kj (+ sum_{j != k} f^sr_kj if
+ * include_sr and eps != 0).  e_sr[k] (if non-NULL) receives half of the
+ * shifted LJ energy of every pair k is in.  pos, u, h, f are n x 3 row-major.
+ */
+void ora_allpairs(int64_t n, const double *pos, const double *u,
+                  double dip_scale, double eps, double sigma, double rcut,
+                  int32_t include_sr, double *h, double *f, double *e_sr)
+{
+    int use_lj = include_sr && eps != 0.0 && rcut > 0.0;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t k = 0; k < n; ++k) {
+        double hk[3] = {0, 0, 0}, fd[3] = {0, 0, 0}, fs[3] = {0, 0, 0};
+        double ek = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == k) continue;
+            double r[3] = {pos[3 * k] - pos[3 * j], pos[3 * k + 1] - pos[3 * j + 1],
+                           pos[3 * k + 2] - pos[3 * j + 2]};
+            if (dot3(r, r) == 0.0) continue;
+            double hp[3], fp[3];
+            ora_pair_dipole(r, &u[3 * k], &u[3 * j], hp, fp);
+            for (int c = 0; c < 3; ++c) { hk[c] += hp[c]; fd[c] += fp[c]; }
+            if (use_lj) {
+                double fl[3];
+                ek += 0.5 * ora_pair_lj(r, eps, sigma, rcut, fl);
+                for (int c = 0; c < 3; ++c) fs[c] += fl[c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            h[3 * k + c] = dip_scale * hk[c];
+            f[3 * k + c] = dip_scale * fd[c] + fs[c];
+        }
+        if (e_sr) e_sr[k] = ek;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Morton keys                                                               */
+/* ------------------------------------------------------------------------ */
+/*
+ * Root cube (kernel 1 of Sec. 3.2): origin = per-axis minimum, side = the
+ * largest extent (1 if every extent is zero).  Quantisation, in the tree
+ * precision and with each operation rounded once:
+ *   q_a = min(floor((x_a - min_a) * S), 2^21 - 1),   S = 2^21 / side.
+ * The 63-bit key interleaves the 21 bits of (q_x, q_y, q_z), most significant
+ * first, x highest within each 3-bit digit, so the digit at level L (root =
+ * level 0) is bits 3(21-L)+2 .. 3(21-L) and names the octant x*4 + y*2 + z.
+ */
+static uint64_t interleave3(uint32_t qx, uint32_t qy, uint32_t qz)
+{
+    uint64_t key = 0;
+    for (int b = 0; b < 21; ++b) {
+        key |= (uint64_t)((qx >> b) & 1u) << (3 * b + 2);
+        key |= (uint64_t)((qy >> b) & 1u) << (3 * b + 1);
+        key |= (uint64_t)((qz >> b) & 1u) << (3 * b);
+    }
+    return key;
+}
+
+static uint32_t quant_f(float x, float mn, float S)
+{
+    float t = x - mn;
+    float s = t * S;
+    float fl = floorf(s);
+    if (!(fl > 0.0f)) return 0u;
+    if (fl >= 2097151.0f) return ORA_QMAX;
+    return (uint32_t)fl;
+}
+
+static uint32_t quant_d(double x, double mn, double S)
+{
+    double t = x - mn;
+    double s = t * S;
+    double fl = floor(s);
+    if (!(fl > 0.0)) return 0u;
+    if (fl >= 2097151.0) return ORA_QMAX;
+    return (uint32_t)fl;
+}
+
+/* root[0..2] = origin, root[3] = side (values of the tree precision) */
+void ora_morton(int64_t n, const double *pos, int32_t prec, uint64_t *keys, double root[4])
+{
+    if (prec == 0) {
+        float mn[3], mx[3];
+        for (int a = 0; a < 3; ++a) { mn[a] = (float)pos[a]; mx[a] = (float)pos[a]; }
+        for (int64_t i = 1; i < n; ++i)
+            for (int a = 0; a < 3; ++a) {
+                float x = (float)pos[3 * i + a];
+                if (x < mn[a]) mn[a] = x;
+                if (x > mx[a]) mx[a] = x;
+            }
+        float side = mx[0] - mn[0];
+        for (int a = 1; a < 3; ++a) { float e = mx[a] - mn[a]; if (e > side) side = e; }
+        if (!(side > 0.0f)) side = 1.0f;
+        float S = 2097152.0f / side;
+        for (int64_t i = 0; i < n; ++i) {
+            uint32_t q[3];
+            for (int a = 0; a < 3; ++a) q[a] = quant_f((float)pos[3 * i + a], mn[a], S);
+            keys[i] = interleave3(q[0], q[1], q[2]);
+        }
+        for (int a = 0; a < 3; ++a) root[a] = mn[a];
+        root[3] = side;
+    } else {
+        double mn[3], mx[3];
+        for (int a = 0; a < 3; ++a) { mn[a] = pos[a]; mx[a] = pos[a]; }
+        for (int64_t i = 1; i < n; ++i)
+            for (int a = 0; a < 3; ++a) {
+                double x = pos[3 * i + a];
+                if (x < mn[a]) mn[a] = x;
+                if (x > mx[a]) mx[a] = x;
+            }
+        double side = mx[0] - mn[0];
+        for (int a = 1; a < 3; ++a) { double e = mx[a] - mn[a]; if (e > side) side = e; }
+        if (!(side > 0.0)) side = 1.0;
+        double S = 2097152.0 / side;
+        for (int64_t i = 0; i < n; ++i) {
+            uint32_t q[3];
+            for (int a = 0; a < 3; ++a) q[a] = quant_d(pos[3 * i + a], mn[a], S);
+            keys[i] = interleave3(q[0], q[1], q[2]);
+        }
+        for (int a = 0; a < 3; ++a) root[a] = mn[a];
+        root[3] = side;
+    }
+}
+
+/* sort by (key, input index): kernel 4 of Sec. 3.2, stable */
+typedef struct { uint64_t key; int64_t idx; } ora_kv;
+
+static int cmp_kv(const void *a, const void *b)
+{
+    const ora_kv *x = (const ora_kv *)a, *y = (const ora_kv *)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+/* ------------------------------------------------------------------------ */
+/* octree (Sec. 3.2)                                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n, cap;
+    int32_t *level, *leaf;
+    int64_t *pbegin, *pend, *skip;
+    /* geometry in the tree precision, stored as double */
+    double *lo;          /* 3 per cell: lower corner of the dyadic cube */
+    double *side;        /* cube side */
+    /* aggregates */
+    double *S64, *U64;   /* 3 per cell: sum of positions, sum of moments */
+    float *S32;          /* 3 per cell: single-precision position sums   */
+    double *cen;         /* 3 per cell: pseudo-particle centre used by the tree precision */
+} ora_tree_t;
+
+static void tree_push(ora_tree_t *t)
+{
+    if (t->n < t->cap) return;
+    int64_t nc = t->cap ? 2 * t->cap : 1024;
+    t->level = realloc(t->level, nc * sizeof(int32_t));
+    t->leaf = realloc(t->leaf, nc * sizeof(int32_t));
+    t->pbegin = realloc(t->pbegin, nc * sizeof(int64_t));
+    t->pend = realloc(t->pend, nc * sizeof(int64_t));
+    t->skip = realloc(t->skip, nc * sizeof(int64_t));
+    t->cap = nc;
+}
+
+static void tree_free(ora_tree_t *t)
+{
+    free(t->level); free(t->leaf); free(t->pbegin); free(t->pend); free(t->skip);
+    free(t->lo); free(t->side); free(t->S64); free(t->U64); free(t->S32); free(t->cen);
+    memset(t, 0, sizeof(*t));
+}
+
+/*
+ * Recursive top-down decomposition (Sec. 3.2): a cell covering sorted
+ * particles [b, e) at level L is a leaf if it holds at most leaf_max
+ * particles (the paper: one) or L = 21 (keys exhausted; coincident particles
+ * stay together); otherwise it is split into its non-empty octants, visited
+ * in octant order 0..7, which are maximal runs of equal level-(L+1) digits.
+ * Cells are recorded in depth-first preorder; skip = index of the first cell
+ * after the subtree.
+ */
+static void build_rec(const uint64_t *skeys, int64_t b, int64_t e, int L, int leaf_max,
+                      ora_tree_t *t)
+{
+    tree_push(t);
+    int64_t idx = t->n++;
+    t->level[idx] = L;
+    t->pbegin[idx] = b;
+    t->pend[idx] = e;
+    if (e - b <= leaf_max || L == ORA_MAXLEVEL) {
+        t->leaf[idx] = 1;
+    } else {
+        t->leaf[idx] = 0;
+        int shift = 3 * (ORA_MAXLEVEL - (L + 1));
+        int64_t s = b;
+        while (s < e) {
+            uint64_t d = (skeys[s] >> shift) & 7u;
+            int64_t s2 = s;
+            while (s2 < e && ((skeys[s2] >> shift) & 7u) == d) ++s2;
+            build_rec(skeys, s, s2, L + 1, leaf_max, t);
+            s = s2;
+        }
+    }
+    t->skip[idx] = t->n;
+}
+
+/* de-interleave the level-L prefix of a key into cube coordinates */
+static void prefix_coords(uint64_t key, int L, uint32_t q[3])
+{
+    q[0] = q[1] = q[2] = 0;
+    for (int l = 1; l <= L; ++l) {
+        int shift = 3 * (ORA_MAXLEVEL - l);
+        uint32_t d = (uint32_t)((key >> shift) & 7u);
+        q[0] = (q[0] << 1) | ((d >> 2) & 1u);
+        q[1] = (q[1] << 1) | ((d >> 1) & 1u);
+        q[2] = (q[2] << 1) | (d & 1u);
+    }
+}
+
+/*
+ * Builds keys, order (sorted position -> input index) and the tree.
+ * Geometry of a level-L cell with integer cube coordinates q:
+ *   side_L = side * 2^-L,  lo_a = origin_a + q_a * side_L
+ * (each operation rounded once in the tree precision).
+ * Aggregates (Eq. magCenter): n = particle count, U = sum of moments,
+ * centre = (sum of positions) / n.  Sums run over a leaf's particles in
+ * sorted order and over an internal cell's children in octant order, each
+ * partial sum starting from the first term.  The FP64 sums give the exact
+ * reference; in single precision the same order is used so the centre that
+ * enters the opening test is a defined single-precision number.
+ */
+static void tree_build(int64_t n, const double *pos, const double *u, int prec,
+                       int leaf_max, uint64_t *skeys, int64_t *order, double root[4],
+                       ora_tree_t *t)
+{
+    uint64_t *keys = malloc(n * sizeof(uint64_t));
+    ora_morton(n, pos, prec, keys, root);
+    ora_kv *kv = malloc(n * sizeof(ora_kv));
+    for (int64_t i = 0; i < n; ++i) { kv[i].key = keys[i]; kv[i].idx = i; }
+    qsort(kv, (size_t)n, sizeof(ora_kv), cmp_kv);
+    for (int64_t i = 0; i < n; ++i) { skeys[i] = kv[i].key; order[i] = kv[i].idx; }
+    free(kv);
+    free(keys);
+
+    memset(t, 0, sizeof(*t));
+    build_rec(skeys, 0, n, 0, leaf_max, t);
+    int64_t nc = t->n;
+    t->lo = malloc(3 * nc * sizeof(double));
+    t->side = malloc(nc * sizeof(double));
+    t->S64 = malloc(3 * nc * sizeof(double));
+    t->U64 = malloc(3 * nc * sizeof(double));
+    t->S32 = malloc(3 * nc * sizeof(float));
+    t->cen = malloc(3 * nc * sizeof(double));
+
+    for (int64_t c = 0; c < nc; ++c) {
+        uint32_t q[3];
+        int L = t->level[c];
+        prefix_coords(skeys[t->pbegin[c]], L, q);
+        if (prec == 0) {
+            float side = ldexpf((float)root[3], -L);
+            t->side[c] = side;
+            for (int a = 0; a < 3; ++a) {
+                float off = (float)q[a] * side;
+                float lo = (float)root[a] + off;
+                t->lo[3 * c + a] = lo;
+            }
+        } else {
+            double side = ldexp(root[3], -L);
+            t->side[c] = side;
+            for (int a = 0; a < 3; ++a) {
+                double off = (double)q[a] * side;
+                t->lo[3 * c + a] = root[a] + off;
+            }
+        }
+    }
+
+    /* bottom-up: in preorder every child has a larger index than its parent */
+    for (int64_t c = nc - 1; c >= 0; --c) {
+        double S[3], U[3];
+        float S32[3];
+        if (t->leaf[c]) {
+            int64_t j0 = order[t->pbegin[c]];
+            for (int a = 0; a < 3; ++a) {
+                S[a] = pos[3 * j0 + a];
+                U[a] = u[3 * j0 + a];
+                S32[a] = (float)pos[3 * j0 + a];
+            }
+            for (int64_t s = t->pbegin[c] + 1; s < t->pend[c]; ++s) {
+                int64_t j = order[s];
+                for (int a = 0; a < 3; ++a) {
+                    S[a] += pos[3 * j + a];
+                    U[a] += u[3 * j + a];
+                    S32[a] = S32[a] + (float)pos[3 * j + a];
+                }
+            }
+        } else {
+            int64_t ch = c + 1;
+            for (int a = 0; a < 3; ++a) {
+                S[a] = t->S64[3 * ch + a];
+                U[a] = t->U64[3 * ch + a];
+                S32[a] = t->S32[3 * ch + a];
+            }
+            ch = t->skip[ch];
+            while (ch < t->skip[c]) {
+                for (int a = 0; a < 3; ++a) {
+                    S[a] += t->S64[3 * ch + a];
+                    U[a] += t->U64[3 * ch + a];
+                    S32[a] = S32[a] + t->S32[3 * ch + a];
+                }
+                ch = t->skip[ch];
+            }
+        }
+        int64_t cnt = t->pend[c] - t->pbegin[c];
+        for (int a = 0; a < 3; ++a) {
+            t->S64[3 * c + a] = S[a];
+            t->U64[3 * c + a] = U[a];
+            t->S32[3 * c + a] = S32[a];
+            if (prec == 0)
+                t->cen[3 * c + a] = (double)(S32[a] / (float)cnt);
+            else
+                t->cen[3 * c + a] = S[a] / (double)cnt;
+        }
+    }
+}
+
+/*
+ * Tree introspection for the topology and aggregation tests.  Returns the
+ * number of cells; if it exceeds cap nothing but keys/order/root is written.
+ * cen: the centre in the tree precision; c64: the FP64 centre S64/n.
+ */
+int64_t ora_tree(int64_t n, const double *pos, const double *u, int32_t prec, int32_t leaf_max,
+                 uint64_t *skeys, int64_t *order, double root[4], int64_t cap,
+                 int32_t *level, int32_t *leaf, int64_t *pbegin, int64_t *pend, int64_t *skip,
+                 double *lo, double *side, double *cen, double *c64, double *U64)
+{
+    ora_tree_t t;
+    tree_build(n, pos, u, prec, leaf_max, skeys, order, root, &t);
+    int64_t nc = t.n;
+    if (nc <= cap) {
+        for (int64_t c = 0; c < nc; ++c) {
+            level[c] = t.level[c];
+            leaf[c] = t.leaf[c];
+            pbegin[c] = t.pbegin[c];
+            pend[c] = t.pend[c];
+            skip[c] = t.skip[c];
+            side[c] = t.side[c];
+            double cnt = (double)(t.pend[c] - t.pbegin[c]);
+            for (int a = 0; a < 3; ++a) {
+                lo[3 * c + a] = t.lo[3 * c + a];
+                cen[3 * c + a] = t.cen[3 * c + a];
+                c64[3 * c + a] = t.S64[3 * c + a] / cnt;
+                U64[3 * c + a] = t.U64[3 * c + a];
+            }
+        }
+    }
+    tree_free(&t);
+    return nc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Barnes-Hut traversal (Sec. 3.2)                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double theta;
+    int32_t leaf_max;
+    int32_t prec;          /* tree precision: 0 single, 1 double */
+    double dip_scale;
+    double lj_eps, lj_sigma, lj_rcut;
+    int32_t include_sr;
+    int32_t pad;
+} ora_bh_params;
+
+/*
+ * Opening test (the paper only says "far enough"; reading): a cell C is used
+ * as its pseudo-particle for particle k iff
+ *   (1) k is not one of C's particles,
+ *   (2) side_C^2 < theta^2 * |rho_k - centre_C|^2   (strict), and
+ *   (3) when the LJ term is on, the distance from rho_k to C's cube is at
+ *       least rcut, so every pair closer than rcut is summed exactly.
+ * Evaluated in the tree precision, each operation rounded once, in this
+ * order: d^2 = (dx*dx + dy*dy) + dz*dz; box distance per axis
+ * max(max(lo - x, 0), x - (lo + side)).
+ */
+static int accept_f(const float xk[3], const float c[3], float side, const float lo[3],
+                    float theta2, int use_rcut, float rcut2)
+{
+    float dx = xk[0] - c[0], dy = xk[1] - c[1], dz = xk[2] - c[2];
+    float dxx = dx * dx, dyy = dy * dy, dzz = dz * dz;
+    float d2 = dxx + dyy;
+    d2 = d2 + dzz;
+    float s2 = side * side;
+    float td = theta2 * d2;
+    if (!(s2 < td)) return 0;
+    if (use_rcut) {
+        float t[3];
+        for (int a = 0; a < 3; ++a) {
+            float hi = lo[a] + side;
+            float below = lo[a] - xk[a];
+            float above = xk[a] - hi;
+            float m = below > 0.0f ? below : 0.0f;
+            t[a] = above > m ? above : m;
+        }
+        float txx = t[0] * t[0], tyy = t[1] * t[1], tzz = t[2] * t[2];
+        float b2 = txx + tyy;
+        b2 = b2 + tzz;
+        if (b2 < rcut2) return 0;
+    }
+    return 1;
+}
+
+static int accept_d(const double xk[3], const double c[3], double side, const double lo[3],
+                    double theta2, int use_rcut, double rcut2)
+{
+    double dx = xk[0] - c[0], dy = xk[1] - c[1], dz = xk[2] - c[2];
+    double d2 = dx * dx + dy * dy;
+    d2 = d2 + dz * dz;
+    double s2 = side * side;
+    if (!(s2 < theta2 * d2)) return 0;
+    if (use_rcut) {
+        double t[3];
+        for (int a = 0; a < 3; ++a) {
+            double hi = lo[a] + side;
+            double below = lo[a] - xk[a];
+            double above = xk[a] - hi;
+            double m = below > 0.0 ? below : 0.0;
+            t[a] = above > m ? above : m;
+        }
+        double b2 = t[0] * t[0] + t[1] * t[1];
+        b2 = b2 + t[2] * t[2];
+        if (b2 < rcut2) return 0;
+    }
+    return 1;
+}
+
+typedef struct {
+    const ora_tree_t *t;
+    const int64_t *order;
+    const double *pos, *u;
+    const ora_bh_params *p;
+    int use_rcut;
+    float theta2_f, rcut2_f;
+    double theta2_d, rcut2_d;
+} bh_ctx;
+
+typedef struct {
+    double h[3], fd[3], fs[3], e_sr;
+    int64_t nacc, npair, nopen, ncover;
+} bh_acc;
+
+/* per-particle recursive visit, children in octant order (Sec. 3.2) */
+static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *acc)
+{
+    const ora_tree_t *t = g->t;
+    const double *xk = &g->pos[3 * k];
+    const double *uk = &g->u[3 * k];
+    int inside = (t->pbegin[c] <= sk && sk < t->pend[c]);
+    int ok = 0;
+    if (!inside) {
+        if (g->p->prec == 0) {
+            float xf[3], cf[3], lof[3];
+            for (int a = 0; a < 3; ++a) {
+                xf[a] = (float)xk[a];
+                cf[a] = (float)t->cen[3 * c + a];
+                lof[a] = (float)t->lo[3 * c + a];
+            }
+            ok = accept_f(xf, cf, (float)t->side[c], lof, g->theta2_f, g->use_rcut, g->rcut2_f);
+        } else {
+            ok = accept_d(xk, &t->cen[3 * c], t->side[c], &t->lo[3 * c], g->theta2_d,
+                          g->use_rcut, g->rcut2_d);
+        }
+    }
+    if (ok) {
+        /* pseudo-particle: moment U, position = centre (Eq. magCenter) */
+        double r[3], hp[3], fp[3];
+        for (int a = 0; a < 3; ++a) r[a] = xk[a] - t->cen[3 * c + a];
+        if (dot3(r, r) > 0.0) {
+            ora_pair_dipole(r, uk, &t->U64[3 * c], hp, fp);
+            for (int a = 0; a < 3; ++a) { acc->h[a] += hp[a]; acc->fd[a] += fp[a]; }
+        }
+        acc->nacc++;
+        acc->ncover += t->pend[c] - t->pbegin[c];
+        return;
+    }
+    if (t->leaf[c]) {
+        for (int64_t s = t->pbegin[c]; s < t->pend[c]; ++s) {
+            if (s == sk) continue;
+            int64_t j = g->order[s];
+            double r[3], hp[3], fp[3];
+            for (int a = 0; a < 3; ++a) r[a] = xk[a] - g->pos[3 * j + a];
+            acc->npair++;
+            if (dot3(r, r) == 0.0) continue;
+            ora_pair_dipole(r, uk, &g->u[3 * j], hp, fp);
+            for (int a = 0; a < 3; ++a) { acc->h[a] += hp[a]; acc->fd[a] += fp[a]; }
+            if (g->use_rcut && g->p->include_sr) {
+                double fl[3];
+                acc->e_sr += 0.5 * ora_pair_lj(r, g->p->lj_eps, g->p->lj_sigma, g->p->lj_rcut, fl);
+                for (int a = 0; a < 3; ++a) acc->fs[a] += fl[a];
+            }
+        }
+        return;
+    }
+    acc->nopen++;
+    int64_t ch = c + 1;
+    while (ch < t->skip[c]) {
+        bh_visit(g, k, sk, ch, acc);
+        ch = t->skip[ch];
+    }
+}
+
+/*
+ * Barnes-Hut field and force on every particle (or on the n_only particles
+ * listed in `only`; other rows are left untouched).  Outputs are in input
+ * order: h = dip_scale * h_dip, f = dip_scale * f_dip + f_sr, e_sr = half
+ * the shifted LJ energy of k's pairs.  nacc / npair / nopen count accepted
+ * cells, exact pairs evaluated and cells opened; ncover counts the particles
+ * inside accepted cells (ncover + npair = n - 1 when every other particle is
+ * reached exactly once).  Returns the cell count.
+ */
+int64_t ora_bh(int64_t n, const double *pos, const double *u, const ora_bh_params *p,
+               const int64_t *only, int64_t n_only,
+               double *h, double *f, double *e_sr, int64_t *nacc, int64_t *npair, int64_t *nopen,
+               int64_t *ncover)
+{
+    uint64_t *skeys = malloc(n * sizeof(uint64_t));
+    int64_t *order = malloc(n * sizeof(int64_t));
+    int64_t *rank = malloc(n * sizeof(int64_t));
+    double root[4];
+    ora_tree_t t;
+    tree_build(n, pos, u, p->prec, p->leaf_max, skeys, order, root, &t);
+    for (int64_t s = 0; s < n; ++s) rank[order[s]] = s;
+
+    bh_ctx g;
+    g.t = &t;
+    g.order = order;
+    g.pos = pos;
+    g.u = u;
+    g.p = p;
+    g.use_rcut = (p->lj_eps != 0.0 && p->lj_rcut > 0.0);
+    g.theta2_d = p->theta * p->theta;
+    g.theta2_f = (float)g.theta2_d;
+    g.rcut2_d = g.use_rcut ? p->lj_rcut * p->lj_rcut : 0.0;
+    g.rcut2_f = (float)g.rcut2_d;
+
+    int64_t cnt = only ? n_only : n;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < cnt; ++q) {
+        int64_t k = only ? only[q] : q;
+        bh_acc acc;
+        memset(&acc, 0, sizeof(acc));
+        bh_visit(&g, k, rank[k], 0, &acc);
+        for (int a = 0; a < 3; ++a) {
+            h[3 * k + a] = p->dip_scale * acc.h[a];
+            f[3 * k + a] = p->dip_scale * acc.fd[a] + acc.fs[a];
+        }
+        if (e_sr) e_sr[k] = acc.e_sr;
+        if (nacc) nacc[k] = acc.nacc;
+        if (npair) npair[k] = acc.npair;
+        if (nopen) nopen[k] = acc.nopen;
+        if (ncover) ncover[k] = acc.ncover;
+    }
+    int64_t nc = t.n;
+    tree_free(&t);
+    free(skeys);
+    free(order);
+    free(rank);
+    return nc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)                         */
+/* ------------------------------------------------------------------------ */
+/*
+ * One round: multiply words 0 and 2 by the round multipliers, take high and
+ * low halves, and mix with the other words and the round key.  Ten rounds;
+ * the key is bumped by the Weyl constants between rounds.
+ */
+static void philox_round(uint32_t c[4], const uint32_t k[2])
+{
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k[0] += 0x9E3779B9u; k[1] += 0xBB67AE85u; }
+        philox_round(c, k);
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+/*
+ * Eight standard normals for particle `id` at step `step` (reading of the
+ * white noise of Sec. 2): key = (seed lo, seed hi), counter = (step lo,
+ * step hi, id, block) for block 0 and 1; each pair (a, b) of words gives
+ * u1 = (a + 1) 2^-32 in (0, 1], u2 = b 2^-32 and, by Box-Muller,
+ * z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = sqrt(-2 ln u1) sin(2 pi u2).
+ */
+void ora_normals(uint64_t seed, uint64_t step, uint32_t id, double z[8])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (uint32_t blk = 0; blk < 2; ++blk) {
+        uint32_t ctr[4] = {(uint32_t)step, (uint32_t)(step >> 32), id, blk};
+        uint32_t w[4];
+        ora_philox4x32_10(ctr, key, w);
+        for (int p = 0; p < 2; ++p) {
+            double u1 = ((double)w[2 * p] + 1.0) * 0x1p-32;
+            double u2 = (double)w[2 * p + 1] * 0x1p-32;
+            double rad = sqrt(-2.0 * log(u1));
+            z[4 * blk + 2 * p] = rad * cos(2.0 * M_PI * u2);
+            z[4 * blk + 2 * p + 1] = rad * sin(2.0 * M_PI * u2);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* walls and the Euler-Maruyama step                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double dt;
+    double gamma_t, gamma_r;
+    double inertia;        /* 2/5 in reduced units (Sec. 2) */
+    double kT;
+    double rot_noise;      /* fluctuation-dissipation: 2 */
+    double h_ext[3];
+    double box_lo[3], box_hi[3];
+    int32_t walls;
+    int32_t pad;
+    double wall_eps;
+    uint64_t seed;
+} ora_dyn;
+
+#define ORA_WALL_SIGMA 0.5
+#define ORA_WALL_WMIN 0.01
+
+/*
+ * Wall force along one axis ("LJ of the same type", Sec. 2): with w the
+ * distance from the centre to the plane, sigma_w = 1/2 and the force cut
+ * where it vanishes (w = sigma_w), F = 24 eps / w [(s/w)^12 - (s/w)^6],
+ * pushing away from the plane; w is clamped below at 0.01.  Energy
+ * 2 eps (s/w)^12 - 4 eps (s/w)^6 + 2 eps (zero at the cut).
+ */
+static double wall_f(double w, double eps, double *e)
+{
+    if (!(w < ORA_WALL_SIGMA)) { *e = 0.0; return 0.0; }
+    if (w < ORA_WALL_WMIN) w = ORA_WALL_WMIN;
+    double s = ORA_WALL_SIGMA / w;
+    double s2 = s * s;
+    double s6 = s2 * s2 * s2;
+    *e = 2.0 * eps * s6 * s6 - 4.0 * eps * s6 + 2.0 * eps;
+    return 24.0 * eps * (s6 * s6 - s6) / w;
+}
+
+/* wall force and energy on one particle; planes at box_lo - 1/2 and box_hi + 1/2 */
+void ora_wall(const double x[3], const ora_dyn *d, double fw[3], double *ew)
+{
+    *ew = 0.0;
+    fw[0] = fw[1] = fw[2] = 0.0;
+    if (!d->walls) return;
+    for (int a = 0; a < 3; ++a) {
+        double e1, e2;
+        fw[a] += wall_f(x[a] - (d->box_lo[a] - 0.5), d->wall_eps, &e1);
+        fw[a] -= wall_f((d->box_hi[a] + 0.5) - x[a], d->wall_eps, &e2);
+        *ew += e1 + e2;
+    }
+}
+
+/*
+ * One explicit Euler-Maruyama step (Sec. 4, dt = 1e-3) of the reduced
+ * Langevin equations of Sec. 2, translational part as printed (unit reduced
+ * mass) and rotational part in vector form (reading of the garbled angle
+ * equations): with h = h_dip + h_ext and f = f_int + f_wall,
+ *   x' = x + dt v
+ *   v' = v + dt (f - G_t v) + sqrt(2 G_t kT dt) xi_t
+ *   w' = w + dt (u x h - G_r w) / I + sqrt(c_r G_r kT dt) / I xi_r
+ *   u' = (u + dt w x u) / |u + dt w x u|
+ * all right-hand sides from the step-n state; xi_t = normals 0..2 and
+ * xi_r = normals 3..5 of (seed, step, id).  Arrays are n x 3, updated in
+ * place.
+ */
+void ora_em_step(int64_t n, double *pos, double *vel, double *u, double *om,
+                 const int64_t *ids, const double *hdip, const double *fint,
+                 const ora_dyn *d, uint64_t step)
+{
+    double st = sqrt(2.0 * d->gamma_t * d->kT * d->dt);
+    double sr = sqrt(d->rot_noise * d->gamma_r * d->kT * d->dt) / d->inertia;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        double *x = &pos[3 * k], *v = &vel[3 * k], *uu = &u[3 * k], *w = &om[3 * k];
+        double h[3], f[3], fw[3], ew, z[8];
+        ora_wall(x, d, fw, &ew);
+        for (int a = 0; a < 3; ++a) {
+            h[a] = hdip[3 * k + a] + d->h_ext[a];
+            f[a] = fint[3 * k + a] + fw[a];
+        }
+        ora_normals(d->seed, step, (uint32_t)ids[k], z);
+        double tq[3] = {uu[1] * h[2] - uu[2] * h[1], uu[2] * h[0] - uu[0] * h[2],
+                        uu[0] * h[1] - uu[1] * h[0]};
+        double wxu[3] = {w[1] * uu[2] - w[2] * uu[1], w[2] * uu[0] - w[0] * uu[2],
+                         w[0] * uu[1] - w[1] * uu[0]};
+        double xn[3], vn[3], wn[3], un[3];
+        for (int a = 0; a < 3; ++a) {
+            xn[a] = x[a] + d->dt * v[a];
+            vn[a] = v[a] + d->dt * (f[a] - d->gamma_t * v[a]) + st * z[a];
+            wn[a] = w[a] + d->dt * (tq[a] - d->gamma_r * w[a]) / d->inertia + sr * z[3 + a];
+            un[a] = uu[a] + d->dt * wxu[a];
+        }
+        double nrm = sqrt(dot3(un, un));
+        for (int a = 0; a < 3; ++a) {
+            x[a] = xn[a];
+            v[a] = vn[a];
+            w[a] = wn[a];
+            uu[a] = un[a] / nrm;
+        }
+    }
+}
+
+/*
+ * Observables (Sec. 5) and energies, FP64:
+ * out[0] e_dip = -1/2 sum u.h_dip      out[1] e_zeeman = -sum u.h_ext
+ * out[2] e_sr  = sum e_sr[k]           out[3] e_wall
+ * out[4] e_kin_t = 1/2 sum v^2         out[5] e_kin_r = I/2 sum w^2
+ * out[6..8] <u> = (1/N) sum u          out[9] <h_dip_z> = (1/N) sum h_dip_z
+ */
+void ora_energy(int64_t n, const double *pos, const double *vel, const double *u,
+                const double *om, const double *hdip, const double *e_sr,
+                const ora_dyn *d, double out[10])
+{
+    memset(out, 0, 10 * sizeof(double));
+    for (int64_t k = 0; k < n; ++k) {
+        const double *uu = &u[3 * k];
+        double fw[3], ew;
+        ora_wall(&pos[3 * k], d, fw, &ew);
+        out[0] += -0.5 * dot3(uu, &hdip[3 * k]);
+        out[1] += -dot3(uu, d->h_ext);
+        out[2] += e_sr ? e_sr[k] : 0.0;
+        out[3] += ew;
+        out[4] += 0.5 * dot3(&vel[3 * k], &vel[3 * k]);
+        out[5] += 0.5 * d->inertia * dot3(&om[3 * k], &om[3 * k]);
+        for (int a = 0; a < 3; ++a) out[6 + a] += uu[a];
+        out[9] += hdip[3 * k + 2];
+    }
+    for (int a = 0; a < 3; ++a) out[6 + a] /= (double)n;
+    out[9] /= (double)n;
+}

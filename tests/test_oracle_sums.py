@@ -1,0 +1,116 @@
+"""Pins for the oracle's all-pairs and Barnes-Hut sums (Sec. 3.1, 3.2).
+
+Conservation laws of a pair interaction (total force and total angular
+momentum vanish), the total energy against the textbook pair energy,
+Barnes-Hut at theta = 0 against all-pairs, every other particle reached
+exactly once by the traversal, error decreasing with theta, and the LJ pairs
+inside the cut-off always summed exactly.
+"""
+import numpy as np
+import pytest
+
+from paper_1212_2934_gb300 import synth
+
+
+def _system(n, seed, phi=0.1):
+    side = synth.box_side_for_fraction(n, phi)
+    return synth.rsa_cube(n, side, seed), synth.isotropic_moments(n, seed)
+
+
+def test_two_dipoles(ora):
+    pos = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 1.5]])
+    u = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0]])
+    h, f, _ = ora.allpairs(pos, u)
+    np.testing.assert_allclose(h, [[0, 0, 2 / 1.5 ** 3]] * 2, rtol=1e-15)
+    np.testing.assert_allclose(f, [[0, 0, 6 / 1.5 ** 4], [0, 0, -6 / 1.5 ** 4]], rtol=1e-15)
+
+
+def test_conservation(ora):
+    pos, u = _system(300, 3)
+    h, f, _ = ora.allpairs(pos, u, lj_eps=1.0)
+    fs = np.abs(f).sum()
+    assert np.abs(f.sum(axis=0)).max() < 1e-13 * fs
+    # total angular momentum: sum u x h + rho x f = 0 for rotation-invariant pair energies
+    L = np.cross(u, h).sum(axis=0) + np.cross(pos, f).sum(axis=0)
+    scale = np.abs(np.cross(u, h)).sum() + np.abs(np.cross(pos, f)).sum()
+    assert np.abs(L).max() < 1e-12 * scale
+
+
+def test_energy_matches_pair_energy(ora):
+    pos, u = _system(120, 4)
+    h, _, _ = ora.allpairs(pos, u)
+    e_field = -0.5 * np.einsum("ij,ij->", u, h)
+    e_pairs = 0.0
+    for k in range(len(pos)):
+        for j in range(k + 1, len(pos)):
+            r = pos[k] - pos[j]
+            rn = np.linalg.norm(r)
+            e_pairs += u[k] @ u[j] / rn ** 3 - 3 * (u[k] @ r) * (u[j] @ r) / rn ** 5
+    np.testing.assert_allclose(e_field, e_pairs, rtol=1e-12)
+
+
+def test_dip_scale_and_self_skip(ora):
+    pos, u = _system(50, 5)
+    h1, f1, _ = ora.allpairs(pos, u, dip_scale=1.0)
+    h2, f2, _ = ora.allpairs(pos, u, dip_scale=0.125)
+    np.testing.assert_allclose(h2, 0.125 * h1, rtol=1e-15)
+    np.testing.assert_allclose(f2, 0.125 * f1, rtol=1e-15)
+    # brute force over ordered pairs with the pair routine
+    hb = np.zeros_like(h1)
+    for k in range(len(pos)):
+        for j in range(len(pos)):
+            if j != k:
+                hb[k] += ora.pair_dipole(pos[k] - pos[j], u[k], u[j])[0]
+    np.testing.assert_allclose(h1, hb, rtol=1e-13)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("leaf_max", [1, 8])
+def test_bh_theta0_equals_allpairs(ora, prec, leaf_max):
+    pos, u = _system(700, 6)
+    if prec == "f32":
+        pos = pos.astype(np.float32).astype(np.float64)
+    h, f, e = ora.allpairs(pos, u, lj_eps=1.0)
+    r = ora.bh(pos, u, 0.0, leaf_max, prec, lj_eps=1.0)
+    assert np.all(r["nacc"] == 0) and np.all(r["npair"] == len(pos) - 1)
+    np.testing.assert_allclose(r["h"], h, rtol=1e-12, atol=1e-14 * np.abs(h).max())
+    np.testing.assert_allclose(r["f"], f, rtol=1e-12, atol=1e-14 * np.abs(f).max())
+    np.testing.assert_allclose(r["e_sr"], e, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.7, 1.2])
+@pytest.mark.parametrize("leaf_max", [1, 4])
+def test_bh_reaches_every_particle_once(ora, theta, leaf_max):
+    pos, u = _system(1500, 7)
+    r = ora.bh(pos, u, theta, leaf_max, "f32", lj_eps=1.0)
+    assert np.all(r["ncover"] + r["npair"] == len(pos) - 1)
+    assert r["nacc"].sum() > 0
+
+
+def test_bh_error_decreases_with_theta(ora):
+    pos, u = _system(2000, 8, phi=0.05)
+    h, f, _ = ora.allpairs(pos, u)
+    from conftest import rel_err
+
+    errs = []
+    for th in (0.9, 0.7, 0.5, 0.3, 0.15):
+        r = ora.bh(pos, u, th, 1, "f64")
+        errs.append(np.sqrt((rel_err(r["h"], h) ** 2).mean()))
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+
+
+def test_bh_lj_pairs_inside_cut_are_exact(ora):
+    pos, u = _system(1500, 9, phi=0.2)
+    _, f_ap, e_ap = ora.allpairs(pos, u, dip_scale=0.0, lj_eps=1.0, lj_rcut=2.5)
+    r = ora.bh(pos, u, 0.9, 1, "f32", dip_scale=0.0, lj_eps=1.0, lj_rcut=2.5)
+    np.testing.assert_allclose(r["f"], f_ap, rtol=1e-12, atol=1e-14 * np.abs(f_ap).max())
+    np.testing.assert_allclose(r["e_sr"], e_ap, rtol=1e-12, atol=1e-14)
+
+
+def test_bh_subset_rows(ora):
+    pos, u = _system(900, 10)
+    full = ora.bh(pos, u, 0.5, 1, "f32", lj_eps=1.0)
+    idx = np.array([0, 17, 450, 899])
+    part = ora.bh(pos, u, 0.5, 1, "f32", lj_eps=1.0, only=idx)
+    np.testing.assert_array_equal(part["h"][idx], full["h"][idx])
+    np.testing.assert_array_equal(part["nacc"][idx], full["nacc"][idx])
