@@ -57,7 +57,7 @@ def lib():
         L.ora_pair_lj.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp]
         L.ora_pair_lj.restype = C.c_double
         L.ora_allpairs.argtypes = [_i64, _dp, _dp, C.c_double, C.c_double, C.c_double,
-                                   C.c_double, C.c_int32, _dp, _dp, C.c_void_p]
+                                   C.c_double, C.c_int32, C.c_int32, _dp, _dp, C.c_void_p]
         L.ora_morton.argtypes = [_i64, _dp, C.c_int32, _u64p, _dp]
         L.ora_tree.argtypes = [_i64, _dp, _dp, C.c_int32, C.c_int32, _u64p, _i64p, _dp, _i64,
                                _i32p, _i32p, _i64p, _i64p, _i64p, _dp, _dp, _dp, _dp, _dp]
@@ -112,15 +112,19 @@ def pair_lj(r, eps=1.0, sigma=1.0, rcut=2.5):
     return f, e
 
 
-def allpairs(pos, u, dip_scale=1.0, lj_eps=0.0, lj_sigma=1.0, lj_rcut=2.5, include_sr=True):
-    """Exact O(N^2) field and force (Sec. 3.1).  Returns (h, f, e_sr), FP64."""
+def allpairs(pos, u, dip_scale=1.0, lj_eps=0.0, lj_sigma=1.0, lj_rcut=2.5, include_sr=True,
+             cut_prec="f64"):
+    """Exact O(N^2) field and force (Sec. 3.1).  Returns (h, f, e_sr), FP64.
+
+    cut_prec: precision of the LJ cut-off test (the single-precision kernel
+    takes it in single precision)."""
     pos, u = _vec3(pos), _vec3(u)
     n = pos.shape[0]
     h = np.zeros((n, 3))
     f = np.zeros((n, 3))
     e = np.zeros(n)
     lib().ora_allpairs(n, pos, u, dip_scale, lj_eps, lj_sigma, lj_rcut, int(bool(include_sr)),
-                       h, f, _ptr(e))
+                       _prec(cut_prec), h, f, _ptr(e))
     return h, f, e
 
 
@@ -271,7 +275,8 @@ def fields(state, algo, theta=0.5, leaf_max=1, prec="f64", dip_scale=1.0, lj_eps
            lj_sigma=1.0, lj_rcut=2.5):
     """Dipolar field and interaction force for a state: AP or BH (tree precision prec)."""
     if algo == "ap":
-        h, f, e = allpairs(state["pos"], state["u"], dip_scale, lj_eps, lj_sigma, lj_rcut, True)
+        h, f, e = allpairs(state["pos"], state["u"], dip_scale, lj_eps, lj_sigma, lj_rcut, True,
+                           prec)
         return h, f, e
     r = bh(state["pos"], state["u"], theta, leaf_max, prec, dip_scale, lj_eps, lj_sigma, lj_rcut,
            True)

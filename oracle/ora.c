@@ -128,6 +128,46 @@ double ora_pair_lj(const double r[3], double eps, double sigma, double rcut,
     return 2.0 * eps * s12 - 4.0 * eps * s6 - shift;
 }
 
+/*
+ * Whether a pair lies inside the LJ cut-off, decided in the given precision
+ * (0 single, 1 double) with each operation rounded once:
+ * r2 = (dx*dx + dy*dy) + dz*dz < rcut^2, with the differences formed in that
+ * precision.  The cut decides a discrete outcome, so it is taken in the
+ * precision of the arithmetic under test.
+ */
+static int lj_inside(const double xk[3], const double xj[3], double rcut, int prec)
+{
+    if (prec == 0) {
+        float d[3];
+        for (int a = 0; a < 3; ++a) d[a] = (float)xk[a] - (float)xj[a];
+        float dxx = d[0] * d[0], dyy = d[1] * d[1], dzz = d[2] * d[2];
+        float r2 = dxx + dyy;
+        r2 = r2 + dzz;
+        float rc2 = (float)(rcut * rcut);
+        return r2 < rc2 && r2 > 0.0f;
+    }
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = xk[a] - xj[a];
+    double r2 = d[0] * d[0] + d[1] * d[1];
+    r2 = r2 + d[2] * d[2];
+    return r2 < rcut * rcut && r2 > 0.0;
+}
+
+/* LJ force and shifted pair energy for a pair already known to be inside the cut */
+static double lj_pair_inside(const double r[3], double eps, double sigma, double rcut, double f[3])
+{
+    double r2 = dot3(r, r);
+    double s2 = sigma * sigma / r2;
+    double s6 = s2 * s2 * s2;
+    double s12 = s6 * s6;
+    double coef = 24.0 * eps * (s12 - s6) / r2;
+    for (int c = 0; c < 3; ++c) f[c] = coef * r[c];
+    double sc2 = sigma * sigma / (rcut * rcut);
+    double sc6 = sc2 * sc2 * sc2;
+    double shift = 2.0 * eps * sc6 * sc6 - 4.0 * eps * sc6;
+    return 2.0 * eps * s12 - 4.0 * eps * s6 - shift;
+}
+
 /* ------------------------------------------------------------------------ */
 /* all pairs (Sec. 3.1, Algorithm 1)                                         */
 /* ------------------------------------------------------------------------ */
@@ -136,10 +176,12 @@ double ora_pair_lj(const double r[3], double eps, double sigma, double rcut,
  * f_k = dip_scale * sum_{j != k} f_kj (+ sum_{j != k} f^sr_kj if
  * include_sr and eps != 0).  e_sr[k] (if non-NULL) receives half of the
  * shifted LJ energy of every pair k is in.  pos, u, h, f are n x 3 row-major.
+ * cut_prec: precision in which the LJ cut-off test is taken (0 single,
+ * 1 double).
  */
 void ora_allpairs(int64_t n, const double *pos, const double *u,
                   double dip_scale, double eps, double sigma, double rcut,
-                  int32_t include_sr, double *h, double *f, double *e_sr)
+                  int32_t include_sr, int32_t cut_prec, double *h, double *f, double *e_sr)
 {
     int use_lj = include_sr && eps != 0.0 && rcut > 0.0;
 #pragma omp parallel for schedule(dynamic, 8)
@@ -154,9 +196,9 @@ void ora_allpairs(int64_t n, const double *pos, const double *u,
             double hp[3], fp[3];
             ora_pair_dipole(r, &u[3 * k], &u[3 * j], hp, fp);
             for (int c = 0; c < 3; ++c) { hk[c] += hp[c]; fd[c] += fp[c]; }
-            if (use_lj) {
+            if (use_lj && lj_inside(&pos[3 * k], &pos[3 * j], rcut, cut_prec)) {
                 double fl[3];
-                ek += 0.5 * ora_pair_lj(r, eps, sigma, rcut, fl);
+                ek += 0.5 * lj_pair_inside(r, eps, sigma, rcut, fl);
                 for (int c = 0; c < 3; ++c) fs[c] += fl[c];
             }
         }
@@ -624,9 +666,10 @@ static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *
             if (dot3(r, r) == 0.0) continue;
             ora_pair_dipole(r, uk, &g->u[3 * j], hp, fp);
             for (int a = 0; a < 3; ++a) { acc->h[a] += hp[a]; acc->fd[a] += fp[a]; }
-            if (g->use_rcut && g->p->include_sr) {
+            if (g->use_rcut && g->p->include_sr &&
+                lj_inside(xk, &g->pos[3 * j], g->p->lj_rcut, g->p->prec)) {
                 double fl[3];
-                acc->e_sr += 0.5 * ora_pair_lj(r, g->p->lj_eps, g->p->lj_sigma, g->p->lj_rcut, fl);
+                acc->e_sr += 0.5 * lj_pair_inside(r, g->p->lj_eps, g->p->lj_sigma, g->p->lj_rcut, fl);
                 for (int a = 0; a < 3; ++a) acc->fs[a] += fl[a];
             }
         }
