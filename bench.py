@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Throughput of the dipolar Barnes-Hut ferrofluid step on GB300.
+
+Metric: particle-steps/s of the full step (root cube, Morton keys, radix
+sort, tree build, aggregation, traversal with near-field pairs, integration
+with Philox noise, FP64 observables) on N = 1,048,576 dipoles at volume
+fraction 0.05, FP32, theta = 0.5, next to the GPU all-pairs kernel and the
+FP64 path.  One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--gpus N > 1 runs under torch.distributed.run: every rank advances its own
+replica of the workload (the single-system method does not shard), timing
+is the maximum over ranks, and value counts all ranks' particle-steps.
+--impl reference times the CPU oracle on this host's cores instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at 1M particles theta=0.5 (FP32 BH vs GPU all-pairs vs FP64)"
+UNIT = "particle-steps/s"
+# algorithmic FP32 operations of one dipole interaction (field + force, FMA = 2):
+# separation 3, r^2 5, rsqrt 1, powers of 1/r 4, three dot products 15,
+# field 14, force 26
+FLOPS_PER_INTERACTION = 68
+SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0  # GB300 unit counts and maximum SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1048576)
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--leaf-max", type=int, default=1)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the all-pairs, FP64, e2e and CPU-baseline legs")
+    return ap.parse_args()
+
+
+def workload(n, seed=1):
+    """Synthetic ensemble (generated once per host and cached under the temp dir)."""
+    from paper_1212_2934_gb300 import synth
+
+    path = os.path.join(tempfile.gettempdir(), "ff_phi05_n%d_s%d.npz" % (n, seed))
+    if os.path.exists(path):
+        d = np.load(path)
+        pos, u, side = d["pos"], d["u"], float(d["side"])
+    else:
+        e = synth.make_ensemble("phi05", seed=seed, n=n)
+        pos, u, side = e["pos"], e["u"], e["side"]
+        tmp = path + ".%d.npz" % os.getpid()
+        np.savez(tmp, pos=pos, u=u, side=side)
+        os.replace(tmp, path)
+    return pos, u, side
+
+
+def config_dict(args, side):
+    return {
+        "workload": "dipoles at volume fraction 0.05 (hard core 1.0, RSA), isotropic moments, "
+                    "h_ext=(0,0,1), kT=1, Gamma_t=Gamma_r=0.1, dt=1e-3, LJ eps=1 sigma=1 "
+                    "rcut=2.5, LJ walls",
+        "n": args.n, "box_side": round(side, 4), "theta": args.theta, "leaf_max": args.leaf_max,
+        "precision": "fp32", "algo": "barnes-hut",
+        "l2": "flushed between timed steps (256 MB write outside the timed events); "
+              "per-step working set ~0.3 GB",
+        "parallelism": "replicas" if args.gpus > 1 else "single-gpu",
+    }
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel_src):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        if d.get("source_sha256") == sha:
+            return d.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_step_sample(pos, u, theta, leaf_max, side, sample, threads=None):
+    """One CPU-oracle step on a bounded sample: tree + integration of all n, traversal of `sample`.
+
+    Returns (particle-steps/s, seconds of CPU work, threads)."""
+    import oracle
+
+    if threads:
+        oracle.set_threads(threads)
+    n = pos.shape[0]
+    p64 = pos.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(n, size=min(sample, n), replace=False))
+    t0 = time.perf_counter()
+    oracle.bh(p64, u, theta, leaf_max, "f32", 1.0, 1.0, 1.0, 2.5, True, only=idx[:1])
+    t1 = time.perf_counter()
+    r = oracle.bh(p64, u, theta, leaf_max, "f32", 1.0, 1.0, 1.0, 2.5, True, only=idx)
+    t2 = time.perf_counter()
+    st = dict(pos=p64.copy(), vel=np.zeros_like(p64), u=u.copy(), om=np.zeros_like(p64),
+              id=np.arange(n, dtype=np.int64))
+    dyn = oracle.make_dyn(h_ext=(0, 0, 1.0), box_lo=(0, 0, 0), box_hi=(side, side, side),
+                          walls=True)
+    t3 = time.perf_counter()
+    oracle.em_step(st, r["h"], r["f"], dyn, 0)
+    t4 = time.perf_counter()
+    t_build = t1 - t0
+    t_trav = max((t2 - t1) - t_build, 1e-9)
+    t_int = t4 - t3
+    per_step = t_build + t_int + t_trav * n / len(idx)
+    return n / per_step, (t4 - t0), oracle.get_threads(), len(idx)
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    pos, u, side = workload(args.n)
+    sample = 65536
+    for _ in range(args.warmup):
+        cpu_step_sample(pos, u, args.theta, args.leaf_max, side, sample)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, _, threads, s = cpu_step_sample(pos, u, args.theta, args.leaf_max, side, sample)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(rates))
+    cfg = config_dict(args, side)
+    cfg["precision"] = "fp64 sums, fp32 tree"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.n / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "per step: tree build, aggregation and integration of all %d "
+                                   "particles, traversal of %d sampled particles, scaled to all"
+                                   % (args.n, s)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1212_2934_gb300 import ff
+
+    n, K, W = args.n, args.steps, args.warmup
+    pos, u, side = workload(n)
+    stream = torch.cuda.current_stream()
+
+    def params(**kw):
+        base = dict(n=n, precision="f32", theta=args.theta, leaf_max=args.leaf_max,
+                    h_ext=(0, 0, 1.0), box_lo=(0, 0, 0), box_hi=(side, side, side), walls=1,
+                    count_interactions=1, seed=1, device=dev, stream=stream.cuda_stream)
+        base.update(kw)
+        return ff.ff_params_default(**base)
+
+    pos_d = torch.tensor(pos, dtype=torch.float32, device="cuda")
+    u_d = torch.tensor(u, dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- main leg: FP32 Barnes-Hut steps
+    ctx = ff.ff_create(params())
+    ff.ff_set_particles(ctx, pos_d, u_d)
+    for _ in range(W):
+        ff.ff_step(ctx, 1)
+        flush.zero_()
+    ff.ff_synchronize(ctx)
+    barrier()
+    ff.ff_profile(ctx, True)
+    clocks = Clocks(dev)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    for k in range(K):
+        evs[k][0].record(stream)
+        ff.ff_step(ctx, 1)
+        evs[k][1].record(stream)
+        flush.zero_()
+    ff.ff_synchronize(ctx)
+    barrier()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    prof = ff.ff_profile_read(ctx)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * n * K / (max_ms / 1e3)
+    info = ff.ff_tree_info(ctx)
+    energy = ff.ff_energy(ctx)
+
+    # roofline of the dominant kernel (the traversal), from this run's events
+    field_ms = prof["ms"]["field"] / max(prof["calls"]["field"], 1)
+    flops = info["interactions"] * FLOPS_PER_INTERACTION
+    peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    achieved = flops / (field_ms / 1e3) / 1e12
+    traffic = traffic_for(os.path.join(ROOT, "paper_1212_2934_gb300", "csrc", "k_field.cu"))
+    stages = {k: v / max(prof["calls"][k], 1) for k, v in prof["ms"].items() if prof["calls"][k]}
+
+    extras = {}
+    e2e = None
+    if not args.no_extras:
+        # ---- FP64 Barnes-Hut path
+        ctx64 = ff.ff_create(params(precision="f64", count_interactions=0))
+        ff.ff_set_particles(ctx64, pos_d.double(), u_d.double())
+        ff.ff_step(ctx64, 1)
+        flush.zero_()
+        barrier()
+        k64 = 3
+        e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k64)]
+        for k in range(k64):
+            e64[k][0].record(stream)
+            ff.ff_step(ctx64, 1)
+            e64[k][1].record(stream)
+            flush.zero_()
+        barrier()
+        ms64 = sum(a.elapsed_time(b) for a, b in e64) / k64
+        del ctx64
+        # ---- GPU all-pairs step (FP32)
+        ctxap = ff.ff_create(params(algo="ap", count_interactions=0))
+        ff.ff_set_particles(ctxap, pos_d, u_d)
+        ff.ff_profile(ctxap, True)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ff.ff_step(ctxap, 1)
+        a1.record(stream)
+        barrier()
+        ms_ap = a0.elapsed_time(a1)
+        prof_ap = ff.ff_profile_read(ctxap)
+        del ctxap
+        ap_field_ms = prof_ap["ms"]["field"]
+        extras = {
+            "bh_fp32": {"particle_steps_per_s": value / world, "ms_per_step": max_ms / K,
+                        "interactions_per_s": info["interactions"] / (field_ms / 1e3),
+                        "interactions_per_particle": info["interactions"] / n},
+            "ap_fp32": {"particle_steps_per_s": n / (ms_ap / 1e3), "ms_per_step": ms_ap,
+                        "pair_interactions_per_s": n * (n - 1) / (ap_field_ms / 1e3),
+                        "field_tflops": n * (n - 1) * FLOPS_PER_INTERACTION / (ap_field_ms / 1e3) / 1e12},
+            "bh_fp64": {"particle_steps_per_s": n / (ms64 / 1e3), "ms_per_step": ms64},
+            "speedup_bh_fp32_over_ap": ms_ap / (max_ms / K),
+            "speedup_bh_fp32_over_fp64": ms64 / (max_ms / K),
+        }
+        # ---- end to end through the C interface with pinned host buffers
+        host = [torch.empty((n, 3), dtype=torch.float32, pin_memory=True) for _ in range(4)]
+        host[0].copy_(torch.from_numpy(pos.astype(np.float32)))
+        host[1].copy_(torch.from_numpy(u.astype(np.float32)))
+        host[2].zero_()
+        host[3].zero_()
+        hn = [h.numpy() for h in host]
+        outs = [torch.empty((n, 3), dtype=torch.float32, pin_memory=True).numpy() for _ in range(4)]
+        ctxe = ff.ff_create(params(count_interactions=0))
+        lib = ff.lib()
+        import ctypes
+
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+
+        def e2e_step():
+            ff._check(ctxe.handle, lib.ff_set_particles(ctxe.handle, *[ptr(h) for h in hn],
+                                                        ff.FF_DTYPE_F32, ff.FF_HOST))
+            ff._check(ctxe.handle, lib.ff_step(ctxe.handle, 1))
+            ff._check(ctxe.handle, lib.ff_get_particles(ctxe.handle, *[ptr(o) for o in outs],
+                                                        ff.FF_DTYPE_F32, ff.FF_HOST))
+            for h, o in zip(hn, outs):
+                h[...] = o  # the next step starts from the state just read back
+
+        for _ in range(max(W, 1)):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            e2e_step()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": world * n * K / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": 4 * n * 3 * 4, "d2h_bytes_per_step": 4 * n * 3 * 4,
+               "note": "ff_set_particles + ff_step + ff_get_particles on pinned host float32 "
+                       "arrays (positions, moments, velocities, angular velocities), wall clock"}
+        del ctxe
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args, side),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_bh (Barnes-Hut traversal)",
+                     "peak_note": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x "
+                                  "2070 MHz (no FP32 SIMT peak in the measured peaks file)",
+                     "algorithmic_flops_per_launch": flops,
+                     "avg_launch_ms": field_ms},
+        "stage_ms_per_step": stages,
+        "gpu_launches": int(prof["launches"]),
+        "clocks": clk,
+        "paths": extras,
+        "observables_last": {"m_z": float(energy["m"][2]), "e_dip_per_particle": energy["e_dip"] / n},
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_extras:
+        rate, cpu_s, threads, s = cpu_step_sample(pos, u, args.theta, args.leaf_max, side, 262144)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "tree build, aggregation and integration of all %d "
+                                          "particles plus traversal of %d sampled particles "
+                                          "(%.1f s of CPU work), scaled to one full step"
+                                          % (n, s, cpu_s)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

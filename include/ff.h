@@ -1,0 +1,232 @@
+/*
+ * ff.h - C interface of the GB300 ferrofluid library (libff.so).
+ *
+ * The library evaluates the long-range dipole-dipole field and force on N
+ * magnetic particles by a Barnes-Hut octree and advances positions and
+ * moments by the Langevin equations, following Polyakov et al.,
+ * "Large-scale Ferrofluid Simulations on Graphics Processing Units"
+ * (arXiv:1212.2934): model in Sec. 2, all-pairs and Barnes-Hut schemes in
+ * Sec. 3, Euler-Maruyama integration in Sec. 4, magnetisation observables in
+ * Sec. 5.  All quantities are in the paper's reduced units, with lengths
+ * measured in hard-core diameters (the dipolar terms carry the factor
+ * dip_scale).
+ *
+ * Conventions for every call:
+ *  - Return value: an ff_status; the library never aborts.  On failure
+ *    ff_last_error(ctx) gives a message.  After FF_ECUDA or FF_EDEVICE the
+ *    context is poisoned and every call except ff_destroy, ff_last_error and
+ *    ff_set_particles returns FF_ESTATE.
+ *  - Arrays passed in or out are n x 3, row-major (x, y, z of particle 0,
+ *    then particle 1, ...), in the caller's particle order, of element type
+ *    `dtype` (FF_DTYPE_F32 = float, FF_DTYPE_F64 = double) and located in
+ *    host memory (loc = FF_HOST, any host pointer) or device memory of the
+ *    context's GPU (loc = FF_DEVICE).  The library copies what it reads and
+ *    writes only what it is asked to; the caller keeps ownership.
+ *  - Device work runs on the context's stream in order.  ff_step returns
+ *    before the GPU finishes; every call that hands results to the caller
+ *    waits for them.
+ *  - One context must not be used from two host threads at once.
+ */
+#ifndef FF_H
+#define FF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ff_ctx ff_ctx; /* opaque; owns all of its device memory */
+
+typedef enum {
+    FF_OK = 0,
+    FF_EINVAL = 1,     /* bad argument (pointer, size, enum, parameter range) */
+    FF_ENOMEM = 2,     /* device or host allocation failed */
+    FF_ECUDA = 3,      /* a CUDA runtime call failed */
+    FF_EDEVICE = 4,    /* a kernel raised its error flag (iteration guard) */
+    FF_ENONFINITE = 5, /* a position was NaN or infinite */
+    FF_ESTATE = 6      /* call not valid now: no particles set, or poisoned */
+} ff_status;
+
+typedef enum { FF_FP32 = 0, FF_FP64 = 1 } ff_precision;
+typedef enum { FF_ALGO_BH = 0, FF_ALGO_AP = 1 } ff_algo;
+typedef enum { FF_DTYPE_F32 = 0, FF_DTYPE_F64 = 1 } ff_dtype;
+typedef enum { FF_HOST = 0, FF_DEVICE = 1 } ff_loc;
+
+/*
+ * Run parameters (reduced units of Sec. 2).  Fill with ff_params_default
+ * and change what differs.  struct_size must be sizeof(ff_params).
+ */
+typedef struct {
+    uint32_t struct_size;
+    int32_t precision;     /* ff_precision of state, tree and arithmetic */
+    int64_t n;             /* particle count, 1 .. 2^27 */
+    int32_t algo;          /* ff_algo used by ff_step and ff_energy */
+    int32_t leaf_max;      /* most particles in a leaf cell, 1..64 (paper: 1, Sec. 3.2) */
+    double theta;          /* opening angle >= 0; 0 sums every pair exactly */
+    double dt;             /* Euler-Maruyama step (paper: 1e-3, Sec. 4) */
+    double gamma_t;        /* translational friction Gamma_t (Sec. 2) */
+    double gamma_r;        /* rotational friction Gamma_r (Sec. 2) */
+    double inertia;        /* reduced moment of inertia (2/5, Sec. 2) */
+    double kT;             /* reduced thermal energy */
+    double rot_noise;      /* rotational noise factor c_r: <xi xi> = c_r kT Gamma_r (2) */
+    double dip_scale;      /* prefactor of the dipolar field and force */
+    double lj_eps;         /* LJ epsilon (Sec. 2, Eq. LJ); 0 turns LJ off */
+    double lj_sigma;       /* LJ sigma: the force vanishes at this distance */
+    double lj_rcut;        /* LJ cut-off radius (> 0 when lj_eps != 0) */
+    double h_ext[3];       /* applied field */
+    double box_lo[3];      /* container: wall planes at box_lo - 1/2 ... */
+    double box_hi[3];      /* ... and box_hi + 1/2 */
+    int32_t walls;         /* 1: LJ-type walls on the container faces */
+    int32_t device;        /* CUDA device ordinal */
+    double wall_eps;       /* wall epsilon */
+    uint64_t seed;         /* Philox key of the thermal noise */
+    int32_t count_interactions; /* 1: record per-particle interaction counts */
+    int32_t reserved;
+    void *stream;          /* cudaStream_t to run on; NULL: the context creates one */
+} ff_params;
+
+/* Energies and observables returned by ff_energy (FP64). */
+typedef struct {
+    double e_dip;      /* -1/2 sum_k u_k . h_dip_k */
+    double e_zeeman;   /* -sum_k u_k . h_ext */
+    double e_sr;       /* LJ pair energy (each pair once), shifted to 0 at rcut */
+    double e_wall;     /* wall energy */
+    double e_kin_t;    /* 1/2 sum v^2 */
+    double e_kin_r;    /* I/2 sum w^2 */
+    double m[3];       /* <u> = (1/N) sum u (Sec. 5) */
+    double hdip_z_mean;/* (1/N) sum h_dip_z (Sec. 5) */
+} ff_energy_t;
+
+/* Size of the last tree and interaction totals (ff_tree_info). */
+typedef struct {
+    int64_t ncells;        /* cells of the last tree */
+    int32_t depth;         /* deepest cell level (root = 0) */
+    int32_t reserved;
+    double root[4];        /* root cube: lower corner x, y, z and side */
+    int64_t interactions;  /* sum over particles of accepted cells + exact pairs (counting on) */
+    int64_t accepted;      /* sum of accepted cells */
+    int64_t pairs;         /* sum of exact pairs */
+    int64_t opened;        /* sum of opened cells */
+} ff_tree_info_t;
+
+/* Fills *p with defaults: FP32, BH, theta 0.5, leaf_max 1, dt 1e-3,
+ * gamma_t = gamma_r = 0.1, inertia 0.4, kT 1, rot_noise 2, dip_scale 1,
+ * LJ eps 1 sigma 1 rcut 2.5, no field, no walls, device 0, seed 1. */
+void ff_params_default(ff_params *p);
+
+/*
+ * Creates a context for p->n particles on p->device (Sec. 2 model, Sec. 3
+ * schemes) and allocates all device memory it will use.  *out receives the
+ * context.  FF_EINVAL for out-of-range parameters, FF_ENOMEM, FF_ECUDA;
+ * the reason is then given by ff_last_error(NULL).
+ */
+ff_status ff_create(const ff_params *p, ff_ctx **out);
+
+/* Frees the context and its memory; NULL is allowed. */
+ff_status ff_destroy(ff_ctx *ctx);
+
+/*
+ * Sets the state of Sec. 2 (positions rho_k, unit moments u_k, velocities,
+ * angular velocities) from n x 3 arrays; vel and omega may be NULL (zero).
+ * Moments are used as given (the caller normalises them).  Clears a
+ * poisoned state.  Waits until the copy is done.
+ */
+ff_status ff_set_particles(ff_ctx *ctx, const void *pos, const void *u, const void *vel,
+                           const void *omega, int32_t dtype, int32_t loc);
+
+/* Copies the current state into n x 3 arrays (any pointer may be NULL). Waits. */
+ff_status ff_get_particles(ff_ctx *ctx, void *pos, void *u, void *vel, void *omega,
+                           int32_t dtype, int32_t loc);
+
+/*
+ * Field and force of the current state (Sec. 3): h_out = dip_scale * sum of
+ * the reduced dipolar fields h_kj (Sec. 2, Eq. h_dip, h_ext excluded) and
+ * f_out = dip_scale * dipolar force (Eq. f_dip) plus, if include_sr, the LJ
+ * force (Eq. LJ) of pairs closer than lj_rcut.  algo = FF_ALGO_AP sums every
+ * pair (Sec. 3.1, Algorithm 1); FF_ALGO_BH uses the octree (Sec. 3.2) with
+ * opening angle theta: a cell stands in for its particles (moment sum at
+ * their geometric centre, Eq. magCenter) iff the particle is not in it,
+ * side^2 < theta^2 |rho_k - centre|^2, and (LJ on) the cell's cube is at
+ * least lj_rcut away.  Either output pointer may be NULL.  Waits.
+ */
+ff_status ff_dipolar_field(ff_ctx *ctx, int32_t algo, double theta, int32_t include_sr,
+                           void *h_out, void *f_out, int32_t dtype, int32_t loc);
+
+/*
+ * Advances nsteps >= 0 Euler-Maruyama steps of dt (Sec. 4) of the Langevin
+ * equations (Sec. 2; rotation in vector form) with the context's algorithm
+ * and theta: per step tree build, field, walls, Philox noise keyed by
+ * (seed, step, particle) and the update of positions, velocities, moments
+ * and angular velocities.  Returns without waiting; errors raised on the GPU
+ * are reported by the next waiting call.
+ */
+ff_status ff_step(ff_ctx *ctx, int64_t nsteps);
+
+/*
+ * Energies and the Sec. 5 observables of the current state, in FP64, with
+ * the field of the context's algorithm.  Waits.
+ */
+ff_status ff_energy(ff_ctx *ctx, ff_energy_t *out);
+
+/* Step counter (the noise of step s is drawn with counter s). */
+ff_status ff_get_step(const ff_ctx *ctx, int64_t *step);
+ff_status ff_set_step(ff_ctx *ctx, int64_t step);
+
+/* Waits for the context's stream and reports any error flag raised on the GPU. */
+ff_status ff_synchronize(ff_ctx *ctx);
+
+/* Tree size and interaction totals of the last Barnes-Hut evaluation (waits). */
+ff_status ff_tree_info(ff_ctx *ctx, ff_tree_info_t *out);
+
+/*
+ * Copies the last Barnes-Hut tree to host arrays (any pointer may be NULL):
+ * keys[n] (sorted 63-bit Morton keys), order[n] (input index of each sorted
+ * position) and, for ncells cells in depth-first preorder, pbegin/pend
+ * (sorted particle range), skip (index after the subtree), level, leaf,
+ * centre[3*ncells] (geometric centre), moment[3*ncells] (moment sum), in
+ * dtype.  Waits.
+ */
+ff_status ff_get_tree(ff_ctx *ctx, uint64_t *keys, uint32_t *order, int32_t *pbegin,
+                      int32_t *pend, int32_t *skip, int32_t *level, int32_t *leaf,
+                      void *centre, void *moment, int32_t dtype);
+
+/*
+ * Per-particle counts of the last Barnes-Hut evaluation in the caller's
+ * order (host arrays of n, any may be NULL): accepted cells, exact pairs and
+ * opened cells.  Needs count_interactions = 1.  Waits.
+ */
+ff_status ff_get_counts(ff_ctx *ctx, int32_t *accepted, int32_t *pairs, int32_t *opened);
+
+/*
+ * Stage timing (CUDA events on the context's stream) and launch counting.
+ * Stages: 0 keys (root cube + Morton keys), 1 radix sort, 2 gather into key
+ * order, 3 tree build, 4 aggregation, 5 field (traversal or all-pairs),
+ * 6 integration and observables, 7 output conversion.  ms[i] and calls[i]
+ * accumulate the device time and the number of timed executions of stage i;
+ * launches counts the kernels this context launched.
+ */
+typedef struct {
+    double ms[8];
+    int64_t calls[8];
+    int64_t launches;
+} ff_profile_t;
+
+/* enable = 1 starts timing and zeroes the counters; 0 stops timing. */
+ff_status ff_profile(ff_ctx *ctx, int32_t enable);
+
+/* Waits for the stream and returns the accumulated stage times and launches. */
+ff_status ff_profile_read(ff_ctx *ctx, ff_profile_t *out);
+
+/* Message for the last failure on this context (never NULL).  With
+ * ctx = NULL: why the last ff_create on the calling thread failed. */
+const char *ff_last_error(const ff_ctx *ctx);
+
+/* Name of a status code. */
+const char *ff_status_string(ff_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FF_H */

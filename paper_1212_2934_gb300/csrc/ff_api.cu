@@ -1,0 +1,940 @@
+// Host runtime and C interface of libff (declared in include/ff.h).
+//
+// A context owns its device memory and one stream.  The state lives on the
+// GPU in two record buffers (positions, velocities, moments, angular
+// velocities, particle ids) that alternate: the key sort gathers the state
+// into Morton order in the other buffer, and the integrator writes the next
+// state into the other buffer again.  Outputs go back to the caller's order
+// through the particle ids.  Nothing crosses to the host inside a step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ff.h"
+#include "ffk.cuh"
+
+namespace {
+
+constexpr int64_t kMaxN = int64_t(1) << 27;
+
+struct Buffers {
+    void* pos = nullptr;
+    void* vel = nullptr;
+    void* u = nullptr;
+    void* om = nullptr;
+    uint32_t* id = nullptr;
+};
+
+}  // namespace
+
+struct ff_ctx {
+    ff_params p;
+    int64_t n = 0;
+    bool fp64 = false;
+    size_t rec = 16;  // bytes per record
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t step = 0;
+    bool have_particles = false;
+    bool poisoned = false;
+    char err[512] = {0};
+
+    Buffers st[2];
+    int cur = 0;
+    uint64_t* keys[2] = {nullptr, nullptr};
+    uint32_t* vals[2] = {nullptr, nullptr};
+    uint32_t* radix_tmp = nullptr;
+    uint32_t* cnt = nullptr;
+    uint32_t* off = nullptr;
+    uint32_t* scan_tmp = nullptr;
+    ffk::BBox* bbox = nullptr;
+
+    int4* node = nullptr;
+    void* cen = nullptr;
+    void* mom = nullptr;
+    void* lo = nullptr;
+    void* sum = nullptr;
+    int* parent = nullptr;
+    int* arrive = nullptr;
+    int64_t cap = 0;
+
+    void* h = nullptr;
+    void* f = nullptr;
+    void* esr = nullptr;
+    int4* counts = nullptr;
+    double* partials = nullptr;
+    double* obs = nullptr;       // observables of the last ff_energy
+    double* obs_step = nullptr;  // observables of the state at the start of the last step
+    int* dflags = nullptr;
+    int* hflags = nullptr;       // pinned mirror
+    double* hobs = nullptr;      // pinned mirror of 10 doubles
+    void* staging = nullptr;     // 4 x 3n doubles
+    bool tree_valid = false;     // a Barnes-Hut tree of some state exists
+    bool counts_valid = false;
+
+    // stage timing
+    struct Mark {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    bool prof = false;
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[8] = {0};
+    int64_t prof_calls[8] = {0};
+    int64_t launches = 0;
+};
+
+namespace {
+
+thread_local char g_create_err[256] = {0};
+
+ff_status create_fail(ff_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_create_err, sizeof(g_create_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+ff_status fail(ff_ctx* c, ff_status s, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+        if (s == FF_ECUDA || s == FF_EDEVICE || s == FF_ENONFINITE) c->poisoned = true;
+    }
+    return s;
+}
+
+#define FF_CUDA(ctx, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), FF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+#define FF_LAUNCHED(ctx)                                                                     \
+    do {                                                                                     \
+        cudaError_t e_ = cudaGetLastError();                                                 \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), FF_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+ff_status usable(ff_ctx* c, bool need_particles)
+{
+    if (!c) return FF_EINVAL;
+    if (c->poisoned) return fail(c, FF_ESTATE, "context is poisoned by an earlier error; set particles again");
+    if (need_particles && !c->have_particles) return fail(c, FF_ESTATE, "no particles set");
+    FF_CUDA(c, cudaSetDevice(c->p.device));
+    return FF_OK;
+}
+
+size_t dsize(int32_t dtype) { return dtype == FF_DTYPE_F64 ? 8 : 4; }
+
+bool valid_dtype_loc(int32_t dtype, int32_t loc)
+{
+    return (dtype == FF_DTYPE_F32 || dtype == FF_DTYPE_F64) && (loc == FF_HOST || loc == FF_DEVICE);
+}
+
+template <typename R>
+ffk::Tree<R> tree_of(ff_ctx* c)
+{
+    ffk::Tree<R> t;
+    t.node = c->node;
+    t.cen = static_cast<ffk::vec4<R>*>(c->cen);
+    t.mom = static_cast<ffk::vec4<R>*>(c->mom);
+    t.lo = static_cast<ffk::vec4<R>*>(c->lo);
+    t.sum = static_cast<ffk::vec4<R>*>(c->sum);
+    t.parent = c->parent;
+    t.arrive = c->arrive;
+    t.ncells = reinterpret_cast<int*>(c->off + c->n);
+    t.cap = c->cap;
+    return t;
+}
+
+template <typename R>
+ffk::FieldParams<R> field_params(const ff_ctx* c, double theta, int include_sr)
+{
+    const ff_params& p = c->p;
+    ffk::FieldParams<R> fp;
+    const bool lj_on = p.lj_eps != 0.0 && p.lj_rcut > 0.0;
+    fp.theta2 = (R)(theta * theta);
+    fp.rcut2 = lj_on ? (R)(p.lj_rcut * p.lj_rcut) : R(0);
+    fp.use_rcut = lj_on ? 1 : 0;
+    fp.include_sr = (include_sr && lj_on) ? 1 : 0;
+    fp.dip_scale = (R)p.dip_scale;
+    fp.lj_eps24 = (R)(24.0 * p.lj_eps);
+    fp.lj_sigma2 = (R)(p.lj_sigma * p.lj_sigma);
+    fp.lj_rcut2 = (R)(p.lj_rcut * p.lj_rcut);
+    fp.lj_rcut2_hi = (R)((double)fp.lj_rcut2 * (sizeof(R) == 4 ? 1.0 + 1e-5 : 1.0 + 1e-12));
+    fp.lj_e2 = (R)(2.0 * p.lj_eps);
+    fp.lj_e4 = (R)(4.0 * p.lj_eps);
+    double sc2 = lj_on ? p.lj_sigma * p.lj_sigma / (p.lj_rcut * p.lj_rcut) : 0.0;
+    double sc6 = sc2 * sc2 * sc2;
+    fp.lj_shift = (R)(2.0 * p.lj_eps * sc6 * sc6 - 4.0 * p.lj_eps * sc6);
+    return fp;
+}
+
+template <typename R>
+ffk::DynParams<R> dyn_params(const ff_ctx* c)
+{
+    const ff_params& p = c->p;
+    ffk::DynParams<R> d;
+    d.dt = (R)p.dt;
+    d.gamma_t = (R)p.gamma_t;
+    d.gamma_r = (R)p.gamma_r;
+    d.inv_inertia = (R)(1.0 / p.inertia);
+    d.sig_t = (R)std::sqrt(2.0 * p.gamma_t * p.kT * p.dt);
+    d.sig_r = (R)(std::sqrt(p.rot_noise * p.gamma_r * p.kT * p.dt) / p.inertia);
+    d.hx = (R)p.h_ext[0];
+    d.hy = (R)p.h_ext[1];
+    d.hz = (R)p.h_ext[2];
+    for (int a = 0; a < 3; ++a) {
+        d.lo[a] = (R)(p.box_lo[a] - 0.5);
+        d.hi[a] = (R)(p.box_hi[a] + 0.5);
+    }
+    d.wall_eps24 = (R)(24.0 * p.wall_eps);
+    d.wall_e2 = (R)(2.0 * p.wall_eps);
+    d.wall_e4 = (R)(4.0 * p.wall_eps);
+    d.walls = p.walls ? 1 : 0;
+    d.key0 = (uint32_t)p.seed;
+    d.key1 = (uint32_t)(p.seed >> 32);
+    d.ctr0 = (uint32_t)c->step;
+    d.ctr1 = (uint32_t)((uint64_t)c->step >> 32);
+    return d;
+}
+
+template <typename R>
+ffk::vec4<R>* V(void* p) { return static_cast<ffk::vec4<R>*>(p); }
+
+enum Stage { S_KEYS = 0, S_SORT, S_GATHER, S_BUILD, S_AGG, S_FIELD, S_STEP, S_OUT };
+
+cudaEvent_t take_event(ff_ctx* c)
+{
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one stage with events on the context's stream when timing is on.
+struct StageTimer {
+    ff_ctx* c;
+    int stage;
+    cudaEvent_t a = nullptr;
+    StageTimer(ff_ctx* cc, int st) : c(cc), stage(st)
+    {
+        if (c->prof) {
+            a = take_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~StageTimer()
+    {
+        if (!a) return;
+        cudaEvent_t b = take_event(c);
+        cudaEventRecord(b, c->stream);
+        c->marks.push_back({stage, a, b});
+    }
+};
+
+// Adds the kernels launched during one API call to the context's tally.
+struct LaunchTally {
+    ff_ctx* c;
+    int64_t start;
+    explicit LaunchTally(ff_ctx* cc) : c(cc), start(ffk::g_launches.load()) {}
+    ~LaunchTally()
+    {
+        if (c) c->launches += ffk::g_launches.load() - start;
+    }
+};
+
+// Sort the state into Morton order (the other buffer), build and aggregate
+// the tree, traverse.  h, f, esr (and counts) end in sorted order.
+template <typename R>
+ff_status eval_bh(ff_ctx* c, double theta, int include_sr)
+{
+    const int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    Buffers& a = c->st[c->cur];
+    Buffers& b = c->st[1 - c->cur];
+    {
+        StageTimer st(c, S_KEYS);
+        ffk::morton_keys<R>(V<R>(a.pos), n, c->bbox, c->keys[0], c->vals[0], c->dflags, s);
+    }
+    {
+        StageTimer st(c, S_SORT);
+        ffk::radix_sort_pairs(c->keys[0], c->vals[0], c->keys[1], c->vals[1], n, c->radix_tmp, s);
+    }
+    {
+        StageTimer st(c, S_GATHER);
+        ffk::gather_state<R>(c->vals[0], n, V<R>(a.pos), V<R>(a.vel), V<R>(a.u), V<R>(a.om), a.id,
+                             V<R>(b.pos), V<R>(b.vel), V<R>(b.u), V<R>(b.om), b.id, s);
+    }
+    c->cur = 1 - c->cur;
+    ffk::Tree<R> t = tree_of<R>(c);
+    {
+        StageTimer st(c, S_BUILD);
+        ffk::build_tree<R>(c->keys[0], n, c->p.leaf_max, c->bbox, t, c->cnt, c->off, c->scan_tmp,
+                           c->dflags, s);
+    }
+    {
+        StageTimer st(c, S_AGG);
+        ffk::aggregate_tree<R>(V<R>(b.pos), V<R>(b.u), n, c->cnt, c->off, t, c->dflags, s);
+    }
+    {
+        StageTimer st(c, S_FIELD);
+        ffk::bh_field<R>(V<R>(b.pos), V<R>(b.u), n, t, field_params<R>(c, theta, include_sr),
+                         V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr),
+                         c->p.count_interactions ? c->counts : nullptr, c->dflags, s);
+    }
+    FF_LAUNCHED(c);
+    c->tree_valid = true;
+    c->counts_valid = c->p.count_interactions != 0;
+    return FF_OK;
+}
+
+template <typename R>
+ff_status eval_ap(ff_ctx* c, int include_sr)
+{
+    Buffers& a = c->st[c->cur];
+    {
+        StageTimer st(c, S_FIELD);
+        ffk::ap_field<R>(V<R>(a.pos), V<R>(a.u), c->n, field_params<R>(c, 0.0, include_sr),
+                         V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr), c->stream);
+    }
+    FF_LAUNCHED(c);
+    return FF_OK;
+}
+
+template <typename R>
+ff_status eval_field(ff_ctx* c, int algo, double theta, int include_sr)
+{
+    return algo == FF_ALGO_AP ? eval_ap<R>(c, include_sr) : eval_bh<R>(c, theta, include_sr);
+}
+
+template <typename R>
+ff_status do_step(ff_ctx* c)
+{
+    ff_status st = eval_field<R>(c, c->p.algo, c->p.theta, 1);
+    if (st != FF_OK) return st;
+    Buffers& a = c->st[c->cur];
+    Buffers& b = c->st[1 - c->cur];
+    {
+        StageTimer tm(c, S_STEP);
+        ffk::integrate<R>(c->n, V<R>(a.pos), V<R>(a.vel), V<R>(a.u), V<R>(a.om), a.id, V<R>(c->h),
+                          V<R>(c->f), static_cast<R*>(c->esr), dyn_params<R>(c), V<R>(b.pos),
+                          V<R>(b.vel), V<R>(b.u), V<R>(b.om), b.id, c->partials, c->stream);
+        ffk::reduce_partials(c->partials, ffk::integrate_blocks(c->n), 1.0 / (double)c->n,
+                             0.5 * c->p.inertia, c->obs_step, c->stream);
+    }
+    FF_LAUNCHED(c);
+    c->cur = 1 - c->cur;
+    c->step += 1;
+    return FF_OK;
+}
+
+// Waits for the stream and turns device flags into a status.
+ff_status sync_and_check(ff_ctx* c)
+{
+    FF_CUDA(c, cudaMemcpyAsync(c->hflags, c->dflags, sizeof(int), cudaMemcpyDeviceToHost,
+                               c->stream));
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int fl = *c->hflags;
+    if (fl & ffk::FLAG_NONFINITE) return fail(c, FF_ENONFINITE, "a particle position is NaN or infinite");
+    if (fl & ffk::FLAG_CAPACITY) return fail(c, FF_EDEVICE, "tree needs more cells than allocated");
+    if (fl & ffk::FLAG_TRAVERSE) return fail(c, FF_EDEVICE, "traversal guard tripped");
+    if (fl & ffk::FLAG_AGGREGATE) return fail(c, FF_EDEVICE, "aggregation guard tripped");
+    return FF_OK;
+}
+
+void free_all(ff_ctx* c)
+{
+    void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->radix_tmp, c->cnt, c->off,
+                    c->scan_tmp, c->bbox, c->node, c->cen, c->mom, c->lo, c->sum, c->parent,
+                    c->arrive, c->h, c->f, c->esr, c->counts, c->partials, c->obs, c->obs_step,
+                    c->dflags, c->staging};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    for (int k = 0; k < 2; ++k) {
+        void* bp[] = {c->st[k].pos, c->st[k].vel, c->st[k].u, c->st[k].om, c->st[k].id};
+        for (void* q : bp)
+            if (q) cudaFree(q);
+    }
+    for (auto& m : c->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    c->marks.clear();
+    c->pool.clear();
+    if (c->hflags) cudaFreeHost(c->hflags);
+    if (c->hobs) cudaFreeHost(c->hobs);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t bytes)
+{
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes > 0 ? bytes : 16);
+}
+
+ff_status alloc_all(ff_ctx* c)
+{
+    const int64_t n = c->n;
+    const size_t rec = c->rec;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t bytes) {
+        if (e == cudaSuccess) e = dalloc(p, bytes);
+    };
+    for (int k = 0; k < 2; ++k) {
+        A(&c->st[k].pos, rec * n);
+        A(&c->st[k].vel, rec * n);
+        A(&c->st[k].u, rec * n);
+        A(&c->st[k].om, rec * n);
+        A(&c->st[k].id, sizeof(uint32_t) * n);
+        A(&c->keys[k], sizeof(uint64_t) * n);
+        A(&c->vals[k], sizeof(uint32_t) * n);
+    }
+    A(&c->radix_tmp, sizeof(uint32_t) * ffk::radix_tmp_words(n));
+    A(&c->cnt, sizeof(uint32_t) * (n + 1));
+    A(&c->off, sizeof(uint32_t) * (n + 1));
+    A(&c->scan_tmp, sizeof(uint32_t) * ffk::scan_tmp_words(n));
+    A(&c->bbox, sizeof(ffk::BBox));
+    // Every particle starts at most 22 cells (levels 0..21), so 22 n + 1 cells
+    // always suffice.
+    c->cap = 22 * n + 1;
+    A(&c->node, sizeof(int4) * c->cap);
+    A(&c->cen, rec * c->cap);
+    A(&c->mom, rec * c->cap);
+    A(&c->lo, rec * c->cap);
+    A(&c->sum, rec * c->cap);
+    A(&c->parent, sizeof(int) * c->cap);
+    A(&c->arrive, sizeof(int) * c->cap);
+    A(&c->h, rec * n);
+    A(&c->f, rec * n);
+    A(&c->esr, (c->fp64 ? 8 : 4) * n);
+    A(&c->counts, sizeof(int4) * n);
+    A(&c->partials, sizeof(double) * ffk::kObs * ffk::integrate_blocks(n));
+    A(&c->obs, sizeof(double) * ffk::kObs);
+    A(&c->obs_step, sizeof(double) * ffk::kObs);
+    A(&c->dflags, sizeof(int));
+    A(&c->staging, sizeof(double) * 12 * n);
+    if (e != cudaSuccess) return fail(c, FF_ENOMEM, "device allocation failed: %s", cudaGetErrorString(e));
+    if (cudaMallocHost(reinterpret_cast<void**>(&c->hflags), sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&c->hobs), sizeof(double) * ffk::kObs) != cudaSuccess)
+        return fail(c, FF_ENOMEM, "pinned host allocation failed");
+    FF_CUDA(c, cudaMemsetAsync(c->dflags, 0, sizeof(int), c->stream));
+    FF_CUDA(c, cudaMemsetAsync(c->obs_step, 0, sizeof(double) * ffk::kObs, c->stream));
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return FF_OK;
+}
+
+const char* check_params(const ff_params* p)
+{
+    if (p->struct_size != sizeof(ff_params)) return "struct_size does not match sizeof(ff_params)";
+    if (p->n < 1 || p->n > kMaxN) return "n out of range (1 .. 2^27)";
+    if (p->precision != FF_FP32 && p->precision != FF_FP64) return "bad precision";
+    if (p->algo != FF_ALGO_BH && p->algo != FF_ALGO_AP) return "bad algo";
+    if (p->leaf_max < 1 || p->leaf_max > ffk::kMaxLeaf) return "leaf_max out of range (1 .. 64)";
+    if (!(p->theta >= 0.0) || !std::isfinite(p->theta)) return "theta must be finite and >= 0";
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return "dt must be > 0";
+    if (!(p->inertia > 0.0)) return "inertia must be > 0";
+    if (!(p->gamma_t >= 0.0) || !(p->gamma_r >= 0.0)) return "friction must be >= 0";
+    if (!(p->kT >= 0.0) || !(p->rot_noise >= 0.0)) return "kT and rot_noise must be >= 0";
+    if (!std::isfinite(p->dip_scale)) return "dip_scale must be finite";
+    if (p->lj_eps != 0.0 && (!(p->lj_sigma > 0.0) || !(p->lj_rcut > 0.0)))
+        return "LJ needs sigma > 0 and rcut > 0";
+    if (p->walls) {
+        for (int a = 0; a < 3; ++a)
+            if (!(p->box_lo[a] < p->box_hi[a])) return "walls need box_lo < box_hi";
+        if (!(p->wall_eps >= 0.0)) return "wall_eps must be >= 0";
+    }
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p->h_ext[a])) return "h_ext must be finite";
+    return nullptr;
+}
+
+template <typename R>
+ff_status load_array(ff_ctx* c, const void* src, int32_t dtype, int32_t loc, void* dst, int slot)
+{
+    const int64_t n = c->n;
+    if (!src) {
+        ffk::fill_zero4<R>(V<R>(dst), n, c->stream);
+        return FF_OK;
+    }
+    const void* dsrc = src;
+    if (loc == FF_HOST) {
+        char* stg = static_cast<char*>(c->staging) + (size_t)slot * 3 * n * sizeof(double);
+        FF_CUDA(c, cudaMemcpyAsync(stg, src, 3 * n * dsize(dtype), cudaMemcpyHostToDevice, c->stream));
+        dsrc = stg;
+    }
+    if (dtype == FF_DTYPE_F64)
+        ffk::load3<R, double>(static_cast<const double*>(dsrc), n, V<R>(dst), c->stream);
+    else
+        ffk::load3<R, float>(static_cast<const float*>(dsrc), n, V<R>(dst), c->stream);
+    return FF_OK;
+}
+
+template <typename R>
+ff_status set_particles(ff_ctx* c, const void* pos, const void* u, const void* vel,
+                        const void* om, int32_t dtype, int32_t loc)
+{
+    Buffers& a = c->st[c->cur];
+    ff_status s;
+    if ((s = load_array<R>(c, pos, dtype, loc, a.pos, 0)) != FF_OK) return s;
+    if ((s = load_array<R>(c, u, dtype, loc, a.u, 1)) != FF_OK) return s;
+    if ((s = load_array<R>(c, vel, dtype, loc, a.vel, 2)) != FF_OK) return s;
+    if ((s = load_array<R>(c, om, dtype, loc, a.om, 3)) != FF_OK) return s;
+    ffk::iota32(a.id, c->n, c->stream);
+    FF_CUDA(c, cudaMemsetAsync(c->dflags, 0, sizeof(int), c->stream));
+    FF_LAUNCHED(c);
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return FF_OK;
+}
+
+// Writes one record array (sorted order) to a caller array in caller order.
+template <typename R>
+ff_status store_array(ff_ctx* c, const void* src, const uint32_t* id, void* dst, int32_t dtype,
+                      int32_t loc, int slot)
+{
+    if (!dst) return FF_OK;
+    const int64_t n = c->n;
+    void* ddst = dst;
+    char* stg = static_cast<char*>(c->staging) + (size_t)slot * 3 * n * sizeof(double);
+    if (loc == FF_HOST) ddst = stg;
+    StageTimer tm(c, S_OUT);
+    if (dtype == FF_DTYPE_F64)
+        ffk::scatter3<R, double>(static_cast<const ffk::vec4<R>*>(src), id, n,
+                                 static_cast<double*>(ddst), c->stream);
+    else
+        ffk::scatter3<R, float>(static_cast<const ffk::vec4<R>*>(src), id, n,
+                                static_cast<float*>(ddst), c->stream);
+    FF_LAUNCHED(c);
+    if (loc == FF_HOST)
+        FF_CUDA(c, cudaMemcpyAsync(dst, stg, 3 * n * dsize(dtype), cudaMemcpyDeviceToHost, c->stream));
+    return FF_OK;
+}
+
+template <typename R>
+ff_status get_particles(ff_ctx* c, void* pos, void* u, void* vel, void* om, int32_t dtype,
+                        int32_t loc)
+{
+    Buffers& a = c->st[c->cur];
+    ff_status s;
+    if ((s = store_array<R>(c, a.pos, a.id, pos, dtype, loc, 0)) != FF_OK) return s;
+    if ((s = store_array<R>(c, a.u, a.id, u, dtype, loc, 1)) != FF_OK) return s;
+    if ((s = store_array<R>(c, a.vel, a.id, vel, dtype, loc, 2)) != FF_OK) return s;
+    if ((s = store_array<R>(c, a.om, a.id, om, dtype, loc, 3)) != FF_OK) return s;
+    return sync_and_check(c);
+}
+
+template <typename R>
+ff_status dipolar_field(ff_ctx* c, int32_t algo, double theta, int32_t include_sr, void* h_out,
+                        void* f_out, int32_t dtype, int32_t loc)
+{
+    ff_status s = eval_field<R>(c, algo, theta, include_sr);
+    if (s != FF_OK) return s;
+    const uint32_t* id = c->st[c->cur].id;
+    if ((s = store_array<R>(c, c->h, id, h_out, dtype, loc, 0)) != FF_OK) return s;
+    if ((s = store_array<R>(c, c->f, id, f_out, dtype, loc, 1)) != FF_OK) return s;
+    return sync_and_check(c);
+}
+
+template <typename R>
+ff_status energy(ff_ctx* c, ff_energy_t* out)
+{
+    ff_status s = eval_field<R>(c, c->p.algo, c->p.theta, 1);
+    if (s != FF_OK) return s;
+    Buffers& a = c->st[c->cur];
+    ffk::observables<R>(c->n, V<R>(a.pos), V<R>(a.vel), V<R>(a.u), V<R>(a.om), V<R>(c->h),
+                        static_cast<R*>(c->esr), dyn_params<R>(c), c->partials, c->stream);
+    ffk::reduce_partials(c->partials, ffk::integrate_blocks(c->n), 1.0 / (double)c->n,
+                         0.5 * c->p.inertia, c->obs, c->stream);
+    FF_LAUNCHED(c);
+    FF_CUDA(c, cudaMemcpyAsync(c->hobs, c->obs, sizeof(double) * ffk::kObs, cudaMemcpyDeviceToHost,
+                               c->stream));
+    if ((s = sync_and_check(c)) != FF_OK) return s;
+    const double* o = c->hobs;
+    out->e_dip = o[0];
+    out->e_zeeman = o[1];
+    out->e_sr = o[2];
+    out->e_wall = o[3];
+    out->e_kin_t = o[4];
+    out->e_kin_r = o[5];
+    out->m[0] = o[6];
+    out->m[1] = o[7];
+    out->m[2] = o[8];
+    out->hdip_z_mean = o[9];
+    return FF_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void ff_params_default(ff_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->struct_size = sizeof(ff_params);
+    p->precision = FF_FP32;
+    p->n = 1;
+    p->algo = FF_ALGO_BH;
+    p->leaf_max = 1;
+    p->theta = 0.5;
+    p->dt = 1e-3;
+    p->gamma_t = 0.1;
+    p->gamma_r = 0.1;
+    p->inertia = 0.4;
+    p->kT = 1.0;
+    p->rot_noise = 2.0;
+    p->dip_scale = 1.0;
+    p->lj_eps = 1.0;
+    p->lj_sigma = 1.0;
+    p->lj_rcut = 2.5;
+    p->walls = 0;
+    p->device = 0;
+    p->wall_eps = 1.0;
+    p->seed = 1;
+    p->count_interactions = 0;
+    p->stream = nullptr;
+}
+
+ff_status ff_create(const ff_params* p, ff_ctx** out)
+{
+    if (!p || !out) return create_fail(FF_EINVAL, "p and out must not be NULL");
+    *out = nullptr;
+    if (const char* why = check_params(p)) return create_fail(FF_EINVAL, "%s", why);
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) return create_fail(FF_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    ff_ctx* c = new (std::nothrow) ff_ctx();
+    if (!c) return create_fail(FF_ENOMEM, "host allocation failed");
+    c->p = *p;
+    c->n = p->n;
+    c->fp64 = p->precision == FF_FP64;
+    c->rec = c->fp64 ? sizeof(ffk::dvec4) : sizeof(float4);
+    if (p->stream) {
+        c->stream = static_cast<cudaStream_t>(p->stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return create_fail(FF_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    ff_status s = alloc_all(c);
+    if (s != FF_OK) {
+        create_fail(s, "%s", c->err);
+        free_all(c);
+        delete c;
+        return s;
+    }
+    g_create_err[0] = 0;
+    *out = c;
+    return FF_OK;
+}
+
+ff_status ff_destroy(ff_ctx* c)
+{
+    if (!c) return FF_OK;
+    cudaSetDevice(c->p.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return FF_OK;
+}
+
+ff_status ff_set_particles(ff_ctx* c, const void* pos, const void* u, const void* vel,
+                           const void* omega, int32_t dtype, int32_t loc)
+{
+    LaunchTally tally_(c);
+    if (!c) return FF_EINVAL;
+    if (!pos || !u) return fail(c, FF_EINVAL, "pos and u are required");
+    if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
+    FF_CUDA(c, cudaSetDevice(c->p.device));
+    c->poisoned = false;
+    c->cur = 0;
+    ff_status s = c->fp64 ? set_particles<double>(c, pos, u, vel, omega, dtype, loc)
+                          : set_particles<float>(c, pos, u, vel, omega, dtype, loc);
+    if (s != FF_OK) return s;
+    c->have_particles = true;
+    c->tree_valid = false;
+    c->counts_valid = false;
+    return FF_OK;
+}
+
+ff_status ff_get_particles(ff_ctx* c, void* pos, void* u, void* vel, void* omega, int32_t dtype,
+                           int32_t loc)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
+    return c->fp64 ? get_particles<double>(c, pos, u, vel, omega, dtype, loc)
+                   : get_particles<float>(c, pos, u, vel, omega, dtype, loc);
+}
+
+ff_status ff_dipolar_field(ff_ctx* c, int32_t algo, double theta, int32_t include_sr, void* h_out,
+                           void* f_out, int32_t dtype, int32_t loc)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (algo != FF_ALGO_BH && algo != FF_ALGO_AP) return fail(c, FF_EINVAL, "bad algo");
+    if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(c, FF_EINVAL, "theta must be finite and >= 0");
+    if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
+    return c->fp64 ? dipolar_field<double>(c, algo, theta, include_sr, h_out, f_out, dtype, loc)
+                   : dipolar_field<float>(c, algo, theta, include_sr, h_out, f_out, dtype, loc);
+}
+
+ff_status ff_step(ff_ctx* c, int64_t nsteps)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (nsteps < 0) return fail(c, FF_EINVAL, "nsteps must be >= 0");
+    for (int64_t k = 0; k < nsteps; ++k) {
+        s = c->fp64 ? do_step<double>(c) : do_step<float>(c);
+        if (s != FF_OK) return s;
+    }
+    return FF_OK;
+}
+
+ff_status ff_energy(ff_ctx* c, ff_energy_t* out)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (!out) return fail(c, FF_EINVAL, "out is NULL");
+    return c->fp64 ? energy<double>(c, out) : energy<float>(c, out);
+}
+
+ff_status ff_get_step(const ff_ctx* c, int64_t* step)
+{
+    if (!c || !step) return FF_EINVAL;
+    *step = c->step;
+    return FF_OK;
+}
+
+ff_status ff_set_step(ff_ctx* c, int64_t step)
+{
+    if (!c) return FF_EINVAL;
+    if (step < 0) return fail(c, FF_EINVAL, "step must be >= 0");
+    c->step = step;
+    return FF_OK;
+}
+
+ff_status ff_synchronize(ff_ctx* c)
+{
+    ff_status s = usable(c, false);
+    if (s != FF_OK) return s;
+    return sync_and_check(c);
+}
+
+ff_status ff_tree_info(ff_ctx* c, ff_tree_info_t* out)
+{
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (!out) return fail(c, FF_EINVAL, "out is NULL");
+    if (!c->tree_valid) return fail(c, FF_ESTATE, "no Barnes-Hut tree has been built");
+    if ((s = sync_and_check(c)) != FF_OK) return s;
+    std::memset(out, 0, sizeof(*out));
+    uint32_t nc = 0;
+    FF_CUDA(c, cudaMemcpy(&nc, c->off + c->n, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    out->ncells = nc;
+    std::vector<int4> nodes(nc);
+    if (nc) FF_CUDA(c, cudaMemcpy(nodes.data(), c->node, sizeof(int4) * nc, cudaMemcpyDeviceToHost));
+    int depth = 0;
+    for (const int4& v : nodes) depth = std::max(depth, v.w & 0xff);
+    out->depth = depth;
+    ffk::BBox bb;
+    FF_CUDA(c, cudaMemcpy(&bb, c->bbox, sizeof(bb), cudaMemcpyDeviceToHost));
+    double mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) {
+        if (c->fp64) {
+            long long e0 = bb.lo[a], e1 = bb.hi[a];
+            e0 = e0 >= 0 ? e0 : e0 ^ 0x7fffffffffffffffLL;
+            e1 = e1 >= 0 ? e1 : e1 ^ 0x7fffffffffffffffLL;
+            std::memcpy(&mn[a], &e0, 8);
+            std::memcpy(&mx[a], &e1, 8);
+        } else {
+            int e0 = (int)bb.lo[a], e1 = (int)bb.hi[a];
+            e0 = e0 >= 0 ? e0 : e0 ^ 0x7fffffff;
+            e1 = e1 >= 0 ? e1 : e1 ^ 0x7fffffff;
+            float f0, f1;
+            std::memcpy(&f0, &e0, 4);
+            std::memcpy(&f1, &e1, 4);
+            mn[a] = f0;
+            mx[a] = f1;
+        }
+    }
+    double side = 0.0;
+    if (c->fp64) {
+        side = mx[0] - mn[0];
+        for (int a = 1; a < 3; ++a) side = std::max(side, mx[a] - mn[a]);
+        if (!(side > 0.0)) side = 1.0;
+    } else {
+        float sd = (float)mx[0] - (float)mn[0];
+        for (int a = 1; a < 3; ++a) sd = std::max(sd, (float)mx[a] - (float)mn[a]);
+        if (!(sd > 0.0f)) sd = 1.0f;
+        side = sd;
+    }
+    for (int a = 0; a < 3; ++a) out->root[a] = mn[a];
+    out->root[3] = side;
+    if (c->counts_valid) {
+        std::vector<int4> cn(c->n);
+        FF_CUDA(c, cudaMemcpy(cn.data(), c->counts, sizeof(int4) * c->n, cudaMemcpyDeviceToHost));
+        for (const int4& v : cn) {
+            out->accepted += v.x;
+            out->pairs += v.y;
+            out->opened += v.z;
+        }
+        out->interactions = out->accepted + out->pairs;
+    }
+    return FF_OK;
+}
+
+ff_status ff_get_tree(ff_ctx* c, uint64_t* keys, uint32_t* order, int32_t* pbegin, int32_t* pend,
+                      int32_t* skip, int32_t* level, int32_t* leaf, void* centre, void* moment,
+                      int32_t dtype)
+{
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (!c->tree_valid) return fail(c, FF_ESTATE, "no Barnes-Hut tree has been built");
+    if (dtype != FF_DTYPE_F32 && dtype != FF_DTYPE_F64) return fail(c, FF_EINVAL, "bad dtype");
+    if ((s = sync_and_check(c)) != FF_OK) return s;
+    const int64_t n = c->n;
+    uint32_t nc = 0;
+    FF_CUDA(c, cudaMemcpy(&nc, c->off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (keys) FF_CUDA(c, cudaMemcpy(keys, c->keys[0], sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+    if (order) FF_CUDA(c, cudaMemcpy(order, c->st[c->cur].id, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    if (pbegin || pend || skip || level || leaf) {
+        std::vector<int4> nodes(nc);
+        if (nc) FF_CUDA(c, cudaMemcpy(nodes.data(), c->node, sizeof(int4) * nc, cudaMemcpyDeviceToHost));
+        for (uint32_t i = 0; i < nc; ++i) {
+            if (pbegin) pbegin[i] = nodes[i].x;
+            if (pend) pend[i] = nodes[i].y;
+            if (skip) skip[i] = nodes[i].z;
+            if (level) level[i] = nodes[i].w & 0xff;
+            if (leaf) leaf[i] = (nodes[i].w >> 8) & 1;
+        }
+    }
+    void* srcs[2] = {c->cen, c->mom};
+    void* dsts[2] = {centre, moment};
+    for (int q = 0; q < 2; ++q) {
+        if (!dsts[q] || nc == 0) continue;
+        std::vector<unsigned char> raw((size_t)nc * c->rec);
+        FF_CUDA(c, cudaMemcpy(raw.data(), srcs[q], raw.size(), cudaMemcpyDeviceToHost));
+        for (uint32_t i = 0; i < nc; ++i) {
+            double v[3];
+            if (c->fp64) {
+                const double* r = reinterpret_cast<const double*>(raw.data() + (size_t)i * c->rec);
+                v[0] = r[0]; v[1] = r[1]; v[2] = r[2];
+            } else {
+                const float* r = reinterpret_cast<const float*>(raw.data() + (size_t)i * c->rec);
+                v[0] = r[0]; v[1] = r[1]; v[2] = r[2];
+            }
+            for (int a = 0; a < 3; ++a) {
+                if (dtype == FF_DTYPE_F64) static_cast<double*>(dsts[q])[3 * (size_t)i + a] = v[a];
+                else static_cast<float*>(dsts[q])[3 * (size_t)i + a] = (float)v[a];
+            }
+        }
+    }
+    return FF_OK;
+}
+
+ff_status ff_get_counts(ff_ctx* c, int32_t* accepted, int32_t* pairs, int32_t* opened)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (!c->counts_valid) return fail(c, FF_ESTATE, "no interaction counts recorded (count_interactions = 0 or no BH evaluation)");
+    const int64_t n = c->n;
+    int32_t* stg = static_cast<int32_t*>(c->staging);
+    ffk::scatter_counts<float>(c->counts, c->st[c->cur].id, n, stg, stg + n, stg + 2 * n, c->stream);
+    FF_LAUNCHED(c);
+    if ((s = sync_and_check(c)) != FF_OK) return s;
+    int32_t* dst[3] = {accepted, pairs, opened};
+    for (int q = 0; q < 3; ++q)
+        if (dst[q]) FF_CUDA(c, cudaMemcpy(dst[q], stg + q * n, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    return FF_OK;
+}
+
+ff_status ff_profile(ff_ctx* c, int32_t enable)
+{
+    if (!c) return FF_EINVAL;
+    FF_CUDA(c, cudaSetDevice(c->p.device));
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& m : c->marks) {
+        c->pool.push_back(m.a);
+        c->pool.push_back(m.b);
+    }
+    c->marks.clear();
+    if (enable) {
+        for (int i = 0; i < 8; ++i) {
+            c->prof_ms[i] = 0.0;
+            c->prof_calls[i] = 0;
+        }
+        c->launches = 0;
+    }
+    c->prof = enable != 0;
+    return FF_OK;
+}
+
+ff_status ff_profile_read(ff_ctx* c, ff_profile_t* out)
+{
+    if (!c || !out) return FF_EINVAL;
+    FF_CUDA(c, cudaSetDevice(c->p.device));
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& m : c->marks) {
+        float ms = 0.0f;
+        FF_CUDA(c, cudaEventElapsedTime(&ms, m.a, m.b));
+        c->prof_ms[m.stage] += ms;
+        c->prof_calls[m.stage] += 1;
+        c->pool.push_back(m.a);
+        c->pool.push_back(m.b);
+    }
+    c->marks.clear();
+    for (int i = 0; i < 8; ++i) {
+        out->ms[i] = c->prof_ms[i];
+        out->calls[i] = c->prof_calls[i];
+    }
+    out->launches = c->launches;
+    return FF_OK;
+}
+
+const char* ff_last_error(const ff_ctx* c)
+{
+    if (!c) return g_create_err;
+    return c->err;
+}
+
+const char* ff_status_string(ff_status s)
+{
+    switch (s) {
+        case FF_OK: return "FF_OK";
+        case FF_EINVAL: return "FF_EINVAL";
+        case FF_ENOMEM: return "FF_ENOMEM";
+        case FF_ECUDA: return "FF_ECUDA";
+        case FF_EDEVICE: return "FF_EDEVICE";
+        case FF_ENONFINITE: return "FF_ENONFINITE";
+        case FF_ESTATE: return "FF_ESTATE";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

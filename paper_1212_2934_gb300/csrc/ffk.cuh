@@ -1,0 +1,162 @@
+// Internal declarations shared by the CUDA translation units of libff.
+// Kernels are templated on the arithmetic type R (float or double); every
+// launcher takes the stream explicitly and enqueues asynchronously.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ffk {
+
+// Kernels launched by this library (all contexts); read as differences.
+extern std::atomic<int64_t> g_launches;
+inline void counted(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// 32-byte aligned 4-vector of doubles (one 32-byte load per record).
+struct alignas(32) dvec4 {
+    double x, y, z, w;
+};
+
+template <typename R> struct V4;
+template <> struct V4<float> { using T = float4; };
+template <> struct V4<double> { using T = dvec4; };
+template <typename R> using vec4 = typename V4<R>::T;
+
+// Device error flags (one int32 word per context).
+enum : int {
+    FLAG_NONFINITE = 1,   // a position was NaN or infinite
+    FLAG_TRAVERSE = 2,    // traversal guard tripped (corrupt skip pointers)
+    FLAG_CAPACITY = 4,    // more cells than allocated
+    FLAG_AGGREGATE = 8,   // aggregation walk exceeded the level bound
+};
+
+constexpr int kMaxLevel = 21;        // 21 bits per axis -> 63-bit Morton keys
+constexpr int kMaxLeaf = 64;         // largest leaf_max accepted
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kSortThreads = 256;    // = kRadixBins: one digit per thread in the scatter
+constexpr int kSortItems = 8;        // keys per thread per block tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// Root cube, written by the bbox kernels and read by the key kernel.
+// lo/hi hold order-preserving integer encodings of the extrema.
+struct BBox {
+    long long lo[3];
+    long long hi[3];
+};
+
+// Field evaluation parameters in the arithmetic type.
+template <typename R>
+struct FieldParams {
+    R theta2;        // theta^2 rounded to R once from the double product
+    R rcut2;         // opening-test cut: lj_rcut^2 (0 when LJ is off)
+    R dip_scale;
+    R lj_eps24;      // 24 eps
+    R lj_sigma2;     // sigma^2
+    R lj_rcut2;      // rcut^2: the pair cut (decided on an exactly rounded r^2)
+    R lj_rcut2_hi;   // slightly above lj_rcut2: pre-test on a fused r^2
+    R lj_e2, lj_e4;  // 2 eps, 4 eps (pair energy)
+    R lj_shift;      // pair energy at rcut
+    int use_rcut;    // LJ on: cells closer than rcut are always opened
+    int include_sr;  // add the LJ force to f
+};
+
+// Integrator parameters (Sec. 2 reduced equations; Sec. 4 Euler-Maruyama).
+template <typename R>
+struct DynParams {
+    R dt, gamma_t, gamma_r, inv_inertia, sig_t, sig_r;
+    R hx, hy, hz;
+    R lo[3], hi[3];
+    R wall_eps24, wall_e2, wall_e4;
+    int walls;
+    uint32_t key0, key1;  // Philox key (seed)
+    uint32_t ctr0, ctr1;  // step counter
+};
+
+// Tree arrays (device pointers), cells in depth-first preorder.
+template <typename R>
+struct Tree {
+    int4* node;          // pbegin, pend, skip, level | leaf << 8
+    vec4<R>* cen;        // geometric centre xyz, cube side
+    vec4<R>* mom;        // moment sum xyz, particle count
+    vec4<R>* lo;         // lower cube corner xyz, cube side
+    vec4<R>* sum;        // position sum xyz (aggregation scratch)
+    int* parent;         // parent cell (-1 for the root)
+    int* arrive;         // aggregation arrival counters
+    int* ncells;         // device word: number of cells
+    int64_t cap;         // allocated cells
+};
+
+// ---------------------------------------------------------------- launchers
+// Scan: exclusive prefix sum of n uint32 values into out[0..n]; out[n] = total.
+// tmp must hold scan_tmp_words(n) words.
+size_t scan_tmp_words(int64_t n);
+void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs, keys < 2^63, eight passes of
+// eight bits: the sorted data end in (k0, v0); (k1, v1) is scratch.
+size_t radix_tmp_words(int64_t n);
+void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                      uint32_t* tmp, cudaStream_t s);
+
+template <typename R>
+void morton_keys(const vec4<R>* pos, int64_t n, BBox* bb, uint64_t* keys, uint32_t* vals,
+                 int* flags, cudaStream_t s);
+
+template <typename R>
+void gather_state(const uint32_t* perm, int64_t n, const vec4<R>* pos, const vec4<R>* vel,
+                  const vec4<R>* u, const vec4<R>* om, const uint32_t* id, vec4<R>* pos2,
+                  vec4<R>* vel2, vec4<R>* u2, vec4<R>* om2, uint32_t* id2, cudaStream_t s);
+
+// Tree build from sorted keys: cnt/off are n+1 words of scratch.
+template <typename R>
+void build_tree(const uint64_t* skeys, int64_t n, int leaf_max, const BBox* bb, Tree<R> t,
+                uint32_t* cnt, uint32_t* off, uint32_t* scan_tmp, int* flags, cudaStream_t s);
+
+template <typename R>
+void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint32_t* cnt,
+                    const uint32_t* off, Tree<R> t, int* flags, cudaStream_t s);
+
+// Barnes-Hut traversal.  h/f (and esr, counts if non-null) in sorted order.
+template <typename R>
+void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
+              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, cudaStream_t s);
+
+// All-pairs sum (Sec. 3.1, Algorithm 1).
+template <typename R>
+void ap_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, FieldParams<R> fp, vec4<R>* h,
+              vec4<R>* f, R* esr, cudaStream_t s);
+
+// Euler-Maruyama step; writes the new state to the second buffers and, if
+// partials is non-null, per-block FP64 observables of the old state.
+constexpr int kObs = 10;
+int integrate_blocks(int64_t n);
+template <typename R>
+void integrate(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R>* u,
+               const vec4<R>* om, const uint32_t* id, const vec4<R>* h, const vec4<R>* f,
+               const R* esr, DynParams<R> dp, vec4<R>* pos2, vec4<R>* vel2, vec4<R>* u2,
+               vec4<R>* om2, uint32_t* id2, double* partials, cudaStream_t s);
+
+// Observables of the state without stepping (per-block partials).
+template <typename R>
+void observables(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R>* u,
+                 const vec4<R>* om, const vec4<R>* h, const R* esr, DynParams<R> dp,
+                 double* partials, cudaStream_t s);
+void reduce_partials(const double* partials, int nblocks, double inv_n, double inertia_half,
+                     double* out, cudaStream_t s);
+
+// Layout conversion between caller arrays (n x 3, float or double) and
+// records; scatter/gather through the particle ids.
+template <typename R, typename I>
+void load3(const I* in, int64_t n, vec4<R>* out, cudaStream_t s);
+template <typename R>
+void fill_zero4(vec4<R>* out, int64_t n, cudaStream_t s);
+void iota32(uint32_t* out, int64_t n, cudaStream_t s);
+template <typename R, typename O>
+void scatter3(const vec4<R>* in, const uint32_t* id, int64_t n, O* out, cudaStream_t s);
+template <typename R>
+void scatter_counts(const int4* in, const uint32_t* id, int64_t n, int32_t* a, int32_t* p,
+                    int32_t* o, cudaStream_t s);
+
+}  // namespace ffk

@@ -1,0 +1,298 @@
+// Dipolar field and force kernels: the Barnes-Hut traversal (Sec. 3.2,
+// kernel 5 of the paper's scheme, redesigned) and the all-pairs sum
+// (Sec. 3.1, Algorithm 1).
+//
+// Traversal: one warp serves 32 consecutive particles of the Morton order.
+// Each lane keeps its own position in the depth-first cell list (`nxt`);
+// the warp visits cell i = min over lanes of nxt, and only the lanes whose
+// nxt == i act on it.  A lane therefore makes exactly the decisions of its
+// own per-particle traversal, in the same order (children in octant order),
+// while the cell record is fetched once per warp (one broadcast load).
+// Skip pointers replace a stack.  Every lane's nxt strictly increases, so
+// the loop ends after at most ncells visits.
+#include "ffk.cuh"
+
+namespace ffk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+
+// Reduced dipolar field of u_j and force on u_k at separation r = rho_k - rho_j
+// (Sec. 2, reduced Eqs. h_dip and f_dip), accumulated:
+//   h += [3 r (u_j.r) - u_j r^2] / r^5
+//   f += 3 [r (u_j.u_k) + u_k (u_j.r) + u_j (u_k.r)] / r^5 - 15 r (u_k.r)(u_j.r) / r^7
+template <typename R>
+__device__ __forceinline__ void dipole(R rx, R ry, R rz, R r2, R ukx, R uky, R ukz, R ujx, R ujy,
+                                       R ujz, R& hx, R& hy, R& hz, R& fx, R& fy, R& fz)
+{
+    const R ir = rsq(r2);
+    const R ir2 = ir * ir;
+    const R ir3 = ir2 * ir;
+    const R ir5 = ir3 * ir2;
+    const R ir7 = ir5 * ir2;
+    const R bj = ujx * rx + ujy * ry + ujz * rz;
+    const R bk = ukx * rx + uky * ry + ukz * rz;
+    const R a = ujx * ukx + ujy * uky + ujz * ukz;
+    const R t = R(3) * bj * ir5;
+    hx += rx * t - ujx * ir3;
+    hy += ry * t - ujy * ir3;
+    hz += rz * t - ujz * ir3;
+    const R s3 = R(3) * ir5;
+    const R cr = s3 * a - R(15) * bk * bj * ir7;
+    const R cuk = s3 * bj, cuj = s3 * bk;
+    fx += rx * cr + ukx * cuk + ujx * cuj;
+    fy += ry * cr + uky * cuk + ujy * cuj;
+    fz += rz * cr + ukz * cuk + ujz * cuj;
+}
+
+// Printed LJ force (Sec. 2, Eq. LJ) inside the cut, and half the pair
+// energy 2 eps (s/r)^12 - 4 eps (s/r)^6 shifted to zero at the cut.  Whether
+// the pair is inside is decided on r^2 = (rx rx + ry ry) + rz rz with every
+// operation rounded once (r2 from the field code may carry fused rounding);
+// that exact value is formed only near the cut.
+template <typename R>
+__device__ __forceinline__ void lj(const FieldParams<R>& fp, R rx, R ry, R rz, R r2, R& fx, R& fy,
+                                   R& fz, R& e)
+{
+    if (!(r2 < fp.lj_rcut2_hi)) return;
+    const R r2e = radd(radd(rmul(rx, rx), rmul(ry, ry)), rmul(rz, rz));
+    if (r2e < fp.lj_rcut2 && r2e > R(0)) {
+        const R ir2 = R(1) / r2e;
+        const R s2 = fp.lj_sigma2 * ir2;
+        const R s6 = s2 * s2 * s2;
+        const R s12 = s6 * s6;
+        const R c = fp.lj_eps24 * (s12 - s6) * ir2;
+        fx += c * rx;
+        fy += c * ry;
+        fz += c * rz;
+        e += R(0.5) * (fp.lj_e2 * s12 - fp.lj_e4 * s6 - fp.lj_shift);
+    }
+}
+
+// Opening test in the tree precision, each operation rounded once:
+// side^2 < theta^2 ((dx dx + dy dy) + dz dz), and with LJ on, the distance
+// from the particle to the cell's cube is at least rcut.
+template <typename R>
+__device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& x, const vec4<R>& c,
+                                       const vec4<R>* __restrict__ lo_arr, int i)
+{
+    const R dx = rsub(x.x, c.x), dy = rsub(x.y, c.y), dz = rsub(x.z, c.z);
+    const R d2 = radd(radd(rmul(dx, dx), rmul(dy, dy)), rmul(dz, dz));
+    const R s2 = rmul(c.w, c.w);
+    if (!(s2 < rmul(fp.theta2, d2))) return false;
+    if (fp.use_rcut) {
+        const vec4<R> lo = lo_arr[i];
+        const R side = lo.w;
+        R t[3];
+        const R xs[3] = {x.x, x.y, x.z};
+        const R ls[3] = {lo.x, lo.y, lo.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R hi = radd(ls[a], side);
+            const R below = rsub(ls[a], xs[a]);
+            const R above = rsub(xs[a], hi);
+            const R m = below > R(0) ? below : R(0);
+            t[a] = above > m ? above : m;
+        }
+        const R b2 = radd(radd(rmul(t[0], t[0]), rmul(t[1], t[1])), rmul(t[2], t[2]));
+        if (b2 < fp.rcut2) return false;
+    }
+    return true;
+}
+
+template <typename R, bool COUNT>
+__global__ void __launch_bounds__(128) k_bh(const vec4<R>* __restrict__ pos,
+                                            const vec4<R>* __restrict__ u, int n, Tree<R> t,
+                                            FieldParams<R> fp, vec4<R>* __restrict__ h,
+                                            vec4<R>* __restrict__ f, R* __restrict__ esr,
+                                            int4* __restrict__ counts, int* flags)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k - lane >= n) return;  // the whole warp is past the end
+    if (*flags & FLAG_CAPACITY) return;
+    const bool active = k < n;
+    vec4<R> xk, uk;
+    if (active) {
+        xk = pos[k];
+        uk = u[k];
+    } else {
+        xk.x = xk.y = xk.z = xk.w = R(0);
+        uk = xk;
+    }
+    R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0;
+    int nacc = 0, npair = 0, nopen = 0;
+    const unsigned ncells = (unsigned)*t.ncells;
+    unsigned nxt = active ? 0u : 0xffffffffu;
+    for (;;) {
+        const unsigned i = __reduce_min_sync(kFull, nxt);
+        if (i >= ncells) break;
+        if (nxt == i) {
+            const int4 nd = t.node[i];
+            const bool inside = nd.x <= k && k < nd.y;
+            const bool leaf = (nd.w >> 8) != 0;
+            const bool single = leaf && (nd.y - nd.x == 1);
+            const vec4<R> c = t.cen[i];
+            const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i);
+            if (acc || (single && !inside)) {
+                // the cell's pseudo-particle; for a one-particle leaf it is the
+                // particle itself (centre and moment sum of one term are exact)
+                const vec4<R> m = t.mom[i];
+                const R rx = xk.x - c.x, ry = xk.y - c.y, rz = xk.z - c.z;
+                const R r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 > R(0))
+                    dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, m.x, m.y, m.z, hx, hy, hz, fx, fy,
+                              fz);
+                if (acc) {
+                    if (COUNT) ++nacc;
+                } else {
+                    if (fp.include_sr) lj<R>(fp, rx, ry, rz, r2, sx, sy, sz, es);
+                    if (COUNT) ++npair;
+                }
+                nxt = (unsigned)nd.z;
+            } else if (leaf) {
+                if (!single) {
+                    for (int s = nd.x; s < nd.y; ++s) {
+                        if (s == k) continue;
+                        const vec4<R> xj = pos[s], uj = u[s];
+                        const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
+                        const R r2 = rx * rx + ry * ry + rz * rz;
+                        if (r2 > R(0)) {
+                            dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, uj.x, uj.y, uj.z, hx, hy,
+                                      hz, fx, fy, fz);
+                            if (fp.include_sr) lj<R>(fp, rx, ry, rz, r2, sx, sy, sz, es);
+                        }
+                        if (COUNT) ++npair;
+                    }
+                }
+                nxt = (unsigned)nd.z;
+            } else {
+                if (COUNT) ++nopen;
+                nxt = i + 1;
+            }
+            if (nxt <= i) {  // skip pointers must move forward
+                atomicOr(flags, FLAG_TRAVERSE);
+                nxt = 0xffffffffu;
+            }
+        }
+    }
+    if (!active) return;
+    vec4<R> ho, fo;
+    ho.x = fp.dip_scale * hx;
+    ho.y = fp.dip_scale * hy;
+    ho.z = fp.dip_scale * hz;
+    ho.w = R(0);
+    fo.x = fp.dip_scale * fx + sx;
+    fo.y = fp.dip_scale * fy + sy;
+    fo.z = fp.dip_scale * fz + sz;
+    fo.w = R(0);
+    h[k] = ho;
+    f[k] = fo;
+    if (esr) esr[k] = es;
+    if (COUNT) counts[k] = make_int4(nacc, npair, nopen, 0);
+}
+
+// All pairs: one thread per target; source records staged through shared
+// memory one block-sized tile at a time (Sec. 3.1, Algorithm 1).
+constexpr int kApThreads = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kApThreads) k_ap(const vec4<R>* __restrict__ pos,
+                                                   const vec4<R>* __restrict__ u, int n,
+                                                   FieldParams<R> fp, vec4<R>* __restrict__ h,
+                                                   vec4<R>* __restrict__ f, R* __restrict__ esr)
+{
+    __shared__ vec4<R> sp[kApThreads];
+    __shared__ vec4<R> su[kApThreads];
+    const int k = blockIdx.x * kApThreads + threadIdx.x;
+    const bool active = k < n;
+    vec4<R> xk, uk;
+    if (active) {
+        xk = pos[k];
+        uk = u[k];
+    } else {
+        xk.x = xk.y = xk.z = xk.w = R(0);
+        uk = xk;
+    }
+    R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0;
+    for (int tile = 0; tile < n; tile += kApThreads) {
+        const int j = tile + threadIdx.x;
+        if (j < n) {
+            sp[threadIdx.x] = pos[j];
+            su[threadIdx.x] = u[j];
+        }
+        __syncthreads();
+        const int lim = min(kApThreads, n - tile);
+        for (int jj = 0; jj < lim; ++jj) {
+            if (tile + jj == k) continue;
+            const vec4<R> xj = sp[jj], uj = su[jj];
+            const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
+            const R r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 > R(0)) {
+                dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, uj.x, uj.y, uj.z, hx, hy, hz, fx, fy,
+                          fz);
+                if (fp.include_sr) lj<R>(fp, rx, ry, rz, r2, sx, sy, sz, es);
+            }
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    vec4<R> ho, fo;
+    ho.x = fp.dip_scale * hx;
+    ho.y = fp.dip_scale * hy;
+    ho.z = fp.dip_scale * hz;
+    ho.w = R(0);
+    fo.x = fp.dip_scale * fx + sx;
+    fo.y = fp.dip_scale * fy + sy;
+    fo.z = fp.dip_scale * fz + sz;
+    fo.w = R(0);
+    h[k] = ho;
+    f[k] = fo;
+    if (esr) esr[k] = es;
+}
+
+}  // namespace
+
+template <typename R>
+void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
+              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, cudaStream_t s)
+{
+    const unsigned g = (unsigned)((n + 127) / 128);
+    if (counts)
+        k_bh<R, true><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags);
+    else
+        k_bh<R, false><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags);
+    counted();
+}
+
+template <typename R>
+void ap_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, FieldParams<R> fp, vec4<R>* h,
+              vec4<R>* f, R* esr, cudaStream_t s)
+{
+    const unsigned g = (unsigned)((n + kApThreads - 1) / kApThreads);
+    k_ap<R><<<g, kApThreads, 0, s>>>(pos, u, (int)n, fp, h, f, esr);
+    counted();
+}
+
+template void bh_field<float>(const float4*, const float4*, int64_t, Tree<float>,
+                              FieldParams<float>, float4*, float4*, float*, int4*, int*,
+                              cudaStream_t);
+template void bh_field<double>(const dvec4*, const dvec4*, int64_t, Tree<double>,
+                               FieldParams<double>, dvec4*, dvec4*, double*, int4*, int*,
+                               cudaStream_t);
+template void ap_field<float>(const float4*, const float4*, int64_t, FieldParams<float>, float4*,
+                              float4*, float*, cudaStream_t);
+template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<double>, dvec4*,
+                               dvec4*, double*, cudaStream_t);
+
+}  // namespace ffk

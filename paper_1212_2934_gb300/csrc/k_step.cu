@@ -1,0 +1,376 @@
+// Integration step (Sec. 4, Euler-Maruyama with the reduced Langevin
+// equations of Sec. 2; kernel 6 of the paper's scheme), thermal noise from
+// a counter-based generator, FP64 observables (Sec. 5), and the layout
+// conversions between the caller's n x 3 arrays and the 16/32-byte records.
+#include "ffk.cuh"
+
+namespace ffk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kStepThreads = 256;
+
+// Philox4x32 with ten rounds (Salmon, Moraes, Dror, Shaw, SC'11): each round
+// multiplies words 0 and 2 by fixed odd constants and mixes the high halves
+// with the other words and the round key; the key advances by the Weyl
+// increments between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Box-Muller on one pair of words: u1 = (a + 1) 2^-32 in (0, 1],
+// u2 = b 2^-32; z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = ... sin(2 pi u2).
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1)
+{
+    const float u1 = __fmaf_rn(__uint2float_rn(a), 0x1p-32f, 0x1p-32f);
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(__uint2float_rn(b) * 0x1p-31f, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+}
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, double& z1)
+{
+    const double u1 = ((double)a + 1.0) * 0x1p-32;
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi((double)b * 0x1p-31, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+}
+
+// Six normals for (seed, step, id): counter (step lo, step hi, id, block).
+template <typename R>
+__device__ __forceinline__ void normals6(const DynParams<R>& dp, uint32_t id, R z[6])
+{
+    const uint4 w0 = philox10(make_uint4(dp.ctr0, dp.ctr1, id, 0u), dp.key0, dp.key1);
+    const uint4 w1 = philox10(make_uint4(dp.ctr0, dp.ctr1, id, 1u), dp.key0, dp.key1);
+    box_muller(w0.x, w0.y, z[0], z[1]);
+    box_muller(w0.z, w0.w, z[2], z[3]);
+    box_muller(w1.x, w1.y, z[4], z[5]);
+}
+
+// LJ-type wall along one axis: distance w to the plane, sigma_w = 1/2, cut
+// where the force vanishes (w = 1/2), w clamped below at 0.01.
+template <typename R>
+__device__ __forceinline__ R wall_force(R w, const DynParams<R>& dp, double& e)
+{
+    if (!(w < R(0.5))) return R(0);
+    if (w < R(0.01)) w = R(0.01);
+    const R s = R(0.5) / w;
+    const R s2 = s * s;
+    const R s6 = s2 * s2 * s2;
+    e += (double)(dp.wall_e2 * s6 * s6 - dp.wall_e4 * s6 + dp.wall_e2);
+    return dp.wall_eps24 * (s6 * s6 - s6) / w;
+}
+
+template <typename R>
+__device__ __forceinline__ void walls3(const DynParams<R>& dp, const vec4<R>& x, R& fx, R& fy,
+                                       R& fz, double& e)
+{
+    if (!dp.walls) return;
+    fx += wall_force<R>(x.x - dp.lo[0], dp, e) - wall_force<R>(dp.hi[0] - x.x, dp, e);
+    fy += wall_force<R>(x.y - dp.lo[1], dp, e) - wall_force<R>(dp.hi[1] - x.y, dp, e);
+    fz += wall_force<R>(x.z - dp.lo[2], dp, e) - wall_force<R>(dp.hi[2] - x.z, dp, e);
+}
+
+// Block sum of kObs doubles; thread 0 writes them to out.
+__device__ __forceinline__ void block_sum_obs(double v[kObs], double* out)
+{
+    __shared__ double sh[kStepThreads / 32][kObs];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kObs; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(kFull, v[q], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kObs; ++q) sh[w][q] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < kObs) {
+        double s = 0.0;
+        for (int ww = 0; ww < kStepThreads / 32; ++ww) s += sh[ww][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// Accumulates one particle's terms: e_dip, e_zeeman, e_sr, e_wall, e_kin_t,
+// w^2 (scaled by I/2 later), u (3), h_dip_z.
+template <typename R>
+__device__ __forceinline__ void obs_terms(double v[kObs], const DynParams<R>& dp, const vec4<R>& uu,
+                                          const vec4<R>& hd, const vec4<R>& vv, const vec4<R>& w,
+                                          R es, double ew)
+{
+    const double ux = uu.x, uy = uu.y, uz = uu.z;
+    v[0] += -0.5 * (ux * (double)hd.x + uy * (double)hd.y + uz * (double)hd.z);
+    v[1] += -(ux * (double)dp.hx + uy * (double)dp.hy + uz * (double)dp.hz);
+    v[2] += (double)es;
+    v[3] += ew;
+    v[4] += 0.5 * ((double)vv.x * vv.x + (double)vv.y * vv.y + (double)vv.z * vv.z);
+    v[5] += (double)w.x * w.x + (double)w.y * w.y + (double)w.z * w.z;
+    v[6] += ux;
+    v[7] += uy;
+    v[8] += uz;
+    v[9] += (double)hd.z;
+}
+
+// x' = x + dt v; v' = v + dt (f - G_t v) + sig_t xi_t;
+// w' = w + dt (u x h - G_r w) / I + sig_r xi_r; u' = normalise(u + dt w x u).
+template <typename R, bool OBS>
+__global__ void __launch_bounds__(kStepThreads) k_integrate(
+    int64_t n, const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ vel,
+    const vec4<R>* __restrict__ u, const vec4<R>* __restrict__ om, const uint32_t* __restrict__ id,
+    const vec4<R>* __restrict__ hdip, const vec4<R>* __restrict__ fint, const R* __restrict__ esr,
+    DynParams<R> dp, vec4<R>* __restrict__ pos2, vec4<R>* __restrict__ vel2,
+    vec4<R>* __restrict__ u2, vec4<R>* __restrict__ om2, uint32_t* __restrict__ id2,
+    double* __restrict__ partials)
+{
+    double v[kObs];
+#pragma unroll
+    for (int q = 0; q < kObs; ++q) v[q] = 0.0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const vec4<R> x = pos[s], vv = vel[s], uu = u[s], w = om[s], hd = hdip[s], fi = fint[s];
+        const uint32_t pid = id[s];
+        double ew = 0.0;
+        R fx = fi.x, fy = fi.y, fz = fi.z;
+        walls3<R>(dp, x, fx, fy, fz, ew);
+        const R hx = hd.x + dp.hx, hy = hd.y + dp.hy, hz = hd.z + dp.hz;
+        R z[6];
+        normals6<R>(dp, pid, z);
+        const R tx = uu.y * hz - uu.z * hy, ty = uu.z * hx - uu.x * hz, tz = uu.x * hy - uu.y * hx;
+        const R cx = w.y * uu.z - w.z * uu.y, cy = w.z * uu.x - w.x * uu.z,
+                cz = w.x * uu.y - w.y * uu.x;
+        vec4<R> xn, vn, wn, un;
+        xn.x = x.x + dp.dt * vv.x;
+        xn.y = x.y + dp.dt * vv.y;
+        xn.z = x.z + dp.dt * vv.z;
+        xn.w = x.w;
+        vn.x = vv.x + dp.dt * (fx - dp.gamma_t * vv.x) + dp.sig_t * z[0];
+        vn.y = vv.y + dp.dt * (fy - dp.gamma_t * vv.y) + dp.sig_t * z[1];
+        vn.z = vv.z + dp.dt * (fz - dp.gamma_t * vv.z) + dp.sig_t * z[2];
+        vn.w = R(0);
+        wn.x = w.x + dp.dt * (tx - dp.gamma_r * w.x) * dp.inv_inertia + dp.sig_r * z[3];
+        wn.y = w.y + dp.dt * (ty - dp.gamma_r * w.y) * dp.inv_inertia + dp.sig_r * z[4];
+        wn.z = w.z + dp.dt * (tz - dp.gamma_r * w.z) * dp.inv_inertia + dp.sig_r * z[5];
+        wn.w = R(0);
+        const R ax = uu.x + dp.dt * cx, ay = uu.y + dp.dt * cy, az = uu.z + dp.dt * cz;
+        const R inv = R(1) / sqrt(ax * ax + ay * ay + az * az);
+        un.x = ax * inv;
+        un.y = ay * inv;
+        un.z = az * inv;
+        un.w = R(0);
+        pos2[s] = xn;
+        vel2[s] = vn;
+        u2[s] = un;
+        om2[s] = wn;
+        id2[s] = pid;
+        if (OBS) obs_terms<R>(v, dp, uu, hd, vv, w, esr ? esr[s] : R(0), ew);
+    }
+    if (OBS) block_sum_obs(v, partials + (int64_t)blockIdx.x * kObs);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kStepThreads) k_observables(
+    int64_t n, const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ vel,
+    const vec4<R>* __restrict__ u, const vec4<R>* __restrict__ om,
+    const vec4<R>* __restrict__ hdip, const R* __restrict__ esr, DynParams<R> dp,
+    double* __restrict__ partials)
+{
+    double v[kObs];
+#pragma unroll
+    for (int q = 0; q < kObs; ++q) v[q] = 0.0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const vec4<R> x = pos[s];
+        double ew = 0.0;
+        R fx = 0, fy = 0, fz = 0;
+        walls3<R>(dp, x, fx, fy, fz, ew);
+        obs_terms<R>(v, dp, u[s], hdip[s], vel[s], om[s], esr ? esr[s] : R(0), ew);
+    }
+    block_sum_obs(v, partials + (int64_t)blockIdx.x * kObs);
+}
+
+// Deterministic final sum: one thread per quantity, blocks in order.
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks, double inv_n,
+                                  double inertia_half, double* __restrict__ out)
+{
+    const int q = threadIdx.x;
+    if (q >= kObs) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * kObs + q];
+    if (q == 5) s *= inertia_half;
+    if (q >= 6) s *= inv_n;
+    out[q] = s;
+}
+
+template <typename R, typename I>
+__global__ void k_load3(const I* __restrict__ in, int64_t n, vec4<R>* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    vec4<R> v;
+    v.x = (R)in[3 * i];
+    v.y = (R)in[3 * i + 1];
+    v.z = (R)in[3 * i + 2];
+    v.w = R(0);
+    out[i] = v;
+}
+
+template <typename R>
+__global__ void k_zero4(vec4<R>* __restrict__ out, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    vec4<R> v;
+    v.x = v.y = v.z = v.w = R(0);
+    out[i] = v;
+}
+
+__global__ void k_iota(uint32_t* __restrict__ out, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (uint32_t)i;
+}
+
+template <typename R, typename O>
+__global__ void k_scatter3(const vec4<R>* __restrict__ in, const uint32_t* __restrict__ id,
+                           int64_t n, O* __restrict__ out)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const vec4<R> v = in[s];
+    const int64_t d = id[s];
+    out[3 * d] = (O)v.x;
+    out[3 * d + 1] = (O)v.y;
+    out[3 * d + 2] = (O)v.z;
+}
+
+__global__ void k_scatter_counts(const int4* __restrict__ in, const uint32_t* __restrict__ id,
+                                 int64_t n, int32_t* a, int32_t* p, int32_t* o)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int4 v = in[s];
+    const int64_t d = id[s];
+    if (a) a[d] = v.x;
+    if (p) p[d] = v.y;
+    if (o) o[d] = v.z;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+int integrate_blocks(int64_t n)
+{
+    int64_t b = (n + kStepThreads - 1) / kStepThreads;
+    if (b > 152 * 8) b = 152 * 8;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename R>
+void integrate(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R>* u,
+               const vec4<R>* om, const uint32_t* id, const vec4<R>* h, const vec4<R>* f,
+               const R* esr, DynParams<R> dp, vec4<R>* pos2, vec4<R>* vel2, vec4<R>* u2,
+               vec4<R>* om2, uint32_t* id2, double* partials, cudaStream_t s)
+{
+    const int g = integrate_blocks(n);
+    if (partials)
+        k_integrate<R, true><<<g, kStepThreads, 0, s>>>(n, pos, vel, u, om, id, h, f, esr, dp, pos2,
+                                                        vel2, u2, om2, id2, partials);
+    else
+        k_integrate<R, false><<<g, kStepThreads, 0, s>>>(n, pos, vel, u, om, id, h, f, esr, dp,
+                                                         pos2, vel2, u2, om2, id2, partials);
+    counted();
+}
+
+template <typename R>
+void observables(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R>* u,
+                 const vec4<R>* om, const vec4<R>* h, const R* esr, DynParams<R> dp,
+                 double* partials, cudaStream_t s)
+{
+    k_observables<R><<<integrate_blocks(n), kStepThreads, 0, s>>>(n, pos, vel, u, om, h, esr, dp,
+                                                                  partials);
+    counted();
+}
+
+void reduce_partials(const double* partials, int nblocks, double inv_n, double inertia_half,
+                     double* out, cudaStream_t s)
+{
+    k_reduce_partials<<<1, 32, 0, s>>>(partials, nblocks, inv_n, inertia_half, out);
+    counted();
+}
+
+template <typename R, typename I>
+void load3(const I* in, int64_t n, vec4<R>* out, cudaStream_t s)
+{
+    k_load3<R, I><<<nblk(n, 256), 256, 0, s>>>(in, n, out);
+    counted();
+}
+
+template <typename R>
+void fill_zero4(vec4<R>* out, int64_t n, cudaStream_t s)
+{
+    k_zero4<R><<<nblk(n, 256), 256, 0, s>>>(out, n);
+    counted();
+}
+
+void iota32(uint32_t* out, int64_t n, cudaStream_t s)
+{
+    k_iota<<<nblk(n, 256), 256, 0, s>>>(out, n);
+    counted();
+}
+
+template <typename R, typename O>
+void scatter3(const vec4<R>* in, const uint32_t* id, int64_t n, O* out, cudaStream_t s)
+{
+    k_scatter3<R, O><<<nblk(n, 256), 256, 0, s>>>(in, id, n, out);
+    counted();
+}
+
+template <typename R>
+void scatter_counts(const int4* in, const uint32_t* id, int64_t n, int32_t* a, int32_t* p,
+                    int32_t* o, cudaStream_t s)
+{
+    k_scatter_counts<<<nblk(n, 256), 256, 0, s>>>(in, id, n, a, p, o);
+    counted();
+}
+
+#define FFK_INST(R)                                                                             \
+    template void integrate<R>(int64_t, const vec4<R>*, const vec4<R>*, const vec4<R>*,          \
+                               const vec4<R>*, const uint32_t*, const vec4<R>*, const vec4<R>*,  \
+                               const R*, DynParams<R>, vec4<R>*, vec4<R>*, vec4<R>*, vec4<R>*,   \
+                               uint32_t*, double*, cudaStream_t);                               \
+    template void observables<R>(int64_t, const vec4<R>*, const vec4<R>*, const vec4<R>*,        \
+                                 const vec4<R>*, const vec4<R>*, const R*, DynParams<R>,         \
+                                 double*, cudaStream_t);                                        \
+    template void load3<R, float>(const float*, int64_t, vec4<R>*, cudaStream_t);               \
+    template void load3<R, double>(const double*, int64_t, vec4<R>*, cudaStream_t);             \
+    template void fill_zero4<R>(vec4<R>*, int64_t, cudaStream_t);                               \
+    template void scatter3<R, float>(const vec4<R>*, const uint32_t*, int64_t, float*,           \
+                                     cudaStream_t);                                             \
+    template void scatter3<R, double>(const vec4<R>*, const uint32_t*, int64_t, double*,         \
+                                      cudaStream_t);                                            \
+    template void scatter_counts<R>(const int4*, const uint32_t*, int64_t, int32_t*, int32_t*,   \
+                                    int32_t*, cudaStream_t);
+FFK_INST(float)
+FFK_INST(double)
+#undef FFK_INST
+
+}  // namespace ffk

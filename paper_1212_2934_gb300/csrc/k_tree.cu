@@ -1,0 +1,667 @@
+// Octree construction on the GPU (Sec. 3.2, kernels 1-4 of the paper's
+// scheme, redesigned): root cube by reduction, 63-bit Morton keys, a stable
+// LSD radix sort, and a parallel build of the depth-first-preorder octree
+// straight from the sorted keys, followed by one bottom-up aggregation
+// launch.  No kernel here waits on another block: the build needs no locks
+// and the aggregation uses arrival counters (the last child to arrive sums
+// its parent), so every loop is bounded.
+#include <climits>
+
+#include "ffk.cuh"
+
+namespace ffk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------ scan
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ uint32_t block_exscan(uint32_t v, uint32_t* total)
+{
+    __shared__ uint32_t ws[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kScanThreads / 32 ? ws[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < kScanThreads / 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kScanThreads / 32) ws[lane] = w;
+    }
+    __syncthreads();
+    uint32_t pre = warp ? ws[warp - 1] : 0u;
+    *total = ws[kScanThreads / 32 - 1];
+    __syncthreads();
+    return pre + x - v;
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+                              uint32_t* __restrict__ bsum)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (base + j < n) s += in[base + j];
+    uint32_t tot;
+    block_exscan(s, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the block sums in place; bsum[nb] = total,
+// out_total (if non-null) = total.
+__global__ void k_scan_top(uint32_t* __restrict__ bsum, int64_t nb, uint32_t* out_total)
+{
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanTile) {
+        const int64_t b0 = base + (int64_t)threadIdx.x * kScanItems;
+        uint32_t v[kScanItems];
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            v[j] = (b0 + j < nb) ? bsum[b0 + j] : 0u;
+            s += v[j];
+        }
+        uint32_t tot;
+        uint32_t ex = block_exscan(s, &tot) + carry;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            if (b0 + j < nb) bsum[b0 + j] = ex;
+            ex += v[j];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        bsum[nb] = carry;
+        if (out_total) *out_total = carry;
+    }
+}
+
+__global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t n,
+                            const uint32_t* __restrict__ bsum, uint32_t* __restrict__ out)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = (base + j < n) ? in[base + j] : 0u;
+        s += v[j];
+    }
+    uint32_t tot;
+    uint32_t ex = block_exscan(s, &tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < n) out[base + j] = ex;
+        ex += v[j];
+    }
+}
+
+// ------------------------------------------------------------ radix sort
+__global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                             uint32_t* __restrict__ hist, int64_t nb)
+{
+    __shared__ uint32_t h[kRadixBins];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = base + r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kRadixBins - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: within a tile, keys keep their index order; ranks among
+// equal digits come from warp match masks and per-warp digit counts.
+__global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                int64_t n, int shift, const uint32_t* __restrict__ offs,
+                                int64_t nb)
+{
+    __shared__ uint32_t s_base[kRadixBins];
+    __shared__ uint32_t s_w[kSortThreads / 32][kRadixBins];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    s_base[t] = offs[(int64_t)t * nb + blockIdx.x];
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; ++r) {
+#pragma unroll
+        for (int j = 0; j < kRadixBins / 32; ++j) s_w[w][lane + 32 * j] = 0;
+        __syncthreads();
+        const int64_t i = base + r * kSortThreads + t;
+        const bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0ull;
+        uint32_t d = valid ? (uint32_t)((key >> shift) & (kRadixBins - 1)) : (uint32_t)kRadixBins;
+        const uint32_t peers = __match_any_sync(kFull, d);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) s_w[w][d] = __popc(peers);
+        __syncthreads();
+        uint32_t run = s_base[t];
+#pragma unroll
+        for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+            uint32_t c = s_w[ww][t];
+            s_w[ww][t] = run;
+            run += c;
+        }
+        s_base[t] = run;
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = s_w[w][d] + rank;
+            kout[pos] = key;
+            vout[pos] = vin[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- bbox and keys
+__device__ __forceinline__ long long enc(float x)
+{
+    int i = __float_as_int(x);
+    return (long long)(i >= 0 ? i : i ^ 0x7fffffff);
+}
+__device__ __forceinline__ long long enc(double x)
+{
+    long long i = __double_as_longlong(x);
+    return i >= 0 ? i : i ^ 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ void dec(long long e, float* x)
+{
+    int i = (int)e;
+    *x = __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
+}
+__device__ __forceinline__ void dec(long long e, double* x)
+{
+    *x = __longlong_as_double(e >= 0 ? e : e ^ 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rfloor(float a) { return floorf(a); }
+__device__ __forceinline__ double rfloor(double a) { return floor(a); }
+__device__ __forceinline__ float rscale2(float a, int e) { return ldexpf(a, e); }
+__device__ __forceinline__ double rscale2(double a, int e) { return ldexp(a, e); }
+
+__global__ void k_bbox_init(BBox* bb)
+{
+    for (int a = 0; a < 3; ++a) {
+        bb->lo[a] = LLONG_MAX;
+        bb->hi[a] = LLONG_MIN;
+    }
+}
+
+template <typename R>
+__global__ void k_bbox(const vec4<R>* __restrict__ pos, int64_t n, BBox* bb, int* flags)
+{
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
+    long long hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        vec4<R> p = pos[i];
+        R c[3] = {p.x, p.y, p.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bad |= !isfinite(c[a]);
+            long long e = enc(c[a]);
+            lo[a] = min(lo[a], e);
+            hi[a] = max(hi[a], e);
+        }
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, FLAG_NONFINITE);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(kFull, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(kFull, hi[a], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&bb->lo[a], lo[a]);
+            atomicMax(&bb->hi[a], hi[a]);
+        }
+    }
+}
+
+// Root cube: origin = minimum corner, side = largest extent (1 if all zero).
+template <typename R>
+__device__ __forceinline__ void root_cube(const BBox* bb, R mn[3], R* side)
+{
+    R mx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        dec(bb->lo[a], &mn[a]);
+        dec(bb->hi[a], &mx[a]);
+    }
+    R s = rsub(mx[0], mn[0]);
+#pragma unroll
+    for (int a = 1; a < 3; ++a) {
+        R e = rsub(mx[a], mn[a]);
+        if (e > s) s = e;
+    }
+    if (!(s > R(0))) s = R(1);
+    *side = s;
+}
+
+template <typename R>
+__device__ __forceinline__ uint32_t quantise(R x, R mn, R S)
+{
+    R fl = rfloor(rmul(rsub(x, mn), S));
+    if (!(fl > R(0))) return 0u;
+    if (fl >= R(2097151)) return 2097151u;
+    return (uint32_t)fl;
+}
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+
+template <typename R>
+__global__ void k_morton(const vec4<R>* __restrict__ pos, int64_t n, const BBox* __restrict__ bb,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    R mn[3], side;
+    root_cube<R>(bb, mn, &side);
+    const R S = rdiv(R(2097152), side);
+    vec4<R> p = pos[i];
+    uint32_t qx = quantise<R>(p.x, mn[0], S);
+    uint32_t qy = quantise<R>(p.y, mn[1], S);
+    uint32_t qz = quantise<R>(p.z, mn[2], S);
+    keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    vals[i] = (uint32_t)i;
+}
+
+template <typename R>
+__global__ void k_gather(const uint32_t* __restrict__ perm, int64_t n,
+                         const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ vel,
+                         const vec4<R>* __restrict__ u, const vec4<R>* __restrict__ om,
+                         const uint32_t* __restrict__ id, vec4<R>* __restrict__ pos2,
+                         vec4<R>* __restrict__ vel2, vec4<R>* __restrict__ u2,
+                         vec4<R>* __restrict__ om2, uint32_t* __restrict__ id2)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t p = perm[s];
+    pos2[s] = pos[p];
+    vel2[s] = vel[p];
+    u2[s] = u[p];
+    om2[s] = om[p];
+    id2[s] = id[p];
+}
+
+// ------------------------------------------------------------ tree build
+// Split level of sorted position j: the first level at which particles j-1
+// and j fall in different cells (0 for j = 0 and j = n; 22 for equal keys).
+__device__ __forceinline__ int split_level(const uint64_t* __restrict__ k, int64_t j, int64_t n)
+{
+    if (j <= 0 || j >= n) return 0;
+    uint64_t x = k[j] ^ k[j - 1];
+    if (!x) return kMaxLevel + 1;
+    return (__clzll((long long)x) - 1) / 3 + 1;
+}
+
+// Per particle i: depth d_i of its leaf and the number of cells whose first
+// particle is i (levels l_i .. d_i).  The level-L cell holding i has more
+// than m particles iff some a + b = m has the a positions i, i-1, ..
+// i-a+1 and the b positions i+1 .. i+b all with split level > L.
+__global__ void k_levels(const uint64_t* __restrict__ k, int64_t n, int m,
+                         uint32_t* __restrict__ cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int right[kMaxLeaf + 1];
+    right[0] = 99;
+    for (int b = 1; b <= m; ++b) right[b] = min(right[b - 1], split_level(k, i + b, n));
+    int left = 99;
+    int D = min(left, right[m]);
+    for (int a = 1; a <= m; ++a) {
+        left = min(left, split_level(k, i - a + 1, n));
+        D = max(D, min(left, right[m - a]));
+    }
+    const int d = min(D, kMaxLevel);
+    const int li = split_level(k, i, n);
+    cnt[i] = d >= li ? (uint32_t)(d - li + 1) : 0u;
+}
+
+// First j in [lo, n) with k[j] >= bound, given k[lo-1] < bound.
+__device__ __forceinline__ int64_t gallop_right(const uint64_t* __restrict__ k, int64_t lo,
+                                                int64_t n, uint64_t bound)
+{
+    if (lo >= n || k[lo] >= bound) return lo;
+    int64_t step = 1, hi = lo + 1;
+    while (hi < n && k[hi] < bound) {
+        lo = hi;
+        step <<= 1;
+        hi = lo + step;
+    }
+    if (hi > n) hi = n;
+    while (hi - lo > 1) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (k[mid] < bound) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+// First j in [0, hi] with k[j] >= bound, given k[hi] >= bound.
+__device__ __forceinline__ int64_t gallop_left(const uint64_t* __restrict__ k, int64_t hi,
+                                               uint64_t bound)
+{
+    int64_t lo = -1, step = 1;
+    for (;;) {
+        int64_t c = hi - step;
+        if (c < 0) break;
+        if (k[c] < bound) {
+            lo = c;
+            break;
+        }
+        hi = c;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (k[mid] < bound) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+// Writes the cells whose first particle is i: level L covers the run of
+// keys sharing i's level-L prefix; skip = first cell of the particle after
+// the run; the deepest of them is i's leaf.  Cube of a level-L cell with
+// integer coordinates q: lo = origin + q * (side 2^-L), each op rounded once.
+template <typename R>
+__global__ void k_emit(const uint64_t* __restrict__ k, int64_t n, const uint32_t* __restrict__ cnt,
+                       const uint32_t* __restrict__ off, const BBox* __restrict__ bb, Tree<R> t,
+                       int* flags)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)cnt[i];
+    if (c == 0) return;
+    const int li = split_level(k, i, n);
+    const int d = li + c - 1;
+    const int64_t base = off[i];
+    if (base + c > t.cap || (int64_t)off[n] > t.cap) {
+        atomicOr(flags, FLAG_CAPACITY);
+        return;
+    }
+    R mn[3], side;
+    root_cube<R>(bb, mn, &side);
+    const uint64_t key = k[i];
+    int64_t pe = i + 1;
+    for (int L = d; L >= li; --L) {
+        const int64_t idx = base + (L - li);
+        if (L == 0) {
+            pe = n;
+        } else {
+            const int sh = 3 * (kMaxLevel - L);
+            const uint64_t bound = ((key >> sh) + 1ull) << sh;
+            pe = gallop_right(k, pe, n, bound);
+        }
+        const int skip = (int)off[pe];
+        const int leaf = (L == d) ? 1 : 0;
+        t.node[idx] = make_int4((int)i, (int)pe, skip, L | (leaf << 8));
+        int parent;
+        if (L == 0) {
+            parent = -1;
+        } else if (L > li) {
+            parent = (int)idx - 1;
+        } else {
+            const int sh2 = 3 * (kMaxLevel - (L - 1));
+            const uint64_t lowb = (key >> sh2) << sh2;
+            const int64_t s = gallop_left(k, i, lowb);
+            parent = (int)off[s] + (L - 1 - split_level(k, s, n));
+        }
+        t.parent[idx] = parent;
+        t.arrive[idx] = 0;
+        const R sL = rscale2(side, -L);
+        const uint64_t pre = (L == 0) ? 0ull : (key >> (3 * (kMaxLevel - L)));
+        const R qx = (R)compact3(pre >> 2), qy = (R)compact3(pre >> 1), qz = (R)compact3(pre);
+        vec4<R> lo;
+        lo.x = radd(mn[0], rmul(qx, sL));
+        lo.y = radd(mn[1], rmul(qy, sL));
+        lo.z = radd(mn[2], rmul(qz, sL));
+        lo.w = sL;
+        t.lo[idx] = lo;
+    }
+}
+
+__device__ __forceinline__ float4 ldcg4(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ dvec4 ldcg4(const dvec4* p)
+{
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = __ldcg(q), b = __ldcg(q + 1);
+    dvec4 r;
+    r.x = a.x;
+    r.y = a.y;
+    r.z = b.x;
+    r.w = b.y;
+    return r;
+}
+
+// Bottom-up aggregation (Eq. magCenter): leaves sum their particles in
+// sorted order; the last child to arrive at a parent sums the parent's
+// children in octant order.  centre = position sum / count.
+template <typename R>
+__global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u,
+                            int64_t n, const uint32_t* __restrict__ cnt,
+                            const uint32_t* __restrict__ off, Tree<R> t, const int* flags_in,
+                            int* flags)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c0 = (int)cnt[i];
+    if (c0 == 0) return;
+    if (*flags_in & FLAG_CAPACITY) return;
+    int c = (int)off[i] + c0 - 1;
+    int4 nd = t.node[c];
+    vec4<R> p = pos[nd.x], q = u[nd.x];
+    R sx = p.x, sy = p.y, sz = p.z, ux = q.x, uy = q.y, uz = q.z;
+    for (int s = nd.x + 1; s < nd.y; ++s) {
+        p = pos[s];
+        q = u[s];
+        sx = radd(sx, p.x);
+        sy = radd(sy, p.y);
+        sz = radd(sz, p.z);
+        ux = radd(ux, q.x);
+        uy = radd(uy, q.y);
+        uz = radd(uz, q.z);
+    }
+    int guard = 0;
+    for (;;) {
+        const int cntc = nd.y - nd.x;
+        const R rn = (R)cntc;
+        vec4<R> sm, mm, cc;
+        sm.x = sx; sm.y = sy; sm.z = sz; sm.w = R(0);
+        mm.x = ux; mm.y = uy; mm.z = uz; mm.w = rn;
+        cc.x = rdiv(sx, rn); cc.y = rdiv(sy, rn); cc.z = rdiv(sz, rn); cc.w = t.lo[c].w;
+        t.sum[c] = sm;
+        t.mom[c] = mm;
+        t.cen[c] = cc;
+        const int par = t.parent[c];
+        if (par < 0) break;
+        __threadfence();
+        const int old = atomicAdd(&t.arrive[par], cntc);
+        const int4 pn = t.node[par];
+        if (old + cntc != pn.y - pn.x) break;
+        __threadfence();
+        int ch = par + 1;
+        vec4<R> a = ldcg4(&t.sum[ch]), b = ldcg4(&t.mom[ch]);
+        sx = a.x; sy = a.y; sz = a.z; ux = b.x; uy = b.y; uz = b.z;
+        ch = t.node[ch].z;
+        int kids = 1;
+        while (ch < pn.z && kids < 8) {
+            a = ldcg4(&t.sum[ch]);
+            b = ldcg4(&t.mom[ch]);
+            sx = radd(sx, a.x);
+            sy = radd(sy, a.y);
+            sz = radd(sz, a.z);
+            ux = radd(ux, b.x);
+            uy = radd(uy, b.y);
+            uz = radd(uz, b.z);
+            ch = t.node[ch].z;
+            ++kids;
+        }
+        if (ch != pn.z || ++guard > kMaxLevel + 1) {
+            atomicOr(flags, FLAG_AGGREGATE);
+            break;
+        }
+        c = par;
+        nd = pn;
+    }
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ================================================================ launchers
+std::atomic<int64_t> g_launches{0};
+
+size_t scan_tmp_words(int64_t n)
+{
+    return (size_t)((n + kScanTile - 1) / kScanTile) + 1;
+}
+
+void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s)
+{
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb > 0) k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(tmp, nb, out + n);
+    if (nb > 0) k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, out);
+    counted(nb > 0 ? 3 : 1);
+}
+
+size_t radix_tmp_words(int64_t n)
+{
+    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    const int64_t h = (int64_t)kRadixBins * nb;
+    return (size_t)(h + (h + 1) + scan_tmp_words(h));
+}
+
+void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                      uint32_t* tmp, cudaStream_t s)
+{
+    if (n <= 1) return;
+    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    const int64_t h = (int64_t)kRadixBins * nb;
+    uint32_t* hist = tmp;
+    uint32_t* offs = tmp + h;
+    uint32_t* stmp = offs + h + 1;
+    uint64_t* ka = k0;
+    uint32_t* va = v0;
+    uint64_t* kb = k1;
+    uint32_t* vb = v1;
+    for (int shift = 0; shift < 64; shift += kRadixBits) {
+        k_radix_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, n, shift, hist, nb);
+        scan_exclusive(hist, offs, h, stmp, s);
+        k_radix_scatter<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, offs, nb);
+        counted(2);
+        uint64_t* tk = ka; ka = kb; kb = tk;
+        uint32_t* tv = va; va = vb; vb = tv;
+    }
+    // eight passes: the sorted data are back in (k0, v0)
+}
+
+template <typename R>
+void morton_keys(const vec4<R>* pos, int64_t n, BBox* bb, uint64_t* keys, uint32_t* vals,
+                 int* flags, cudaStream_t s)
+{
+    k_bbox_init<<<1, 1, 0, s>>>(bb);
+    unsigned g = nblk(n, 256);
+    if (g > 152u * 8u) g = 152u * 8u;
+    k_bbox<R><<<g, 256, 0, s>>>(pos, n, bb, flags);
+    k_morton<R><<<nblk(n, 256), 256, 0, s>>>(pos, n, bb, keys, vals);
+    counted(3);
+}
+
+template <typename R>
+void gather_state(const uint32_t* perm, int64_t n, const vec4<R>* pos, const vec4<R>* vel,
+                  const vec4<R>* u, const vec4<R>* om, const uint32_t* id, vec4<R>* pos2,
+                  vec4<R>* vel2, vec4<R>* u2, vec4<R>* om2, uint32_t* id2, cudaStream_t s)
+{
+    k_gather<R><<<nblk(n, 256), 256, 0, s>>>(perm, n, pos, vel, u, om, id, pos2, vel2, u2, om2,
+                                              id2);
+    counted();
+}
+
+template <typename R>
+void build_tree(const uint64_t* skeys, int64_t n, int leaf_max, const BBox* bb, Tree<R> t,
+                uint32_t* cnt, uint32_t* off, uint32_t* scan_tmp, int* flags, cudaStream_t s)
+{
+    k_levels<<<nblk(n, 128), 128, 0, s>>>(skeys, n, leaf_max, cnt);
+    scan_exclusive(cnt, off, n, scan_tmp, s);
+    k_emit<R><<<nblk(n, 128), 128, 0, s>>>(skeys, n, cnt, off, bb, t, flags);
+    counted(2);
+}
+
+template <typename R>
+void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint32_t* cnt,
+                    const uint32_t* off, Tree<R> t, int* flags, cudaStream_t s)
+{
+    k_aggregate<R><<<nblk(n, 128), 128, 0, s>>>(pos, u, n, cnt, off, t, flags, flags);
+    counted();
+}
+
+#define FFK_INST(R)                                                                            \
+    template void morton_keys<R>(const vec4<R>*, int64_t, BBox*, uint64_t*, uint32_t*, int*,   \
+                                 cudaStream_t);                                                \
+    template void gather_state<R>(const uint32_t*, int64_t, const vec4<R>*, const vec4<R>*,     \
+                                  const vec4<R>*, const vec4<R>*, const uint32_t*, vec4<R>*,   \
+                                  vec4<R>*, vec4<R>*, vec4<R>*, uint32_t*, cudaStream_t);      \
+    template void build_tree<R>(const uint64_t*, int64_t, int, const BBox*, Tree<R>, uint32_t*, \
+                                uint32_t*, uint32_t*, int*, cudaStream_t);                     \
+    template void aggregate_tree<R>(const vec4<R>*, const vec4<R>*, int64_t, const uint32_t*,   \
+                                    const uint32_t*, Tree<R>, int*, cudaStream_t);
+FFK_INST(float)
+FFK_INST(double)
+#undef FFK_INST
+
+}  // namespace ffk

@@ -1,0 +1,330 @@
+"""Python binding of libff (include/ff.h): argument marshalling only.
+
+Every entry point has the name of its C counterpart and passes plain pointers
+and sizes.  Arrays may be numpy arrays (host memory) or torch CUDA tensors
+(device memory, the context's GPU), shaped (n, 3), C-contiguous, float32 or
+float64.  All compute runs in the CUDA library; if libff.so is missing or
+cannot be loaded this module raises instead of falling back to anything.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libff.so")
+
+FF_OK, FF_EINVAL, FF_ENOMEM, FF_ECUDA, FF_EDEVICE, FF_ENONFINITE, FF_ESTATE = range(7)
+FF_FP32, FF_FP64 = 0, 1
+FF_ALGO_BH, FF_ALGO_AP = 0, 1
+FF_DTYPE_F32, FF_DTYPE_F64 = 0, 1
+FF_HOST, FF_DEVICE = 0, 1
+
+
+class FFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+_STATUS = {0: "FF_OK", 1: "FF_EINVAL", 2: "FF_ENOMEM", 3: "FF_ECUDA", 4: "FF_EDEVICE",
+           5: "FF_ENONFINITE", 6: "FF_ESTATE"}
+
+
+class ff_params(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("precision", C.c_int32), ("n", C.c_int64),
+                ("algo", C.c_int32), ("leaf_max", C.c_int32), ("theta", C.c_double),
+                ("dt", C.c_double), ("gamma_t", C.c_double), ("gamma_r", C.c_double),
+                ("inertia", C.c_double), ("kT", C.c_double), ("rot_noise", C.c_double),
+                ("dip_scale", C.c_double), ("lj_eps", C.c_double), ("lj_sigma", C.c_double),
+                ("lj_rcut", C.c_double), ("h_ext", C.c_double * 3), ("box_lo", C.c_double * 3),
+                ("box_hi", C.c_double * 3), ("walls", C.c_int32), ("device", C.c_int32),
+                ("wall_eps", C.c_double), ("seed", C.c_uint64),
+                ("count_interactions", C.c_int32), ("reserved", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class ff_energy_t(C.Structure):
+    _fields_ = [("e_dip", C.c_double), ("e_zeeman", C.c_double), ("e_sr", C.c_double),
+                ("e_wall", C.c_double), ("e_kin_t", C.c_double), ("e_kin_r", C.c_double),
+                ("m", C.c_double * 3), ("hdip_z_mean", C.c_double)]
+
+    def as_dict(self):
+        return dict(e_dip=self.e_dip, e_zeeman=self.e_zeeman, e_sr=self.e_sr, e_wall=self.e_wall,
+                    e_kin_t=self.e_kin_t, e_kin_r=self.e_kin_r, m=np.array(self.m[:]),
+                    hdip_z_mean=self.hdip_z_mean)
+
+
+class ff_tree_info_t(C.Structure):
+    _fields_ = [("ncells", C.c_int64), ("depth", C.c_int32), ("reserved", C.c_int32),
+                ("root", C.c_double * 4), ("interactions", C.c_int64), ("accepted", C.c_int64),
+                ("pairs", C.c_int64), ("opened", C.c_int64)]
+
+
+class ff_profile_t(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("calls", C.c_int64 * 8), ("launches", C.c_int64)]
+
+
+STAGES = ("keys", "sort", "gather", "build", "aggregate", "field", "integrate", "output")
+
+_lib = None
+_vp = C.c_void_p
+_st = C.c_int
+_SIGS = {
+    "ff_params_default": (None, [C.POINTER(ff_params)]),
+    "ff_create": (_st, [C.POINTER(ff_params), C.POINTER(_vp)]),
+    "ff_destroy": (_st, [_vp]),
+    "ff_set_particles": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32]),
+    "ff_get_particles": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32]),
+    "ff_dipolar_field": (_st, [_vp, C.c_int32, C.c_double, C.c_int32, _vp, _vp, C.c_int32,
+                               C.c_int32]),
+    "ff_step": (_st, [_vp, C.c_int64]),
+    "ff_energy": (_st, [_vp, C.POINTER(ff_energy_t)]),
+    "ff_get_step": (_st, [_vp, C.POINTER(C.c_int64)]),
+    "ff_set_step": (_st, [_vp, C.c_int64]),
+    "ff_synchronize": (_st, [_vp]),
+    "ff_tree_info": (_st, [_vp, C.POINTER(ff_tree_info_t)]),
+    "ff_get_tree": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32]),
+    "ff_get_counts": (_st, [_vp, _vp, _vp, _vp]),
+    "ff_profile": (_st, [_vp, C.c_int32]),
+    "ff_profile_read": (_st, [_vp, C.POINTER(ff_profile_t)]),
+    "ff_last_error": (C.c_char_p, [_vp]),
+    "ff_status_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def lib():
+    """The loaded libff.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libff.so not found at %s; build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, status):
+    if status != FF_OK:
+        msg = lib().ff_last_error(ctx)
+        raise FFError(status, msg.decode() if msg else "")
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _arr_in(a, n):
+    """(pointer, dtype, loc, keepalive) for an (n, 3) input array."""
+    if a is None:
+        return None, None, None, None
+    if _is_torch(a):
+        import torch
+
+        if a.dtype not in (torch.float32, torch.float64) or tuple(a.shape) != (n, 3):
+            raise ValueError("expected an (n, 3) float32/float64 tensor")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        dt = FF_DTYPE_F64 if a.dtype == torch.float64 else FF_DTYPE_F32
+        if a.is_cuda:
+            return C.c_void_p(a.data_ptr()), dt, FF_DEVICE, a
+        a = a.numpy()
+    a = np.ascontiguousarray(a)
+    if a.dtype not in (np.float32, np.float64):
+        a = a.astype(np.float64)
+    if a.shape != (n, 3):
+        raise ValueError("expected shape (%d, 3), got %s" % (n, a.shape))
+    dt = FF_DTYPE_F64 if a.dtype == np.float64 else FF_DTYPE_F32
+    return C.c_void_p(a.ctypes.data), dt, FF_HOST, a
+
+
+class Context:
+    """Owns one ff_ctx handle; destroyed with the object."""
+
+    def __init__(self, handle, n, precision):
+        self.handle = handle
+        self.n = n
+        self.precision = precision
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ff_destroy(self.handle)
+            self.handle = None
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def ff_params_default(**overrides):
+    """Default parameters (ff_params_default) with keyword overrides; lists fill arrays."""
+    p = ff_params()
+    lib().ff_params_default(C.byref(p))
+    for k, v in overrides.items():
+        if k in ("h_ext", "box_lo", "box_hi"):
+            arr = getattr(p, k)
+            for i in range(3):
+                arr[i] = float(v[i])
+        elif k == "precision" and isinstance(v, str):
+            p.precision = FF_FP64 if v in ("f64", "fp64", "float64") else FF_FP32
+        elif k == "algo" and isinstance(v, str):
+            p.algo = FF_ALGO_AP if v == "ap" else FF_ALGO_BH
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def ff_create(params):
+    h = C.c_void_p()
+    st = lib().ff_create(C.byref(params), C.byref(h))
+    _check(None, st)
+    return Context(h, int(params.n), int(params.precision))
+
+
+def ff_destroy(ctx):
+    if ctx.handle:
+        _check(None, lib().ff_destroy(ctx.handle))
+        ctx.handle = None
+
+
+def ff_set_particles(ctx, pos, u, vel=None, omega=None):
+    args = [_arr_in(a, ctx.n) for a in (pos, u, vel, omega)]
+    dts = {a[1] for a in args if a[0] is not None}
+    locs = {a[2] for a in args if a[0] is not None}
+    if len(dts) != 1 or len(locs) != 1:
+        raise ValueError("all arrays must share dtype and location")
+    _check(ctx.handle, lib().ff_set_particles(ctx.handle, args[0][0], args[1][0], args[2][0],
+                                              args[3][0], dts.pop(), locs.pop()))
+
+
+def _out_pair(out, n):
+    if out is None:
+        return None, None, None
+    p, dt, loc, keep = _arr_in(out, n)
+    if loc == FF_HOST and keep is not out:
+        raise ValueError("host outputs must be C-contiguous float32/float64 numpy arrays")
+    return p, dt, loc
+
+
+def _alloc_out(n, dtype, like):
+    if like is not None and _is_torch(like) and like.is_cuda:
+        import torch
+
+        return torch.empty((n, 3), dtype=torch.float64 if dtype == np.float64 else torch.float32,
+                           device=like.device)
+    return np.empty((n, 3), dtype=dtype)
+
+
+def ff_get_particles(ctx, dtype=np.float64, device_like=None):
+    """Returns (pos, u, vel, omega) in the caller's order (numpy unless device_like is a CUDA tensor)."""
+    outs = [_alloc_out(ctx.n, dtype, device_like) for _ in range(4)]
+    ptrs = [_out_pair(o, ctx.n) for o in outs]
+    _check(ctx.handle, lib().ff_get_particles(ctx.handle, ptrs[0][0], ptrs[1][0], ptrs[2][0],
+                                              ptrs[3][0], ptrs[0][1], ptrs[0][2]))
+    return tuple(outs)
+
+
+def ff_dipolar_field(ctx, algo=FF_ALGO_BH, theta=0.5, include_sr=True, h_out=None, f_out=None,
+                     dtype=np.float64):
+    """Field and force in the caller's order; allocates host outputs when none are given."""
+    if h_out is None and f_out is None:
+        h_out = np.empty((ctx.n, 3), dtype=dtype)
+        f_out = np.empty((ctx.n, 3), dtype=dtype)
+    ph = _out_pair(h_out, ctx.n)
+    pf = _out_pair(f_out, ctx.n)
+    ref = ph if ph[0] is not None else pf
+    if ph[0] is not None and pf[0] is not None and ph[1:] != pf[1:]:
+        raise ValueError("h_out and f_out must share dtype and location")
+    _check(ctx.handle, lib().ff_dipolar_field(ctx.handle, int(algo), float(theta),
+                                              int(bool(include_sr)), ph[0], pf[0], ref[1], ref[2]))
+    return h_out, f_out
+
+
+def ff_step(ctx, nsteps=1):
+    _check(ctx.handle, lib().ff_step(ctx.handle, int(nsteps)))
+
+
+def ff_energy(ctx):
+    e = ff_energy_t()
+    _check(ctx.handle, lib().ff_energy(ctx.handle, C.byref(e)))
+    return e.as_dict()
+
+
+def ff_get_step(ctx):
+    s = C.c_int64()
+    _check(ctx.handle, lib().ff_get_step(ctx.handle, C.byref(s)))
+    return s.value
+
+
+def ff_set_step(ctx, step):
+    _check(ctx.handle, lib().ff_set_step(ctx.handle, int(step)))
+
+
+def ff_synchronize(ctx):
+    _check(ctx.handle, lib().ff_synchronize(ctx.handle))
+
+
+def ff_tree_info(ctx):
+    t = ff_tree_info_t()
+    _check(ctx.handle, lib().ff_tree_info(ctx.handle, C.byref(t)))
+    return dict(ncells=t.ncells, depth=t.depth, root=np.array(t.root[:]),
+                interactions=t.interactions, accepted=t.accepted, pairs=t.pairs, opened=t.opened)
+
+
+def ff_get_tree(ctx, dtype=np.float64):
+    """The last Barnes-Hut tree: dict of keys, order, pbegin, pend, skip, level, leaf, centre, moment."""
+    info = ff_tree_info(ctx)
+    n, nc = ctx.n, int(info["ncells"])
+    keys = np.empty(n, dtype=np.uint64)
+    order = np.empty(n, dtype=np.uint32)
+    ints = {k: np.empty(max(nc, 1), dtype=np.int32) for k in ("pbegin", "pend", "skip", "level", "leaf")}
+    cen = np.empty((max(nc, 1), 3), dtype=dtype)
+    mom = np.empty((max(nc, 1), 3), dtype=dtype)
+    p = lambda a: C.c_void_p(a.ctypes.data)
+    _check(ctx.handle, lib().ff_get_tree(ctx.handle, p(keys), p(order), p(ints["pbegin"]),
+                                         p(ints["pend"]), p(ints["skip"]), p(ints["level"]),
+                                         p(ints["leaf"]), p(cen), p(mom),
+                                         FF_DTYPE_F64 if dtype == np.float64 else FF_DTYPE_F32))
+    out = dict(keys=keys, order=order, centre=cen[:nc], moment=mom[:nc], info=info)
+    for k, v in ints.items():
+        out[k] = v[:nc]
+    return out
+
+
+def ff_get_counts(ctx):
+    """Per-particle (accepted, pairs, opened) of the last Barnes-Hut evaluation, caller order."""
+    a, b, c = (np.empty(ctx.n, dtype=np.int32) for _ in range(3))
+    p = lambda x: C.c_void_p(x.ctypes.data)
+    _check(ctx.handle, lib().ff_get_counts(ctx.handle, p(a), p(b), p(c)))
+    return a, b, c
+
+
+def ff_profile(ctx, enable=True):
+    _check(ctx.handle, lib().ff_profile(ctx.handle, int(bool(enable))))
+
+
+def ff_profile_read(ctx):
+    """Accumulated stage times (ms), timed executions per stage and kernel launches."""
+    p = ff_profile_t()
+    _check(ctx.handle, lib().ff_profile_read(ctx.handle, C.byref(p)))
+    return dict(ms={k: p.ms[i] for i, k in enumerate(STAGES)},
+                calls={k: p.calls[i] for i, k in enumerate(STAGES)}, launches=p.launches)
+
+
+def ff_last_error(ctx=None):
+    m = lib().ff_last_error(ctx.handle if ctx is not None else None)
+    return m.decode() if m else ""
+
+
+def ff_status_string(status):
+    return lib().ff_status_string(int(status)).decode()
+
+
+def exported_symbols():
+    """Names of the functions include/ff.h declares (as bound here)."""
+    return sorted(_SIGS)
