@@ -240,7 +240,10 @@ def run_ours(args):
 
     n, K, W = args.n, args.steps, args.warmup
     pos, u, side = workload(n)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library launches on it, and the CUDA events, the L2
+    # flush and every torch op of the timed region are issued on the same stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
 
     def params(**kw):
         base = dict(n=n, precision="f32", theta=args.theta, leaf_max=args.leaf_max,

@@ -224,6 +224,8 @@ __global__ void __launch_bounds__(kApThreads) k_ap(const vec4<R>* __restrict__ p
         xk.x = xk.y = xk.z = xk.w = R(0);
         uk = xk;
     }
+    // two-level sums: each tile is summed on its own, then added to the total,
+    // so rounding grows with sqrt(tile) + sqrt(n / tile) terms instead of sqrt(n)
     R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0;
     for (int tile = 0; tile < n; tile += kApThreads) {
         const int j = tile + threadIdx.x;
@@ -233,17 +235,24 @@ __global__ void __launch_bounds__(kApThreads) k_ap(const vec4<R>* __restrict__ p
         }
         __syncthreads();
         const int lim = min(kApThreads, n - tile);
+        R thx = 0, thy = 0, thz = 0, tfx = 0, tfy = 0, tfz = 0;
         for (int jj = 0; jj < lim; ++jj) {
             if (tile + jj == k) continue;
             const vec4<R> xj = sp[jj], uj = su[jj];
             const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
             const R r2 = rx * rx + ry * ry + rz * rz;
             if (r2 > R(0)) {
-                dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, uj.x, uj.y, uj.z, hx, hy, hz, fx, fy,
-                          fz);
+                dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, uj.x, uj.y, uj.z, thx, thy, thz, tfx,
+                          tfy, tfz);
                 if (fp.include_sr) lj<R>(fp, rx, ry, rz, r2, sx, sy, sz, es);
             }
         }
+        hx += thx;
+        hy += thy;
+        hz += thz;
+        fx += tfx;
+        fy += tfy;
+        fz += tfz;
         __syncthreads();
     }
     if (!active) return;

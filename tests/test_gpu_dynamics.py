@@ -71,15 +71,21 @@ def test_noise_matches_oracle(ff, ora):
 
 
 def _run_oracle(ora, e, nsteps, prec):
+    """Oracle trajectory; in single precision the state is stored rounded to FP32 after every
+    step, as the kernel stores it (the arithmetic of each step stays FP64)."""
     s = dict(pos=e["pos"].copy(), vel=np.zeros_like(e["pos"]), u=e["u"].copy(),
              om=np.zeros_like(e["pos"]), id=np.arange(e["n"], dtype=np.int64))
-    if prec == "f32":
-        for k in ("pos", "u"):
-            s[k] = s[k].astype(np.float32).astype(np.float64)
     dyn = _odyn(ora, e)
-    ora.run(s, nsteps, dyn, "bh", 0, theta=e["theta"], leaf_max=e["leaf_max"], prec=prec,
-            dip_scale=e["dip_scale"], lj_eps=e["lj_eps"], lj_sigma=e["lj_sigma"],
-            lj_rcut=e["lj_rcut"])
+    kw = dict(theta=e["theta"], leaf_max=e["leaf_max"], prec=prec, dip_scale=e["dip_scale"],
+              lj_eps=e["lj_eps"], lj_sigma=e["lj_sigma"], lj_rcut=e["lj_rcut"])
+    for k in range(nsteps):
+        if prec == "f32":
+            for key in ("pos", "vel", "u", "om"):
+                s[key] = np.ascontiguousarray(s[key].astype(np.float32).astype(np.float64))
+        ora.run(s, 1, dyn, "bh", k, **kw)
+    if prec == "f32":
+        for key in ("pos", "vel", "u", "om"):
+            s[key] = s[key].astype(np.float32).astype(np.float64)
     return s
 
 

@@ -142,19 +142,24 @@ def test_bh_theta0_equals_allpairs_on_gpu(ff):
 
 
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
-def test_bh_within_theta_bound_of_allpairs(ff, ora, theta):
+@pytest.mark.parametrize("work", ["dense4096", "phi05_n20000"])
+def test_bh_within_theta_bound_of_allpairs(ff, ora, theta, work):
+    # the workloads on which the bound was measured (tests/golden/make_theta_bound.py)
+    from paper_1212_2934_gb300 import synth
+
     bound = json.load(open(os.path.join(GOLDEN, "theta_bound.json")))["bound"][str(theta)]
-    pos, u, _ = _system(8000, 51)
-    pos32, u32 = _cast("f32", pos, u)
-    ctx = _ctx(ff, 8000, "f32")
+    e = synth.make_ensemble("dense4096") if work == "dense4096" else synth.make_ensemble("phi05", n=20000)
+    pos32, u32 = _cast("f32", e["pos"], e["u"])
+    n = pos32.shape[0]
+    ctx = _ctx(ff, n, "f32")
     ff.ff_set_particles(ctx, pos32, u32)
     h, f = ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, theta, True)
     rh, rf, _ = ora.allpairs(pos32.astype(np.float64), u32.astype(np.float64), 1.0, 1.0, 1.0, 2.5,
                              True, "f32")
     for got, ref, q in ((h, rh, "h"), (f, rf, "f")):
-        e = rel_err(got, ref)
-        assert np.sqrt((e ** 2).mean()) <= bound[q]["rms"], q
-        assert np.percentile(e, 99) <= bound[q]["p99"], q
+        e_ = rel_err(got, ref)
+        assert np.sqrt((e_ ** 2).mean()) <= bound[q]["rms"], q
+        assert np.percentile(e_, 99) <= bound[q]["p99"], q
 
 
 def test_device_buffers_match_host(ff):
@@ -215,3 +220,34 @@ def test_errors_reported(ff):
     ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, 0.5, True)
     with pytest.raises(ff.FFError):
         ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, -1.0, True)
+
+
+@pytest.mark.slow
+def test_full_size_sampled(ff, ora):
+    """The bench workload (N = 1,048,576, phi = 0.05, FP32, theta = 0.5, leaf_max = 1) in the
+    bench's launch configuration: keys bit-exact for every particle; field, force and
+    interaction counts of 3000 sampled particles against the oracle's Barnes-Hut."""
+    from paper_1212_2934_gb300 import synth
+
+    e = synth.make_ensemble("phi05")
+    n = e["n"]
+    pos32, u32 = _cast("f32", e["pos"], e["u"])
+    side = e["side"]
+    p = ff.ff_params_default(n=n, precision="f32", theta=0.5, leaf_max=1, count_interactions=1,
+                             h_ext=(0, 0, 1.0), walls=1, box_lo=(0, 0, 0), box_hi=(side, side, side))
+    ctx = ff.ff_create(p)
+    ff.ff_set_particles(ctx, pos32, u32)
+    h, f = ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, 0.5, True)
+    keys, root = ora.morton(pos32.astype(np.float64), "f32")
+    g = ff.ff_get_tree(ctx)
+    assert np.array_equal(g["keys"], np.sort(keys))
+    idx = np.random.default_rng(9).choice(n, 3000, replace=False)
+    ref = ora.bh(pos32.astype(np.float64), u32.astype(np.float64), 0.5, 1, "f32", 1.0, 1.0, 1.0,
+                 2.5, True, only=idx)
+    assert rel_err(h[idx], ref["h"][idx]).max() <= TOL32
+    assert rel_err(f[idx], ref["f"][idx]).max() <= TOL32
+    acc, pairs, opened = ff.ff_get_counts(ctx)
+    assert np.array_equal(acc[idx], ref["nacc"][idx])
+    assert np.array_equal(pairs[idx], ref["npair"][idx])
+    assert np.array_equal(opened[idx], ref["nopen"][idx])
+    assert ref["ncells"] == ff.ff_tree_info(ctx)["ncells"]
