@@ -82,7 +82,8 @@ typedef struct {
     double wall_eps;       /* wall epsilon */
     uint64_t seed;         /* Philox key of the thermal noise */
     int32_t count_interactions; /* 1: record per-particle interaction counts */
-    int32_t reserved;
+    int32_t traverse_group;  /* lanes walking the cell list together: 1,2,4,8,16,32; 0 = default.
+                                Results do not depend on it (every lane decides for itself). */
     void *stream;          /* cudaStream_t to run on; NULL: the context creates one */
 } ff_params;
 

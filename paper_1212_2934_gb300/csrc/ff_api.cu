@@ -214,6 +214,14 @@ ffk::DynParams<R> dyn_params(const ff_ctx* c)
 template <typename R>
 ffk::vec4<R>* V(void* p) { return static_cast<ffk::vec4<R>*>(p); }
 
+// Lanes that walk the cell list together (see k_field.cu).
+constexpr int kDefaultGroup = 32;
+int traverse_group(const ff_ctx* c)
+{
+    const int g = c->p.traverse_group;
+    return (g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32) ? g : kDefaultGroup;
+}
+
 enum Stage { S_KEYS = 0, S_SORT, S_GATHER, S_BUILD, S_AGG, S_FIELD, S_STEP, S_OUT };
 
 cudaEvent_t take_event(ff_ctx* c)
@@ -297,7 +305,8 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr)
         StageTimer st(c, S_FIELD);
         ffk::bh_field<R>(V<R>(b.pos), V<R>(b.u), n, t, field_params<R>(c, theta, include_sr),
                          V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr),
-                         c->p.count_interactions ? c->counts : nullptr, c->dflags, s);
+                         c->p.count_interactions ? c->counts : nullptr, c->dflags,
+                         traverse_group(c), s);
     }
     FF_LAUNCHED(c);
     c->tree_valid = true;
@@ -454,6 +463,10 @@ const char* check_params(const ff_params* p)
     if (!(p->gamma_t >= 0.0) || !(p->gamma_r >= 0.0)) return "friction must be >= 0";
     if (!(p->kT >= 0.0) || !(p->rot_noise >= 0.0)) return "kT and rot_noise must be >= 0";
     if (!std::isfinite(p->dip_scale)) return "dip_scale must be finite";
+    if (p->traverse_group != 0 && p->traverse_group != 1 && p->traverse_group != 2 &&
+        p->traverse_group != 4 && p->traverse_group != 8 && p->traverse_group != 16 &&
+        p->traverse_group != 32)
+        return "traverse_group must be 0, 1, 2, 4, 8, 16 or 32";
     if (p->lj_eps != 0.0 && (!(p->lj_sigma > 0.0) || !(p->lj_rcut > 0.0)))
         return "LJ needs sigma > 0 and rcut > 0";
     if (p->walls) {

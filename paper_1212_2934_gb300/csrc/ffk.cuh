@@ -118,10 +118,12 @@ template <typename R>
 void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint32_t* cnt,
                     const uint32_t* off, Tree<R> t, int* flags, cudaStream_t s);
 
-// Barnes-Hut traversal.  h/f (and esr, counts if non-null) in sorted order.
+// Barnes-Hut traversal.  h/f (and esr, counts if non-null) in sorted order;
+// group = lanes that walk the cell list together (1, 2, 4, 8, 16 or 32).
 template <typename R>
 void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
-              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, cudaStream_t s);
+              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int group,
+              cudaStream_t s);
 
 // All-pairs sum (Sec. 3.1, Algorithm 1).
 template <typename R>

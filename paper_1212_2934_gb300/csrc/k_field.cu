@@ -2,14 +2,16 @@
 // kernel 5 of the paper's scheme, redesigned) and the all-pairs sum
 // (Sec. 3.1, Algorithm 1).
 //
-// Traversal: one warp serves 32 consecutive particles of the Morton order.
-// Each lane keeps its own position in the depth-first cell list (`nxt`);
-// the warp visits cell i = min over lanes of nxt, and only the lanes whose
-// nxt == i act on it.  A lane therefore makes exactly the decisions of its
-// own per-particle traversal, in the same order (children in octant order),
-// while the cell record is fetched once per warp (one broadcast load).
-// Skip pointers replace a stack.  Every lane's nxt strictly increases, so
-// the loop ends after at most ncells visits.
+// Traversal: a warp serves 32 consecutive particles of the Morton order,
+// split into groups of G lanes.  Each lane keeps its own position in the
+// depth-first cell list (`nxt`); a group visits cell i = min over its lanes
+// of nxt, and only the lanes whose nxt == i act on it.  A lane therefore
+// makes exactly the decisions of its own per-particle traversal, in the
+// same order (children in octant order), while the cell record is fetched
+// once per group (a broadcast load).  Large groups share more loads; small
+// groups waste fewer lane slots on cells only some lanes need.  Skip
+// pointers replace a stack.  Every lane's nxt strictly increases, so the
+// loop ends after at most ncells visits per group.
 #include "ffk.cuh"
 
 namespace ffk {
@@ -110,7 +112,17 @@ __device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& 
     return true;
 }
 
-template <typename R, bool COUNT>
+// Minimum of v over each aligned group of G lanes.
+template <int G>
+__device__ __forceinline__ unsigned group_min(unsigned v)
+{
+    if (G == 32) return __reduce_min_sync(kFull, v);
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) v = min(v, __shfl_xor_sync(kFull, v, o, G));
+    return v;
+}
+
+template <typename R, bool COUNT, int G>
 __global__ void __launch_bounds__(128) k_bh(const vec4<R>* __restrict__ pos,
                                             const vec4<R>* __restrict__ u, int n, Tree<R> t,
                                             FieldParams<R> fp, vec4<R>* __restrict__ h,
@@ -135,8 +147,12 @@ __global__ void __launch_bounds__(128) k_bh(const vec4<R>* __restrict__ pos,
     const unsigned ncells = (unsigned)*t.ncells;
     unsigned nxt = active ? 0u : 0xffffffffu;
     for (;;) {
-        const unsigned i = __reduce_min_sync(kFull, nxt);
-        if (i >= ncells) break;
+        const unsigned i = group_min<G>(nxt);
+        if (G == 32) {
+            if (i >= ncells) break;
+        } else if (!__any_sync(kFull, i < ncells)) {
+            break;
+        }
         if (nxt == i) {
             const int4 nd = t.node[i];
             const bool inside = nd.x <= k && k < nd.y;
@@ -272,15 +288,30 @@ __global__ void __launch_bounds__(kApThreads) k_ap(const vec4<R>* __restrict__ p
 
 }  // namespace
 
-template <typename R>
-void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
-              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, cudaStream_t s)
+template <typename R, bool COUNT>
+void bh_launch(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
+               vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int group,
+               cudaStream_t s)
 {
     const unsigned g = (unsigned)((n + 127) / 128);
+    switch (group) {
+        case 1: k_bh<R, COUNT, 1><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
+        case 2: k_bh<R, COUNT, 2><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
+        case 4: k_bh<R, COUNT, 4><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
+        case 8: k_bh<R, COUNT, 8><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
+        case 16: k_bh<R, COUNT, 16><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
+        default: k_bh<R, COUNT, 32><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
+    }
+}
+
+template <typename R>
+void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
+              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int group, cudaStream_t s)
+{
     if (counts)
-        k_bh<R, true><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags);
+        bh_launch<R, true>(pos, u, n, t, fp, h, f, esr, counts, flags, group, s);
     else
-        k_bh<R, false><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags);
+        bh_launch<R, false>(pos, u, n, t, fp, h, f, esr, counts, flags, group, s);
     counted();
 }
 
@@ -294,10 +325,10 @@ void ap_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, FieldParams<R> fp
 }
 
 template void bh_field<float>(const float4*, const float4*, int64_t, Tree<float>,
-                              FieldParams<float>, float4*, float4*, float*, int4*, int*,
+                              FieldParams<float>, float4*, float4*, float*, int4*, int*, int,
                               cudaStream_t);
 template void bh_field<double>(const dvec4*, const dvec4*, int64_t, Tree<double>,
-                               FieldParams<double>, dvec4*, dvec4*, double*, int4*, int*,
+                               FieldParams<double>, dvec4*, dvec4*, double*, int4*, int*, int,
                                cudaStream_t);
 template void ap_field<float>(const float4*, const float4*, int64_t, FieldParams<float>, float4*,
                               float4*, float*, cudaStream_t);

@@ -40,7 +40,7 @@ class ff_params(C.Structure):
                 ("lj_rcut", C.c_double), ("h_ext", C.c_double * 3), ("box_lo", C.c_double * 3),
                 ("box_hi", C.c_double * 3), ("walls", C.c_int32), ("device", C.c_int32),
                 ("wall_eps", C.c_double), ("seed", C.c_uint64),
-                ("count_interactions", C.c_int32), ("reserved", C.c_int32),
+                ("count_interactions", C.c_int32), ("traverse_group", C.c_int32),
                 ("stream", C.c_void_p)]
 
 

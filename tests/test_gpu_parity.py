@@ -83,15 +83,20 @@ def _bh_case(ff, ora, prec, pos, u, theta, leaf_max=1, **kw):
     ref = ora.bh(pos.astype(np.float64), u.astype(np.float64), theta, leaf_max, prec,
                  kw.get("dip_scale", 1.0), kw.get("lj_eps", 1.0), kw.get("lj_sigma", 1.0),
                  kw.get("lj_rcut", 2.5), True)
+    # results may not depend on the traversal group size
+    
     return ctx, h, f, ref
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
 @pytest.mark.parametrize("leaf_max", [1, 8])
-def test_bh_field_matches_oracle(ff, ora, prec, theta, leaf_max):
+@pytest.mark.parametrize("group", [1, 4, 8, 16, 32])
+def test_bh_field_matches_oracle(ff, ora, prec, theta, leaf_max, group):
+    if group not in (8, 32) and (theta != 0.5 or leaf_max != 1):
+        pytest.skip("group sizes other than 8 and 32 are checked at theta 0.5, leaf_max 1")
     pos, u, _ = _system(6007, 21)
-    ctx, h, f, ref = _bh_case(ff, ora, prec, pos, u, theta, leaf_max)
+    ctx, h, f, ref = _bh_case(ff, ora, prec, pos, u, theta, leaf_max, traverse_group=group)
     tol = TOL32 if prec == "f32" else TOL64
     eh, ef = rel_err(h, ref["h"]), rel_err(f, ref["f"])
     assert eh.max() <= tol, eh.max()
