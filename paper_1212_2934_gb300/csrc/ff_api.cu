@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -35,6 +36,7 @@ struct ff_ctx {
     int64_t n = 0;
     bool fp64 = false;
     size_t rec = 16;  // bytes per record
+    size_t cell_bytes = 32;  // bytes per Cell record
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int64_t step = 0;
@@ -52,8 +54,7 @@ struct ff_ctx {
     uint32_t* scan_tmp = nullptr;
     ffk::BBox* bbox = nullptr;
 
-    int4* node = nullptr;
-    void* cen = nullptr;
+    void* cell = nullptr;  // Cell<R> records: topology + centre
     void* mom = nullptr;
     void* lo = nullptr;
     void* sum = nullptr;
@@ -147,8 +148,7 @@ template <typename R>
 ffk::Tree<R> tree_of(ff_ctx* c)
 {
     ffk::Tree<R> t;
-    t.node = c->node;
-    t.cen = static_cast<ffk::vec4<R>*>(c->cen);
+    t.cell = static_cast<ffk::Cell<R>*>(c->cell);
     t.mom = static_cast<ffk::vec4<R>*>(c->mom);
     t.lo = static_cast<ffk::vec4<R>*>(c->lo);
     t.sum = static_cast<ffk::vec4<R>*>(c->sum);
@@ -371,7 +371,7 @@ ff_status sync_and_check(ff_ctx* c)
 void free_all(ff_ctx* c)
 {
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->radix_tmp, c->cnt, c->off,
-                    c->scan_tmp, c->bbox, c->node, c->cen, c->mom, c->lo, c->sum, c->parent,
+                    c->scan_tmp, c->bbox, c->cell, c->mom, c->lo, c->sum, c->parent,
                     c->arrive, c->h, c->f, c->esr, c->counts, c->partials, c->obs, c->obs_step,
                     c->dflags, c->staging};
     for (void* q : ptrs)
@@ -424,8 +424,7 @@ ff_status alloc_all(ff_ctx* c)
     // Every particle starts at most 22 cells (levels 0..21), so 22 n + 1 cells
     // always suffice.
     c->cap = 22 * n + 1;
-    A(&c->node, sizeof(int4) * c->cap);
-    A(&c->cen, rec * c->cap);
+    A(&c->cell, c->cell_bytes * c->cap);
     A(&c->mom, rec * c->cap);
     A(&c->lo, rec * c->cap);
     A(&c->sum, rec * c->cap);
@@ -639,6 +638,7 @@ ff_status ff_create(const ff_params* p, ff_ctx** out)
     c->n = p->n;
     c->fp64 = p->precision == FF_FP64;
     c->rec = c->fp64 ? sizeof(ffk::dvec4) : sizeof(float4);
+    c->cell_bytes = c->fp64 ? sizeof(ffk::Cell<double>) : sizeof(ffk::Cell<float>);
     if (p->stream) {
         c->stream = static_cast<cudaStream_t>(p->stream);
     } else {
@@ -770,7 +770,7 @@ ff_status ff_tree_info(ff_ctx* c, ff_tree_info_t* out)
     FF_CUDA(c, cudaMemcpy(&nc, c->off + c->n, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     out->ncells = nc;
     std::vector<int4> nodes(nc);
-    if (nc) FF_CUDA(c, cudaMemcpy(nodes.data(), c->node, sizeof(int4) * nc, cudaMemcpyDeviceToHost));
+    if (nc) FF_CUDA(c, cudaMemcpy2D(nodes.data(), sizeof(int4), c->cell, c->cell_bytes, sizeof(int4), nc, cudaMemcpyDeviceToHost));
     int depth = 0;
     for (const int4& v : nodes) depth = std::max(depth, v.w & 0xff);
     out->depth = depth;
@@ -837,7 +837,7 @@ ff_status ff_get_tree(ff_ctx* c, uint64_t* keys, uint32_t* order, int32_t* pbegi
     if (order) FF_CUDA(c, cudaMemcpy(order, c->st[c->cur].id, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
     if (pbegin || pend || skip || level || leaf) {
         std::vector<int4> nodes(nc);
-        if (nc) FF_CUDA(c, cudaMemcpy(nodes.data(), c->node, sizeof(int4) * nc, cudaMemcpyDeviceToHost));
+        if (nc) FF_CUDA(c, cudaMemcpy2D(nodes.data(), sizeof(int4), c->cell, c->cell_bytes, sizeof(int4), nc, cudaMemcpyDeviceToHost));
         for (uint32_t i = 0; i < nc; ++i) {
             if (pbegin) pbegin[i] = nodes[i].x;
             if (pend) pend[i] = nodes[i].y;
@@ -846,12 +846,14 @@ ff_status ff_get_tree(ff_ctx* c, uint64_t* keys, uint32_t* order, int32_t* pbegi
             if (leaf) leaf[i] = (nodes[i].w >> 8) & 1;
         }
     }
-    void* srcs[2] = {c->cen, c->mom};
+    // the centre is the second half of each Cell record; the moment sum is its own array
+    void* srcs[2] = {static_cast<char*>(c->cell) + (c->fp64 ? offsetof(ffk::Cell<double>, cen) : offsetof(ffk::Cell<float>, cen)), c->mom};
+    const size_t pitch[2] = {c->cell_bytes, c->rec};
     void* dsts[2] = {centre, moment};
     for (int q = 0; q < 2; ++q) {
         if (!dsts[q] || nc == 0) continue;
         std::vector<unsigned char> raw((size_t)nc * c->rec);
-        FF_CUDA(c, cudaMemcpy(raw.data(), srcs[q], raw.size(), cudaMemcpyDeviceToHost));
+        FF_CUDA(c, cudaMemcpy2D(raw.data(), c->rec, srcs[q], pitch[q], c->rec, nc, cudaMemcpyDeviceToHost));
         for (uint32_t i = 0; i < nc; ++i) {
             double v[3];
             if (c->fp64) {

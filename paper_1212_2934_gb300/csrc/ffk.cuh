@@ -74,11 +74,18 @@ struct DynParams {
     uint32_t ctr0, ctr1;  // step counter
 };
 
+// What the traversal reads for every visited cell, in one record (32 bytes
+// in single precision): topology and the pseudo-particle position.
+template <typename R>
+struct alignas(32) Cell {
+    int4 node;     // pbegin, pend, skip, level | leaf << 8
+    vec4<R> cen;   // geometric centre xyz, cube side
+};
+
 // Tree arrays (device pointers), cells in depth-first preorder.
 template <typename R>
 struct Tree {
-    int4* node;          // pbegin, pend, skip, level | leaf << 8
-    vec4<R>* cen;        // geometric centre xyz, cube side
+    Cell<R>* cell;       // topology + centre
     vec4<R>* mom;        // moment sum xyz, particle count
     vec4<R>* lo;         // lower cube corner xyz, cube side
     vec4<R>* sum;        // position sum xyz (aggregation scratch)

@@ -153,12 +153,15 @@ __global__ void __launch_bounds__(128) k_bh(const vec4<R>* __restrict__ pos,
         } else if (!__any_sync(kFull, i < ncells)) {
             break;
         }
-        if (nxt == i) {
-            const int4 nd = t.node[i];
+        // a finished group keeps looping with i >= ncells while other groups of
+        // the warp still work; its lanes must not touch cell i then
+        if (nxt == i && i < ncells) {
+            const Cell<R> cl = t.cell[i];
+            const int4 nd = cl.node;
             const bool inside = nd.x <= k && k < nd.y;
             const bool leaf = (nd.w >> 8) != 0;
             const bool single = leaf && (nd.y - nd.x == 1);
-            const vec4<R> c = t.cen[i];
+            const vec4<R> c = cl.cen;
             const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i);
             if (acc || (single && !inside)) {
                 // the cell's pseudo-particle; for a one-particle leaf it is the

@@ -205,17 +205,28 @@ __global__ void __launch_bounds__(kStepThreads) k_observables(
     block_sum_obs(v, partials + (int64_t)blockIdx.x * kObs);
 }
 
-// Deterministic final sum: one thread per quantity, blocks in order.
-__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks, double inv_n,
-                                  double inertia_half, double* __restrict__ out)
+// Deterministic final sum: one block per quantity; thread t adds partials
+// t, t + 256, ... in order, then a fixed-shape tree combines the threads.
+__global__ void __launch_bounds__(kStepThreads) k_reduce_partials(
+    const double* __restrict__ partials, int nblocks, double inv_n, double inertia_half,
+    double* __restrict__ out)
 {
-    const int q = threadIdx.x;
-    if (q >= kObs) return;
+    __shared__ double sh[kStepThreads];
+    const int q = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * kObs + q];
-    if (q == 5) s *= inertia_half;
-    if (q >= 6) s *= inv_n;
-    out[q] = s;
+    for (int b = threadIdx.x; b < nblocks; b += kStepThreads) s += partials[(int64_t)b * kObs + q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kStepThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double v = sh[0];
+        if (q == 5) v *= inertia_half;
+        if (q >= 6) v *= inv_n;
+        out[q] = v;
+    }
 }
 
 template <typename R, typename I>
@@ -278,8 +289,9 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 int integrate_blocks(int64_t n)
 {
+    // one particle per thread up to 2^16 blocks (16.7 M particles), grid-stride beyond
     int64_t b = (n + kStepThreads - 1) / kStepThreads;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > 65536) b = 65536;
     if (b < 1) b = 1;
     return (int)b;
 }
@@ -313,7 +325,7 @@ void observables(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R
 void reduce_partials(const double* partials, int nblocks, double inv_n, double inertia_half,
                      double* out, cudaStream_t s)
 {
-    k_reduce_partials<<<1, 32, 0, s>>>(partials, nblocks, inv_n, inertia_half, out);
+    k_reduce_partials<<<kObs, kStepThreads, 0, s>>>(partials, nblocks, inv_n, inertia_half, out);
     counted();
 }
 

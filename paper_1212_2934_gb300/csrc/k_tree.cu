@@ -447,7 +447,7 @@ __global__ void k_emit(const uint64_t* __restrict__ k, int64_t n, const uint32_t
         }
         const int skip = (int)off[pe];
         const int leaf = (L == d) ? 1 : 0;
-        t.node[idx] = make_int4((int)i, (int)pe, skip, L | (leaf << 8));
+        t.cell[idx].node = make_int4((int)i, (int)pe, skip, L | (leaf << 8));
         int parent;
         if (L == 0) {
             parent = -1;
@@ -501,7 +501,7 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
     if (c0 == 0) return;
     if (*flags_in & FLAG_CAPACITY) return;
     int c = (int)off[i] + c0 - 1;
-    int4 nd = t.node[c];
+    int4 nd = t.cell[c].node;
     vec4<R> p = pos[nd.x], q = u[nd.x];
     R sx = p.x, sy = p.y, sz = p.z, ux = q.x, uy = q.y, uz = q.z;
     for (int s = nd.x + 1; s < nd.y; ++s) {
@@ -524,18 +524,18 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
         cc.x = rdiv(sx, rn); cc.y = rdiv(sy, rn); cc.z = rdiv(sz, rn); cc.w = t.lo[c].w;
         t.sum[c] = sm;
         t.mom[c] = mm;
-        t.cen[c] = cc;
+        t.cell[c].cen = cc;
         const int par = t.parent[c];
         if (par < 0) break;
         __threadfence();
         const int old = atomicAdd(&t.arrive[par], cntc);
-        const int4 pn = t.node[par];
+        const int4 pn = t.cell[par].node;
         if (old + cntc != pn.y - pn.x) break;
         __threadfence();
         int ch = par + 1;
         vec4<R> a = ldcg4(&t.sum[ch]), b = ldcg4(&t.mom[ch]);
         sx = a.x; sy = a.y; sz = a.z; ux = b.x; uy = b.y; uz = b.z;
-        ch = t.node[ch].z;
+        ch = t.cell[ch].node.z;
         int kids = 1;
         while (ch < pn.z && kids < 8) {
             a = ldcg4(&t.sum[ch]);
@@ -546,7 +546,7 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
             ux = radd(ux, b.x);
             uy = radd(uy, b.y);
             uz = radd(uz, b.z);
-            ch = t.node[ch].z;
+            ch = t.cell[ch].node.z;
             ++kids;
         }
         if (ch != pn.z || ++guard > kMaxLevel + 1) {
