@@ -215,7 +215,7 @@ template <typename R>
 ffk::vec4<R>* V(void* p) { return static_cast<ffk::vec4<R>*>(p); }
 
 // Lanes that walk the cell list together (see k_field.cu).
-constexpr int kDefaultGroup = 32;
+constexpr int kDefaultGroup = 1;
 int traverse_group(const ff_ctx* c)
 {
     const int g = c->p.traverse_group;
