@@ -220,11 +220,43 @@ ff_status ff_profile(ff_ctx *ctx, int32_t enable);
 ff_status ff_profile_read(ff_ctx *ctx, ff_profile_t *out);
 
 /* Message for the last failure on this context (never NULL).  With
- * ctx = NULL: why the last ff_create on the calling thread failed. */
+ * ctx = NULL: why the last ff_create or ff_morton_order_noalloc on the
+ * calling thread failed. */
 const char *ff_last_error(const ff_ctx *ctx);
 
 /* Name of a status code. */
 const char *ff_status_string(ff_status s);
+
+/*
+ * Allocation-free Morton ordering, for callers that cannot allocate device
+ * memory: code running while a CUDA stream is being captured (where
+ * cudaMalloc is not allowed), applications whose device memory belongs to
+ * their own pool, and loops that cannot stall on an allocation.  The paper
+ * has no counterpart; it is the key-sort stage of the Barnes-Hut path
+ * packaged without allocation.
+ *
+ * pos: device pointer, n x 3 float, caller's order.  Writes keys_out[n]
+ * (device, uint64: the sorted 63-bit Morton keys of the root cube of these
+ * positions) and order_out[n] (device, uint32: the input index of each sorted
+ * position; ties keep input order), exactly as ff_get_tree reports them for a
+ * single-precision context.  stream: a cudaStream_t, NULL for the default
+ * stream.  Waits for the stream before returning.
+ *
+ * Nothing is allocated: besides the caller's buffers the work uses one fixed
+ * scratch array inside the library, sized for n <= FF_NOALLOC_MAX_N (about
+ * 3.7 MB, held on every GPU that loads the library until the process exits).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call shares the array: calls
+ * whose GPU work overlaps (other streams, other host threads on the same
+ * device) race and must not be issued.
+ *
+ * FF_EINVAL: a NULL pointer, or n outside 1 .. FF_NOALLOC_MAX_N.
+ * FF_ENONFINITE: a position is NaN or infinite.  FF_ECUDA: a CUDA call
+ * failed.  The reason is given by ff_last_error(NULL).
+ */
+#define FF_NOALLOC_MAX_N 131072
+ff_status ff_morton_order_noalloc(const float *pos, int64_t n, uint64_t *keys_out,
+                                  uint32_t *order_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -102,6 +102,15 @@ ff_status create_fail(ff_status s, const char* fmt, ...)
     return s;
 }
 
+}  // namespace
+
+void ffk::set_thread_error(const char* msg)
+{
+    std::snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+}
+
+namespace {
+
 ff_status fail(ff_ctx* c, ff_status s, const char* fmt, ...)
 {
     if (c) {

@@ -1,0 +1,137 @@
+// Allocation-free Morton ordering (declared in include/ff.h).
+//
+// Some callers may not allocate device memory at all: code that runs while a
+// stream is being captured (cudaMalloc is not allowed there), applications
+// whose memory is owned by their own pool or allocator, and latency-bound
+// loops that cannot afford an allocation on the way.  For them this entry
+// point computes the root cube, the 63-bit Morton keys and the stable key
+// sort of up to kNoAllocMaxN particles using only the caller's input and
+// output buffers plus one fixed scratch array that lives in this file.
+//
+// The scratch array is a static device variable: every GPU that loads the
+// library keeps it (about 3.7 MB) until the process exits.  Its name in host
+// code is only a host-side stand-in, so the device address is looked up with
+// cudaGetSymbolAddress, once per device, on the first call made with that
+// device current.  All calls share the array and it keeps the contents of the
+// last call; calls whose GPU work overlaps (different streams, or several host
+// threads on one device) race on it.
+#include <cstddef>
+#include <cstdio>
+#include <mutex>
+
+#include "ff.h"
+#include "ffk.cuh"
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 131072;
+constexpr int kMaxDevices = 64;
+
+// Scratch layout (bytes, each part 256-byte aligned): position records,
+// second key/value buffers of the radix sort, radix histograms and scan
+// space, root-cube extrema, error flags.
+constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kRecOff = 0;
+constexpr size_t kRecBytes = align256(sizeof(float4) * kNoAllocMaxN);
+constexpr size_t kKeyOff = kRecOff + kRecBytes;
+constexpr size_t kKeyBytes = align256(sizeof(uint64_t) * kNoAllocMaxN);
+constexpr size_t kValOff = kKeyOff + kKeyBytes;
+constexpr size_t kValBytes = align256(sizeof(uint32_t) * kNoAllocMaxN);
+constexpr size_t kRadixOff = kValOff + kValBytes;
+// radix scratch: 256 x tiles histogram, 256 x tiles + 1 offsets, scan block sums
+constexpr int64_t kTiles = (kNoAllocMaxN + ffk::kSortTile - 1) / ffk::kSortTile;
+constexpr int64_t kHist = int64_t(ffk::kRadixBins) * kTiles;
+constexpr size_t kRadixWords = size_t(kHist + kHist + 1 + kHist / 2048 + 2);
+constexpr size_t kRadixBytes = align256(sizeof(uint32_t) * kRadixWords);
+constexpr size_t kBoxOff = kRadixOff + kRadixBytes;
+constexpr size_t kBoxBytes = align256(sizeof(ffk::BBox));
+constexpr size_t kFlagOff = kBoxOff + kBoxBytes;
+constexpr size_t kScratchBytes = kFlagOff + 256;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char ff_noalloc_scratch[kScratchBytes];
+
+namespace {
+
+static_assert(kNoAllocMaxN == FF_NOALLOC_MAX_N, "scratch sized for FF_NOALLOC_MAX_N");
+
+std::mutex g_mutex;
+unsigned char* g_base[kMaxDevices] = {nullptr};
+
+// The reason is reported through ff_last_error(NULL) on the calling thread.
+ff_status noalloc_fail(ff_status s, const char* msg, cudaError_t e = cudaSuccess)
+{
+    char buf[256];
+    if (e != cudaSuccess)
+        std::snprintf(buf, sizeof(buf), "ff_morton_order_noalloc: %s: %s", msg, cudaGetErrorString(e));
+    else
+        std::snprintf(buf, sizeof(buf), "ff_morton_order_noalloc: %s", msg);
+    ffk::set_thread_error(buf);
+    return s;
+}
+
+// Device address of the scratch array on the current device (set up once per
+// device with that device current).
+ff_status scratch_base(unsigned char** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(FF_ECUDA, "cudaGetDevice", e);
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(FF_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_base[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, ff_noalloc_scratch);
+        if (e != cudaSuccess) return noalloc_fail(FF_ECUDA, "cudaGetSymbolAddress", e);
+        g_base[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_base[dev];
+    return FF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ff_status ff_morton_order_noalloc(const float* pos, int64_t n, uint64_t* keys_out,
+                                  uint32_t* order_out, void* stream)
+{
+    if (!pos || !keys_out || !order_out) return noalloc_fail(FF_EINVAL, "pos, keys_out and order_out are required");
+    if (n < 1 || n > kNoAllocMaxN) {
+        char msg[160];
+        std::snprintf(msg, sizeof(msg), "n = %lld is outside 1 .. %lld, the size of the fixed scratch",
+                      (long long)n, (long long)kNoAllocMaxN);
+        return noalloc_fail(FF_EINVAL, msg);
+    }
+    if (ffk::radix_tmp_words(n) > kRadixWords) return noalloc_fail(FF_EINVAL, "radix scratch too small");
+    unsigned char* base = nullptr;
+    ff_status st = scratch_base(&base);
+    if (st != FF_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float4* rec = reinterpret_cast<float4*>(base + kRecOff);
+    uint64_t* k1 = reinterpret_cast<uint64_t*>(base + kKeyOff);
+    uint32_t* v1 = reinterpret_cast<uint32_t*>(base + kValOff);
+    uint32_t* rtmp = reinterpret_cast<uint32_t*>(base + kRadixOff);
+    ffk::BBox* bb = reinterpret_cast<ffk::BBox*>(base + kBoxOff);
+    int* flags = reinterpret_cast<int*>(base + kFlagOff);
+    // the flag word must start at zero; everything else is rewritten in full
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int), s);
+    if (e != cudaSuccess) return noalloc_fail(FF_ECUDA, "cudaMemsetAsync", e);
+    ffk::load3<float, float>(pos, n, rec, s);
+    // keys and values are built directly in the caller's outputs, which the
+    // eight-pass sort leaves holding the sorted data
+    ffk::morton_keys<float>(rec, n, bb, keys_out, order_out, flags, s);
+    ffk::radix_sort_pairs(keys_out, order_out, k1, v1, n, rtmp, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(FF_ECUDA, "kernel launch", e);
+    int hflag = 0;
+    e = cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return noalloc_fail(FF_ECUDA, "cudaMemcpyAsync", e);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return noalloc_fail(FF_ECUDA, "cudaStreamSynchronize", e);
+    if (hflag & ffk::FLAG_NONFINITE) return noalloc_fail(FF_ENONFINITE, "a particle position is NaN or infinite");
+    return FF_OK;
+}
+
+}  // extern "C"

@@ -9,6 +9,9 @@
 
 namespace ffk {
 
+// Sets the message returned by ff_last_error(NULL) on the calling thread.
+void set_thread_error(const char* msg);
+
 // Kernels launched by this library (all contexts); read as differences.
 extern std::atomic<int64_t> g_launches;
 inline void counted(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }

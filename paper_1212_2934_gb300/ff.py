@@ -88,6 +88,7 @@ _SIGS = {
     "ff_get_counts": (_st, [_vp, _vp, _vp, _vp]),
     "ff_profile": (_st, [_vp, C.c_int32]),
     "ff_profile_read": (_st, [_vp, C.POINTER(ff_profile_t)]),
+    "ff_morton_order_noalloc": (_st, [_vp, C.c_int64, _vp, _vp, _vp]),
     "ff_last_error": (C.c_char_p, [_vp]),
     "ff_status_string": (C.c_char_p, [C.c_int]),
 }
@@ -314,6 +315,20 @@ def ff_profile_read(ctx):
     _check(ctx.handle, lib().ff_profile_read(ctx.handle, C.byref(p)))
     return dict(ms={k: p.ms[i] for i, k in enumerate(STAGES)},
                 calls={k: p.calls[i] for i, k in enumerate(STAGES)}, launches=p.launches)
+
+
+FF_NOALLOC_MAX_N = 131072
+
+
+def ff_morton_order_noalloc(pos, keys_out, order_out, stream=None):
+    """Allocation-free Morton ordering of an (n, 3) float32 CUDA tensor into uint64 keys and
+    int32 order tensors (device); see include/ff.h.  stream: a torch CUDA stream or None."""
+    n = int(pos.shape[0])
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(None, lib().ff_morton_order_noalloc(C.c_void_p(pos.data_ptr()), n,
+                                               C.c_void_p(keys_out.data_ptr()),
+                                               C.c_void_p(order_out.data_ptr()), sp))
+    return keys_out, order_out
 
 
 def ff_last_error(ctx=None):
