@@ -40,7 +40,7 @@ SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0  # GB300 unit counts and maximum 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1048576)
@@ -85,9 +85,10 @@ def config_dict(args, side):
 
 
 class Clocks:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons; only samples whose timestamps fall
+    inside the marked timed window are reported."""
 
-    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+    FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "power.draw",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
 
@@ -95,20 +96,34 @@ class Clocks:
         self.dev = device_index
         self.proc = None
         self.out = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.out, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # wait (bounded) for the first sample so the window is covered from its start
+        for _ in range(50):
+            time.sleep(0.1)
+            if os.path.getsize(self.out.name) > 0:
+                break
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.25)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -118,24 +133,36 @@ class Clocks:
         self.out.seek(0)
         rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
         os.unlink(self.out.name)
-        sm, mx, reasons = [], [], set()
+        import datetime
+
+        sm, mx, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             r = [x.strip() for x in r]
             if len(r) < len(self.FIELDS):
                 continue
             try:
-                sm.append(float(r[0]))
-                mx.append(float(r[1]))
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                c, m = float(r[1]), float(r[2])
             except ValueError:
                 continue
+            # a sample describes the interval that ends at its timestamp
+            if self.t0 is not None and not (self.t0 - 0.05 <= ts <= self.t1 + 0.1):
+                continue
+            sm.append(c)
+            mx.append(m)
+            try:
+                power.append(float(r[3]))
+            except ValueError:
+                pass
             for name, val in zip(names, r[4:8]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
         if not sm:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": float(np.median(power)) if power else None}
 
 
 def traffic_for(kernel_src):
@@ -269,22 +296,24 @@ def run_ours(args):
     # ---- main leg: FP32 Barnes-Hut steps (interaction counting off while timed)
     ctx = ff.ff_create(params(count_interactions=0))
     ff.ff_set_particles(ctx, pos_d, u_d)
+    clocks = Clocks(dev)
+    clocks.start()
     for _ in range(W):
         ff.ff_step(ctx, 1)
         flush.zero_()
     ff.ff_synchronize(ctx)
     barrier()
     ff.ff_profile(ctx, True)
-    clocks = Clocks(dev)
-    clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(K)]
+    clocks.mark_start()
     for k in range(K):
         evs[k][0].record(stream)
         ff.ff_step(ctx, 1)
         evs[k][1].record(stream)
         flush.zero_()
     ff.ff_synchronize(ctx)
+    clocks.mark_end()
     barrier()
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
@@ -349,7 +378,11 @@ def run_ours(args):
         extras = {
             "bh_fp32": {"particle_steps_per_s": value / world, "ms_per_step": max_ms / K,
                         "interactions_per_s": info["interactions"] / (field_ms / 1e3),
-                        "interactions_per_particle": info["interactions"] / n},
+                        "interactions_per_particle": info["interactions"] / n,
+                        "accepted_cells_per_particle": info["accepted"] / n,
+                        "exact_pairs_per_particle": info["pairs"] / n,
+                        "opened_cells_per_particle": info["opened"] / n,
+                        "cells": info["ncells"]},
             "ap_fp32": {"particle_steps_per_s": n / (ms_ap / 1e3), "ms_per_step": ms_ap,
                         "pair_interactions_per_s": n * (n - 1) / (ap_field_ms / 1e3),
                         "field_tflops": n * (n - 1) * FLOPS_PER_INTERACTION / (ap_field_ms / 1e3) / 1e12},

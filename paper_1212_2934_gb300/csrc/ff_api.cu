@@ -66,6 +66,7 @@ struct ff_ctx {
     void* f = nullptr;
     void* esr = nullptr;
     int4* counts = nullptr;
+    int* work = nullptr;         // traversal task counters
     double* partials = nullptr;
     double* obs = nullptr;       // observables of the last ff_energy
     double* obs_step = nullptr;  // observables of the state at the start of the last step
@@ -176,6 +177,7 @@ ffk::FieldParams<R> field_params(const ff_ctx* c, double theta, int include_sr)
     const bool lj_on = p.lj_eps != 0.0 && p.lj_rcut > 0.0;
     fp.theta2 = (R)(theta * theta);
     fp.rcut2 = lj_on ? (R)(p.lj_rcut * p.lj_rcut) : R(0);
+    fp.rcut = lj_on ? (R)p.lj_rcut : R(0);
     fp.use_rcut = lj_on ? 1 : 0;
     fp.include_sr = (include_sr && lj_on) ? 1 : 0;
     fp.dip_scale = (R)p.dip_scale;
@@ -314,7 +316,7 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr)
         StageTimer st(c, S_FIELD);
         ffk::bh_field<R>(V<R>(b.pos), V<R>(b.u), n, t, field_params<R>(c, theta, include_sr),
                          V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr),
-                         c->p.count_interactions ? c->counts : nullptr, c->dflags,
+                         c->p.count_interactions ? c->counts : nullptr, c->dflags, c->work,
                          traverse_group(c), s);
     }
     FF_LAUNCHED(c);
@@ -381,7 +383,7 @@ void free_all(ff_ctx* c)
 {
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->radix_tmp, c->cnt, c->off,
                     c->scan_tmp, c->bbox, c->cell, c->mom, c->lo, c->sum, c->parent,
-                    c->arrive, c->h, c->f, c->esr, c->counts, c->partials, c->obs, c->obs_step,
+                    c->arrive, c->h, c->f, c->esr, c->counts, c->work, c->partials, c->obs, c->obs_step,
                     c->dflags, c->staging};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -443,6 +445,7 @@ ff_status alloc_all(ff_ctx* c)
     A(&c->f, rec * n);
     A(&c->esr, (c->fp64 ? 8 : 4) * n);
     A(&c->counts, sizeof(int4) * n);
+    A(&c->work, sizeof(int) * ffk::kWorkSegments);
     A(&c->partials, sizeof(double) * ffk::kObs * ffk::integrate_blocks(n));
     A(&c->obs, sizeof(double) * ffk::kObs);
     A(&c->obs_step, sizeof(double) * ffk::kObs);

@@ -54,6 +54,7 @@ template <typename R>
 struct FieldParams {
     R theta2;        // theta^2 rounded to R once from the double product
     R rcut2;         // opening-test cut: lj_rcut^2 (0 when LJ is off)
+    R rcut;          // lj_rcut (0 when LJ is off)
     R dip_scale;
     R lj_eps24;      // 24 eps
     R lj_sigma2;     // sigma^2
@@ -129,10 +130,12 @@ void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint3
                     const uint32_t* off, Tree<R> t, int* flags, cudaStream_t s);
 
 // Barnes-Hut traversal.  h/f (and esr, counts if non-null) in sorted order;
-// group = lanes that walk the cell list together (1, 2, 4, 8, 16 or 32).
+// group = lanes that walk the cell list together (1, 2, 4, 8, 16 or 32);
+// work = kWorkSegments task counters (scratch, zeroed by the launcher).
+constexpr int kWorkSegments = 1024;
 template <typename R>
 void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
-              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int group,
+              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
               cudaStream_t s);
 
 // All-pairs sum (Sec. 3.1, Algorithm 1).

@@ -93,6 +93,11 @@ __device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& 
     const R s2 = rmul(c.w, c.w);
     if (!(s2 < rmul(fp.theta2, d2))) return false;
     if (fp.use_rcut) {
+        // The centre lies in the cube, so the cube is at least d - sqrt(3) side
+        // away; beyond rcut + sqrt(3) side (with a margin far above the rounding
+        // of d and of the centre) the exact test below cannot fail.
+        const R far = (fp.rcut + R(1.7320509) * c.w) * R(1.00001) + R(0.01);
+        if (d2 >= far * far) return true;
         const vec4<R> lo = lo_arr[i];
         const R side = lo.w;
         R t[3];
@@ -122,17 +127,16 @@ __device__ __forceinline__ unsigned group_min(unsigned v)
     return v;
 }
 
+// One task: the 32 consecutive particles task*32 .. task*32+31 of the key order.
 template <typename R, bool COUNT, int G>
-__global__ void __launch_bounds__(128) k_bh(const vec4<R>* __restrict__ pos,
-                                            const vec4<R>* __restrict__ u, int n, Tree<R> t,
-                                            FieldParams<R> fp, vec4<R>* __restrict__ h,
-                                            vec4<R>* __restrict__ f, R* __restrict__ esr,
-                                            int4* __restrict__ counts, int* flags)
+__device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ pos,
+                                        const vec4<R>* __restrict__ u, int n, const Tree<R>& t,
+                                        const FieldParams<R>& fp, unsigned ncells,
+                                        vec4<R>* __restrict__ h, vec4<R>* __restrict__ f,
+                                        R* __restrict__ esr, int4* __restrict__ counts, int* flags)
 {
     const int lane = threadIdx.x & 31;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k - lane >= n) return;  // the whole warp is past the end
-    if (*flags & FLAG_CAPACITY) return;
+    const int k = task * 32 + lane;
     const bool active = k < n;
     vec4<R> xk, uk;
     if (active) {
@@ -144,7 +148,6 @@ __global__ void __launch_bounds__(128) k_bh(const vec4<R>* __restrict__ pos,
     }
     R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0;
     int nacc = 0, npair = 0, nopen = 0;
-    const unsigned ncells = (unsigned)*t.ncells;
     unsigned nxt = active ? 0u : 0xffffffffu;
     for (;;) {
         const unsigned i = group_min<G>(nxt);
@@ -221,6 +224,41 @@ __global__ void __launch_bounds__(128) k_bh(const vec4<R>* __restrict__ pos,
     if (COUNT) counts[k] = make_int4(nacc, npair, nopen, 0);
 }
 
+// Persistent traversal: the key order is cut into nseg contiguous segments of
+// 32-particle tasks; a warp takes tasks from the segment of the SM it runs on
+// (so warps sharing an L1 cache walk neighbouring parts of the tree) and then
+// from the following segments once its own is used up.  Task counters
+// (work[0..nseg)) start at zero; every task is taken exactly once.
+template <typename R, bool COUNT, int G>
+__global__ void __launch_bounds__(128) k_bh(const vec4<R>* __restrict__ pos,
+                                            const vec4<R>* __restrict__ u, int n, Tree<R> t,
+                                            FieldParams<R> fp, vec4<R>* __restrict__ h,
+                                            vec4<R>* __restrict__ f, R* __restrict__ esr,
+                                            int4* __restrict__ counts, int* flags,
+                                            int* __restrict__ work, int nseg)
+{
+    if (*flags & FLAG_CAPACITY) return;
+    const unsigned ncells = (unsigned)*t.ncells;
+    const int ntask = (n + 31) / 32;
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    const int home = (int)(smid % (unsigned)nseg);
+    const int lane = threadIdx.x & 31;
+    for (int probe = 0; probe < nseg; ++probe) {
+        const int sg = (home + probe) % nseg;
+        const int t0 = (int)((int64_t)ntask * sg / nseg);
+        const int t1 = (int)((int64_t)ntask * (sg + 1) / nseg);
+        for (;;) {
+            int got = 0;
+            if (lane == 0) got = atomicAdd(&work[sg], 1);
+            got = __shfl_sync(kFull, got, 0);
+            const int task = t0 + got;
+            if (task >= t1) break;
+            bh_task<R, COUNT, G>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags);
+        }
+    }
+}
+
 // All pairs: one thread per target; source records staged through shared
 // memory one block-sized tile at a time (Sec. 3.1, Algorithm 1).
 constexpr int kApThreads = 256;
@@ -291,30 +329,55 @@ __global__ void __launch_bounds__(kApThreads) k_ap(const vec4<R>* __restrict__ p
 
 }  // namespace
 
+template <typename R, bool COUNT, int G>
+void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
+                 vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work,
+                 cudaStream_t s)
+{
+    // persistent grid: as many blocks as fit on the device at once; the L1
+    // cache gets the largest share of the unified L1/shared storage
+    static int blocks = 0, nsm = 0;
+    if (blocks == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_bh<R, COUNT, G>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G>, 128, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (nsm < 1) nsm = 1;
+        if (nsm > kWorkSegments) nsm = kWorkSegments;
+        blocks = per_sm * nsm;
+    }
+    cudaMemsetAsync(work, 0, sizeof(int) * nsm, s);
+    k_bh<R, COUNT, G><<<blocks, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags, work,
+                                             nsm);
+}
+
 template <typename R, bool COUNT>
 void bh_launch(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
-               vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int group,
+               vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
                cudaStream_t s)
 {
-    const unsigned g = (unsigned)((n + 127) / 128);
     switch (group) {
-        case 1: k_bh<R, COUNT, 1><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
-        case 2: k_bh<R, COUNT, 2><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
-        case 4: k_bh<R, COUNT, 4><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
-        case 8: k_bh<R, COUNT, 8><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
-        case 16: k_bh<R, COUNT, 16><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
-        default: k_bh<R, COUNT, 32><<<g, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags); break;
+        case 1: bh_launch_g<R, COUNT, 1>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
+        case 2: bh_launch_g<R, COUNT, 2>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
+        case 4: bh_launch_g<R, COUNT, 4>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
+        case 8: bh_launch_g<R, COUNT, 8>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
+        case 16: bh_launch_g<R, COUNT, 16>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
+        default: bh_launch_g<R, COUNT, 32>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
     }
 }
 
 template <typename R>
 void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
-              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int group, cudaStream_t s)
+              vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
+              cudaStream_t s)
 {
     if (counts)
-        bh_launch<R, true>(pos, u, n, t, fp, h, f, esr, counts, flags, group, s);
+        bh_launch<R, true>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, s);
     else
-        bh_launch<R, false>(pos, u, n, t, fp, h, f, esr, counts, flags, group, s);
+        bh_launch<R, false>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, s);
     counted();
 }
 
@@ -328,11 +391,11 @@ void ap_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, FieldParams<R> fp
 }
 
 template void bh_field<float>(const float4*, const float4*, int64_t, Tree<float>,
-                              FieldParams<float>, float4*, float4*, float*, int4*, int*, int,
-                              cudaStream_t);
+                              FieldParams<float>, float4*, float4*, float*, int4*, int*, int*,
+                              int, cudaStream_t);
 template void bh_field<double>(const dvec4*, const dvec4*, int64_t, Tree<double>,
-                               FieldParams<double>, dvec4*, dvec4*, double*, int4*, int*, int,
-                               cudaStream_t);
+                               FieldParams<double>, dvec4*, dvec4*, double*, int4*, int*, int*,
+                               int, cudaStream_t);
 template void ap_field<float>(const float4*, const float4*, int64_t, FieldParams<float>, float4*,
                               float4*, float*, cudaStream_t);
 template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<double>, dvec4*,
