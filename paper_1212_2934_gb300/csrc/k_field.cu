@@ -230,7 +230,7 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
 // from the following segments once its own is used up.  Task counters
 // (work[0..nseg)) start at zero; every task is taken exactly once.
 template <typename R, bool COUNT, int G>
-__global__ void __launch_bounds__(128) k_bh(const vec4<R>* __restrict__ pos,
+__global__ void __launch_bounds__(128, 12) k_bh(const vec4<R>* __restrict__ pos,
                                             const vec4<R>* __restrict__ u, int n, Tree<R> t,
                                             FieldParams<R> fp, vec4<R>* __restrict__ h,
                                             vec4<R>* __restrict__ f, R* __restrict__ esr,
@@ -334,14 +334,12 @@ void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, Fie
                  vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work,
                  cudaStream_t s)
 {
-    // persistent grid: as many blocks as fit on the device at once; the L1
-    // cache gets the largest share of the unified L1/shared storage
+    // persistent grid: as many blocks as fit on the device at once
     static int blocks = 0, nsm = 0;
     if (blocks == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_bh<R, COUNT, G>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G>, 128, 0);
         if (per_sm < 1) per_sm = 1;

@@ -65,20 +65,20 @@ __device__ __forceinline__ void normals6(const DynParams<R>& dp, uint32_t id, R 
 // LJ-type wall along one axis: distance w to the plane, sigma_w = 1/2, cut
 // where the force vanishes (w = 1/2), w clamped below at 0.01.
 template <typename R>
-__device__ __forceinline__ R wall_force(R w, const DynParams<R>& dp, double& e)
+__device__ __forceinline__ R wall_force(R w, const DynParams<R>& dp, R& e)
 {
     if (!(w < R(0.5))) return R(0);
     if (w < R(0.01)) w = R(0.01);
     const R s = R(0.5) / w;
     const R s2 = s * s;
     const R s6 = s2 * s2 * s2;
-    e += (double)(dp.wall_e2 * s6 * s6 - dp.wall_e4 * s6 + dp.wall_e2);
+    e += dp.wall_e2 * s6 * s6 - dp.wall_e4 * s6 + dp.wall_e2;
     return dp.wall_eps24 * (s6 * s6 - s6) / w;
 }
 
 template <typename R>
 __device__ __forceinline__ void walls3(const DynParams<R>& dp, const vec4<R>& x, R& fx, R& fy,
-                                       R& fz, double& e)
+                                       R& fz, R& e)
 {
     if (!dp.walls) return;
     fx += wall_force<R>(x.x - dp.lo[0], dp, e) - wall_force<R>(dp.hi[0] - x.x, dp, e);
@@ -86,8 +86,12 @@ __device__ __forceinline__ void walls3(const DynParams<R>& dp, const vec4<R>& x,
     fz += wall_force<R>(x.z - dp.lo[2], dp, e) - wall_force<R>(dp.hi[2] - x.z, dp, e);
 }
 
-// Block sum of kObs doubles; thread 0 writes them to out.
-__device__ __forceinline__ void block_sum_obs(double v[kObs], double* out)
+// Block sum of kObs per-thread values: warp sums in the arithmetic type R
+// (32 terms), then the warp sums in FP64 in a fixed order; thread q < kObs
+// writes quantity q.  Cancellation in the global sums (magnetisation,
+// energies of a million particles) happens in FP64.
+template <typename R>
+__device__ __forceinline__ void block_sum_obs(R v[kObs], double* out)
 {
     __shared__ double sh[kStepThreads / 32][kObs];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -98,7 +102,7 @@ __device__ __forceinline__ void block_sum_obs(double v[kObs], double* out)
     }
     if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < kObs; ++q) sh[w][q] = v[q];
+        for (int q = 0; q < kObs; ++q) sh[w][q] = (double)v[q];
     }
     __syncthreads();
     if (threadIdx.x < kObs) {
@@ -111,21 +115,20 @@ __device__ __forceinline__ void block_sum_obs(double v[kObs], double* out)
 // Accumulates one particle's terms: e_dip, e_zeeman, e_sr, e_wall, e_kin_t,
 // w^2 (scaled by I/2 later), u (3), h_dip_z.
 template <typename R>
-__device__ __forceinline__ void obs_terms(double v[kObs], const DynParams<R>& dp, const vec4<R>& uu,
+__device__ __forceinline__ void obs_terms(R v[kObs], const DynParams<R>& dp, const vec4<R>& uu,
                                           const vec4<R>& hd, const vec4<R>& vv, const vec4<R>& w,
-                                          R es, double ew)
+                                          R es, R ew)
 {
-    const double ux = uu.x, uy = uu.y, uz = uu.z;
-    v[0] += -0.5 * (ux * (double)hd.x + uy * (double)hd.y + uz * (double)hd.z);
-    v[1] += -(ux * (double)dp.hx + uy * (double)dp.hy + uz * (double)dp.hz);
-    v[2] += (double)es;
+    v[0] += R(-0.5) * (uu.x * hd.x + uu.y * hd.y + uu.z * hd.z);
+    v[1] += -(uu.x * dp.hx + uu.y * dp.hy + uu.z * dp.hz);
+    v[2] += es;
     v[3] += ew;
-    v[4] += 0.5 * ((double)vv.x * vv.x + (double)vv.y * vv.y + (double)vv.z * vv.z);
-    v[5] += (double)w.x * w.x + (double)w.y * w.y + (double)w.z * w.z;
-    v[6] += ux;
-    v[7] += uy;
-    v[8] += uz;
-    v[9] += (double)hd.z;
+    v[4] += R(0.5) * (vv.x * vv.x + vv.y * vv.y + vv.z * vv.z);
+    v[5] += w.x * w.x + w.y * w.y + w.z * w.z;
+    v[6] += uu.x;
+    v[7] += uu.y;
+    v[8] += uu.z;
+    v[9] += hd.z;
 }
 
 // x' = x + dt v; v' = v + dt (f - G_t v) + sig_t xi_t;
@@ -139,14 +142,14 @@ __global__ void __launch_bounds__(kStepThreads) k_integrate(
     vec4<R>* __restrict__ u2, vec4<R>* __restrict__ om2, uint32_t* __restrict__ id2,
     double* __restrict__ partials)
 {
-    double v[kObs];
+    R v[kObs];
 #pragma unroll
-    for (int q = 0; q < kObs; ++q) v[q] = 0.0;
+    for (int q = 0; q < kObs; ++q) v[q] = R(0);
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
         const vec4<R> x = pos[s], vv = vel[s], uu = u[s], w = om[s], hd = hdip[s], fi = fint[s];
         const uint32_t pid = id[s];
-        double ew = 0.0;
+        R ew = R(0);
         R fx = fi.x, fy = fi.y, fz = fi.z;
         walls3<R>(dp, x, fx, fy, fz, ew);
         const R hx = hd.x + dp.hx, hy = hd.y + dp.hy, hz = hd.z + dp.hz;
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(kStepThreads) k_integrate(
         id2[s] = pid;
         if (OBS) obs_terms<R>(v, dp, uu, hd, vv, w, esr ? esr[s] : R(0), ew);
     }
-    if (OBS) block_sum_obs(v, partials + (int64_t)blockIdx.x * kObs);
+    if (OBS) block_sum_obs<R>(v, partials + (int64_t)blockIdx.x * kObs);
 }
 
 template <typename R>
@@ -191,18 +194,18 @@ __global__ void __launch_bounds__(kStepThreads) k_observables(
     const vec4<R>* __restrict__ hdip, const R* __restrict__ esr, DynParams<R> dp,
     double* __restrict__ partials)
 {
-    double v[kObs];
+    R v[kObs];
 #pragma unroll
-    for (int q = 0; q < kObs; ++q) v[q] = 0.0;
+    for (int q = 0; q < kObs; ++q) v[q] = R(0);
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
         const vec4<R> x = pos[s];
-        double ew = 0.0;
+        R ew = R(0);
         R fx = 0, fy = 0, fz = 0;
         walls3<R>(dp, x, fx, fy, fz, ew);
         obs_terms<R>(v, dp, u[s], hdip[s], vel[s], om[s], esr ? esr[s] : R(0), ew);
     }
-    block_sum_obs(v, partials + (int64_t)blockIdx.x * kObs);
+    block_sum_obs<R>(v, partials + (int64_t)blockIdx.x * kObs);
 }
 
 // Deterministic final sum: one block per quantity; thread t adds partials
