@@ -70,6 +70,11 @@ struct ff_ctx {
     double* partials = nullptr;
     double* obs = nullptr;       // observables of the last ff_energy
     double* obs_step = nullptr;  // observables of the state at the start of the last step
+    unsigned long long* dstep = nullptr;  // device copy of the step counter (noise counter)
+    // one captured step per starting state buffer (CUDA graphs)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int gend[2] = {0, 0};           // state buffer after the captured step
+    int64_t glaunch[2] = {0, 0};    // kernels in the captured step
     int* dflags = nullptr;
     int* hflags = nullptr;       // pinned mirror
     double* hobs = nullptr;      // pinned mirror of 10 doubles
@@ -217,8 +222,7 @@ ffk::DynParams<R> dyn_params(const ff_ctx* c)
     d.walls = p.walls ? 1 : 0;
     d.key0 = (uint32_t)p.seed;
     d.key1 = (uint32_t)(p.seed >> 32);
-    d.ctr0 = (uint32_t)c->step;
-    d.ctr1 = (uint32_t)((uint64_t)c->step >> 32);
+    d.step = c->dstep;
     return d;
 }
 
@@ -358,6 +362,7 @@ ff_status do_step(ff_ctx* c)
                           V<R>(b.vel), V<R>(b.u), V<R>(b.om), b.id, c->partials, c->stream);
         ffk::reduce_partials(c->partials, ffk::integrate_blocks(c->n), 1.0 / (double)c->n,
                              0.5 * c->p.inertia, c->obs_step, c->stream);
+        ffk::step_advance(c->dstep, c->stream);
     }
     FF_LAUNCHED(c);
     c->cur = 1 - c->cur;
@@ -383,7 +388,7 @@ void free_all(ff_ctx* c)
 {
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->radix_tmp, c->cnt, c->off,
                     c->scan_tmp, c->bbox, c->cell, c->mom, c->lo, c->sum, c->parent,
-                    c->arrive, c->h, c->f, c->esr, c->counts, c->work, c->partials, c->obs, c->obs_step,
+                    c->arrive, c->h, c->f, c->esr, c->counts, c->work, c->partials, c->obs, c->obs_step, c->dstep,
                     c->dflags, c->staging};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -397,6 +402,8 @@ void free_all(ff_ctx* c)
         cudaEventDestroy(m.b);
     }
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k)
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
     c->marks.clear();
     c->pool.clear();
     if (c->hflags) cudaFreeHost(c->hflags);
@@ -449,6 +456,7 @@ ff_status alloc_all(ff_ctx* c)
     A(&c->partials, sizeof(double) * ffk::kObs * ffk::integrate_blocks(n));
     A(&c->obs, sizeof(double) * ffk::kObs);
     A(&c->obs_step, sizeof(double) * ffk::kObs);
+    A(&c->dstep, sizeof(unsigned long long));
     A(&c->dflags, sizeof(int));
     A(&c->staging, sizeof(double) * 12 * n);
     if (e != cudaSuccess) return fail(c, FF_ENOMEM, "device allocation failed: %s", cudaGetErrorString(e));
@@ -457,6 +465,7 @@ ff_status alloc_all(ff_ctx* c)
         return fail(c, FF_ENOMEM, "pinned host allocation failed");
     FF_CUDA(c, cudaMemsetAsync(c->dflags, 0, sizeof(int), c->stream));
     FF_CUDA(c, cudaMemsetAsync(c->obs_step, 0, sizeof(double) * ffk::kObs, c->stream));
+    FF_CUDA(c, cudaMemsetAsync(c->dstep, 0, sizeof(unsigned long long), c->stream));
     FF_CUDA(c, cudaStreamSynchronize(c->stream));
     return FF_OK;
 }
@@ -732,9 +741,45 @@ ff_status ff_step(ff_ctx* c, int64_t nsteps)
     ff_status s = usable(c, true);
     if (s != FF_OK) return s;
     if (nsteps < 0) return fail(c, FF_EINVAL, "nsteps must be >= 0");
+    if (c->prof) {
+        // stage timing needs the events between stages: launch eagerly
+        for (int64_t k = 0; k < nsteps; ++k) {
+            s = c->fp64 ? do_step<double>(c) : do_step<float>(c);
+            if (s != FF_OK) return s;
+        }
+        return FF_OK;
+    }
     for (int64_t k = 0; k < nsteps; ++k) {
-        s = c->fp64 ? do_step<double>(c) : do_step<float>(c);
-        if (s != FF_OK) return s;
+        const int start = c->cur;
+        if (!c->gexec[start]) {
+            // capture one step; nothing runs during capture, so the buffer index
+            // and the host step counter are put back afterwards
+            const int64_t l0 = ffk::g_launches.load();
+            const int64_t step0 = c->step;
+            FF_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            s = c->fp64 ? do_step<double>(c) : do_step<float>(c);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+            if (s != FF_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return s;
+            }
+            if (e != cudaSuccess) return fail(c, FF_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&c->gexec[start], graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(c, FF_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+            c->gend[start] = c->cur;
+            c->glaunch[start] = ffk::g_launches.load() - l0;
+            ffk::g_launches.fetch_sub(c->glaunch[start]);
+            c->cur = start;
+            c->step = step0;
+        }
+        FF_CUDA(c, cudaGraphLaunch(c->gexec[start], c->stream));
+        ffk::counted((int)c->glaunch[start]);
+        c->cur = c->gend[start];
+        c->step += 1;
+        c->tree_valid = c->tree_valid || c->p.algo == FF_ALGO_BH;
+        c->counts_valid = c->p.algo == FF_ALGO_BH && c->p.count_interactions != 0;
     }
     return FF_OK;
 }
@@ -759,6 +804,10 @@ ff_status ff_set_step(ff_ctx* c, int64_t step)
 {
     if (!c) return FF_EINVAL;
     if (step < 0) return fail(c, FF_EINVAL, "step must be >= 0");
+    FF_CUDA(c, cudaSetDevice(c->p.device));
+    const unsigned long long v = (unsigned long long)step;
+    FF_CUDA(c, cudaMemcpyAsync(c->dstep, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
     c->step = step;
     return FF_OK;
 }

@@ -74,8 +74,8 @@ struct DynParams {
     R lo[3], hi[3];
     R wall_eps24, wall_e2, wall_e4;
     int walls;
-    uint32_t key0, key1;  // Philox key (seed)
-    uint32_t ctr0, ctr1;  // step counter
+    uint32_t key0, key1;                 // Philox key (seed)
+    const unsigned long long* step;      // device word: the step counter
 };
 
 // What the traversal reads for every visited cell, in one record (32 bytes
@@ -160,6 +160,8 @@ void observables(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R
                  double* partials, cudaStream_t s);
 void reduce_partials(const double* partials, int nblocks, double inv_n, double inertia_half,
                      double* out, cudaStream_t s);
+// Advances the device step counter by one.
+void step_advance(unsigned long long* step, cudaStream_t s);
 
 // Layout conversion between caller arrays (n x 3, float or double) and
 // records; scatter/gather through the particle ids.

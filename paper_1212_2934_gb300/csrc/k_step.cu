@@ -55,8 +55,10 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, d
 template <typename R>
 __device__ __forceinline__ void normals6(const DynParams<R>& dp, uint32_t id, R z[6])
 {
-    const uint4 w0 = philox10(make_uint4(dp.ctr0, dp.ctr1, id, 0u), dp.key0, dp.key1);
-    const uint4 w1 = philox10(make_uint4(dp.ctr0, dp.ctr1, id, 1u), dp.key0, dp.key1);
+    const unsigned long long st = *dp.step;
+    const uint32_t c0 = (uint32_t)st, c1 = (uint32_t)(st >> 32);
+    const uint4 w0 = philox10(make_uint4(c0, c1, id, 0u), dp.key0, dp.key1);
+    const uint4 w1 = philox10(make_uint4(c0, c1, id, 1u), dp.key0, dp.key1);
     box_muller(w0.x, w0.y, z[0], z[1]);
     box_muller(w0.z, w0.w, z[2], z[3]);
     box_muller(w1.x, w1.y, z[4], z[5]);
@@ -232,6 +234,8 @@ __global__ void __launch_bounds__(kStepThreads) k_reduce_partials(
     }
 }
 
+__global__ void k_step_advance(unsigned long long* step) { *step += 1ull; }
+
 template <typename R, typename I>
 __global__ void k_load3(const I* __restrict__ in, int64_t n, vec4<R>* __restrict__ out)
 {
@@ -329,6 +333,12 @@ void reduce_partials(const double* partials, int nblocks, double inv_n, double i
                      double* out, cudaStream_t s)
 {
     k_reduce_partials<<<kObs, kStepThreads, 0, s>>>(partials, nblocks, inv_n, inertia_half, out);
+    counted();
+}
+
+void step_advance(unsigned long long* step, cudaStream_t s)
+{
+    k_step_advance<<<1, 1, 0, s>>>(step);
     counted();
 }
 
