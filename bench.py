@@ -180,6 +180,22 @@ def traffic_for(kernel_src):
     return None
 
 
+def max_over_ranks(x, device="cpu"):
+    """Maximum of a float over the ranks of the default process group (the value itself
+    when no group is initialised); the tensor lives on `device` (cuda for NCCL)."""
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_per_rank, steps, world, max_seconds):
+    """Units all ranks processed divided by the slowest rank's time (replicas: weak scaling)."""
+    return world * n_per_rank * steps / max_seconds
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,11 +343,8 @@ def run_ours(args):
         flush.zero_()
     prof = ff.ff_profile_read(ctx)
     ff.ff_profile(ctx, False)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * n * K / (max_ms / 1e3)
+    max_ms = max_over_ranks(total_ms, "cuda")
+    value = whole_job_rate(n, K, world, max_ms / 1e3)
     energy = ff.ff_energy(ctx)
     # interaction counts of the final state, from one counted evaluation (the timed steps
     # move particles by ~1e-4 diameters, so the per-launch work is the same to < 0.1 %)
@@ -430,10 +443,7 @@ def run_ours(args):
             e2e_step()
         barrier()
         e2e_s = time.perf_counter() - t0
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": world * n * K / float(te.item()), "unit": UNIT,
+        e2e = {"value": whole_job_rate(n, K, world, max_over_ranks(e2e_s, "cuda")), "unit": UNIT,
                "h2d_bytes_per_step": 4 * n * 3 * 4, "d2h_bytes_per_step": 4 * n * 3 * 4,
                "note": "ff_set_particles + ff_step + ff_get_particles on pinned host float32 "
                        "arrays (positions, moments, velocities, angular velocities), wall clock"}

@@ -117,6 +117,14 @@ __device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& 
     return true;
 }
 
+// Preferred shared-memory share of the traversal (percent of the maximum):
+// 7 % selects 16 KB, room for the per-block reservation of 12 resident
+// blocks; the rest of the unified storage serves as L1 cache.
+#ifndef FFK_TRAVERSE_CARVEOUT
+#define FFK_TRAVERSE_CARVEOUT 7
+#endif
+constexpr int kTraverseCarveout = FFK_TRAVERSE_CARVEOUT;
+
 // Minimum of v over each aligned group of G lanes.
 template <int G>
 __device__ __forceinline__ unsigned group_min(unsigned v)
@@ -224,6 +232,86 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
     if (COUNT) counts[k] = make_int4(nacc, npair, nopen, 0);
 }
 
+// Independent per-lane walk (group size 1): each lane follows its own path
+// through the cell list; no vote or shuffle per visited cell.
+template <typename R, bool COUNT>
+__device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ pos,
+                                         const vec4<R>* __restrict__ u, int n, const Tree<R>& t,
+                                         const FieldParams<R>& fp, unsigned ncells,
+                                         vec4<R>* __restrict__ h, vec4<R>* __restrict__ f,
+                                         R* __restrict__ esr, int4* __restrict__ counts, int* flags)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = task * 32 + lane;
+    if (k >= n) return;
+    const vec4<R> xk = pos[k], uk = u[k];
+    R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0;
+    int nacc = 0, npair = 0, nopen = 0;
+    unsigned i = 0;
+    while (i < ncells) {
+        const Cell<R> cl = t.cell[i];
+        const int4 nd = cl.node;
+        const bool inside = nd.x <= k && k < nd.y;
+        const bool leaf = (nd.w >> 8) != 0;
+        const bool single = leaf && (nd.y - nd.x == 1);
+        const vec4<R> c = cl.cen;
+        const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i);
+        unsigned nxt = i + 1;
+        if (acc || (single && !inside)) {
+            // the cell's pseudo-particle; for a one-particle leaf it is the
+            // particle itself (centre and moment sum of one term are exact)
+            const vec4<R> m = t.mom[i];
+            const R rx = xk.x - c.x, ry = xk.y - c.y, rz = xk.z - c.z;
+            const R r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 > R(0))
+                dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, m.x, m.y, m.z, hx, hy, hz, fx, fy, fz);
+            if (acc) {
+                if (COUNT) ++nacc;
+            } else {
+                if (fp.include_sr) lj<R>(fp, rx, ry, rz, r2, sx, sy, sz, es);
+                if (COUNT) ++npair;
+            }
+            nxt = (unsigned)nd.z;
+        } else if (leaf) {
+            if (!single) {
+                for (int s = nd.x; s < nd.y; ++s) {
+                    if (s == k) continue;
+                    const vec4<R> xj = pos[s], uj = u[s];
+                    const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
+                    const R r2 = rx * rx + ry * ry + rz * rz;
+                    if (r2 > R(0)) {
+                        dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, uj.x, uj.y, uj.z, hx, hy, hz,
+                                  fx, fy, fz);
+                        if (fp.include_sr) lj<R>(fp, rx, ry, rz, r2, sx, sy, sz, es);
+                    }
+                    if (COUNT) ++npair;
+                }
+            }
+            nxt = (unsigned)nd.z;
+        } else {
+            if (COUNT) ++nopen;
+        }
+        if (nxt <= i) {  // skip pointers must move forward
+            atomicOr(flags, FLAG_TRAVERSE);
+            break;
+        }
+        i = nxt;
+    }
+    vec4<R> ho, fo;
+    ho.x = fp.dip_scale * hx;
+    ho.y = fp.dip_scale * hy;
+    ho.z = fp.dip_scale * hz;
+    ho.w = R(0);
+    fo.x = fp.dip_scale * fx + sx;
+    fo.y = fp.dip_scale * fy + sy;
+    fo.z = fp.dip_scale * fz + sz;
+    fo.w = R(0);
+    h[k] = ho;
+    f[k] = fo;
+    if (esr) esr[k] = es;
+    if (COUNT) counts[k] = make_int4(nacc, npair, nopen, 0);
+}
+
 // Persistent traversal: the key order is cut into nseg contiguous segments of
 // 32-particle tasks; a warp takes tasks from the segment of the SM it runs on
 // (so warps sharing an L1 cache walk neighbouring parts of the tree) and then
@@ -254,7 +342,10 @@ __global__ void __launch_bounds__(128, 12) k_bh(const vec4<R>* __restrict__ pos,
             got = __shfl_sync(kFull, got, 0);
             const int task = t0 + got;
             if (task >= t1) break;
-            bh_task<R, COUNT, G>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags);
+            if (G == 1)
+                bh_task1<R, COUNT>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags);
+            else
+                bh_task<R, COUNT, G>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags);
         }
     }
 }
@@ -334,12 +425,15 @@ void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, Fie
                  vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work,
                  cudaStream_t s)
 {
-    // persistent grid: as many blocks as fit on the device at once
+    // persistent grid: as many blocks as fit on the device at once; a small
+    // shared-memory carveout (the kernel uses none) leaves the rest to L1
     static int blocks = 0, nsm = 0;
     if (blocks == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_bh<R, COUNT, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             kTraverseCarveout);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G>, 128, 0);
         if (per_sm < 1) per_sm = 1;
