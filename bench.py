@@ -384,6 +384,22 @@ def run_ours(args):
         barrier()
         ms64 = sum(a.elapsed_time(b) for a, b in e64) / k64
         del ctx64
+        # ---- FP32 Barnes-Hut with up to 8 particles per leaf (same theta; near field exact
+        # inside leaves) -- a tuning comparison, not the paper's one-particle leaves
+        ctx8 = ff.ff_create(params(leaf_max=8, count_interactions=0))
+        ff.ff_set_particles(ctx8, pos_d, u_d)
+        ff.ff_step(ctx8, 2)
+        barrier()
+        e8 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(10)]
+        for a, b in e8:
+            a.record(stream)
+            ff.ff_step(ctx8, 1)
+            b.record(stream)
+            flush.zero_()
+        barrier()
+        ms8 = sum(a.elapsed_time(b) for a, b in e8) / len(e8)
+        del ctx8
         # ---- GPU all-pairs step (FP32)
         ctxap = ff.ff_create(params(algo="ap", count_interactions=0))
         ff.ff_set_particles(ctxap, pos_d, u_d)
@@ -409,6 +425,8 @@ def run_ours(args):
                         "pair_interactions_per_s": n * (n - 1) / (ap_field_ms / 1e3),
                         "field_tflops": n * (n - 1) * FLOPS_PER_INTERACTION / (ap_field_ms / 1e3) / 1e12},
             "bh_fp64": {"particle_steps_per_s": n / (ms64 / 1e3), "ms_per_step": ms64},
+            "bh_fp32_leaf8": {"particle_steps_per_s": n / (ms8 / 1e3), "ms_per_step": ms8,
+                              "note": "leaf_max = 8 (the paper's leaves hold one particle)"},
             "speedup_bh_fp32_over_ap": ms_ap / (max_ms / K),
             "speedup_bh_fp32_over_fp64": ms64 / (max_ms / K),
         }

@@ -125,6 +125,11 @@ __device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& 
 #endif
 constexpr int kTraverseCarveout = FFK_TRAVERSE_CARVEOUT;
 
+// 1: the per-lane walk requests a cell's moment sum together with its record.
+#ifndef FFK_HOIST_MOMENT
+#define FFK_HOIST_MOMENT 1
+#endif
+
 // Minimum of v over each aligned group of G lanes.
 template <int G>
 __device__ __forceinline__ unsigned group_min(unsigned v)
@@ -250,6 +255,10 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
     unsigned i = 0;
     while (i < ncells) {
         const Cell<R> cl = t.cell[i];
+#if FFK_HOIST_MOMENT
+        // requested with the cell so that one latency covers both loads
+        const vec4<R> m = t.mom[i];
+#endif
         const int4 nd = cl.node;
         const bool inside = nd.x <= k && k < nd.y;
         const bool leaf = (nd.w >> 8) != 0;
@@ -260,7 +269,9 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
         if (acc || (single && !inside)) {
             // the cell's pseudo-particle; for a one-particle leaf it is the
             // particle itself (centre and moment sum of one term are exact)
+#if !FFK_HOIST_MOMENT
             const vec4<R> m = t.mom[i];
+#endif
             const R rx = xk.x - c.x, ry = xk.y - c.y, rz = xk.z - c.z;
             const R r2 = rx * rx + ry * ry + rz * rz;
             if (r2 > R(0))
