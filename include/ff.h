@@ -174,6 +174,32 @@ ff_status ff_energy(ff_ctx *ctx, ff_energy_t *out);
 ff_status ff_get_step(const ff_ctx *ctx, int64_t *step);
 ff_status ff_set_step(ff_ctx *ctx, int64_t step);
 
+/*
+ * Batched ensembles: splits the n particles into nsys independent systems
+ * (particles 0 .. counts[0]-1 form system 0, the next counts[1] system 1,
+ * and so on, in the caller's order), each with its own root cube and tree
+ * (Sec. 3.2), its own applied field h_ext[3*s .. 3*s+2] and, when walls are
+ * on, its own container box_lo/box_hi[3*s ..] (NULL: the context's field or
+ * box for every system).  Systems never interact; every other parameter is
+ * shared.  This is how the magnetisation curves of Sec. 5 are run: many
+ * ensembles at different field amplitudes advanced together, one CUDA graph
+ * per step for all of them.  nsys = 1 .. 65536, counts >= 1 summing to n.
+ * All-pairs evaluation is not available for batched systems.  Waits.
+ */
+ff_status ff_set_systems(ff_ctx *ctx, int32_t nsys, const int64_t *counts, const double *h_ext,
+                         const double *box_lo, const double *box_hi);
+
+/*
+ * Per-system sums accumulated by ff_step since the last reset (or since
+ * ff_set_systems): out[4*s + q] = sum over steps and over the particles of
+ * system s of u_x, u_y, u_z (q = 0..2) and h_dip_z (q = 3), taken from the
+ * state at the start of each step (Sec. 5: <u> and <h_dip_z> follow by
+ * dividing by steps x particles).  *nsteps receives the number of steps.
+ * reset = 1 clears the sums afterwards.  The sums are formed with FP64
+ * atomics, so their last bits may differ between runs.  Waits.
+ */
+ff_status ff_system_moments(ff_ctx *ctx, double *out, int64_t *nsteps, int32_t reset);
+
 /* Waits for the context's stream and reports any error flag raised on the GPU. */
 ff_status ff_synchronize(ff_ctx *ctx);
 

@@ -82,6 +82,16 @@ struct ff_ctx {
     bool tree_valid = false;     // a Barnes-Hut tree of some state exists
     bool counts_valid = false;
 
+    // batched ensembles (ff_set_systems); nsys = 0: one system with the context's field and box
+    int nsys = 0;
+    uint32_t* sys_of_pos = nullptr;  // device: system of each position
+    int* sys_start = nullptr;        // device: nsys + 1 offsets
+    void* sys_h = nullptr;           // device: vec4<R>[nsys] applied field
+    void* sys_lo = nullptr;          // device: vec4<R>[nsys] lower wall planes
+    void* sys_hi = nullptr;          // device: vec4<R>[nsys] upper wall planes
+    double* sys_acc = nullptr;       // device: nsys x 4 sums of u and h_dip_z
+    int64_t sys_steps = 0;           // steps accumulated in sys_acc
+
     // stage timing
     struct Mark {
         int stage;
@@ -174,6 +184,17 @@ ffk::Tree<R> tree_of(ff_ctx* c)
     return t;
 }
 
+ffk::Segs segs_of(const ff_ctx* c)
+{
+    ffk::Segs sg;
+    if (c->nsys > 0) {
+        sg.of_pos = c->sys_of_pos;
+        sg.start = c->sys_start;
+        sg.nseg = c->nsys;
+    }
+    return sg;
+}
+
 template <typename R>
 ffk::FieldParams<R> field_params(const ff_ctx* c, double theta, int include_sr)
 {
@@ -223,6 +244,11 @@ ffk::DynParams<R> dyn_params(const ff_ctx* c)
     d.key0 = (uint32_t)p.seed;
     d.key1 = (uint32_t)(p.seed >> 32);
     d.step = c->dstep;
+    d.sys_h = static_cast<const ffk::vec4<R>*>(c->sys_h);
+    d.sys_lo = static_cast<const ffk::vec4<R>*>(c->sys_lo);
+    d.sys_hi = static_cast<const ffk::vec4<R>*>(c->sys_hi);
+    d.sys_of_pos = c->nsys > 0 ? c->sys_of_pos : nullptr;
+    d.sys_acc = c->nsys > 0 ? c->sys_acc : nullptr;
     return d;
 }
 
@@ -294,11 +320,14 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr)
     Buffers& b = c->st[1 - c->cur];
     {
         StageTimer st(c, S_KEYS);
-        ffk::morton_keys<R>(V<R>(a.pos), n, c->bbox, c->keys[0], c->vals[0], c->dflags, s);
+        ffk::morton_keys<R>(V<R>(a.pos), n, c->bbox, c->keys[0], c->vals[0], c->dflags,
+                            segs_of(c), s);
     }
     {
         StageTimer st(c, S_SORT);
         ffk::radix_sort_pairs(c->keys[0], c->vals[0], c->keys[1], c->vals[1], n, c->radix_tmp, s);
+        ffk::radix_sort_systems(c->keys[0], c->vals[0], c->keys[1], c->vals[1], n, c->radix_tmp,
+                                segs_of(c), s);
     }
     {
         StageTimer st(c, S_GATHER);
@@ -310,7 +339,7 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr)
     {
         StageTimer st(c, S_BUILD);
         ffk::build_tree<R>(c->keys[0], n, c->p.leaf_max, c->bbox, t, c->cnt, c->off, c->scan_tmp,
-                           c->dflags, s);
+                           c->dflags, segs_of(c), s);
     }
     {
         StageTimer st(c, S_AGG);
@@ -321,7 +350,7 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr)
         ffk::bh_field<R>(V<R>(b.pos), V<R>(b.u), n, t, field_params<R>(c, theta, include_sr),
                          V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr),
                          c->p.count_interactions ? c->counts : nullptr, c->dflags, c->work,
-                         traverse_group(c), s);
+                         traverse_group(c), c->off, segs_of(c), s);
     }
     FF_LAUNCHED(c);
     c->tree_valid = true;
@@ -388,7 +417,8 @@ void free_all(ff_ctx* c)
 {
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->radix_tmp, c->cnt, c->off,
                     c->scan_tmp, c->bbox, c->cell, c->mom, c->lo, c->sum, c->parent,
-                    c->arrive, c->h, c->f, c->esr, c->counts, c->work, c->partials, c->obs, c->obs_step, c->dstep,
+                    c->arrive, c->h, c->f, c->esr, c->counts, c->work, c->partials, c->obs, c->obs_step, c->dstep, c->sys_of_pos, c->sys_start, c->sys_h, c->sys_lo,
+                    c->sys_hi, c->sys_acc,
                     c->dflags, c->staging};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -616,6 +646,34 @@ ff_status energy(ff_ctx* c, ff_energy_t* out)
 }  // namespace
 
 // =================================================================== C ABI
+namespace {
+
+template <typename R>
+void fill_sys_records(std::vector<unsigned char>& out, int nsys, const double* v3, double add,
+                      const double* fallback)
+{
+    out.assign(sizeof(ffk::vec4<R>) * nsys, 0);
+    ffk::vec4<R>* r = reinterpret_cast<ffk::vec4<R>*>(out.data());
+    for (int s = 0; s < nsys; ++s) {
+        const double* src = v3 ? v3 + 3 * (size_t)s : fallback;
+        r[s].x = (R)(src[0] + add);
+        r[s].y = (R)(src[1] + add);
+        r[s].z = (R)(src[2] + add);
+        r[s].w = R(0);
+    }
+}
+
+void drop_graphs(ff_ctx* c)
+{
+    for (int k = 0; k < 2; ++k)
+        if (c->gexec[k]) {
+            cudaGraphExecDestroy(c->gexec[k]);
+            c->gexec[k] = nullptr;
+        }
+}
+
+}  // namespace
+
 extern "C" {
 
 void ff_params_default(ff_params* p)
@@ -729,6 +787,7 @@ ff_status ff_dipolar_field(ff_ctx* c, int32_t algo, double theta, int32_t includ
     ff_status s = usable(c, true);
     if (s != FF_OK) return s;
     if (algo != FF_ALGO_BH && algo != FF_ALGO_AP) return fail(c, FF_EINVAL, "bad algo");
+    if (algo == FF_ALGO_AP && c->nsys > 0) return fail(c, FF_EINVAL, "all-pairs is not available for batched systems");
     if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(c, FF_EINVAL, "theta must be finite and >= 0");
     if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
     return c->fp64 ? dipolar_field<double>(c, algo, theta, include_sr, h_out, f_out, dtype, loc)
@@ -741,11 +800,13 @@ ff_status ff_step(ff_ctx* c, int64_t nsteps)
     ff_status s = usable(c, true);
     if (s != FF_OK) return s;
     if (nsteps < 0) return fail(c, FF_EINVAL, "nsteps must be >= 0");
+    if (c->p.algo == FF_ALGO_AP && c->nsys > 0) return fail(c, FF_EINVAL, "all-pairs is not available for batched systems");
     if (c->prof) {
         // stage timing needs the events between stages: launch eagerly
         for (int64_t k = 0; k < nsteps; ++k) {
             s = c->fp64 ? do_step<double>(c) : do_step<float>(c);
             if (s != FF_OK) return s;
+            if (c->nsys > 0) c->sys_steps += 1;
         }
         return FF_OK;
     }
@@ -778,6 +839,7 @@ ff_status ff_step(ff_ctx* c, int64_t nsteps)
         ffk::counted((int)c->glaunch[start]);
         c->cur = c->gend[start];
         c->step += 1;
+        if (c->nsys > 0) c->sys_steps += 1;
         c->tree_valid = c->tree_valid || c->p.algo == FF_ALGO_BH;
         c->counts_valid = c->p.algo == FF_ALGO_BH && c->p.count_interactions != 0;
     }
@@ -790,6 +852,7 @@ ff_status ff_energy(ff_ctx* c, ff_energy_t* out)
     ff_status s = usable(c, true);
     if (s != FF_OK) return s;
     if (!out) return fail(c, FF_EINVAL, "out is NULL");
+    if (c->p.algo == FF_ALGO_AP && c->nsys > 0) return fail(c, FF_EINVAL, "all-pairs is not available for batched systems");
     return c->fp64 ? energy<double>(c, out) : energy<float>(c, out);
 }
 
@@ -947,6 +1010,91 @@ ff_status ff_get_counts(ff_ctx* c, int32_t* accepted, int32_t* pairs, int32_t* o
     int32_t* dst[3] = {accepted, pairs, opened};
     for (int q = 0; q < 3; ++q)
         if (dst[q]) FF_CUDA(c, cudaMemcpy(dst[q], stg + q * n, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    return FF_OK;
+}
+
+ff_status ff_set_systems(ff_ctx* c, int32_t nsys, const int64_t* counts, const double* h_ext,
+                         const double* box_lo, const double* box_hi)
+{
+    if (!c) return FF_EINVAL;
+    if (nsys < 1 || nsys > 65536 || !counts) return fail(c, FF_EINVAL, "nsys must be 1 .. 65536 with counts");
+    int64_t total = 0;
+    for (int s = 0; s < nsys; ++s) {
+        if (counts[s] < 1) return fail(c, FF_EINVAL, "every system needs at least one particle");
+        total += counts[s];
+    }
+    if (total != c->n) return fail(c, FF_EINVAL, "system counts must add up to n");
+    if (c->p.walls && box_lo && box_hi)
+        for (int s = 0; s < nsys; ++s)
+            for (int a = 0; a < 3; ++a)
+                if (!(box_lo[3 * s + a] < box_hi[3 * s + a])) return fail(c, FF_EINVAL, "walls need box_lo < box_hi");
+    FF_CUDA(c, cudaSetDevice(c->p.device));
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    void* olds[] = {c->sys_of_pos, c->sys_start, c->sys_h, c->sys_lo, c->sys_hi, c->sys_acc, c->bbox};
+    for (void* q : olds)
+        if (q) cudaFree(q);
+    c->sys_of_pos = nullptr;
+    c->sys_start = nullptr;
+    c->sys_h = c->sys_lo = c->sys_hi = nullptr;
+    c->sys_acc = nullptr;
+    c->bbox = nullptr;
+    c->nsys = 0;
+    std::vector<int> start(nsys + 1, 0);
+    std::vector<uint32_t> of_pos(c->n);
+    for (int s = 0; s < nsys; ++s) {
+        start[s + 1] = start[s] + (int)counts[s];
+        for (int64_t i = start[s]; i < start[s + 1]; ++i) of_pos[i] = (uint32_t)s;
+    }
+    std::vector<unsigned char> rh, rlo, rhi;
+    const double* blo = box_lo;
+    const double* bhi = box_hi;
+    if (c->fp64) {
+        fill_sys_records<double>(rh, nsys, h_ext, 0.0, c->p.h_ext);
+        fill_sys_records<double>(rlo, nsys, blo, -0.5, c->p.box_lo);
+        fill_sys_records<double>(rhi, nsys, bhi, 0.5, c->p.box_hi);
+    } else {
+        fill_sys_records<float>(rh, nsys, h_ext, 0.0, c->p.h_ext);
+        fill_sys_records<float>(rlo, nsys, blo, -0.5, c->p.box_lo);
+        fill_sys_records<float>(rhi, nsys, bhi, 0.5, c->p.box_hi);
+    }
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t bytes) {
+        if (e == cudaSuccess) e = dalloc(p, bytes);
+    };
+    A(&c->sys_of_pos, sizeof(uint32_t) * c->n);
+    A(&c->sys_start, sizeof(int) * (nsys + 1));
+    A(&c->sys_h, rh.size());
+    A(&c->sys_lo, rlo.size());
+    A(&c->sys_hi, rhi.size());
+    A(&c->sys_acc, sizeof(double) * 4 * nsys);
+    A(&c->bbox, sizeof(ffk::BBox) * nsys);
+    if (e != cudaSuccess) return fail(c, FF_ENOMEM, "device allocation failed: %s", cudaGetErrorString(e));
+    FF_CUDA(c, cudaMemcpy(c->sys_of_pos, of_pos.data(), sizeof(uint32_t) * c->n, cudaMemcpyHostToDevice));
+    FF_CUDA(c, cudaMemcpy(c->sys_start, start.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice));
+    FF_CUDA(c, cudaMemcpy(c->sys_h, rh.data(), rh.size(), cudaMemcpyHostToDevice));
+    FF_CUDA(c, cudaMemcpy(c->sys_lo, rlo.data(), rlo.size(), cudaMemcpyHostToDevice));
+    FF_CUDA(c, cudaMemcpy(c->sys_hi, rhi.data(), rhi.size(), cudaMemcpyHostToDevice));
+    FF_CUDA(c, cudaMemset(c->sys_acc, 0, sizeof(double) * 4 * nsys));
+    c->nsys = nsys;
+    c->sys_steps = 0;
+    c->tree_valid = false;
+    c->counts_valid = false;
+    return FF_OK;
+}
+
+ff_status ff_system_moments(ff_ctx* c, double* out, int64_t* nsteps, int32_t reset)
+{
+    ff_status s = usable(c, false);
+    if (s != FF_OK) return s;
+    if (c->nsys < 1) return fail(c, FF_ESTATE, "no systems set (ff_set_systems)");
+    if ((s = sync_and_check(c)) != FF_OK) return s;
+    if (out) FF_CUDA(c, cudaMemcpy(out, c->sys_acc, sizeof(double) * 4 * c->nsys, cudaMemcpyDeviceToHost));
+    if (nsteps) *nsteps = c->sys_steps;
+    if (reset) {
+        FF_CUDA(c, cudaMemset(c->sys_acc, 0, sizeof(double) * 4 * c->nsys));
+        c->sys_steps = 0;
+    }
     return FF_OK;
 }
 

@@ -121,7 +121,7 @@ ff_status ff_morton_order_noalloc(const float* pos, int64_t n, uint64_t* keys_ou
     ffk::load3<float, float>(pos, n, rec, s);
     // keys and values are built directly in the caller's outputs, which the
     // eight-pass sort leaves holding the sorted data
-    ffk::morton_keys<float>(rec, n, bb, keys_out, order_out, flags, s);
+    ffk::morton_keys<float>(rec, n, bb, keys_out, order_out, flags, ffk::Segs(), s);
     ffk::radix_sort_pairs(keys_out, order_out, k1, v1, n, rtmp, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(FF_ECUDA, "kernel launch", e);

@@ -49,6 +49,16 @@ struct BBox {
     long long hi[3];
 };
 
+// Independent systems advanced together (batched ensembles).  System s owns
+// the fixed positions [start[s], start[s+1]) of the particle order at all
+// times (keys are sorted within each system), has its own root cube, tree,
+// applied field and box.  A single system is described by null pointers.
+struct Segs {
+    const uint32_t* of_pos = nullptr;  // system of each position (n entries)
+    const int* start = nullptr;        // nseg + 1 position offsets
+    int nseg = 1;
+};
+
 // Field evaluation parameters in the arithmetic type.
 template <typename R>
 struct FieldParams {
@@ -76,6 +86,13 @@ struct DynParams {
     int walls;
     uint32_t key0, key1;                 // Philox key (seed)
     const unsigned long long* step;      // device word: the step counter
+    // batched ensembles (null for a single system): per-system applied field
+    // and wall planes, system of each position, per-system sums of u and h_dip_z
+    const vec4<R>* sys_h;                // nseg records: h_ext xyz
+    const vec4<R>* sys_lo;               // nseg records: box_lo - 1/2
+    const vec4<R>* sys_hi;               // nseg records: box_hi + 1/2
+    const uint32_t* sys_of_pos;
+    double* sys_acc;                     // nseg x 4 (u_x, u_y, u_z, h_dip_z), accumulated
 };
 
 // What the traversal reads for every visited cell, in one record (32 bytes
@@ -111,9 +128,15 @@ size_t radix_tmp_words(int64_t n);
 void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
                       uint32_t* tmp, cudaStream_t s);
 
+// bb holds one root cube per system.
 template <typename R>
 void morton_keys(const vec4<R>* pos, int64_t n, BBox* bb, uint64_t* keys, uint32_t* vals,
-                 int* flags, cudaStream_t s);
+                 int* flags, Segs sg, cudaStream_t s);
+
+// Stable passes on the system of each element (the element's value is its
+// position before the sort), restoring system-major order after the key passes.
+void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                        uint32_t* tmp, Segs sg, cudaStream_t s);
 
 template <typename R>
 void gather_state(const uint32_t* perm, int64_t n, const vec4<R>* pos, const vec4<R>* vel,
@@ -123,7 +146,8 @@ void gather_state(const uint32_t* perm, int64_t n, const vec4<R>* pos, const vec
 // Tree build from sorted keys: cnt/off are n+1 words of scratch.
 template <typename R>
 void build_tree(const uint64_t* skeys, int64_t n, int leaf_max, const BBox* bb, Tree<R> t,
-                uint32_t* cnt, uint32_t* off, uint32_t* scan_tmp, int* flags, cudaStream_t s);
+                uint32_t* cnt, uint32_t* off, uint32_t* scan_tmp, int* flags, Segs sg,
+                cudaStream_t s);
 
 template <typename R>
 void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint32_t* cnt,
@@ -133,10 +157,12 @@ void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint3
 // group = lanes that walk the cell list together (1, 2, 4, 8, 16 or 32);
 // work = kWorkSegments task counters (scratch, zeroed by the launcher).
 constexpr int kWorkSegments = 1024;
+// off = the build's cell offsets (the first cell of position p is off[p]);
+// with several systems a particle walks only its own system's cells.
 template <typename R>
 void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
               vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
-              cudaStream_t s);
+              const uint32_t* off, Segs sg, cudaStream_t s);
 
 // All-pairs sum (Sec. 3.1, Algorithm 1).
 template <typename R>

@@ -146,7 +146,8 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
                                         const vec4<R>* __restrict__ u, int n, const Tree<R>& t,
                                         const FieldParams<R>& fp, unsigned ncells,
                                         vec4<R>* __restrict__ h, vec4<R>* __restrict__ f,
-                                        R* __restrict__ esr, int4* __restrict__ counts, int* flags)
+                                        R* __restrict__ esr, int4* __restrict__ counts, int* flags,
+                                        const uint32_t* __restrict__ off, const Segs& sg)
 {
     const int lane = threadIdx.x & 31;
     const int k = task * 32 + lane;
@@ -161,7 +162,14 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
     }
     R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0;
     int nacc = 0, npair = 0, nopen = 0;
-    unsigned nxt = active ? 0u : 0xffffffffu;
+    // the cells of this particle's system: [first, end)
+    unsigned first = 0, end = ncells;
+    if (sg.of_pos && active) {
+        const int sys = (int)sg.of_pos[k];
+        first = off[sg.start[sys]];
+        end = off[sg.start[sys + 1]];
+    }
+    unsigned nxt = active && first < end ? first : 0xffffffffu;
     for (;;) {
         const unsigned i = group_min<G>(nxt);
         if (G == 32) {
@@ -219,6 +227,7 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
                 atomicOr(flags, FLAG_TRAVERSE);
                 nxt = 0xffffffffu;
             }
+            if (nxt >= end) nxt = 0xffffffffu;  // this lane's system is done
         }
     }
     if (!active) return;
@@ -244,7 +253,8 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
                                          const vec4<R>* __restrict__ u, int n, const Tree<R>& t,
                                          const FieldParams<R>& fp, unsigned ncells,
                                          vec4<R>* __restrict__ h, vec4<R>* __restrict__ f,
-                                         R* __restrict__ esr, int4* __restrict__ counts, int* flags)
+                                         R* __restrict__ esr, int4* __restrict__ counts, int* flags,
+                                         const uint32_t* __restrict__ off, const Segs& sg)
 {
     const int lane = threadIdx.x & 31;
     const int k = task * 32 + lane;
@@ -252,8 +262,14 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
     const vec4<R> xk = pos[k], uk = u[k];
     R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0;
     int nacc = 0, npair = 0, nopen = 0;
-    unsigned i = 0;
-    while (i < ncells) {
+    // the cells of this particle's system: [i, end)
+    unsigned i = 0, end = ncells;
+    if (sg.of_pos) {
+        const int sys = (int)sg.of_pos[k];
+        i = off[sg.start[sys]];
+        end = off[sg.start[sys + 1]];
+    }
+    while (i < end) {
         const Cell<R> cl = t.cell[i];
 #if FFK_HOIST_MOMENT
         // requested with the cell so that one latency covers both loads
@@ -334,7 +350,8 @@ __global__ void __launch_bounds__(128, 12) k_bh(const vec4<R>* __restrict__ pos,
                                             FieldParams<R> fp, vec4<R>* __restrict__ h,
                                             vec4<R>* __restrict__ f, R* __restrict__ esr,
                                             int4* __restrict__ counts, int* flags,
-                                            int* __restrict__ work, int nseg)
+                                            int* __restrict__ work, int nseg,
+                                            const uint32_t* __restrict__ off, Segs sg)
 {
     if (*flags & FLAG_CAPACITY) return;
     const unsigned ncells = (unsigned)*t.ncells;
@@ -344,19 +361,21 @@ __global__ void __launch_bounds__(128, 12) k_bh(const vec4<R>* __restrict__ pos,
     const int home = (int)(smid % (unsigned)nseg);
     const int lane = threadIdx.x & 31;
     for (int probe = 0; probe < nseg; ++probe) {
-        const int sg = (home + probe) % nseg;
-        const int t0 = (int)((int64_t)ntask * sg / nseg);
-        const int t1 = (int)((int64_t)ntask * (sg + 1) / nseg);
+        const int ws = (home + probe) % nseg;
+        const int t0 = (int)((int64_t)ntask * ws / nseg);
+        const int t1 = (int)((int64_t)ntask * (ws + 1) / nseg);
         for (;;) {
             int got = 0;
-            if (lane == 0) got = atomicAdd(&work[sg], 1);
+            if (lane == 0) got = atomicAdd(&work[ws], 1);
             got = __shfl_sync(kFull, got, 0);
             const int task = t0 + got;
             if (task >= t1) break;
             if (G == 1)
-                bh_task1<R, COUNT>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags);
+                bh_task1<R, COUNT>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags, off,
+                                   sg);
             else
-                bh_task<R, COUNT, G>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags);
+                bh_task<R, COUNT, G>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags, off,
+                                     sg);
         }
     }
 }
@@ -434,7 +453,7 @@ __global__ void __launch_bounds__(kApThreads) k_ap(const vec4<R>* __restrict__ p
 template <typename R, bool COUNT, int G>
 void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
                  vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work,
-                 cudaStream_t s)
+                 const uint32_t* off, Segs sg, cudaStream_t s)
 {
     // persistent grid: as many blocks as fit on the device at once; a small
     // shared-memory carveout (the kernel uses none) leaves the rest to L1
@@ -454,33 +473,35 @@ void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, Fie
     }
     cudaMemsetAsync(work, 0, sizeof(int) * nsm, s);
     k_bh<R, COUNT, G><<<blocks, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags, work,
-                                             nsm);
+                                             nsm, off, sg);
 }
 
 template <typename R, bool COUNT>
 void bh_launch(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
                vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
-               cudaStream_t s)
+               const uint32_t* off, Segs sg, cudaStream_t s)
 {
+#define FFK_BH_CASE(G) bh_launch_g<R, COUNT, G>(pos, u, n, t, fp, h, f, esr, counts, flags, work, off, sg, s)
     switch (group) {
-        case 1: bh_launch_g<R, COUNT, 1>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
-        case 2: bh_launch_g<R, COUNT, 2>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
-        case 4: bh_launch_g<R, COUNT, 4>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
-        case 8: bh_launch_g<R, COUNT, 8>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
-        case 16: bh_launch_g<R, COUNT, 16>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
-        default: bh_launch_g<R, COUNT, 32>(pos, u, n, t, fp, h, f, esr, counts, flags, work, s); break;
+        case 1: FFK_BH_CASE(1); break;
+        case 2: FFK_BH_CASE(2); break;
+        case 4: FFK_BH_CASE(4); break;
+        case 8: FFK_BH_CASE(8); break;
+        case 16: FFK_BH_CASE(16); break;
+        default: FFK_BH_CASE(32); break;
     }
+#undef FFK_BH_CASE
 }
 
 template <typename R>
 void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
               vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
-              cudaStream_t s)
+              const uint32_t* off, Segs sg, cudaStream_t s)
 {
     if (counts)
-        bh_launch<R, true>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, s);
+        bh_launch<R, true>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, off, sg, s);
     else
-        bh_launch<R, false>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, s);
+        bh_launch<R, false>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, off, sg, s);
     counted();
 }
 
@@ -495,10 +516,10 @@ void ap_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, FieldParams<R> fp
 
 template void bh_field<float>(const float4*, const float4*, int64_t, Tree<float>,
                               FieldParams<float>, float4*, float4*, float*, int4*, int*, int*,
-                              int, cudaStream_t);
+                              int, const uint32_t*, Segs, cudaStream_t);
 template void bh_field<double>(const dvec4*, const dvec4*, int64_t, Tree<double>,
                                FieldParams<double>, dvec4*, dvec4*, double*, int4*, int*, int*,
-                               int, cudaStream_t);
+                               int, const uint32_t*, Segs, cudaStream_t);
 template void ap_field<float>(const float4*, const float4*, int64_t, FieldParams<float>, float4*,
                               float4*, float*, cudaStream_t);
 template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<double>, dvec4*,

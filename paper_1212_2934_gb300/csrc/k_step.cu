@@ -78,14 +78,67 @@ __device__ __forceinline__ R wall_force(R w, const DynParams<R>& dp, R& e)
     return dp.wall_eps24 * (s6 * s6 - s6) / w;
 }
 
+// Wall planes and applied field of the system owning position s.
 template <typename R>
-__device__ __forceinline__ void walls3(const DynParams<R>& dp, const vec4<R>& x, R& fx, R& fy,
-                                       R& fz, R& e)
+struct Local {
+    R lo[3], hi[3], hx, hy, hz;
+    int sys;
+};
+
+template <typename R>
+__device__ __forceinline__ Local<R> local_of(const DynParams<R>& dp, int64_t s)
+{
+    Local<R> L;
+    if (dp.sys_of_pos) {
+        L.sys = (int)dp.sys_of_pos[s];
+        const vec4<R> a = dp.sys_lo[L.sys], b = dp.sys_hi[L.sys], h = dp.sys_h[L.sys];
+        L.lo[0] = a.x; L.lo[1] = a.y; L.lo[2] = a.z;
+        L.hi[0] = b.x; L.hi[1] = b.y; L.hi[2] = b.z;
+        L.hx = h.x; L.hy = h.y; L.hz = h.z;
+    } else {
+        L.sys = -1;
+        for (int q = 0; q < 3; ++q) {
+            L.lo[q] = dp.lo[q];
+            L.hi[q] = dp.hi[q];
+        }
+        L.hx = dp.hx; L.hy = dp.hy; L.hz = dp.hz;
+    }
+    return L;
+}
+
+template <typename R>
+__device__ __forceinline__ void walls3(const DynParams<R>& dp, const Local<R>& L, const vec4<R>& x,
+                                       R& fx, R& fy, R& fz, R& e)
 {
     if (!dp.walls) return;
-    fx += wall_force<R>(x.x - dp.lo[0], dp, e) - wall_force<R>(dp.hi[0] - x.x, dp, e);
-    fy += wall_force<R>(x.y - dp.lo[1], dp, e) - wall_force<R>(dp.hi[1] - x.y, dp, e);
-    fz += wall_force<R>(x.z - dp.lo[2], dp, e) - wall_force<R>(dp.hi[2] - x.z, dp, e);
+    fx += wall_force<R>(x.x - L.lo[0], dp, e) - wall_force<R>(L.hi[0] - x.x, dp, e);
+    fy += wall_force<R>(x.y - L.lo[1], dp, e) - wall_force<R>(L.hi[1] - x.y, dp, e);
+    fz += wall_force<R>(x.z - L.lo[2], dp, e) - wall_force<R>(L.hi[2] - x.z, dp, e);
+}
+
+// Adds u and h_dip_z of one particle to its system's sums (warp-aggregated
+// when every active lane belongs to the same system).
+template <typename R>
+__device__ __forceinline__ void system_acc(const DynParams<R>& dp, int sys, const vec4<R>& uu,
+                                           R hdz)
+{
+    const unsigned am = __activemask();
+    const int s0 = __shfl_sync(am, sys, __ffs(am) - 1);
+    R v[4] = {uu.x, uu.y, uu.z, hdz};
+    if (am == kFull && __all_sync(kFull, sys == s0)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(kFull, v[q], o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) atomicAdd(&dp.sys_acc[4 * sys + q], (double)v[q]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) atomicAdd(&dp.sys_acc[4 * sys + q], (double)v[q]);
+    }
 }
 
 // Block sum of kObs per-thread values: warp sums in the arithmetic type R
@@ -117,12 +170,12 @@ __device__ __forceinline__ void block_sum_obs(R v[kObs], double* out)
 // Accumulates one particle's terms: e_dip, e_zeeman, e_sr, e_wall, e_kin_t,
 // w^2 (scaled by I/2 later), u (3), h_dip_z.
 template <typename R>
-__device__ __forceinline__ void obs_terms(R v[kObs], const DynParams<R>& dp, const vec4<R>& uu,
+__device__ __forceinline__ void obs_terms(R v[kObs], const Local<R>& L, const vec4<R>& uu,
                                           const vec4<R>& hd, const vec4<R>& vv, const vec4<R>& w,
                                           R es, R ew)
 {
     v[0] += R(-0.5) * (uu.x * hd.x + uu.y * hd.y + uu.z * hd.z);
-    v[1] += -(uu.x * dp.hx + uu.y * dp.hy + uu.z * dp.hz);
+    v[1] += -(uu.x * L.hx + uu.y * L.hy + uu.z * L.hz);
     v[2] += es;
     v[3] += ew;
     v[4] += R(0.5) * (vv.x * vv.x + vv.y * vv.y + vv.z * vv.z);
@@ -151,10 +204,11 @@ __global__ void __launch_bounds__(kStepThreads) k_integrate(
          s += (int64_t)gridDim.x * blockDim.x) {
         const vec4<R> x = pos[s], vv = vel[s], uu = u[s], w = om[s], hd = hdip[s], fi = fint[s];
         const uint32_t pid = id[s];
+        const Local<R> L = local_of<R>(dp, s);
         R ew = R(0);
         R fx = fi.x, fy = fi.y, fz = fi.z;
-        walls3<R>(dp, x, fx, fy, fz, ew);
-        const R hx = hd.x + dp.hx, hy = hd.y + dp.hy, hz = hd.z + dp.hz;
+        walls3<R>(dp, L, x, fx, fy, fz, ew);
+        const R hx = hd.x + L.hx, hy = hd.y + L.hy, hz = hd.z + L.hz;
         R z[6];
         normals6<R>(dp, pid, z);
         const R tx = uu.y * hz - uu.z * hy, ty = uu.z * hx - uu.x * hz, tz = uu.x * hy - uu.y * hx;
@@ -184,7 +238,8 @@ __global__ void __launch_bounds__(kStepThreads) k_integrate(
         u2[s] = un;
         om2[s] = wn;
         id2[s] = pid;
-        if (OBS) obs_terms<R>(v, dp, uu, hd, vv, w, esr ? esr[s] : R(0), ew);
+        if (OBS) obs_terms<R>(v, L, uu, hd, vv, w, esr ? esr[s] : R(0), ew);
+        if (dp.sys_acc) system_acc<R>(dp, L.sys, uu, hd.z);
     }
     if (OBS) block_sum_obs<R>(v, partials + (int64_t)blockIdx.x * kObs);
 }
@@ -202,10 +257,11 @@ __global__ void __launch_bounds__(kStepThreads) k_observables(
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
         const vec4<R> x = pos[s];
+        const Local<R> L = local_of<R>(dp, s);
         R ew = R(0);
         R fx = 0, fy = 0, fz = 0;
-        walls3<R>(dp, x, fx, fy, fz, ew);
-        obs_terms<R>(v, dp, u[s], hdip[s], vel[s], om[s], esr ? esr[s] : R(0), ew);
+        walls3<R>(dp, L, x, fx, fy, fz, ew);
+        obs_terms<R>(v, L, u[s], hdip[s], vel[s], om[s], esr ? esr[s] : R(0), ew);
     }
     block_sum_obs<R>(v, partials + (int64_t)blockIdx.x * kObs);
 }

@@ -112,7 +112,19 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t n,
 }
 
 // ------------------------------------------------------------ radix sort
-__global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+// Digit of element i: bits [shift, shift + 8) of its key or, in a system pass
+// (sys != null), of the system that owned the element's pre-sort position.
+__device__ __forceinline__ uint32_t radix_digit(const uint64_t* __restrict__ keys,
+                                                const uint32_t* __restrict__ vals,
+                                                const uint32_t* __restrict__ sys, int64_t i,
+                                                int shift)
+{
+    if (sys) return (sys[vals[i]] >> shift) & (kRadixBins - 1);
+    return (uint32_t)((keys[i] >> shift) & (kRadixBins - 1));
+}
+
+__global__ void k_radix_hist(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                             const uint32_t* __restrict__ sys, int64_t n, int shift,
                              uint32_t* __restrict__ hist, int64_t nb)
 {
     __shared__ uint32_t h[kRadixBins];
@@ -122,7 +134,7 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int s
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t i = base + r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kRadixBins - 1)], 1u);
+        if (i < n) atomicAdd(&h[radix_digit(keys, vals, sys, i, shift)], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
@@ -131,9 +143,9 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int s
 // Stable scatter: within a tile, keys keep their index order; ranks among
 // equal digits come from warp match masks and per-warp digit counts.
 __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                int64_t n, int shift, const uint32_t* __restrict__ offs,
-                                int64_t nb)
+                                const uint32_t* __restrict__ sys, uint64_t* __restrict__ kout,
+                                uint32_t* __restrict__ vout, int64_t n, int shift,
+                                const uint32_t* __restrict__ offs, int64_t nb)
 {
     __shared__ uint32_t s_base[kRadixBins];
     __shared__ uint32_t s_w[kSortThreads / 32][kRadixBins];
@@ -148,7 +160,7 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t
         const int64_t i = base + r * kSortThreads + t;
         const bool valid = i < n;
         uint64_t key = valid ? kin[i] : 0ull;
-        uint32_t d = valid ? (uint32_t)((key >> shift) & (kRadixBins - 1)) : (uint32_t)kRadixBins;
+        uint32_t d = valid ? radix_digit(kin, vin, sys, i, shift) : (uint32_t)kRadixBins;
         const uint32_t peers = __match_any_sync(kFull, d);
         const uint32_t rank = __popc(peers & lt);
         if (valid && rank == 0) s_w[w][d] = __popc(peers);
@@ -210,6 +222,54 @@ __global__ void k_bbox_init(BBox* bb)
     for (int a = 0; a < 3; ++a) {
         bb->lo[a] = LLONG_MAX;
         bb->hi[a] = LLONG_MIN;
+    }
+}
+
+// One block per system: extrema of the positions [start[s], start[s+1]).
+template <typename R>
+__global__ void k_bbox_seg(const vec4<R>* __restrict__ pos, const int* __restrict__ start,
+                           BBox* bb, int* flags)
+{
+    const int sgi = blockIdx.x;
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
+    long long hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    bool bad = false;
+    for (int64_t i = start[sgi] + threadIdx.x; i < start[sgi + 1]; i += blockDim.x) {
+        vec4<R> p = pos[i];
+        R c[3] = {p.x, p.y, p.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bad |= !isfinite(c[a]);
+            long long e = enc(c[a]);
+            lo[a] = min(lo[a], e);
+            hi[a] = max(hi[a], e);
+        }
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, FLAG_NONFINITE);
+    __shared__ long long sl[3][32], sh[3][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(kFull, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(kFull, hi[a], o));
+        }
+        if (lane == 0) {
+            sl[a][w] = lo[a];
+            sh[a][w] = hi[a];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int a = threadIdx.x;
+        long long l = LLONG_MAX, h = LLONG_MIN;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
+            l = min(l, sl[a][ww]);
+            h = max(h, sh[a][ww]);
+        }
+        bb[sgi].lo[a] = l;
+        bb[sgi].hi[a] = h;
     }
 }
 
@@ -302,12 +362,13 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x)
 
 template <typename R>
 __global__ void k_morton(const vec4<R>* __restrict__ pos, int64_t n, const BBox* __restrict__ bb,
-                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                         const uint32_t* __restrict__ of_pos)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     R mn[3], side;
-    root_cube<R>(bb, mn, &side);
+    root_cube<R>(of_pos ? bb + of_pos[i] : bb, mn, &side);
     const R S = rdiv(R(2097152), side);
     vec4<R> p = pos[i];
     uint32_t qx = quantise<R>(p.x, mn[0], S);
@@ -338,9 +399,11 @@ __global__ void k_gather(const uint32_t* __restrict__ perm, int64_t n,
 // ------------------------------------------------------------ tree build
 // Split level of sorted position j: the first level at which particles j-1
 // and j fall in different cells (0 for j = 0 and j = n; 22 for equal keys).
-__device__ __forceinline__ int split_level(const uint64_t* __restrict__ k, int64_t j, int64_t n)
+__device__ __forceinline__ int split_level(const uint64_t* __restrict__ k, int64_t j, int64_t n,
+                                           const uint32_t* __restrict__ of_pos)
 {
     if (j <= 0 || j >= n) return 0;
+    if (of_pos && of_pos[j] != of_pos[j - 1]) return 0;  // first particle of a system
     uint64_t x = k[j] ^ k[j - 1];
     if (!x) return kMaxLevel + 1;
     return (__clzll((long long)x) - 1) / 3 + 1;
@@ -351,21 +414,21 @@ __device__ __forceinline__ int split_level(const uint64_t* __restrict__ k, int64
 // than m particles iff some a + b = m has the a positions i, i-1, ..
 // i-a+1 and the b positions i+1 .. i+b all with split level > L.
 __global__ void k_levels(const uint64_t* __restrict__ k, int64_t n, int m,
-                         uint32_t* __restrict__ cnt)
+                         uint32_t* __restrict__ cnt, const uint32_t* __restrict__ of_pos)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int right[kMaxLeaf + 1];
     right[0] = 99;
-    for (int b = 1; b <= m; ++b) right[b] = min(right[b - 1], split_level(k, i + b, n));
+    for (int b = 1; b <= m; ++b) right[b] = min(right[b - 1], split_level(k, i + b, n, of_pos));
     int left = 99;
     int D = min(left, right[m]);
     for (int a = 1; a <= m; ++a) {
-        left = min(left, split_level(k, i - a + 1, n));
+        left = min(left, split_level(k, i - a + 1, n, of_pos));
         D = max(D, min(left, right[m - a]));
     }
     const int d = min(D, kMaxLevel);
-    const int li = split_level(k, i, n);
+    const int li = split_level(k, i, n, of_pos);
     cnt[i] = d >= li ? (uint32_t)(d - li + 1) : 0u;
 }
 
@@ -389,14 +452,14 @@ __device__ __forceinline__ int64_t gallop_right(const uint64_t* __restrict__ k, 
     return hi;
 }
 
-// First j in [0, hi] with k[j] >= bound, given k[hi] >= bound.
+// First j in [first, hi] with k[j] >= bound, given k[hi] >= bound.
 __device__ __forceinline__ int64_t gallop_left(const uint64_t* __restrict__ k, int64_t hi,
-                                               uint64_t bound)
+                                               uint64_t bound, int64_t first)
 {
-    int64_t lo = -1, step = 1;
+    int64_t lo = first - 1, step = 1;
     for (;;) {
         int64_t c = hi - step;
-        if (c < 0) break;
+        if (c < first) break;
         if (k[c] < bound) {
             lo = c;
             break;
@@ -419,13 +482,17 @@ __device__ __forceinline__ int64_t gallop_left(const uint64_t* __restrict__ k, i
 template <typename R>
 __global__ void k_emit(const uint64_t* __restrict__ k, int64_t n, const uint32_t* __restrict__ cnt,
                        const uint32_t* __restrict__ off, const BBox* __restrict__ bb, Tree<R> t,
-                       int* flags)
+                       int* flags, Segs sg)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int c = (int)cnt[i];
     if (c == 0) return;
-    const int li = split_level(k, i, n);
+    const int li = split_level(k, i, n, sg.of_pos);
+    // the positions of i's system: runs and parents never leave them
+    const int sys = sg.of_pos ? (int)sg.of_pos[i] : 0;
+    const int64_t sfirst = sg.of_pos ? sg.start[sys] : 0;
+    const int64_t send = sg.of_pos ? sg.start[sys + 1] : n;
     const int d = li + c - 1;
     const int64_t base = off[i];
     if (base + c > t.cap || (int64_t)off[n] > t.cap) {
@@ -433,17 +500,17 @@ __global__ void k_emit(const uint64_t* __restrict__ k, int64_t n, const uint32_t
         return;
     }
     R mn[3], side;
-    root_cube<R>(bb, mn, &side);
+    root_cube<R>(bb + sys, mn, &side);
     const uint64_t key = k[i];
     int64_t pe = i + 1;
     for (int L = d; L >= li; --L) {
         const int64_t idx = base + (L - li);
         if (L == 0) {
-            pe = n;
+            pe = send;
         } else {
             const int sh = 3 * (kMaxLevel - L);
             const uint64_t bound = ((key >> sh) + 1ull) << sh;
-            pe = gallop_right(k, pe, n, bound);
+            pe = gallop_right(k, pe, send, bound);
         }
         const int skip = (int)off[pe];
         const int leaf = (L == d) ? 1 : 0;
@@ -456,8 +523,8 @@ __global__ void k_emit(const uint64_t* __restrict__ k, int64_t n, const uint32_t
         } else {
             const int sh2 = 3 * (kMaxLevel - (L - 1));
             const uint64_t lowb = (key >> sh2) << sh2;
-            const int64_t s = gallop_left(k, i, lowb);
-            parent = (int)off[s] + (L - 1 - split_level(k, s, n));
+            const int64_t s = gallop_left(k, i, lowb, sfirst);
+            parent = (int)off[s] + (L - 1 - split_level(k, s, n, sg.of_pos));
         }
         t.parent[idx] = parent;
         t.arrive[idx] = 0;
@@ -600,9 +667,10 @@ void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, in
     uint64_t* kb = k1;
     uint32_t* vb = v1;
     for (int shift = 0; shift < 64; shift += kRadixBits) {
-        k_radix_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, n, shift, hist, nb);
+        k_radix_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, n, shift, hist, nb);
         scan_exclusive(hist, offs, h, stmp, s);
-        k_radix_scatter<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, offs, nb);
+        k_radix_scatter<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, kb, vb, n, shift,
+                                                                offs, nb);
         counted(2);
         uint64_t* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
@@ -610,16 +678,52 @@ void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, in
     // eight passes: the sorted data are back in (k0, v0)
 }
 
+void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                        uint32_t* tmp, Segs sg, cudaStream_t s)
+{
+    if (!sg.of_pos || sg.nseg <= 1 || n <= 1) return;
+    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    const int64_t h = (int64_t)kRadixBins * nb;
+    uint32_t* hist = tmp;
+    uint32_t* offs = tmp + h;
+    uint32_t* stmp = offs + h + 1;
+    // an even number of passes leaves the data in (k0, v0); the value of each
+    // element stays its pre-sort position, so its system is of_pos[value]
+    int passes = 0;
+    for (int b = 0; (1 << b) < sg.nseg; b += kRadixBits) ++passes;
+    if (passes & 1) ++passes;
+    uint64_t* ka = k0;
+    uint32_t* va = v0;
+    uint64_t* kb = k1;
+    uint32_t* vb = v1;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * kRadixBits;
+        k_radix_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, sg.of_pos, n, shift, hist, nb);
+        scan_exclusive(hist, offs, h, stmp, s);
+        k_radix_scatter<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, sg.of_pos, kb, vb, n, shift,
+                                                                offs, nb);
+        counted(2);
+        uint64_t* tk = ka; ka = kb; kb = tk;
+        uint32_t* tv = va; va = vb; vb = tv;
+    }
+}
+
 template <typename R>
 void morton_keys(const vec4<R>* pos, int64_t n, BBox* bb, uint64_t* keys, uint32_t* vals,
-                 int* flags, cudaStream_t s)
+                 int* flags, Segs sg, cudaStream_t s)
 {
-    k_bbox_init<<<1, 1, 0, s>>>(bb);
-    unsigned g = nblk(n, 256);
-    if (g > 152u * 8u) g = 152u * 8u;
-    k_bbox<R><<<g, 256, 0, s>>>(pos, n, bb, flags);
-    k_morton<R><<<nblk(n, 256), 256, 0, s>>>(pos, n, bb, keys, vals);
-    counted(3);
+    if (sg.of_pos) {
+        k_bbox_seg<R><<<sg.nseg, 256, 0, s>>>(pos, sg.start, bb, flags);
+        counted();
+    } else {
+        k_bbox_init<<<1, 1, 0, s>>>(bb);
+        unsigned g = nblk(n, 256);
+        if (g > 152u * 8u) g = 152u * 8u;
+        k_bbox<R><<<g, 256, 0, s>>>(pos, n, bb, flags);
+        counted(2);
+    }
+    k_morton<R><<<nblk(n, 256), 256, 0, s>>>(pos, n, bb, keys, vals, sg.of_pos);
+    counted();
 }
 
 template <typename R>
@@ -634,11 +738,12 @@ void gather_state(const uint32_t* perm, int64_t n, const vec4<R>* pos, const vec
 
 template <typename R>
 void build_tree(const uint64_t* skeys, int64_t n, int leaf_max, const BBox* bb, Tree<R> t,
-                uint32_t* cnt, uint32_t* off, uint32_t* scan_tmp, int* flags, cudaStream_t s)
+                uint32_t* cnt, uint32_t* off, uint32_t* scan_tmp, int* flags, Segs sg,
+                cudaStream_t s)
 {
-    k_levels<<<nblk(n, 128), 128, 0, s>>>(skeys, n, leaf_max, cnt);
+    k_levels<<<nblk(n, 128), 128, 0, s>>>(skeys, n, leaf_max, cnt, sg.of_pos);
     scan_exclusive(cnt, off, n, scan_tmp, s);
-    k_emit<R><<<nblk(n, 128), 128, 0, s>>>(skeys, n, cnt, off, bb, t, flags);
+    k_emit<R><<<nblk(n, 128), 128, 0, s>>>(skeys, n, cnt, off, bb, t, flags, sg);
     counted(2);
 }
 
@@ -652,12 +757,12 @@ void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint3
 
 #define FFK_INST(R)                                                                            \
     template void morton_keys<R>(const vec4<R>*, int64_t, BBox*, uint64_t*, uint32_t*, int*,   \
-                                 cudaStream_t);                                                \
+                                 Segs, cudaStream_t);                                          \
     template void gather_state<R>(const uint32_t*, int64_t, const vec4<R>*, const vec4<R>*,     \
                                   const vec4<R>*, const vec4<R>*, const uint32_t*, vec4<R>*,   \
                                   vec4<R>*, vec4<R>*, vec4<R>*, uint32_t*, cudaStream_t);      \
     template void build_tree<R>(const uint64_t*, int64_t, int, const BBox*, Tree<R>, uint32_t*, \
-                                uint32_t*, uint32_t*, int*, cudaStream_t);                     \
+                                uint32_t*, uint32_t*, int*, Segs, cudaStream_t);               \
     template void aggregate_tree<R>(const vec4<R>*, const vec4<R>*, int64_t, const uint32_t*,   \
                                     const uint32_t*, Tree<R>, int*, cudaStream_t);
 FFK_INST(float)

@@ -86,6 +86,8 @@ _SIGS = {
     "ff_tree_info": (_st, [_vp, C.POINTER(ff_tree_info_t)]),
     "ff_get_tree": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int32]),
     "ff_get_counts": (_st, [_vp, _vp, _vp, _vp]),
+    "ff_set_systems": (_st, [_vp, C.c_int32, _vp, _vp, _vp, _vp]),
+    "ff_system_moments": (_st, [_vp, _vp, C.POINTER(C.c_int64), C.c_int32]),
     "ff_profile": (_st, [_vp, C.c_int32]),
     "ff_profile_read": (_st, [_vp, C.POINTER(ff_profile_t)]),
     "ff_morton_order_noalloc": (_st, [_vp, C.c_int64, _vp, _vp, _vp]),
@@ -303,6 +305,35 @@ def ff_get_counts(ctx):
     p = lambda x: C.c_void_p(x.ctypes.data)
     _check(ctx.handle, lib().ff_get_counts(ctx.handle, p(a), p(b), p(c)))
     return a, b, c
+
+
+def ff_set_systems(ctx, counts, h_ext=None, box_lo=None, box_hi=None):
+    """Batched ensembles: consecutive particle ranges of the given counts become independent
+    systems with per-system applied fields and boxes ((nsys, 3) arrays or None)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    nsys = counts.shape[0]
+
+    def arr(a):
+        if a is None:
+            return None, None
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(nsys, 3)
+        return C.c_void_p(a.ctypes.data), a
+
+    ph, kh = arr(h_ext)
+    pl, kl = arr(box_lo)
+    pu, ku = arr(box_hi)
+    _check(ctx.handle, lib().ff_set_systems(ctx.handle, nsys, C.c_void_p(counts.ctypes.data),
+                                            ph, pl, pu))
+    ctx.nsys = nsys
+
+
+def ff_system_moments(ctx, reset=False):
+    """(sums (nsys, 4): u_x, u_y, u_z, h_dip_z summed over steps and particles, steps)."""
+    out = np.zeros((ctx.nsys, 4))
+    st = C.c_int64()
+    _check(ctx.handle, lib().ff_system_moments(ctx.handle, C.c_void_p(out.ctypes.data),
+                                               C.byref(st), int(bool(reset))))
+    return out, st.value
 
 
 def ff_profile(ctx, enable=True):
