@@ -209,6 +209,7 @@ ffk::FieldParams<R> field_params(const ff_ctx* c, double theta, int include_sr)
     fp.dip_scale = (R)p.dip_scale;
     fp.lj_eps24 = (R)(24.0 * p.lj_eps);
     fp.lj_sigma2 = (R)(p.lj_sigma * p.lj_sigma);
+    fp.lj_sigma2_lo = (R)(p.lj_sigma * p.lj_sigma - (double)fp.lj_sigma2);
     fp.lj_rcut2 = (R)(p.lj_rcut * p.lj_rcut);
     fp.lj_rcut2_hi = (R)((double)fp.lj_rcut2 * (sizeof(R) == 4 ? 1.0 + 1e-5 : 1.0 + 1e-12));
     fp.lj_e2 = (R)(2.0 * p.lj_eps);

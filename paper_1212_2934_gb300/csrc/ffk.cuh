@@ -67,7 +67,8 @@ struct FieldParams {
     R rcut;          // lj_rcut (0 when LJ is off)
     R dip_scale;
     R lj_eps24;      // 24 eps
-    R lj_sigma2;     // sigma^2
+    R lj_sigma2;     // sigma^2 rounded to R
+    R lj_sigma2_lo;  // sigma^2 - lj_sigma2 (the FP32 pair's low part; 0 in FP64)
     R lj_rcut2;      // rcut^2: the pair cut (decided on an exactly rounded r^2)
     R lj_rcut2_hi;   // slightly above lj_rcut2: pre-test on a fused r^2
     R lj_e2, lj_e4;  // 2 eps, 4 eps (pair energy)

@@ -57,28 +57,71 @@ __device__ __forceinline__ void dipole(R rx, R ry, R rz, R r2, R ukx, R uky, R u
     fz += rz * cr + ukz * cuk + ujz * cuj;
 }
 
+// Knuth's TwoSum: s + e == a + b exactly (no fused or reordered operations).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// sigma^2 - r^2 without the cancellation error of the rounded r^2.  In FP32
+// each square is split exactly into its rounded value and the remainder an fma
+// recovers, the rounded squares are added with TwoSum so that their rounding
+// errors are kept too, and sigma^2 enters as an unevaluated pair (hi, lo): the
+// result carries one final rounding relative to the difference itself.  In
+// FP64 the plain difference is accurate far beyond the parity bars.
+__device__ __forceinline__ float sigma2_minus_r2(const FieldParams<float>& fp, float rx, float ry,
+                                                 float rz)
+{
+    // streamed so that few temporaries are live at once: t gathers every
+    // rounding error, a the rounded sum of squares
+    float a = __fmul_rn(rx, rx);
+    float t = __fmaf_rn(rx, rx, -a);
+    float p = __fmul_rn(ry, ry);
+    t = __fadd_rn(t, __fmaf_rn(ry, ry, -p));
+    float e;
+    two_sum(a, p, a, e);
+    t = __fadd_rn(t, e);
+    p = __fmul_rn(rz, rz);
+    t = __fadd_rn(t, __fmaf_rn(rz, rz, -p));
+    two_sum(a, p, a, e);
+    t = __fadd_rn(t, e);
+    two_sum(fp.lj_sigma2, -a, a, e);
+    return __fadd_rn(a, __fsub_rn(__fadd_rn(e, fp.lj_sigma2_lo), t));
+}
+
+__device__ __forceinline__ double sigma2_minus_r2(const FieldParams<double>& fp, double rx, double ry,
+                                                  double rz)
+{
+    return fp.lj_sigma2 - (rx * rx + ry * ry + rz * rz);
+}
+
 // Printed LJ force (Sec. 2, Eq. LJ) inside the cut, and half the pair
 // energy 2 eps (s/r)^12 - 4 eps (s/r)^6 shifted to zero at the cut.  Whether
 // the pair is inside is decided on r^2 = (rx rx + ry ry) + rz rz with every
 // operation rounded once (r2 from the field code may carry fused rounding);
-// that exact value is formed only near the cut.
+// that exact value is formed only near the cut.  Near contact (r ~ sigma) the
+// bracket (s/r)^12 - (s/r)^6 is a small difference of two numbers near one, so
+// it is formed as s6 (s6 - 1) with s6 - 1 = (s2 - 1)(s2^2 + s2 + 1) and
+// s2 - 1 = (sigma^2 - r^2) / r^2.
 template <typename R>
 __device__ __forceinline__ void lj(const FieldParams<R>& fp, R rx, R ry, R rz, R r2, R& fx, R& fy,
                                    R& fz, R& e)
 {
     if (!(r2 < fp.lj_rcut2_hi)) return;
     const R r2e = radd(radd(rmul(rx, rx), rmul(ry, ry)), rmul(rz, rz));
-    if (r2e < fp.lj_rcut2 && r2e > R(0)) {
-        const R ir2 = R(1) / r2e;
-        const R s2 = fp.lj_sigma2 * ir2;
-        const R s6 = s2 * s2 * s2;
-        const R s12 = s6 * s6;
-        const R c = fp.lj_eps24 * (s12 - s6) * ir2;
-        fx += c * rx;
-        fy += c * ry;
-        fz += c * rz;
-        e += R(0.5) * (fp.lj_e2 * s12 - fp.lj_e4 * s6 - fp.lj_shift);
-    }
+    if (!(r2e < fp.lj_rcut2 && r2e > R(0))) return;
+    const R ir2 = R(1) / r2e;
+    const R s2m1 = sigma2_minus_r2(fp, rx, ry, rz) * ir2;
+    const R s2 = R(1) + s2m1;
+    const R s6 = s2 * s2 * s2;
+    const R s6m1 = s2m1 * (s2 * s2 + s2 + R(1));
+    const R c = fp.lj_eps24 * (s6 * s6m1) * ir2;
+    fx += c * rx;
+    fy += c * ry;
+    fz += c * rz;
+    e += R(0.5) * (fp.lj_e2 * s6 * s6 - fp.lj_e4 * s6 - fp.lj_shift);
 }
 
 // Opening test in the tree precision, each operation rounded once:
@@ -118,12 +161,28 @@ __device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& 
 }
 
 // Preferred shared-memory share of the traversal (percent of the maximum):
-// 7 % selects 16 KB, room for the per-block reservation of 12 resident
+// 7 % selects 16 KB, room for the per-block reservation of the resident
 // blocks; the rest of the unified storage serves as L1 cache.
 #ifndef FFK_TRAVERSE_CARVEOUT
 #define FFK_TRAVERSE_CARVEOUT 7
 #endif
 constexpr int kTraverseCarveout = FFK_TRAVERSE_CARVEOUT;
+
+// Traversal block shape: warps work independently (no shared memory, no
+// block barrier), so the block size only sets how registers and warps are
+// traded.  Registers are allocated per SM sub-partition (16384 each, a warp
+// taking 32 x its registers), so 128 x 10 allows 48 registers a thread, room
+// for the whole walk without spills; 128 x 12 (48 warps instead of 40) caps
+// it at 40 and spills, which costs more than the extra warps gain.
+#ifndef FFK_BH_THREADS
+#define FFK_BH_THREADS 128
+#endif
+#ifndef FFK_BH_MIN_BLOCKS
+#define FFK_BH_MIN_BLOCKS 10
+#endif
+constexpr int kBhThreads = FFK_BH_THREADS;
+constexpr int kBhMinBlocks = FFK_BH_MIN_BLOCKS;
+static_assert(kBhThreads % 32 == 0, "whole warps");
 
 // 1: the per-lane walk requests a cell's moment sum together with its record.
 #ifndef FFK_HOIST_MOMENT
@@ -345,7 +404,7 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
 // from the following segments once its own is used up.  Task counters
 // (work[0..nseg)) start at zero; every task is taken exactly once.
 template <typename R, bool COUNT, int G>
-__global__ void __launch_bounds__(128, 12) k_bh(const vec4<R>* __restrict__ pos,
+__global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh(const vec4<R>* __restrict__ pos,
                                             const vec4<R>* __restrict__ u, int n, Tree<R> t,
                                             FieldParams<R> fp, vec4<R>* __restrict__ h,
                                             vec4<R>* __restrict__ f, R* __restrict__ esr,
@@ -465,14 +524,14 @@ void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, Fie
         cudaFuncSetAttribute(k_bh<R, COUNT, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              kTraverseCarveout);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G>, kBhThreads, 0);
         if (per_sm < 1) per_sm = 1;
         if (nsm < 1) nsm = 1;
         if (nsm > kWorkSegments) nsm = kWorkSegments;
         blocks = per_sm * nsm;
     }
     cudaMemsetAsync(work, 0, sizeof(int) * nsm, s);
-    k_bh<R, COUNT, G><<<blocks, 128, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags, work,
+    k_bh<R, COUNT, G><<<blocks, kBhThreads, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags, work,
                                              nsm, off, sg);
 }
 

@@ -14,6 +14,9 @@ container, N from 1e3 to 1e6, volume fraction of a few per cent):
     hard-sphere Monte Carlo sweeps;
   * ``rsa_cube``    - random sequential addition with a hard core of 1.0 in
     a cube sized for a given volume fraction (cell-grid neighbour search);
+  * ``dilute_cubes`` / ``batched_ensembles`` - many dilute hard-core gases at
+    once (uniform centres, overlapping ones redrawn) for batched ensembles of
+    log-uniform sizes and a linear grid of applied fields;
   * ``isotropic_moments`` - unit moments from normalised Gaussian triples.
 Lengths are in units of the hard-core diameter.
 """
@@ -22,7 +25,8 @@ import math
 import numpy as np
 
 __all__ = ["box_side_for_fraction", "isotropic_moments", "rsa_cube", "dense_cube",
-           "uniform_cube", "chains_cube", "Ensemble", "make_ensemble"]
+           "uniform_cube", "chains_cube", "batched_sizes", "batched_ensembles", "Ensemble",
+           "make_ensemble"]
 
 
 def box_side_for_fraction(n: int, phi: float, diameter: float = 1.0) -> float:
@@ -212,6 +216,56 @@ def chains_cube(nchains: int, length: int, side: float, seed: int,
     pos = np.concatenate(placed)[: nchains * length]
     u = np.concatenate(placed_u)[: nchains * length]
     return pos, u
+
+
+def batched_sizes(nsys: int = 256, nmin: int = 1024, nmax: int = 65536):
+    """Deterministic log-uniform quantiles: N_i = round(nmin (nmax/nmin)^((i + 1/2) / nsys))."""
+    r = nmax / nmin
+    return np.array([int(round(nmin * r ** ((i + 0.5) / nsys))) for i in range(nsys)],
+                    dtype=np.int64)
+
+
+def dilute_cubes(sizes, sides, seed: int, dmin: float = 1.0, rounds: int = 200):
+    """Hard-core gases for many dilute systems at once: uniform centres in each
+    system's cube, then the later member of every pair closer than dmin is drawn
+    again until no such pair is left.  Systems are placed side by side along x
+    (gap > dmin) so one neighbour search serves them all.  Returns the
+    concatenated centres, each system in its own [0, side]^3."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng([seed, 0xD11E])
+    sizes = np.asarray(sizes, dtype=np.int64)
+    sides = np.asarray(sides, dtype=np.float64)
+    owner = np.repeat(np.arange(sizes.shape[0]), sizes)
+    shift = np.concatenate([[0.0], np.cumsum(sides + 2.0 * dmin)[:-1]])
+    side_of = sides[owner]
+    pos = rng.uniform(0.0, 1.0, (owner.shape[0], 3)) * side_of[:, None]
+    for _ in range(rounds):
+        glob = pos.copy()
+        glob[:, 0] += shift[owner]
+        pairs = cKDTree(glob).query_pairs(np.nextafter(dmin, 0.0), output_type="ndarray")
+        if pairs.size == 0:
+            return pos
+        redo = np.unique(np.maximum(pairs[:, 0], pairs[:, 1]))
+        pos[redo] = rng.uniform(0.0, 1.0, (redo.shape[0], 3)) * side_of[redo, None]
+    raise RuntimeError("dilute_cubes did not converge; the systems are too dense")
+
+
+def batched_ensembles(nsys: int = 256, phi: float = 0.02, hmax: float = 5.0, seed: int = 1):
+    """Independent dilute systems of log-uniform sizes with applied fields 0 .. hmax (along z)
+    on a linear grid, assigned to the sizes by a seeded permutation.  Returns dict with the
+    concatenated positions and moments, sizes, sides, fields (nsys, 3), box_lo, box_hi."""
+    sizes = batched_sizes(nsys)
+    amps = hmax * np.arange(nsys) / max(nsys - 1, 1)
+    perm = np.random.default_rng([seed, 0xF1E1D]).permutation(nsys)
+    fields = np.zeros((nsys, 3))
+    fields[:, 2] = amps[perm]
+    sides = np.array([box_side_for_fraction(int(n), phi) for n in sizes])
+    pos = dilute_cubes(sizes, sides, seed)
+    u = isotropic_moments(int(sizes.sum()), seed * 100003 + 7)
+    return dict(pos=pos, u=u, sizes=sizes, sides=sides,
+                fields=fields, box_lo=np.zeros((nsys, 3)),
+                box_hi=np.repeat(sides[:, None], 3, axis=1))
 
 
 class Ensemble(dict):

@@ -100,8 +100,9 @@ def test_batch_trajectories_and_moments(ff, ora):
     U = np.concatenate(u)
     n = P.shape[0]
     steps = 30
+    big = max(sides)
     p = ff.ff_params_default(n=n, precision="f64", walls=1, seed=3, kT=1.0, gamma_t=0.5,
-                             gamma_r=0.5)
+                             gamma_r=0.5, box_lo=(0, 0, 0), box_hi=(big, big, big))
     ctx = ff.ff_create(p)
     ff.ff_set_systems(ctx, sizes, fields, lo, hi)
     ff.ff_set_particles(ctx, P, U)
@@ -152,8 +153,10 @@ def test_langevin_magnetisation_curve(ff, ora):
     hi = np.array([[s, s, s] for s in sides])
     P = np.concatenate(pos).astype(np.float32)
     U = np.concatenate(u).astype(np.float32)
+    big = max(sides)
     p = ff.ff_params_default(n=P.shape[0], precision="f32", walls=1, kT=1.0, gamma_t=1.0,
-                             gamma_r=1.0, dip_scale=0.125, seed=9)
+                             gamma_r=1.0, dip_scale=0.125, seed=9, box_lo=(0, 0, 0),
+                             box_hi=(big, big, big))
     ctx = ff.ff_create(p)
     ff.ff_set_systems(ctx, sizes, fields, np.zeros((len(alphas), 3)), hi)
     ff.ff_set_particles(ctx, P, U)
