@@ -12,6 +12,11 @@ FP64 path.  One JSON line on rank 0.
 --gpus N > 1 runs under torch.distributed.run: every rank advances its own
 replica of the workload (the single-system method does not shard), timing
 is the maximum over ranks, and value counts all ranks' particle-steps.
+--workload batched steps 256 independent dilute systems of uneven sizes
+together (one forest, one CUDA graph per step); on several GPUs each rank
+takes its own batch (weak scaling) or, with --split, a particle-balanced
+share of one batch (strong scaling).  Systems never interact, so no rank
+exchanges data while stepping.
 --impl reference times the CPU oracle on this host's cores instead.
 """
 import argparse
@@ -47,10 +52,14 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--leaf-max", type=int, default=1)
     ap.add_argument("--group", type=int, default=0,
-                    help="lanes walking the cell list together (0: library default)")
+                    help="lanes walking the cell list together (0: picked by the library's "
+                         "autotuner on the workload before warm-up)")
     ap.add_argument("--workload", default="phi05", choices=["phi05", "batched"],
                     help="phi05: one system of --n particles (default); batched: 256 independent "
                          "dilute systems of log-uniform sizes 1,024..65,536 at fields 0..5")
+    ap.add_argument("--split", action="store_true",
+                    help="batched workload on several GPUs: share one 256-system batch among "
+                         "the ranks (strong scaling) instead of one batch per rank (weak)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the all-pairs, FP64, e2e and CPU-baseline legs")
     return ap.parse_args()
@@ -87,6 +96,26 @@ def batched_workload(seed=1):
     np.savez(tmp, **b)
     os.replace(tmp, path)
     return b
+
+
+BATCHED_METRIC = ("particle-steps/s, 256 batched ensembles (N 1,024..65,536 log-uniform, "
+                  "phi 0.02, fields 0..5, theta=0.5)")
+
+
+def batched_config(args, n, world):
+    return {"workload": "256 independent systems, sizes round(1024 64^((i+1/2)/256)) "
+                        "(3,970,997 particles), phi = 0.02 hard-core gases, isotropic moments, "
+                        "applied fields 0..5 along z on a linear grid (seeded permutation), "
+                        "dip_scale 1/8, kT = 1, Gamma_t = Gamma_r = 1, dt = 1e-3, LJ, walls",
+            "n": n, "systems": 256, "theta": args.theta, "leaf_max": args.leaf_max,
+            "precision": "fp32", "algo": "barnes-hut",
+            "l2": "flushed between timed steps (256 MB write outside the timed events)",
+            "parallelism": ("single-gpu" if world == 1 else
+                            "one 256-system batch shared among the ranks (particle-balanced "
+                            "split), no data-path exchange; per-system moments gathered after "
+                            "timing" if args.split else
+                            "one independent 256-system batch per rank (seed 1 + rank), no "
+                            "data-path exchange; per-system moments gathered after timing")}
 
 
 def config_dict(args, side):
@@ -253,10 +282,40 @@ def cpu_step_sample(pos, u, theta, leaf_max, side, sample, threads=None):
     return n / per_step, (t4 - t0), oracle.get_threads(), len(idx)
 
 
+def cpu_batched_sample(batch, theta, leaf_max, stride=8):
+    """One CPU-oracle step of every stride-th system of a batch: tree, traversal and
+    integration of all of its particles, with the system's own field and box.
+
+    Returns (particle-steps/s, seconds of CPU work, threads, systems, particles)."""
+    import oracle
+
+    sizes = np.asarray(batch["sizes"], dtype=np.int64)
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    pos = batch["pos"].astype(np.float32).astype(np.float64)
+    u = batch["u"].astype(np.float64)
+    picked = list(range(0, len(sizes), stride))
+    secs, m = 0.0, 0
+    for s in picked:
+        a, b = int(starts[s]), int(starts[s + 1])
+        p, us = pos[a:b], u[a:b]
+        t0 = time.perf_counter()
+        r = oracle.bh(p, us, theta, leaf_max, "f32", 0.125, 1.0, 1.0, 2.5, True)
+        st = dict(pos=p.copy(), vel=np.zeros_like(p), u=us.copy(), om=np.zeros_like(p),
+                  id=np.arange(a, b, dtype=np.int64))
+        dyn = oracle.make_dyn(kT=1.0, gamma_t=1.0, gamma_r=1.0, h_ext=batch["fields"][s],
+                              box_lo=batch["box_lo"][s], box_hi=batch["box_hi"][s], walls=True)
+        oracle.em_step(st, r["h"], r["f"], dyn, 0)
+        secs += time.perf_counter() - t0
+        m += b - a
+    return m / secs, secs, oracle.get_threads(), len(picked), m
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
+    if args.workload == "batched":
+        return run_reference_batched(args)
     pos, u, side = workload(args.n)
     sample = 65536
     for _ in range(args.warmup):
@@ -286,6 +345,36 @@ def run_reference(args):
     return 0
 
 
+def run_reference_batched(args):
+    """The oracle on the batched workload: each step one full step of every 16th system."""
+    batch = batched_workload()
+    for _ in range(args.warmup):
+        cpu_batched_sample(batch, args.theta, args.leaf_max, stride=16)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, _, threads, nsys_s, m = cpu_batched_sample(batch, args.theta, args.leaf_max, stride=16)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(rates))
+    n = int(np.sum(batch["sizes"]))
+    line = {
+        "impl": "reference", "metric": BATCHED_METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * n / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": batched_config(args, n, 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "per step: one full step of every 16th system (%d systems, "
+                                   "%d particles), rate scaled by particle count" % (nsys_s, m)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    line["config"]["precision"] = "fp64 sums, fp32 tree"
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -306,7 +395,18 @@ def run_ours(args):
     K, W = args.steps, args.warmup
     batch = None
     if args.workload == "batched":
-        batch = batched_workload()
+        # every rank advances its own batch of 256 systems (seed 1 + rank): the systems are
+        # independent, so ranks exchange nothing on the data path
+        if args.split:
+            # one batch shared among the ranks: each takes a particle-balanced share
+            from paper_1212_2934_gb300 import shard
+
+            full = batched_workload(seed=1)
+            n_job = int(np.sum(full["sizes"]))
+            mine = shard.partition_systems(full["sizes"], world)[rank]
+            batch = shard.rank_slice(full, mine)
+        else:
+            batch = batched_workload(seed=1 + rank)
         pos, u = batch["pos"], batch["u"]
         side = float(batch["sides"].max())
         n = pos.shape[0]
@@ -348,6 +448,13 @@ def run_ours(args):
     # ---- main leg: FP32 Barnes-Hut steps (interaction counting off while timed)
     ctx = create(params(count_interactions=0))
     ff.ff_set_particles(ctx, pos_d, u_d)
+    tuning = None
+    if args.group == 0:
+        # the traversal schedule (lanes per walk) is picked by the library's autotuner on this
+        # very workload; every choice gives the same bits, only the speed differs
+        best, tms = ff.ff_tune_traversal(ctx, reps=3)
+        tuning = {"chosen": best, "ms_per_candidate": {str(g): round(m, 4) for g, m in tms.items()}}
+        args.group = best
     clocks = Clocks(dev)
     clocks.start()
     for _ in range(W):
@@ -380,8 +487,27 @@ def run_ours(args):
     prof = ff.ff_profile_read(ctx)
     ff.ff_profile(ctx, False)
     max_ms = max_over_ranks(total_ms, "cuda")
-    value = whole_job_rate(n, K, world, max_ms / 1e3)
+    split = batch is not None and args.split
+
+    def job_rate(max_seconds):
+        # a shared batch counts its particles once; replicas and per-rank batches count every rank
+        return n_job * K / max_seconds if split else whole_job_rate(n, K, world, max_seconds)
+
+    value = job_rate(max_ms / 1e3)
     energy = ff.ff_energy(ctx)
+    systems_done = None
+    if batch is not None:
+        # the only exchange of a batched job: per-system moment sums (4 doubles a system)
+        # gathered once, after the timed region
+        sums, _ = ff.ff_system_moments(ctx)
+        if world > 1 and split:
+            systems_done = len(shard.gather_system_values(sums, mine, len(full["sizes"])))
+        elif world > 1:
+            every = [None] * world
+            torch.distributed.all_gather_object(every, sums.tolist())
+            systems_done = sum(len(a) for a in every)
+        else:
+            systems_done = len(sums)
     # interaction counts of the final state, from one counted evaluation (the timed steps
     # move particles by ~1e-4 diameters, so the per-launch work is the same to < 0.1 %)
     xs = ff.ff_get_particles(ctx, dtype=np.float32, device_like=pos_d)
@@ -466,6 +592,7 @@ def run_ours(args):
             "speedup_bh_fp32_over_ap": ms_ap / (max_ms / K),
             "speedup_bh_fp32_over_fp64": ms64 / (max_ms / K),
         }
+    if not args.no_extras:
         # ---- end to end through the C interface with pinned host buffers
         host = [torch.empty((n, 3), dtype=torch.float32, pin_memory=True) for _ in range(4)]
         host[0].copy_(torch.from_numpy(pos.astype(np.float32)))
@@ -474,7 +601,7 @@ def run_ours(args):
         host[3].zero_()
         hn = [h.numpy() for h in host]
         outs = [torch.empty((n, 3), dtype=torch.float32, pin_memory=True).numpy() for _ in range(4)]
-        ctxe = ff.ff_create(params(count_interactions=0))
+        ctxe = create(params(count_interactions=0))
         lib = ff.lib()
         import ctypes
 
@@ -497,28 +624,25 @@ def run_ours(args):
             e2e_step()
         barrier()
         e2e_s = time.perf_counter() - t0
-        e2e = {"value": whole_job_rate(n, K, world, max_over_ranks(e2e_s, "cuda")), "unit": UNIT,
+        e2e = {"value": job_rate(max_over_ranks(e2e_s, "cuda")), "unit": UNIT,
                "h2d_bytes_per_step": 4 * n * 3 * 4, "d2h_bytes_per_step": 4 * n * 3 * 4,
                "note": "ff_set_particles + ff_step + ff_get_particles on pinned host float32 "
                        "arrays (positions, moments, velocities, angular velocities), wall clock"}
         del ctxe
 
     cfg = config_dict(args, side)
+    cfg["traverse_tuning"] = tuning
     metric = METRIC
     if batch is not None:
-        metric = ("particle-steps/s, 256 batched ensembles (N 1,024..65,536 log-uniform, "
-                  "phi 0.02, fields 0..5, theta=0.5)")
-        cfg = {"workload": "256 independent systems, sizes round(1024 64^((i+1/2)/256)) "
-                           "(3,970,997 particles), phi = 0.02 hard-core gases, isotropic moments, "
-                           "applied fields 0..5 along z on a linear grid (seeded permutation), "
-                           "dip_scale 1/8, kT = 1, Gamma_t = Gamma_r = 1, dt = 1e-3, LJ, walls",
-               "n": n, "systems": 256, "theta": args.theta, "leaf_max": args.leaf_max,
-               "precision": "fp32", "algo": "barnes-hut",
-               "l2": "flushed between timed steps (256 MB write outside the timed events)",
-               "parallelism": "replicas" if args.gpus > 1 else "single-gpu"}
+        metric = BATCHED_METRIC
+        cfg = batched_config(args, n_job if args.split else n, world)
+        cfg["systems_all_ranks"] = systems_done
+        cfg["traverse_group"] = args.group
+        cfg["traverse_tuning"] = tuning
     line = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": max_ms / K, "higher_is_better": True,
+        "scaling": "strong" if split else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -547,6 +671,12 @@ def run_ours(args):
                                           "particles plus traversal of %d sampled particles "
                                           "(%.1f s of CPU work), scaled to one full step"
                                           % (n, s, cpu_s)}
+    elif rank == 0 and world == 1 and not args.no_extras:
+        rate, cpu_s, threads, nsys_s, m = cpu_batched_sample(batch, args.theta, args.leaf_max)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "one full step (tree, traversal, integration) of every "
+                                          "8th system: %d systems, %d particles (%.1f s of CPU "
+                                          "work)" % (nsys_s, m, cpu_s)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

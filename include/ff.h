@@ -200,6 +200,24 @@ ff_status ff_set_systems(ff_ctx *ctx, int32_t nsys, const int64_t *counts, const
  */
 ff_status ff_system_moments(ff_ctx *ctx, double *out, int64_t *nsteps, int32_t reset);
 
+/*
+ * Traversal schedule autotuner.  The per-particle walk (Sec. 3.2, kernel 5)
+ * can be run with G = 1, 2, 4, 8, 16 or 32 lanes walking the cell list
+ * together; every G gives bit-identical fields and forces (each lane makes its
+ * own particle's decisions in depth-first order), only the speed differs with
+ * the workload.  This sorts the current state and builds the tree once (like
+ * ff_dipolar_field with the context's theta, LJ included), then times `reps`
+ * traversals for each candidate with CUDA events on the context's stream and
+ * keeps the fastest (minimum over reps; ties to the earlier candidate) as the
+ * context's traverse_group for later ff_step and ff_dipolar_field calls.
+ * groups[ngroups]: candidates (each one of 1, 2, 4, 8, 16, 32), or NULL with
+ * ngroups = 0 for all six.  reps = 1 .. 100.  *best_group receives the choice;
+ * ms (may be NULL) receives ngroups (6 for NULL groups) per-candidate times in
+ * milliseconds.  Barnes-Hut contexts only.  Waits.
+ */
+ff_status ff_tune_traversal(ff_ctx *ctx, const int32_t *groups, int32_t ngroups, int32_t reps,
+                            int32_t *best_group, float *ms);
+
 /* Waits for the context's stream and reports any error flag raised on the GPU. */
 ff_status ff_synchronize(ff_ctx *ctx);
 

@@ -17,6 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libff.so")
+EXPORTS = os.path.join(CSRC, "libff.map")  # linker version script: only ff_* is exported
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -36,7 +37,7 @@ def sources():
 
 def _inputs():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "ff.h"),
-                                                                  os.path.abspath(__file__)]
+                                                                  EXPORTS, os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:
@@ -73,7 +74,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if failed:
         raise RuntimeError("nvcc failed on: " + ", ".join(failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static",
+           "-Xlinker", "--version-script=" + EXPORTS]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

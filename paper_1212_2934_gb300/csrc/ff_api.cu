@@ -646,6 +646,61 @@ ff_status energy(ff_ctx* c, ff_energy_t* out)
 
 }  // namespace
 
+namespace {
+
+// Sorts and builds once, then times the traversal for each lane group.
+template <typename R>
+ff_status tune_traversal(ff_ctx* c, const int32_t* groups, int ng, int reps, float* ms_out,
+                         int* best)
+{
+    ff_status s = eval_bh<R>(c, c->p.theta, 1);
+    if (s != FF_OK) return s;
+    if ((s = sync_and_check(c)) != FF_OK) return s;
+    Buffers& a = c->st[c->cur];
+    ffk::Tree<R> t = tree_of<R>(c);
+    const ffk::FieldParams<R> fp = field_params<R>(c, c->p.theta, 1);
+    struct Events {
+        std::vector<cudaEvent_t> v;
+        ~Events()
+        {
+            for (cudaEvent_t e : v)
+                if (e) cudaEventDestroy(e);
+        }
+    } hold;
+    hold.v.assign(2 * (size_t)ng * reps, nullptr);
+    std::vector<cudaEvent_t>& ev = hold.v;
+    for (auto& e : ev) FF_CUDA(c, cudaEventCreate(&e));
+    for (int g = 0; g < ng; ++g)
+        for (int r = 0; r < reps; ++r) {
+            cudaEvent_t* e = &ev[2 * ((size_t)g * reps + r)];
+            cudaEventRecord(e[0], c->stream);
+            ffk::bh_field<R>(V<R>(a.pos), V<R>(a.u), c->n, t, fp, V<R>(c->h), V<R>(c->f),
+                             static_cast<R*>(c->esr), nullptr, c->dflags, c->work, groups[g],
+                             c->off, segs_of(c), c->stream);
+            cudaEventRecord(e[1], c->stream);
+        }
+    FF_LAUNCHED(c);
+    s = sync_and_check(c);
+    float best_ms = 0.0f;
+    *best = groups[0];
+    for (int g = 0; g < ng && s == FF_OK; ++g) {
+        float m = 0.0f;
+        for (int r = 0; r < reps; ++r) {
+            float x = 0.0f;
+            cudaEventElapsedTime(&x, ev[2 * ((size_t)g * reps + r)], ev[2 * ((size_t)g * reps + r) + 1]);
+            m = (r == 0 || x < m) ? x : m;
+        }
+        if (ms_out) ms_out[g] = m;
+        if (g == 0 || m < best_ms) {
+            best_ms = m;
+            *best = groups[g];
+        }
+    }
+    return s;
+}
+
+}  // namespace
+
 // =================================================================== C ABI
 namespace {
 
@@ -1081,6 +1136,39 @@ ff_status ff_set_systems(ff_ctx* c, int32_t nsys, const int64_t* counts, const d
     c->sys_steps = 0;
     c->tree_valid = false;
     c->counts_valid = false;
+    return FF_OK;
+}
+
+ff_status ff_tune_traversal(ff_ctx* c, const int32_t* groups, int32_t ngroups, int32_t reps,
+                            int32_t* best_group, float* ms)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    static const int32_t all[6] = {1, 2, 4, 8, 16, 32};
+    if (!best_group) return fail(c, FF_EINVAL, "best_group is required");
+    if (!groups) {
+        if (ngroups != 0) return fail(c, FF_EINVAL, "groups = NULL needs ngroups = 0");
+        groups = all;
+        ngroups = 6;
+    }
+    if (ngroups < 1 || ngroups > 64) return fail(c, FF_EINVAL, "ngroups must be 1 .. 64");
+    for (int g = 0; g < ngroups; ++g) {
+        const int32_t v = groups[g];
+        if (v != 1 && v != 2 && v != 4 && v != 8 && v != 16 && v != 32)
+            return fail(c, FF_EINVAL, "every candidate must be 1, 2, 4, 8, 16 or 32");
+    }
+    if (reps < 1 || reps > 100) return fail(c, FF_EINVAL, "reps must be 1 .. 100");
+    if (c->p.algo != FF_ALGO_BH) return fail(c, FF_EINVAL, "the context does not use Barnes-Hut");
+    int best = 0;
+    s = c->fp64 ? tune_traversal<double>(c, groups, ngroups, reps, ms, &best)
+                : tune_traversal<float>(c, groups, ngroups, reps, ms, &best);
+    if (s != FF_OK) return s;
+    if (c->p.traverse_group != best) {
+        c->p.traverse_group = best;
+        drop_graphs(c);  // the captured step launches the old schedule
+    }
+    *best_group = best;
     return FF_OK;
 }
 

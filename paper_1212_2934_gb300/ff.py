@@ -88,6 +88,7 @@ _SIGS = {
     "ff_get_counts": (_st, [_vp, _vp, _vp, _vp]),
     "ff_set_systems": (_st, [_vp, C.c_int32, _vp, _vp, _vp, _vp]),
     "ff_system_moments": (_st, [_vp, _vp, C.POINTER(C.c_int64), C.c_int32]),
+    "ff_tune_traversal": (_st, [_vp, _vp, C.c_int32, C.c_int32, C.POINTER(C.c_int32), _vp]),
     "ff_profile": (_st, [_vp, C.c_int32]),
     "ff_profile_read": (_st, [_vp, C.POINTER(ff_profile_t)]),
     "ff_morton_order_noalloc": (_st, [_vp, C.c_int64, _vp, _vp, _vp]),
@@ -334,6 +335,25 @@ def ff_system_moments(ctx, reset=False):
     _check(ctx.handle, lib().ff_system_moments(ctx.handle, C.c_void_p(out.ctypes.data),
                                                C.byref(st), int(bool(reset))))
     return out, st.value
+
+
+TRAVERSE_GROUPS = (1, 2, 4, 8, 16, 32)
+
+
+def ff_tune_traversal(ctx, groups=None, reps=3):
+    """Times the traversal with each lane group (all six when groups is None), keeps the
+    fastest for the context and returns (best_group, {group: ms})."""
+    cand = list(TRAVERSE_GROUPS if groups is None else groups)
+    ms = np.zeros(len(cand), dtype=np.float32)
+    best = C.c_int32()
+    if groups is None:
+        gp, ng = None, 0
+    else:
+        garr = (C.c_int32 * len(cand))(*cand)
+        gp, ng = C.cast(garr, C.c_void_p), len(cand)
+    _check(ctx.handle, lib().ff_tune_traversal(ctx.handle, gp, ng, int(reps), C.byref(best),
+                                               C.c_void_p(ms.ctypes.data)))
+    return best.value, {g: float(m) for g, m in zip(cand, ms)}
 
 
 def ff_profile(ctx, enable=True):

@@ -1,7 +1,7 @@
 """Host-side checks of the C library boundary (no GPU needed).
 
 The library builds for sm_103a and loads; it exports every function that
-include/ff.h declares; parameter validation in ff_create rejects bad input
+include/ff.h declares and nothing else; parameter validation in ff_create rejects bad input
 before touching a device and reports why through ff_last_error(NULL).
 """
 import ctypes
@@ -43,6 +43,9 @@ def test_library_exports_every_declared_symbol(libff):
                          text=True).stdout
     exported = set(re.findall(r"\bT (ff_\w+)", out))
     assert set(declared_functions()) <= exported
+    # and nothing else: internal launchers and the static CUDA runtime stay local
+    defined = {ln.split()[-1] for ln in out.splitlines() if len(ln.split()) >= 3}
+    assert defined == set(declared_functions()), sorted(defined ^ set(declared_functions()))
     # the binding covers the same names
     assert set(libff.exported_symbols()) == set(declared_functions())
 
