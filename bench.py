@@ -54,9 +54,12 @@ def parse():
     ap.add_argument("--group", type=int, default=0,
                     help="lanes walking the cell list together (0: picked by the library's "
                          "autotuner on the workload before warm-up)")
-    ap.add_argument("--workload", default="phi05", choices=["phi05", "batched"],
+    ap.add_argument("--workload", default="phi05", choices=["phi05", "batched", "chains"],
                     help="phi05: one system of --n particles (default); batched: 256 independent "
-                         "dilute systems of log-uniform sizes 1,024..65,536 at fields 0..5")
+                         "dilute systems of log-uniform sizes 1,024..65,536 at fields 0..5; "
+                         "chains: 65,536 straight chains of 64 touching dipoles (4,194,304 "
+                         "particles) at volume fraction 0.01, FP32 with the mixed and FP64 paths "
+                         "timed beside it")
     ap.add_argument("--split", action="store_true",
                     help="batched workload on several GPUs: share one 256-system batch among "
                          "the ranks (strong scaling) instead of one batch per rank (weak)")
@@ -116,6 +119,40 @@ def batched_config(args, n, world):
                             "timing" if args.split else
                             "one independent 256-system batch per rank (seed 1 + rank), no "
                             "data-path exchange; per-system moments gathered after timing")}
+
+
+CHAINS_METRIC = ("particle-steps/s, 4,194,304 dipoles in 65,536 chains of 64, phi 0.01, "
+                 "theta=0.5 (FP32 BH; mixed and FP64 beside)")
+CHAINS, CHAIN_LEN = 65536, 64
+
+
+def chains_workload(seed=1):
+    """65,536 straight chains of 64 touching dipoles, isotropic axes, head-to-tail moments with a
+    random sign per chain, at volume fraction 0.01 (generated once per host and cached)."""
+    from paper_1212_2934_gb300 import synth
+
+    path = os.path.join(tempfile.gettempdir(), "ff_chains%dx%d_s%d.npz" % (CHAINS, CHAIN_LEN, seed))
+    if os.path.exists(path):
+        d = np.load(path)
+        return d["pos"], d["u"], float(d["side"])
+    side = synth.box_side_for_fraction(CHAINS * CHAIN_LEN, 0.01)
+    pos, u = synth.chains_cube(CHAINS, CHAIN_LEN, side, seed)
+    pos, u = pos.astype(np.float32), u.astype(np.float32)
+    tmp = path + ".%d.npz" % os.getpid()
+    np.savez(tmp, pos=pos, u=u, side=side)
+    os.replace(tmp, path)
+    return pos, u, side
+
+
+def chains_config(args, n, side, world):
+    return {"workload": "65,536 straight chains of 64 touching dipoles (spacing 1), isotropic "
+                        "axes, moments along the axis head-to-tail with a random sign per chain, "
+                        "random sequential addition of rods at volume fraction 0.01, h_ext=(0,0,1), "
+                        "kT=1, Gamma_t=Gamma_r=0.1, dt=1e-3, LJ eps=1 sigma=1 rcut=2.5, walls",
+            "n": n, "box_side": round(side, 4), "theta": args.theta, "leaf_max": args.leaf_max,
+            "precision": "fp32 (mixed and fp64 in paths)", "algo": "barnes-hut",
+            "l2": "flushed between timed steps (256 MB write outside the timed events)",
+            "parallelism": "replicas" if world > 1 else "single-gpu"}
 
 
 def config_dict(args, side):
@@ -261,6 +298,7 @@ def cpu_step_sample(pos, u, theta, leaf_max, side, sample, threads=None):
         oracle.set_threads(threads)
     n = pos.shape[0]
     p64 = pos.astype(np.float32).astype(np.float64)
+    u = np.asarray(u, dtype=np.float64)
     rng = np.random.default_rng(5)
     idx = np.sort(rng.choice(n, size=min(sample, n), replace=False))
     t0 = time.perf_counter()
@@ -410,6 +448,9 @@ def run_ours(args):
         pos, u = batch["pos"], batch["u"]
         side = float(batch["sides"].max())
         n = pos.shape[0]
+    elif args.workload == "chains":
+        pos, u, side = chains_workload(seed=1 + rank)
+        n = pos.shape[0]
     else:
         n = args.n
         pos, u, side = workload(n)
@@ -528,7 +569,35 @@ def run_ours(args):
 
     extras = {}
     e2e = None
-    if not args.no_extras and batch is None:
+    if not args.no_extras and args.workload == "chains":
+        # ---- the same chains stepped with FP64 cell sums (mixed) and entirely in FP64
+        for prec, kk in (("mixed", K), ("f64", max(3, K // 10))):
+            c = ff.ff_create(params(precision=prec, count_interactions=0))
+            ff.ff_set_particles(c, pos_d.double() if prec == "f64" else pos_d,
+                                u_d.double() if prec == "f64" else u_d)
+            for _ in range(W):
+                ff.ff_step(c, 1)
+                flush.zero_()
+            barrier()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(kk)]
+            for a, b in ev:
+                a.record(stream)
+                ff.ff_step(c, 1)
+                b.record(stream)
+                flush.zero_()
+            barrier()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / kk
+            extras["bh_" + ("fp64" if prec == "f64" else prec)] = {
+                "particle_steps_per_s": n / (ms / 1e3), "ms_per_step": ms, "steps": kk}
+            del c
+        extras["bh_fp32"] = {"particle_steps_per_s": value / world, "ms_per_step": max_ms / K,
+                             "interactions_per_particle": info["interactions"] / n,
+                             "cells": info["ncells"]}
+        extras["error_note"] = ("errors of each path against the FP64 all-pairs oracle on a "
+                                "16,384-particle subsample are measured by the chain precision "
+                                "test, not here")
+    if not args.no_extras and args.workload == "phi05":
         # ---- FP64 Barnes-Hut path
         ctx64 = ff.ff_create(params(precision="f64", count_interactions=0))
         ff.ff_set_particles(ctx64, pos_d.double(), u_d.double())
@@ -633,6 +702,11 @@ def run_ours(args):
     cfg = config_dict(args, side)
     cfg["traverse_tuning"] = tuning
     metric = METRIC
+    if args.workload == "chains":
+        metric = CHAINS_METRIC
+        cfg = chains_config(args, n, side, world)
+        cfg["traverse_group"] = args.group
+        cfg["traverse_tuning"] = tuning
     if batch is not None:
         metric = BATCHED_METRIC
         cfg = batched_config(args, n_job if args.split else n, world)
@@ -665,7 +739,8 @@ def run_ours(args):
     if e2e is not None:
         line["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_extras and batch is None:
-        rate, cpu_s, threads, s = cpu_step_sample(pos, u, args.theta, args.leaf_max, side, 262144)
+        rate, cpu_s, threads, s = cpu_step_sample(pos, u, args.theta, args.leaf_max, side,
+                                                  262144 if args.workload == "phi05" else 131072)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": "tree build, aggregation and integration of all %d "
                                           "particles plus traversal of %d sampled particles "

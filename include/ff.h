@@ -48,7 +48,15 @@ typedef enum {
     FF_ESTATE = 6      /* call not valid now: no particles set, or poisoned */
 } ff_status;
 
-typedef enum { FF_FP32 = 0, FF_FP64 = 1 } ff_precision;
+/*
+ * FF_FP32: state, tree, traversal and integration in IEEE single (the
+ * paper's choice, Sec. 4).  FF_FP64: everything in double.  FF_MIXED: as
+ * FF_FP32, except that the cell aggregation (Eq. magCenter) sums positions
+ * and moments in double and rounds each centre (double sum / count) and each
+ * moment sum to single once.  Energies and magnetisation are summed in double
+ * in every mode.
+ */
+typedef enum { FF_FP32 = 0, FF_FP64 = 1, FF_MIXED = 2 } ff_precision;
 typedef enum { FF_ALGO_BH = 0, FF_ALGO_AP = 1 } ff_algo;
 typedef enum { FF_DTYPE_F32 = 0, FF_DTYPE_F64 = 1 } ff_dtype;
 typedef enum { FF_HOST = 0, FF_DEVICE = 1 } ff_loc;

@@ -57,14 +57,15 @@ def lib():
         L.ora_pair_lj.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp]
         L.ora_pair_lj.restype = C.c_double
         L.ora_allpairs.argtypes = [_i64, _dp, _dp, C.c_double, C.c_double, C.c_double,
-                                   C.c_double, C.c_int32, C.c_int32, _dp, _dp, C.c_void_p]
+                                   C.c_double, C.c_int32, C.c_int32, C.c_void_p, _i64, _dp, _dp,
+                                   C.c_void_p]
         L.ora_morton.argtypes = [_i64, _dp, C.c_int32, _u64p, _dp]
         L.ora_tree.argtypes = [_i64, _dp, _dp, C.c_int32, C.c_int32, _u64p, _i64p, _dp, _i64,
                                _i32p, _i32p, _i64p, _i64p, _i64p, _dp, _dp, _dp, _dp, _dp]
         L.ora_tree.restype = _i64
         L.ora_bh.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p, _i64,
                              _dp, _dp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                             C.c_void_p]
+                             C.c_void_p, _dp, _dp]
         L.ora_bh.restype = _i64
         L.ora_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.ora_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, _dp]
@@ -113,18 +114,26 @@ def pair_lj(r, eps=1.0, sigma=1.0, rcut=2.5):
 
 
 def allpairs(pos, u, dip_scale=1.0, lj_eps=0.0, lj_sigma=1.0, lj_rcut=2.5, include_sr=True,
-             cut_prec="f64"):
+             cut_prec="f64", only=None):
     """Exact O(N^2) field and force (Sec. 3.1).  Returns (h, f, e_sr), FP64.
 
     cut_prec: precision of the LJ cut-off test (the single-precision kernel
-    takes it in single precision)."""
+    takes it in single precision).  With ``only`` (indices), only those rows are
+    computed (all particles remain sources); other rows are zero."""
     pos, u = _vec3(pos), _vec3(u)
     n = pos.shape[0]
     h = np.zeros((n, 3))
     f = np.zeros((n, 3))
     e = np.zeros(n)
+    if only is not None:
+        only = np.ascontiguousarray(only, dtype=np.int64)
+        if only.size and (only.min() < 0 or only.max() >= n):
+            raise ValueError("only: index out of range")
+        optr, nonly = C.c_void_p(only.ctypes.data), int(only.size)
+    else:
+        optr, nonly = None, 0
     lib().ora_allpairs(n, pos, u, dip_scale, lj_eps, lj_sigma, lj_rcut, int(bool(include_sr)),
-                       _prec(cut_prec), h, f, _ptr(e))
+                       _prec(cut_prec), optr, nonly, h, f, _ptr(e))
     return h, f, e
 
 
@@ -133,6 +142,8 @@ def _prec(p):
         return 0
     if p in (1, "f64", "float64", np.float64):
         return 1
+    if p in (2, "mixed"):
+        return 2
     raise ValueError(p)
 
 
@@ -181,8 +192,9 @@ def bh(pos, u, theta, leaf_max=1, prec="f32", dip_scale=1.0, lj_eps=0.0, lj_sigm
     """Barnes-Hut field and force (Sec. 3.2) with the opening rule stated in ora.c.
 
     Returns a dict with h, f, e_sr (n x 3 / n, FP64, input order), nacc, npair,
-    nopen, ncover (per-particle counts) and ncells.  With ``only`` (indices), rows of
-    other particles are zero.
+    nopen, ncover (per-particle counts), habs, fabs (sums of the magnitudes of the
+    terms summed into h and f) and ncells.  With ``only`` (indices), rows of other
+    particles are zero.
     """
     pos, u = _vec3(pos), _vec3(u)
     n = pos.shape[0]
@@ -196,15 +208,17 @@ def bh(pos, u, theta, leaf_max=1, prec="f32", dip_scale=1.0, lj_eps=0.0, lj_sigm
     npair = np.zeros(n, dtype=np.int64)
     nopen = np.zeros(n, dtype=np.int64)
     ncover = np.zeros(n, dtype=np.int64)
+    habs = np.zeros(n)
+    fabs = np.zeros(n)
     if only is not None:
         only = np.ascontiguousarray(only, dtype=np.int64)
         n_only = only.shape[0]
     else:
         n_only = 0
     nc = lib().ora_bh(n, pos, u, C.byref(p), _ptr(only), n_only, h, f, _ptr(e), _ptr(nacc),
-                      _ptr(npair), _ptr(nopen), _ptr(ncover))
+                      _ptr(npair), _ptr(nopen), _ptr(ncover), habs, fabs)
     return dict(h=h, f=f, e_sr=e, nacc=nacc, npair=npair, nopen=nopen, ncover=ncover,
-                ncells=int(nc))
+                habs=habs, fabs=fabs, ncells=int(nc))
 
 
 def philox4x32_10(ctr, key):

@@ -25,9 +25,10 @@
  * Floating point: all sums are FP64.  The Barnes-Hut *tree* (Morton
  * quantisation, cell centres used for the opening test, the opening decision
  * itself) is computed in the tree precision `prec` (0 = IEEE single, 1 = IEEE
- * double) because these floating-point values decide discrete outcomes
- * (which cell a particle falls in, whether a cell is accepted); the paper ran
- * in single precision.  Build with -ffp-contract=off and without fast-math so
+ * double, 2 = mixed: single, except that each cell centre is the FP64
+ * position sum divided by the count, rounded once to single) because these
+ * floating-point values decide discrete outcomes (which cell a particle falls
+ * in, whether a cell is accepted); the paper ran in single precision.  Build with -ffp-contract=off and without fast-math so
  * every single operation is rounded exactly once in the written order.
  */
 #include <math.h>
@@ -137,7 +138,7 @@ double ora_pair_lj(const double r[3], double eps, double sigma, double rcut,
  */
 static int lj_inside(const double xk[3], const double xj[3], double rcut, int prec)
 {
-    if (prec == 0) {
+    if (prec != 1) {
         float d[3];
         for (int a = 0; a < 3; ++a) d[a] = (float)xk[a] - (float)xj[a];
         float dxx = d[0] * d[0], dyy = d[1] * d[1], dzz = d[2] * d[2];
@@ -177,15 +178,19 @@ static double lj_pair_inside(const double r[3], double eps, double sigma, double
  * include_sr and eps != 0).  e_sr[k] (if non-NULL) receives half of the
  * shifted LJ energy of every pair k is in.  pos, u, h, f are n x 3 row-major.
  * cut_prec: precision in which the LJ cut-off test is taken (0 single,
- * 1 double).
+ * 1 double).  With `only` (n_only indices), only those targets are summed
+ * (every other particle is still a source); other rows are left untouched.
  */
 void ora_allpairs(int64_t n, const double *pos, const double *u,
                   double dip_scale, double eps, double sigma, double rcut,
-                  int32_t include_sr, int32_t cut_prec, double *h, double *f, double *e_sr)
+                  int32_t include_sr, int32_t cut_prec, const int64_t *only, int64_t n_only,
+                  double *h, double *f, double *e_sr)
 {
     int use_lj = include_sr && eps != 0.0 && rcut > 0.0;
+    int64_t cnt = only ? n_only : n;
 #pragma omp parallel for schedule(dynamic, 8)
-    for (int64_t k = 0; k < n; ++k) {
+    for (int64_t q = 0; q < cnt; ++q) {
+        int64_t k = only ? only[q] : q;
         double hk[3] = {0, 0, 0}, fd[3] = {0, 0, 0}, fs[3] = {0, 0, 0};
         double ek = 0.0;
         for (int64_t j = 0; j < n; ++j) {
@@ -256,7 +261,7 @@ static uint32_t quant_d(double x, double mn, double S)
 /* root[0..2] = origin, root[3] = side (values of the tree precision) */
 void ora_morton(int64_t n, const double *pos, int32_t prec, uint64_t *keys, double root[4])
 {
-    if (prec == 0) {
+    if (prec != 1) {
         float mn[3], mx[3];
         for (int a = 0; a < 3; ++a) { mn[a] = (float)pos[a]; mx[a] = (float)pos[a]; }
         for (int64_t i = 1; i < n; ++i)
@@ -431,7 +436,7 @@ static void tree_build(int64_t n, const double *pos, const double *u, int prec,
         uint32_t q[3];
         int L = t->level[c];
         prefix_coords(skeys[t->pbegin[c]], L, q);
-        if (prec == 0) {
+        if (prec != 1) {
             float side = ldexpf((float)root[3], -L);
             t->side[c] = side;
             for (int a = 0; a < 3; ++a) {
@@ -492,6 +497,8 @@ static void tree_build(int64_t n, const double *pos, const double *u, int prec,
             t->S32[3 * c + a] = S32[a];
             if (prec == 0)
                 t->cen[3 * c + a] = (double)(S32[a] / (float)cnt);
+            else if (prec == 2)
+                t->cen[3 * c + a] = (double)(float)(S[a] / (double)cnt);
             else
                 t->cen[3 * c + a] = S[a] / (double)cnt;
         }
@@ -538,7 +545,7 @@ int64_t ora_tree(int64_t n, const double *pos, const double *u, int32_t prec, in
 typedef struct {
     double theta;
     int32_t leaf_max;
-    int32_t prec;          /* tree precision: 0 single, 1 double */
+    int32_t prec;          /* tree precision: 0 single, 1 double, 2 mixed */
     double dip_scale;
     double lj_eps, lj_sigma, lj_rcut;
     int32_t include_sr;
@@ -619,6 +626,7 @@ typedef struct {
 
 typedef struct {
     double h[3], fd[3], fs[3], e_sr;
+    double habs, fdabs, fsabs;   /* sums of the magnitudes of the terms added */
     int64_t nacc, npair, nopen, ncover;
 } bh_acc;
 
@@ -631,7 +639,7 @@ static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *
     int inside = (t->pbegin[c] <= sk && sk < t->pend[c]);
     int ok = 0;
     if (!inside) {
-        if (g->p->prec == 0) {
+        if (g->p->prec != 1) {
             float xf[3], cf[3], lof[3];
             for (int a = 0; a < 3; ++a) {
                 xf[a] = (float)xk[a];
@@ -651,6 +659,8 @@ static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *
         if (dot3(r, r) > 0.0) {
             ora_pair_dipole(r, uk, &t->U64[3 * c], hp, fp);
             for (int a = 0; a < 3; ++a) { acc->h[a] += hp[a]; acc->fd[a] += fp[a]; }
+            acc->habs += sqrt(dot3(hp, hp));
+            acc->fdabs += sqrt(dot3(fp, fp));
         }
         acc->nacc++;
         acc->ncover += t->pend[c] - t->pbegin[c];
@@ -666,11 +676,14 @@ static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *
             if (dot3(r, r) == 0.0) continue;
             ora_pair_dipole(r, uk, &g->u[3 * j], hp, fp);
             for (int a = 0; a < 3; ++a) { acc->h[a] += hp[a]; acc->fd[a] += fp[a]; }
+            acc->habs += sqrt(dot3(hp, hp));
+            acc->fdabs += sqrt(dot3(fp, fp));
             if (g->use_rcut && g->p->include_sr &&
                 lj_inside(xk, &g->pos[3 * j], g->p->lj_rcut, g->p->prec)) {
                 double fl[3];
                 acc->e_sr += 0.5 * lj_pair_inside(r, g->p->lj_eps, g->p->lj_sigma, g->p->lj_rcut, fl);
                 for (int a = 0; a < 3; ++a) acc->fs[a] += fl[a];
+                acc->fsabs += sqrt(dot3(fl, fl));
             }
         }
         return;
@@ -690,12 +703,15 @@ static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *
  * the shifted LJ energy of k's pairs.  nacc / npair / nopen count accepted
  * cells, exact pairs evaluated and cells opened; ncover counts the particles
  * inside accepted cells (ncover + npair = n - 1 when every other particle is
- * reached exactly once).  Returns the cell count.
+ * reached exactly once).  habs / fabs (may be NULL) receive the sums of the
+ * magnitudes of the terms that make up h and f (with the same dip_scale): the
+ * scale against which the rounding of a sum with cancellation is measured.
+ * Returns the cell count.
  */
 int64_t ora_bh(int64_t n, const double *pos, const double *u, const ora_bh_params *p,
                const int64_t *only, int64_t n_only,
                double *h, double *f, double *e_sr, int64_t *nacc, int64_t *npair, int64_t *nopen,
-               int64_t *ncover)
+               int64_t *ncover, double *habs, double *fabs_out)
 {
     uint64_t *skeys = malloc(n * sizeof(uint64_t));
     int64_t *order = malloc(n * sizeof(int64_t));
@@ -733,6 +749,8 @@ int64_t ora_bh(int64_t n, const double *pos, const double *u, const ora_bh_param
         if (npair) npair[k] = acc.npair;
         if (nopen) nopen[k] = acc.nopen;
         if (ncover) ncover[k] = acc.ncover;
+        if (habs) habs[k] = fabs(p->dip_scale) * acc.habs;
+        if (fabs_out) fabs_out[k] = fabs(p->dip_scale) * acc.fdabs + acc.fsabs;
     }
     int64_t nc = t.n;
     tree_free(&t);

@@ -35,6 +35,7 @@ struct ff_ctx {
     ff_params p;
     int64_t n = 0;
     bool fp64 = false;
+    bool mixed = false;  // single-precision tree with FP64 cell sums
     size_t rec = 16;  // bytes per record
     size_t cell_bytes = 32;  // bytes per Cell record
     cudaStream_t stream = nullptr;
@@ -58,6 +59,8 @@ struct ff_ctx {
     void* mom = nullptr;
     void* lo = nullptr;
     void* sum = nullptr;
+    ffk::dvec4* sum_hi = nullptr;  // FP64 cell sums (mixed precision only)
+    ffk::dvec4* mom_hi = nullptr;
     int* parent = nullptr;
     int* arrive = nullptr;
     int64_t cap = 0;
@@ -344,7 +347,12 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr)
     }
     {
         StageTimer st(c, S_AGG);
-        ffk::aggregate_tree<R>(V<R>(b.pos), V<R>(b.u), n, c->cnt, c->off, t, c->dflags, s);
+        if (c->mixed)
+            ffk::aggregate_tree<R, double>(V<R>(b.pos), V<R>(b.u), n, c->cnt, c->off, t, c->sum_hi,
+                                           c->mom_hi, c->dflags, s);
+        else
+            ffk::aggregate_tree<R, R>(V<R>(b.pos), V<R>(b.u), n, c->cnt, c->off, t, t.sum, t.mom,
+                                      c->dflags, s);
     }
     {
         StageTimer st(c, S_FIELD);
@@ -417,7 +425,7 @@ ff_status sync_and_check(ff_ctx* c)
 void free_all(ff_ctx* c)
 {
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->radix_tmp, c->cnt, c->off,
-                    c->scan_tmp, c->bbox, c->cell, c->mom, c->lo, c->sum, c->parent,
+                    c->scan_tmp, c->bbox, c->cell, c->mom, c->lo, c->sum, c->sum_hi, c->mom_hi, c->parent,
                     c->arrive, c->h, c->f, c->esr, c->counts, c->work, c->partials, c->obs, c->obs_step, c->dstep, c->sys_of_pos, c->sys_start, c->sys_h, c->sys_lo,
                     c->sys_hi, c->sys_acc,
                     c->dflags, c->staging};
@@ -477,6 +485,10 @@ ff_status alloc_all(ff_ctx* c)
     A(&c->mom, rec * c->cap);
     A(&c->lo, rec * c->cap);
     A(&c->sum, rec * c->cap);
+    if (c->mixed) {
+        A(&c->sum_hi, sizeof(ffk::dvec4) * c->cap);
+        A(&c->mom_hi, sizeof(ffk::dvec4) * c->cap);
+    }
     A(&c->parent, sizeof(int) * c->cap);
     A(&c->arrive, sizeof(int) * c->cap);
     A(&c->h, rec * n);
@@ -505,7 +517,8 @@ const char* check_params(const ff_params* p)
 {
     if (p->struct_size != sizeof(ff_params)) return "struct_size does not match sizeof(ff_params)";
     if (p->n < 1 || p->n > kMaxN) return "n out of range (1 .. 2^27)";
-    if (p->precision != FF_FP32 && p->precision != FF_FP64) return "bad precision";
+    if (p->precision != FF_FP32 && p->precision != FF_FP64 && p->precision != FF_MIXED)
+        return "bad precision";
     if (p->algo != FF_ALGO_BH && p->algo != FF_ALGO_AP) return "bad algo";
     if (p->leaf_max < 1 || p->leaf_max > ffk::kMaxLeaf) return "leaf_max out of range (1 .. 64)";
     if (!(p->theta >= 0.0) || !std::isfinite(p->theta)) return "theta must be finite and >= 0";
@@ -772,6 +785,7 @@ ff_status ff_create(const ff_params* p, ff_ctx** out)
     c->p = *p;
     c->n = p->n;
     c->fp64 = p->precision == FF_FP64;
+    c->mixed = p->precision == FF_MIXED;
     c->rec = c->fp64 ? sizeof(ffk::dvec4) : sizeof(float4);
     c->cell_bytes = c->fp64 ? sizeof(ffk::Cell<double>) : sizeof(ffk::Cell<float>);
     if (p->stream) {

@@ -150,9 +150,13 @@ void build_tree(const uint64_t* skeys, int64_t n, int leaf_max, const BBox* bb, 
                 uint32_t* cnt, uint32_t* off, uint32_t* scan_tmp, int* flags, Segs sg,
                 cudaStream_t s);
 
-template <typename R>
+// Aggregation sums in A (R, or double for single-precision trees whose cell
+// sums are formed in FP64); ssum/smom hold the A sums (the tree's own sum and
+// mom arrays when A = R).
+template <typename R, typename A>
 void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint32_t* cnt,
-                    const uint32_t* off, Tree<R> t, int* flags, cudaStream_t s);
+                    const uint32_t* off, Tree<R> t, vec4<A>* ssum, vec4<A>* smom, int* flags,
+                    cudaStream_t s);
 
 // Barnes-Hut traversal.  h/f (and esr, counts if non-null) in sorted order;
 // group = lanes that walk the cell list together (1, 2, 4, 8, 16 or 32);

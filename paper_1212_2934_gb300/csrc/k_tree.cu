@@ -555,12 +555,15 @@ __device__ __forceinline__ dvec4 ldcg4(const dvec4* p)
 
 // Bottom-up aggregation (Eq. magCenter): leaves sum their particles in
 // sorted order; the last child to arrive at a parent sums the parent's
-// children in octant order.  centre = position sum / count.
-template <typename R>
+// children in octant order.  centre = position sum / count.  Sums are formed
+// in A and kept in ssum/smom (for A = R these are the tree's own sum and mom
+// arrays); with A wider than R the moment sum and the centre are rounded to R
+// once, from the A sums.
+template <typename R, typename A>
 __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u,
                             int64_t n, const uint32_t* __restrict__ cnt,
-                            const uint32_t* __restrict__ off, Tree<R> t, const int* flags_in,
-                            int* flags)
+                            const uint32_t* __restrict__ off, Tree<R> t, vec4<A>* ssum,
+                            vec4<A>* smom, const int* flags_in, int* flags)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -570,27 +573,33 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
     int c = (int)off[i] + c0 - 1;
     int4 nd = t.cell[c].node;
     vec4<R> p = pos[nd.x], q = u[nd.x];
-    R sx = p.x, sy = p.y, sz = p.z, ux = q.x, uy = q.y, uz = q.z;
+    A sx = p.x, sy = p.y, sz = p.z, ux = q.x, uy = q.y, uz = q.z;
     for (int s = nd.x + 1; s < nd.y; ++s) {
         p = pos[s];
         q = u[s];
-        sx = radd(sx, p.x);
-        sy = radd(sy, p.y);
-        sz = radd(sz, p.z);
-        ux = radd(ux, q.x);
-        uy = radd(uy, q.y);
-        uz = radd(uz, q.z);
+        sx = radd(sx, (A)p.x);
+        sy = radd(sy, (A)p.y);
+        sz = radd(sz, (A)p.z);
+        ux = radd(ux, (A)q.x);
+        uy = radd(uy, (A)q.y);
+        uz = radd(uz, (A)q.z);
     }
     int guard = 0;
     for (;;) {
         const int cntc = nd.y - nd.x;
-        const R rn = (R)cntc;
-        vec4<R> sm, mm, cc;
-        sm.x = sx; sm.y = sy; sm.z = sz; sm.w = R(0);
+        const A rn = (A)cntc;
+        vec4<A> sm, mm;
+        vec4<R> cc;
+        sm.x = sx; sm.y = sy; sm.z = sz; sm.w = A(0);
         mm.x = ux; mm.y = uy; mm.z = uz; mm.w = rn;
-        cc.x = rdiv(sx, rn); cc.y = rdiv(sy, rn); cc.z = rdiv(sz, rn); cc.w = t.lo[c].w;
-        t.sum[c] = sm;
-        t.mom[c] = mm;
+        cc.x = (R)rdiv(sx, rn); cc.y = (R)rdiv(sy, rn); cc.z = (R)rdiv(sz, rn); cc.w = t.lo[c].w;
+        ssum[c] = sm;
+        smom[c] = mm;
+        if (sizeof(A) != sizeof(R)) {
+            vec4<R> mr;
+            mr.x = (R)ux; mr.y = (R)uy; mr.z = (R)uz; mr.w = (R)cntc;
+            t.mom[c] = mr;
+        }
         t.cell[c].cen = cc;
         const int par = t.parent[c];
         if (par < 0) break;
@@ -600,13 +609,13 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
         if (old + cntc != pn.y - pn.x) break;
         __threadfence();
         int ch = par + 1;
-        vec4<R> a = ldcg4(&t.sum[ch]), b = ldcg4(&t.mom[ch]);
+        vec4<A> a = ldcg4(&ssum[ch]), b = ldcg4(&smom[ch]);
         sx = a.x; sy = a.y; sz = a.z; ux = b.x; uy = b.y; uz = b.z;
         ch = t.cell[ch].node.z;
         int kids = 1;
         while (ch < pn.z && kids < 8) {
-            a = ldcg4(&t.sum[ch]);
-            b = ldcg4(&t.mom[ch]);
+            a = ldcg4(&ssum[ch]);
+            b = ldcg4(&smom[ch]);
             sx = radd(sx, a.x);
             sy = radd(sy, a.y);
             sz = radd(sz, a.z);
@@ -747,11 +756,13 @@ void build_tree(const uint64_t* skeys, int64_t n, int leaf_max, const BBox* bb, 
     counted(2);
 }
 
-template <typename R>
+template <typename R, typename A>
 void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint32_t* cnt,
-                    const uint32_t* off, Tree<R> t, int* flags, cudaStream_t s)
+                    const uint32_t* off, Tree<R> t, vec4<A>* ssum, vec4<A>* smom, int* flags,
+                    cudaStream_t s)
 {
-    k_aggregate<R><<<nblk(n, 128), 128, 0, s>>>(pos, u, n, cnt, off, t, flags, flags);
+    k_aggregate<R, A><<<nblk(n, 128), 128, 0, s>>>(pos, u, n, cnt, off, t, ssum, smom, flags,
+                                                   flags);
     counted();
 }
 
@@ -763,10 +774,14 @@ void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint3
                                   vec4<R>*, vec4<R>*, vec4<R>*, uint32_t*, cudaStream_t);      \
     template void build_tree<R>(const uint64_t*, int64_t, int, const BBox*, Tree<R>, uint32_t*, \
                                 uint32_t*, uint32_t*, int*, Segs, cudaStream_t);               \
-    template void aggregate_tree<R>(const vec4<R>*, const vec4<R>*, int64_t, const uint32_t*,   \
-                                    const uint32_t*, Tree<R>, int*, cudaStream_t);
+    template void aggregate_tree<R, R>(const vec4<R>*, const vec4<R>*, int64_t, const uint32_t*, \
+                                       const uint32_t*, Tree<R>, vec4<R>*, vec4<R>*, int*,       \
+                                       cudaStream_t);
 FFK_INST(float)
 FFK_INST(double)
 #undef FFK_INST
+template void aggregate_tree<float, double>(const float4*, const float4*, int64_t, const uint32_t*,
+                                            const uint32_t*, Tree<float>, dvec4*, dvec4*, int*,
+                                            cudaStream_t);
 
 }  // namespace ffk

@@ -15,7 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libff.so")
 
 FF_OK, FF_EINVAL, FF_ENOMEM, FF_ECUDA, FF_EDEVICE, FF_ENONFINITE, FF_ESTATE = range(7)
-FF_FP32, FF_FP64 = 0, 1
+FF_FP32, FF_FP64, FF_MIXED = 0, 1, 2
 FF_ALGO_BH, FF_ALGO_AP = 0, 1
 FF_DTYPE_F32, FF_DTYPE_F64 = 0, 1
 FF_HOST, FF_DEVICE = 0, 1
@@ -175,7 +175,11 @@ def ff_params_default(**overrides):
             for i in range(3):
                 arr[i] = float(v[i])
         elif k == "precision" and isinstance(v, str):
-            p.precision = FF_FP64 if v in ("f64", "fp64", "float64") else FF_FP32
+            names = {"f32": FF_FP32, "fp32": FF_FP32, "float32": FF_FP32, "f64": FF_FP64,
+                     "fp64": FF_FP64, "float64": FF_FP64, "mixed": FF_MIXED}
+            if v not in names:
+                raise ValueError("precision must be one of %s" % sorted(names))
+            p.precision = names[v]
         elif k == "algo" and isinstance(v, str):
             p.algo = FF_ALGO_AP if v == "ap" else FF_ALGO_BH
         else:

@@ -171,30 +171,41 @@ def chains_cube(nchains: int, length: int, side: float, seed: int,
     """Straight chains of touching particles with isotropic axes, overlap-free.
 
     Returns (pos, u): moments lie along each chain's axis with a random sign
-    per chain (head-to-tail).  Chains are placed one batch at a time and a
-    chain is rejected if any of its centres leaves the cube or comes closer
-    than dmin to a centre of an accepted chain or of an earlier chain of its
-    batch.
+    per chain (head-to-tail).  Chains are drawn in batches (uniform start,
+    isotropic axis) and a chain is rejected if any of its centres leaves the
+    cube or comes closer than dmin to a centre of an accepted chain or of an
+    earlier chain of its batch (random sequential addition of rods).  Accepted
+    centres are searched through two k-d trees, a large one rebuilt rarely and
+    a small one holding the chains accepted since, so that a batch costs time
+    in proportion to its own size.
     """
     from scipy.spatial import cKDTree
 
     rng = np.random.default_rng([seed, 0xC4A1])
-    span = (length - 1) * spacing
     placed = []
     placed_u = []
-    tree_pts = np.empty((0, 3))
-    tree = None
     t = np.arange(length) * spacing
-    while len(placed) < nchains:
-        m = min(4096, 2 * (nchains - len(placed)))
+    main_pts = np.empty((0, 3))
+    main_tree = None
+    recent = []
+    recent_tree = None
+    count = 0
+    idle = 0
+    while count < nchains:
+        if idle > 200:
+            raise RuntimeError("chains_cube: no chain fits any more (%d of %d placed); the "
+                               "cube is too small for isotropic rods" % (count, nchains))
+        m = max(1024, min(8192, 2 * (nchains - count)))
         axis = rng.standard_normal((m, 3))
         axis /= np.linalg.norm(axis, axis=1)[:, None]
         start = rng.uniform(0.0, side, (m, 3))
         pts = start[:, None, :] + t[None, :, None] * axis[:, None, :]
         ok = np.all((pts >= 0.0) & (pts <= side), axis=(1, 2))
-        if tree is not None:
-            d, _ = tree.query(pts.reshape(-1, 3), k=1, distance_upper_bound=dmin)
-            ok &= ~np.any((d < dmin).reshape(m, length), axis=1)
+        flat_q = pts.reshape(-1, 3)
+        for tree in (main_tree, recent_tree):
+            if tree is not None:
+                d, _ = tree.query(flat_q, k=1, distance_upper_bound=dmin)
+                ok &= ~np.any((d < dmin).reshape(m, length), axis=1)
         idx = np.nonzero(ok)[0]
         if idx.size:
             flat = pts[idx].reshape(-1, 3)
@@ -205,16 +216,25 @@ def chains_cube(nchains: int, length: int, side: float, seed: int,
                 oa, ob = owner[pairs[:, 0]], owner[pairs[:, 1]]
                 cross = oa != ob
                 keep[np.maximum(oa[cross], ob[cross])] = False
-            idx = idx[keep][: nchains - len(placed)]
-        for i in idx:
-            sgn = 1.0 if rng.uniform() < 0.5 else -1.0
-            placed.append(pts[i])
-            placed_u.append(np.repeat((sgn * axis[i])[None, :], length, axis=0))
-        if idx.size:
-            tree_pts = np.concatenate([tree_pts, pts[idx].reshape(-1, 3)])
-            tree = cKDTree(tree_pts)
-    pos = np.concatenate(placed)[: nchains * length]
-    u = np.concatenate(placed_u)[: nchains * length]
+            idx = idx[keep][: nchains - count]
+        if idx.size == 0:
+            idle += 1
+            continue
+        idle = 0
+        sgn = np.where(rng.uniform(size=idx.size) < 0.5, 1.0, -1.0)
+        placed.append(pts[idx].reshape(-1, 3))
+        placed_u.append(np.repeat(sgn[:, None] * axis[idx], length, axis=0))
+        count += idx.size
+        recent.append(pts[idx].reshape(-1, 3))
+        rpts = np.concatenate(recent)
+        if rpts.shape[0] > max(0.25 * main_pts.shape[0], 65536):
+            main_pts = np.concatenate([main_pts, rpts])
+            main_tree = cKDTree(main_pts)
+            recent, recent_tree = [], None
+        else:
+            recent_tree = cKDTree(rpts)
+    pos = np.concatenate(placed)
+    u = np.concatenate(placed_u)
     return pos, u
 
 

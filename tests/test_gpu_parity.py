@@ -48,11 +48,11 @@ def _ctx(ff, n, prec, leaf_max=1, **kw):
 
 
 def _cast(prec, *arrs):
-    dt = np.float32 if prec == "f32" else np.float64
+    dt = np.float64 if prec == "f64" else np.float32  # f32 and mixed store single
     return [np.ascontiguousarray(a, dtype=dt) for a in arrs]
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "mixed"])
 @pytest.mark.parametrize("n,leaf_max", [(1, 1), (2, 1), (33, 1), (1000, 1), (5003, 1),
                                         (5003, 4), (4099, 16)])
 def test_keys_and_tree_bit_exact(ff, ora, prec, n, leaf_max):
@@ -68,7 +68,11 @@ def test_keys_and_tree_bit_exact(ff, ora, prec, n, leaf_max):
     for k in ("pbegin", "pend", "skip", "level", "leaf"):
         assert np.array_equal(g[k].astype(np.int64), t[k].astype(np.int64)), k
     assert np.array_equal(g["centre"], t["centre"])  # exact in the tree precision
-    np.testing.assert_allclose(g["moment"], t["U"], rtol=0, atol=(2e-5 if prec == "f32" else 1e-12) * max(1, np.abs(t["U"]).max()))
+    if prec == "mixed":
+        # FP64 sums in the oracle's order, rounded once: exact
+        assert np.array_equal(g["moment"], t["U"].astype(np.float32).astype(np.float64))
+    else:
+        np.testing.assert_allclose(g["moment"], t["U"], rtol=0, atol=(2e-5 if prec == "f32" else 1e-12) * max(1, np.abs(t["U"]).max()))
     info = g["info"]
     assert info["ncells"] == len(t["level"])
     assert np.allclose(info["root"], t["root"])
@@ -88,16 +92,18 @@ def _bh_case(ff, ora, prec, pos, u, theta, leaf_max=1, **kw):
     return ctx, h, f, ref
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "mixed"])
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
 @pytest.mark.parametrize("leaf_max", [1, 8])
 @pytest.mark.parametrize("group", [1, 4, 8, 16, 32])
 def test_bh_field_matches_oracle(ff, ora, prec, theta, leaf_max, group):
     if group not in (8, 32) and (theta != 0.5 or leaf_max != 1):
         pytest.skip("group sizes other than 8 and 32 are checked at theta 0.5, leaf_max 1")
+    if prec == "mixed" and group not in (1, 32):
+        pytest.skip("mixed precision is checked with groups 1 and 32")
     pos, u, _ = _system(6007, 21)
     ctx, h, f, ref = _bh_case(ff, ora, prec, pos, u, theta, leaf_max, traverse_group=group)
-    tol = TOL32 if prec == "f32" else TOL64
+    tol = TOL64 if prec == "f64" else TOL32
     eh, ef = rel_err(h, ref["h"]), rel_err(f, ref["f"])
     assert eh.max() <= tol, eh.max()
     assert ef.max() <= tol, ef.max()

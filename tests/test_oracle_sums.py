@@ -114,3 +114,56 @@ def test_bh_subset_rows(ora):
     part = ora.bh(pos, u, 0.5, 1, "f32", lj_eps=1.0, only=idx)
     np.testing.assert_array_equal(part["h"][idx], full["h"][idx])
     np.testing.assert_array_equal(part["nacc"][idx], full["nacc"][idx])
+
+
+def test_allpairs_target_subset(ora, rng):
+    """Rows of a target subset equal the same rows of the full sum (sources are all particles)."""
+    n = 700
+    pos = rng.uniform(0, 12, (n, 3))
+    u = rng.normal(size=(n, 3))
+    h, f, e = ora.allpairs(pos, u, lj_eps=1.0)
+    idx = np.array([0, 5, 699, 123, 5])
+    hs, fs, es = ora.allpairs(pos, u, lj_eps=1.0, only=idx)
+    assert np.array_equal(hs[idx], h[idx]) and np.array_equal(fs[idx], f[idx])
+    assert np.array_equal(es[idx], e[idx])
+    rest = np.setdiff1d(np.arange(n), idx)
+    assert not hs[rest].any() and not fs[rest].any()
+
+
+def test_term_magnitude_sums(ora, rng):
+    """habs/fabs: the sums of the magnitudes of the terms summed into h and f (the scale of
+    the rounding error of a sum with cancellation)."""
+    # three touching head-to-tail dipoles on a line: the middle one feels two pair forces of
+    # magnitude 6 (collinear unit dipoles at unit distance: 6 / r^4) that cancel
+    pos = np.array([[0.0, 0, 0], [1.0, 0, 0], [2.0, 0, 0]])
+    u = np.array([[1.0, 0, 0]] * 3)
+    r = ora.bh(pos, u, 0.0, 1, "f64")
+    assert r["fabs"][1] == pytest.approx(12.0, rel=1e-14)
+    assert np.abs(r["f"][1]).max() < 1e-12
+    assert r["habs"][1] == pytest.approx(4.0, rel=1e-14)  # |h| of each neighbour: 2 / r^3
+    assert np.linalg.norm(r["h"][1]) == pytest.approx(4.0, rel=1e-14)  # fields add here
+    # a single pair: one term each
+    r2 = ora.bh(pos[:2], u[:2], 0.0, 1, "f64", 0.5)
+    np.testing.assert_allclose(r2["fabs"], np.linalg.norm(r2["f"], axis=1), rtol=1e-14)
+    np.testing.assert_allclose(r2["habs"], np.linalg.norm(r2["h"], axis=1), rtol=1e-14)
+    # brute force at theta = 0 with LJ, and the triangle inequality at theta = 0.5
+    n = 24
+    pos = synth.rsa_cube(n, 5.0, 8)
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    r = ora.bh(pos, u, 0.0, 1, "f64", 0.7, 1.0, 1.0, 2.5, True)
+    for k in range(n):
+        hs = fs = 0.0
+        for j in range(n):
+            if j == k:
+                continue
+            h, f = ora.pair_dipole(pos[k] - pos[j], u[k], u[j])
+            hs += 0.7 * np.linalg.norm(h)
+            fs += 0.7 * np.linalg.norm(f)
+            if np.linalg.norm(pos[k] - pos[j]) < 2.5:
+                fs += np.linalg.norm(ora.pair_lj(pos[k] - pos[j])[0])
+        assert r["habs"][k] == pytest.approx(hs, rel=1e-12)
+        assert r["fabs"][k] == pytest.approx(fs, rel=1e-12)
+    r = ora.bh(synth.rsa_cube(500, 12.0, 2), rng.normal(size=(500, 3)), 0.5, 1, "f32")
+    assert np.all(r["habs"] >= np.linalg.norm(r["h"], axis=1) * (1 - 1e-12))
+    assert np.all(r["fabs"] >= np.linalg.norm(r["f"], axis=1) * (1 - 1e-12))

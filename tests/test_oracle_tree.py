@@ -181,3 +181,46 @@ def test_aggregates(ora, rng):
             # every particle lies in its cell's cube (up to one quantisation step)
             q = t["side"][c] * 1e-6 + 2 ** -21 * t["root"][3]
             assert np.all(p[idx] >= t["lo"][c] - q) and np.all(p[idx] <= t["lo"][c] + t["side"][c] + q)
+
+
+def test_mixed_precision_tree(ora, rng):
+    """Mixed precision: keys, topology and cube geometry are those of the single-precision
+    tree; each centre is the FP64 mean of the cell's particles rounded once to single."""
+    n = 3000
+    pos = rng.uniform(0, 40, (n, 3)).astype(np.float32).astype(np.float64)
+    u = rng.normal(size=(n, 3))
+    s = ora.tree(pos, u, "f32", 1)
+    m = ora.tree(pos, u, "mixed", 1)
+    for k in ("keys", "order", "level", "leaf", "pbegin", "pend", "skip", "lo", "side", "root"):
+        assert np.array_equal(s[k], m[k]), k
+    order = m["order"]
+    for c in range(len(m["level"])):
+        idx = order[m["pbegin"][c]:m["pend"][c]]
+        mean = pos[idx].mean(axis=0)
+        np.testing.assert_allclose(m["centre64"][c], mean, rtol=1e-13)
+    assert np.array_equal(m["centre"], m["centre64"].astype(np.float32).astype(np.float64))
+    # one-particle leaves: the particle itself in both modes
+    one = (m["pend"] - m["pbegin"]) == 1
+    assert np.array_equal(m["centre"][one], s["centre"][one])
+    # cells of many particles: single-precision sums drift, the rounded FP64 mean does not
+    big = (m["pend"] - m["pbegin"]) >= 256
+    err_s = np.abs(s["centre"][big] - m["centre64"][big]).max()
+    err_m = np.abs(m["centre"][big] - m["centre64"][big]).max()
+    assert err_m <= 2.0 ** -24 * 40 and err_m <= err_s
+
+
+def test_mixed_precision_bh(ora, rng):
+    """Mixed-precision Barnes-Hut: theta = 0 is all-pairs; at theta = 0.5 it agrees with the
+    single-precision tree to rounding (only the centres differ, by a few single ulps)."""
+    n = 1500
+    pos = rng.uniform(0, 25, (n, 3)).astype(np.float32).astype(np.float64)
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    ap_h, ap_f, _ = ora.allpairs(pos, u, include_sr=False)
+    r0 = ora.bh(pos, u, 0.0, 1, "mixed")
+    np.testing.assert_allclose(r0["h"], ap_h, rtol=1e-12, atol=1e-12 * np.abs(ap_h).max())
+    rs = ora.bh(pos, u, 0.5, 1, "f32")
+    rm = ora.bh(pos, u, 0.5, 1, "mixed")
+    scale = np.sqrt((rs["h"] ** 2).sum(axis=1)).mean()
+    assert np.abs(rm["h"] - rs["h"]).max() <= 1e-4 * scale
+    assert (rm["ncover"] + rm["npair"] == n - 1).all()
