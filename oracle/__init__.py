@@ -59,6 +59,9 @@ def lib():
         L.ora_allpairs.argtypes = [_i64, _dp, _dp, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int32, C.c_int32, C.c_void_p, _i64, _dp, _dp,
                                    C.c_void_p]
+        L.ora_bh_energy_grad.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p, _dp,
+                                         _dp]
+        L.ora_bh_energy_grad.restype = C.c_double
         L.ora_morton.argtypes = [_i64, _dp, C.c_int32, _u64p, _dp]
         L.ora_tree.argtypes = [_i64, _dp, _dp, C.c_int32, C.c_int32, _u64p, _i64p, _dp, _i64,
                                _i32p, _i32p, _i64p, _i64p, _i64p, _dp, _dp, _dp, _dp, _dp]
@@ -219,6 +222,27 @@ def bh(pos, u, theta, leaf_max=1, prec="f32", dip_scale=1.0, lj_eps=0.0, lj_sigm
                       _ptr(npair), _ptr(nopen), _ptr(ncover), habs, fabs)
     return dict(h=h, f=f, e_sr=e, nacc=nacc, npair=npair, nopen=nopen, ncover=ncover,
                 habs=habs, fabs=fabs, ncells=int(nc))
+
+
+def bh_energy_grad(pos, u, theta, leaf_max=1, prec="f64", dip_scale=1.0, lj_eps=0.0,
+                   lj_sigma=1.0, lj_rcut=2.5, pos_dec=None):
+    """Barnes-Hut dipolar energy E = -1/2 sum u.h and its exact gradient with the opening
+    decisions taken on pos_dec (default: pos) and frozen.  Returns (E, grad_pos, grad_u)."""
+    pos, u = _vec3(pos), _vec3(u)
+    n = pos.shape[0]
+    p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec),
+                 dip_scale=float(dip_scale), lj_eps=float(lj_eps), lj_sigma=float(lj_sigma),
+                 lj_rcut=float(lj_rcut), include_sr=0, pad=0)
+    gp = np.zeros((n, 3))
+    gu = np.zeros((n, 3))
+    keep = None
+    if pos_dec is not None:
+        keep = _vec3(pos_dec)
+        if keep.shape != pos.shape:
+            raise ValueError("pos_dec must match pos")
+    e = lib().ora_bh_energy_grad(n, pos, u, C.byref(p),
+                                 None if keep is None else C.c_void_p(keep.ctypes.data), gp, gu)
+    return float(e), gp, gu
 
 
 def philox4x32_10(ctr, key):

@@ -761,6 +761,196 @@ int64_t ora_bh(int64_t n, const double *pos, const double *u, const ora_bh_param
 }
 
 /* ------------------------------------------------------------------------ */
+/* gradient of the Barnes-Hut dipolar energy (decisions frozen)             */
+/* ------------------------------------------------------------------------ */
+/*
+ * E = -1/2 * dip_scale * sum_m u_m . H_m with H_m = sum over m's sources s of
+ * T(rho_m - x_s) w_s, T(r) = (3 r r^T - r^2 I) / r^5 (Sec. 2, Eq. h_dip), the
+ * sources being the cells m accepts (x = mean position of the cell's
+ * particles, w = their moment sum, Eq. magCenter) and the particles it sums
+ * exactly.  Which sources m sees is decided on a reference configuration
+ * pos_dec (the opening test of Sec. 3.2 is piecewise constant in the
+ * positions); E and its gradient are evaluated at pos with those decisions
+ * frozen, so a central difference of E that moves pos but keeps pos_dec is a
+ * difference of one smooth function.
+ *
+ * With phi(r; a, b) = a . T(r) b (symmetric in a, b; its r-gradient is the
+ * printed force f_dip):
+ *   dE/du_k   = -1/2 ds [ H_k + sum over (m, s) with k in s of T(rho_m - x_s) u_m ]
+ *   dE/drho_k = -1/2 ds [ F_k - sum over (m, s) with k in s of
+ *                          grad phi(rho_m - x_s; u_m, w_s) / n_s ]
+ * where F_k = sum_s grad phi(rho_k - x_s; u_k, w_s) and n_s is the number of
+ * particles in s.  Returns E; grad_pos and grad_u are n x 3.
+ */
+typedef struct {
+    const bh_ctx *g;          /* decisions: tree of pos_dec */
+    const double *pos_dec;
+    const double *cc, *uc;    /* current centre and moment sum of every cell */
+    double *acc;              /* this thread's source sums: 6 per cell, then 6 per particle */
+    double H[3], F[3];
+} grad_ctx;
+
+static void grad_term(grad_ctx *q, int64_t m, const double *xs, const double *ws, double *sum6)
+{
+    const double *xm = &q->g->pos[3 * m];
+    const double *um = &q->g->u[3 * m];
+    double r[3], hp[3], fp[3], hr[3], fr[3];
+    for (int a = 0; a < 3; ++a) r[a] = xm[a] - xs[a];
+    if (dot3(r, r) == 0.0) return;
+    ora_pair_dipole(r, um, ws, hp, fp);   /* field of the source at m, force on m */
+    for (int a = 0; a < 3; ++a) { q->H[a] += hp[a]; q->F[a] += fp[a]; }
+    ora_pair_dipole(r, ws, um, hr, fr);   /* T(r) u_m and grad phi(r; w_s, u_m) */
+    for (int a = 0; a < 3; ++a) { sum6[a] += hr[a]; sum6[3 + a] += fr[a]; }
+}
+
+static void grad_visit(grad_ctx *q, int64_t m, int64_t sm, int64_t c)
+{
+    const bh_ctx *g = q->g;
+    const ora_tree_t *t = g->t;
+    const double *xd = &q->pos_dec[3 * m];
+    int inside = (t->pbegin[c] <= sm && sm < t->pend[c]);
+    int ok = 0;
+    if (!inside) {
+        if (g->p->prec != 1) {
+            float xf[3], cf[3], lof[3];
+            for (int a = 0; a < 3; ++a) {
+                xf[a] = (float)xd[a];
+                cf[a] = (float)t->cen[3 * c + a];
+                lof[a] = (float)t->lo[3 * c + a];
+            }
+            ok = accept_f(xf, cf, (float)t->side[c], lof, g->theta2_f, g->use_rcut, g->rcut2_f);
+        } else {
+            ok = accept_d(xd, &t->cen[3 * c], t->side[c], &t->lo[3 * c], g->theta2_d,
+                          g->use_rcut, g->rcut2_d);
+        }
+    }
+    if (ok) {
+        grad_term(q, m, &q->cc[3 * c], &q->uc[3 * c], &q->acc[6 * c]);
+        return;
+    }
+    if (t->leaf[c]) {
+        for (int64_t s = t->pbegin[c]; s < t->pend[c]; ++s) {
+            if (s == sm) continue;
+            int64_t j = g->order[s];
+            grad_term(q, m, &g->pos[3 * j], &g->u[3 * j], &q->acc[6 * (t->n + j)]);
+        }
+        return;
+    }
+    int64_t ch = c + 1;
+    while (ch < t->skip[c]) {
+        grad_visit(q, m, sm, ch);
+        ch = t->skip[ch];
+    }
+}
+
+double ora_bh_energy_grad(int64_t n, const double *pos, const double *u, const ora_bh_params *p,
+                          const double *pos_dec, double *grad_pos, double *grad_u)
+{
+    if (!pos_dec) pos_dec = pos;
+    uint64_t *skeys = malloc(n * sizeof(uint64_t));
+    int64_t *order = malloc(n * sizeof(int64_t));
+    int64_t *rank = malloc(n * sizeof(int64_t));
+    double root[4];
+    ora_tree_t t;
+    tree_build(n, pos_dec, u, p->prec, p->leaf_max, skeys, order, root, &t);
+    for (int64_t s = 0; s < n; ++s) rank[order[s]] = s;
+    const int64_t nc = t.n;
+
+    /* current geometry of every cell: plain FP64 sums over its particles */
+    double *cc = calloc(3 * nc, sizeof(double));
+    double *uc = calloc(3 * nc, sizeof(double));
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int64_t s = t.pbegin[c]; s < t.pend[c]; ++s) {
+            int64_t j = order[s];
+            for (int a = 0; a < 3; ++a) {
+                cc[3 * c + a] += pos[3 * j + a];
+                uc[3 * c + a] += u[3 * j + a];
+            }
+        }
+        double cnt = (double)(t.pend[c] - t.pbegin[c]);
+        for (int a = 0; a < 3; ++a) cc[3 * c + a] /= cnt;
+    }
+
+    bh_ctx g;
+    g.t = &t;
+    g.order = order;
+    g.pos = pos;
+    g.u = u;
+    g.p = p;
+    g.use_rcut = (p->lj_eps != 0.0 && p->lj_rcut > 0.0);
+    g.theta2_d = p->theta * p->theta;
+    g.theta2_f = (float)g.theta2_d;
+    g.rcut2_d = g.use_rcut ? p->lj_rcut * p->lj_rcut : 0.0;
+    g.rcut2_f = (float)g.rcut2_d;
+
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    const int64_t nsrc = nc + n;
+    double *acc = calloc((size_t)nthr * 6 * nsrc, sizeof(double));
+    double *H = calloc(3 * n, sizeof(double));
+    double *F = calloc(3 * n, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < n; ++m) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        grad_ctx q;
+        q.g = &g;
+        q.pos_dec = pos_dec;
+        q.cc = cc;
+        q.uc = uc;
+        q.acc = acc + (size_t)tid * 6 * nsrc;
+        memset(q.H, 0, sizeof(q.H));
+        memset(q.F, 0, sizeof(q.F));
+        grad_visit(&q, m, rank[m], 0);
+        for (int a = 0; a < 3; ++a) {
+            H[3 * m + a] = q.H[a];
+            F[3 * m + a] = q.F[a];
+        }
+    }
+    /* source sums over the threads, in thread order */
+    for (int th = 1; th < nthr; ++th)
+        for (int64_t i = 0; i < 6 * nsrc; ++i) acc[i] += acc[(size_t)th * 6 * nsrc + i];
+
+    /* push each cell's sums to its particles; particle sources to themselves */
+    double *gsum = calloc(3 * n, sizeof(double));
+    double *qsum = calloc(3 * n, sizeof(double));
+    for (int64_t c = 0; c < nc; ++c) {
+        double cnt = (double)(t.pend[c] - t.pbegin[c]);
+        for (int64_t s = t.pbegin[c]; s < t.pend[c]; ++s) {
+            int64_t k = order[s];
+            for (int a = 0; a < 3; ++a) {
+                gsum[3 * k + a] += acc[6 * c + a];
+                qsum[3 * k + a] += acc[6 * c + 3 + a] / cnt;
+            }
+        }
+    }
+    for (int64_t k = 0; k < n; ++k)
+        for (int a = 0; a < 3; ++a) {
+            gsum[3 * k + a] += acc[6 * (nc + k) + a];
+            qsum[3 * k + a] += acc[6 * (nc + k) + 3 + a];
+        }
+    double E = 0.0;
+    const double ds = p->dip_scale;
+    for (int64_t k = 0; k < n; ++k) {
+        E += dot3(&u[3 * k], &H[3 * k]);
+        for (int a = 0; a < 3; ++a) {
+            grad_u[3 * k + a] = -0.5 * ds * (H[3 * k + a] + gsum[3 * k + a]);
+            grad_pos[3 * k + a] = -0.5 * ds * (F[3 * k + a] - qsum[3 * k + a]);
+        }
+    }
+    E *= -0.5 * ds;
+    free(gsum); free(qsum); free(acc); free(H); free(F); free(cc); free(uc);
+    tree_free(&t);
+    free(skeys); free(order); free(rank);
+    return E;
+}
+
+
+/* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)                         */
 /* ------------------------------------------------------------------------ */
 /*
