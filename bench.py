@@ -54,12 +54,13 @@ def parse():
     ap.add_argument("--group", type=int, default=0,
                     help="lanes walking the cell list together (0: picked by the library's "
                          "autotuner on the workload before warm-up)")
-    ap.add_argument("--workload", default="phi05", choices=["phi05", "batched", "chains"],
+    ap.add_argument("--workload", default="phi05", choices=["phi05", "batched", "chains", "grad"],
                     help="phi05: one system of --n particles (default); batched: 256 independent "
                          "dilute systems of log-uniform sizes 1,024..65,536 at fields 0..5; "
                          "chains: 65,536 straight chains of 64 touching dipoles (4,194,304 "
                          "particles) at volume fraction 0.01, FP32 with the mixed and FP64 paths "
-                         "timed beside it")
+                         "timed beside it; grad: gradient of the dipolar energy with respect to "
+                         "all positions and moments at N = 262,144, volume fraction 0.05")
     ap.add_argument("--split", action="store_true",
                     help="batched workload on several GPUs: share one 256-system batch among "
                          "the ranks (strong scaling) instead of one batch per rank (weak)")
@@ -354,7 +355,13 @@ def run_reference(args):
         return 0
     if args.workload == "batched":
         return run_reference_batched(args)
-    pos, u, side = workload(args.n)
+    if args.workload == "grad":
+        return run_reference_grad(args)
+    if args.workload == "chains":
+        pos, u, side = chains_workload(seed=1)
+        args.n = pos.shape[0]
+    else:
+        pos, u, side = workload(args.n)
     sample = 65536
     for _ in range(args.warmup):
         cpu_step_sample(pos, u, args.theta, args.leaf_max, side, sample)
@@ -365,10 +372,11 @@ def run_reference(args):
         rates.append(r)
     wall = time.perf_counter() - t0
     value = float(np.mean(rates))
-    cfg = config_dict(args, side)
+    cfg = config_dict(args, side) if args.workload != "chains" else chains_config(args, args.n,
+                                                                                     side, 1)
     cfg["precision"] = "fp64 sums, fp32 tree"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC if args.workload != "chains" else CHAINS_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.n / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
@@ -377,6 +385,44 @@ def run_reference(args):
                                    "particles, traversal of %d sampled particles, scaled to all"
                                    % (args.n, s)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_grad(args):
+    """The oracle's energy gradient (all particles) per step on the gradient workload."""
+    import oracle
+
+    pos, u, side = workload(GRAD_N)
+    p64 = pos.astype(np.float32).astype(np.float64)
+    u64 = u.astype(np.float64)
+
+    def once():
+        oracle.bh_energy_grad(p64, u64, args.theta, args.leaf_max, "f32", lj_eps=1.0,
+                              tree_centres=True)
+
+    for _ in range(args.warmup):
+        once()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        once()
+    wall = time.perf_counter() - t0
+    value = GRAD_N * args.steps / wall
+    line = {
+        "impl": "reference", "metric": GRAD_METRIC, "value": value,
+        "unit": "particle-gradients/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gradient of E_dip (Barnes-Hut, decisions frozen), volume "
+                               "fraction 0.05", "n": GRAD_N, "theta": args.theta,
+                   "leaf_max": args.leaf_max, "precision": "fp64 sums, fp32 tree"},
+        "cpu_baseline": {"value": value, "unit": "particle-gradients/s",
+                         "cores": oracle.get_threads(), "kind": "oracle",
+                         "sample": "every step: the full gradient of all %d particles" % GRAD_N},
+        "e2e": {"value": value, "unit": "particle-gradients/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
         "wall_s": wall,
     }
     print(json.dumps(line))
@@ -759,10 +805,159 @@ def run_ours(args):
     return 0
 
 
+GRAD_METRIC = ("particle-gradients/s: dE_dip/dpos and dE_dip/du of the Barnes-Hut energy "
+               "(decisions frozen) at N=262,144, phi 0.05, theta=0.5, FP32")
+GRAD_N = 262144
+
+
+def run_grad(args):
+    """Times ff_energy_grad (energy and its gradient w.r.t. every position and moment) on one
+    GPU; each repetition re-sorts, rebuilds and traverses the current state."""
+    import torch
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1212_2934_gb300 import ff
+
+    K, W = args.steps, args.warmup
+    pos, u, side = workload(GRAD_N)
+    n = GRAD_N
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    p = ff.ff_params_default(n=n, precision="f32", theta=args.theta, leaf_max=args.leaf_max,
+                             device=dev, stream=stream.cuda_stream)
+    ctx = ff.ff_create(p)
+    pos_d = torch.tensor(pos, dtype=torch.float32, device="cuda")
+    u_d = torch.tensor(u, dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ff.ff_set_particles(ctx, pos_d, u_d)
+    gp = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    gu = torch.empty_like(gp)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def grad_once():
+        e = ff.C.c_double()
+        ff._check(ctx.handle, ff.lib().ff_energy_grad(
+            ctx.handle, ff.FF_ALGO_BH, float(args.theta), ff.C.byref(e),
+            ff.C.c_void_p(gp.data_ptr()), ff.C.c_void_p(gu.data_ptr()), ff.FF_DTYPE_F32,
+            ff.FF_DEVICE))
+        return e.value
+
+    for _ in range(W):
+        grad_once()
+        flush.zero_()
+    barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    launches0 = ff.ff_profile_read(ctx)["launches"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    clocks.mark_start()
+    for a, b in evs:
+        a.record(stream)
+        e = grad_once()
+        b.record(stream)
+        flush.zero_()
+    barrier()
+    clocks.mark_end()
+    clk = clocks.stop()
+    launches = ff.ff_profile_read(ctx)["launches"] - launches0
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    max_ms = max_over_ranks(total_ms, "cuda")
+    value = whole_job_rate(n, K, world, max_ms / 1e3)
+    # the forward field alone on the same state, for the cost ratio
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hb = torch.empty_like(gp)
+    fb = torch.empty_like(gp)
+    f0.record(stream)
+    for _ in range(K):
+        ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, args.theta, False, hb, fb)
+    f1.record(stream)
+    barrier()
+    field_ms = f0.elapsed_time(f1) / K
+    # end to end: host state in, gradients out to pinned host memory
+    host_p = torch.from_numpy(pos.astype(np.float32)).pin_memory().numpy()
+    host_u = torch.from_numpy(u.astype(np.float32)).pin_memory().numpy()
+    out_p = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+    out_u = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+    ptr = lambda a: ff.C.c_void_p(a.ctypes.data)
+
+    def e2e_once():
+        ff._check(ctx.handle, ff.lib().ff_set_particles(ctx.handle, ptr(host_p), ptr(host_u), None,
+                                                        None, ff.FF_DTYPE_F32, ff.FF_HOST))
+        e = ff.C.c_double()
+        ff._check(ctx.handle, ff.lib().ff_energy_grad(ctx.handle, ff.FF_ALGO_BH, float(args.theta),
+                                                      ff.C.byref(e), ptr(out_p), ptr(out_u),
+                                                      ff.FF_DTYPE_F32, ff.FF_HOST))
+
+    e2e_once()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        e2e_once()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    line = {
+        "metric": GRAD_METRIC, "value": value, "unit": "particle-gradients/s", "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": max_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "gradient of E_dip = -1/2 sum u.h (Barnes-Hut, decisions frozen) "
+                               "w.r.t. all positions and moments; dipoles at volume fraction "
+                               "0.05 (hard core 1.0, RSA), isotropic moments",
+                   "n": n, "box_side": round(side, 4), "theta": args.theta,
+                   "leaf_max": args.leaf_max, "precision": "fp32",
+                   "l2": "flushed between timed evaluations (256 MB write outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "paths": {"field_only_ms": field_ms, "gradient_over_field": (max_ms / K) / field_ms,
+                  "energy": e},
+        "e2e": {"value": whole_job_rate(n, K, world, max_over_ranks(e2e_s, "cuda")),
+                "unit": "particle-gradients/s", "h2d_bytes_per_step": 2 * n * 3 * 4,
+                "d2h_bytes_per_step": 2 * n * 3 * 4,
+                "note": "ff_set_particles + ff_energy_grad on pinned host float32 arrays, "
+                        "wall clock"},
+    }
+    if rank == 0 and world == 1 and not args.no_extras:
+        import oracle
+
+        p64 = pos.astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.bh_energy_grad(p64, u.astype(np.float64), args.theta, args.leaf_max, "f32",
+                              lj_eps=1.0, tree_centres=True)
+        cpu_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n / cpu_s, "unit": "particle-gradients/s",
+                                "cores": oracle.get_threads(), "kind": "oracle",
+                                "sample": "one full gradient of all %d particles (%.1f s)"
+                                          % (n, cpu_s)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "grad":
+        return run_grad(args)
     return run_ours(args)
 
 

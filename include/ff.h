@@ -226,6 +226,26 @@ ff_status ff_system_moments(ff_ctx *ctx, double *out, int64_t *nsteps, int32_t r
 ff_status ff_tune_traversal(ff_ctx *ctx, const int32_t *groups, int32_t ngroups, int32_t reps,
                             int32_t *best_group, float *ms);
 
+/*
+ * Dipolar energy E = -1/2 sum_k u_k . h_k (Sec. 5; h from algo, LJ excluded)
+ * and its gradient with respect to every position and moment.  With
+ * FF_ALGO_AP every pair is exact: dE/du = -h and dE/drho = -f (the dipolar
+ * force).  With FF_ALGO_BH the gradient is exact for the Barnes-Hut energy
+ * with this evaluation's opening decisions frozen (the decisions are
+ * piecewise constant in the positions, Sec. 3.2): besides -1/2 h_k and
+ * -1/2 f_k it carries the reverse sums over every interaction whose source
+ * (an accepted cell, or a particle summed exactly) contains particle k.
+ * The current state is evaluated (and, for Barnes-Hut, sorted into key
+ * order); *energy (may be NULL) receives E in FP64; grad_pos and grad_u (may
+ * be NULL) receive n x 3 values in the caller's order, dtype/loc as in
+ * ff_get_particles.  The Barnes-Hut gradient records one entry per
+ * interaction (12 bytes x 2 buffers; about 1000 interactions per particle
+ * at theta = 0.5), allocated on first use and grown as needed; more than
+ * 2^32 - 1 interactions is FF_EINVAL.  Waits.
+ */
+ff_status ff_energy_grad(ff_ctx *ctx, int32_t algo, double theta, double *energy, void *grad_pos,
+                         void *grad_u, int32_t dtype, int32_t loc);
+
 /* Waits for the context's stream and reports any error flag raised on the GPU. */
 ff_status ff_synchronize(ff_ctx *ctx);
 

@@ -59,8 +59,8 @@ def lib():
         L.ora_allpairs.argtypes = [_i64, _dp, _dp, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int32, C.c_int32, C.c_void_p, _i64, _dp, _dp,
                                    C.c_void_p]
-        L.ora_bh_energy_grad.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p, _dp,
-                                         _dp]
+        L.ora_bh_energy_grad.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p,
+                                         C.c_int32, _dp, _dp]
         L.ora_bh_energy_grad.restype = C.c_double
         L.ora_morton.argtypes = [_i64, _dp, C.c_int32, _u64p, _dp]
         L.ora_tree.argtypes = [_i64, _dp, _dp, C.c_int32, C.c_int32, _u64p, _i64p, _dp, _i64,
@@ -225,9 +225,11 @@ def bh(pos, u, theta, leaf_max=1, prec="f32", dip_scale=1.0, lj_eps=0.0, lj_sigm
 
 
 def bh_energy_grad(pos, u, theta, leaf_max=1, prec="f64", dip_scale=1.0, lj_eps=0.0,
-                   lj_sigma=1.0, lj_rcut=2.5, pos_dec=None):
+                   lj_sigma=1.0, lj_rcut=2.5, pos_dec=None, tree_centres=False):
     """Barnes-Hut dipolar energy E = -1/2 sum u.h and its exact gradient with the opening
-    decisions taken on pos_dec (default: pos) and frozen.  Returns (E, grad_pos, grad_u)."""
+    decisions taken on pos_dec (default: pos) and frozen.  Returns (E, grad_pos, grad_u).
+    tree_centres: place each cell at the decision tree's centre in its own precision (as
+    the Barnes-Hut field does) instead of the exact mean of the current positions."""
     pos, u = _vec3(pos), _vec3(u)
     n = pos.shape[0]
     p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec),
@@ -241,7 +243,8 @@ def bh_energy_grad(pos, u, theta, leaf_max=1, prec="f64", dip_scale=1.0, lj_eps=
         if keep.shape != pos.shape:
             raise ValueError("pos_dec must match pos")
     e = lib().ora_bh_energy_grad(n, pos, u, C.byref(p),
-                                 None if keep is None else C.c_void_p(keep.ctypes.data), gp, gu)
+                                 None if keep is None else C.c_void_p(keep.ctypes.data),
+                                 int(bool(tree_centres)), gp, gu)
     return float(e), gp, gu
 
 

@@ -781,6 +781,11 @@ int64_t ora_bh(int64_t n, const double *pos, const double *u, const ora_bh_param
  *                          grad phi(rho_m - x_s; u_m, w_s) / n_s ]
  * where F_k = sum_s grad phi(rho_k - x_s; u_k, w_s) and n_s is the number of
  * particles in s.  Returns E; grad_pos and grad_u are n x 3.
+ * tree_centres = 0: a cell's x_s is the exact mean of its particles' current
+ * positions (E is then one smooth function of pos); 1: the centre of the
+ * decision tree in its own precision (as the Barnes-Hut field uses it; with
+ * pos = pos_dec this differs from the exact mean by the tree precision's
+ * rounding only), for comparing with a single-precision implementation.
  */
 typedef struct {
     const bh_ctx *g;          /* decisions: tree of pos_dec */
@@ -844,7 +849,8 @@ static void grad_visit(grad_ctx *q, int64_t m, int64_t sm, int64_t c)
 }
 
 double ora_bh_energy_grad(int64_t n, const double *pos, const double *u, const ora_bh_params *p,
-                          const double *pos_dec, double *grad_pos, double *grad_u)
+                          const double *pos_dec, int32_t tree_centres, double *grad_pos,
+                          double *grad_u)
 {
     if (!pos_dec) pos_dec = pos;
     uint64_t *skeys = malloc(n * sizeof(uint64_t));
@@ -868,7 +874,8 @@ double ora_bh_energy_grad(int64_t n, const double *pos, const double *u, const o
             }
         }
         double cnt = (double)(t.pend[c] - t.pbegin[c]);
-        for (int a = 0; a < 3; ++a) cc[3 * c + a] /= cnt;
+        for (int a = 0; a < 3; ++a)
+            cc[3 * c + a] = tree_centres ? t.cen[3 * c + a] : cc[3 * c + a] / cnt;
     }
 
     bh_ctx g;

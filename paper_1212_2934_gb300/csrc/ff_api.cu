@@ -82,6 +82,21 @@ struct ff_ctx {
     int* hflags = nullptr;       // pinned mirror
     double* hobs = nullptr;      // pinned mirror of 10 doubles
     void* staging = nullptr;     // 4 x 3n doubles
+    // energy gradient (allocated on first use; entry buffers grow as needed)
+    uint32_t* e_cnt = nullptr;   // entries per particle (n)
+    uint32_t* e_base = nullptr;  // their exclusive scan (n + 1)
+    unsigned long long* e_total = nullptr;
+    void* g_pos = nullptr;       // gradients in sorted order (records)
+    void* g_u = nullptr;
+    uint64_t* e_keys[2] = {nullptr, nullptr};
+    uint32_t* e_vals[2] = {nullptr, nullptr};
+    uint32_t* e_tmp = nullptr;
+    int64_t e_cap = 0;           // entries the buffers hold
+    uint32_t* s_beg = nullptr;   // per source: entry range
+    uint32_t* s_end = nullptr;
+    double* s_G = nullptr;       // per source: 3 + 3 sums
+    double* s_Q = nullptr;
+    int64_t s_cap = 0;           // sources the buffers hold
     bool tree_valid = false;     // a Barnes-Hut tree of some state exists
     bool counts_valid = false;
 
@@ -316,7 +331,7 @@ struct LaunchTally {
 // Sort the state into Morton order (the other buffer), build and aggregate
 // the tree, traverse.  h, f, esr (and counts) end in sorted order.
 template <typename R>
-ff_status eval_bh(ff_ctx* c, double theta, int include_sr)
+ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = false)
 {
     const int64_t n = c->n;
     cudaStream_t s = c->stream;
@@ -358,12 +373,13 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr)
         StageTimer st(c, S_FIELD);
         ffk::bh_field<R>(V<R>(b.pos), V<R>(b.u), n, t, field_params<R>(c, theta, include_sr),
                          V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr),
-                         c->p.count_interactions ? c->counts : nullptr, c->dflags, c->work,
+                         (c->p.count_interactions || force_counts) ? c->counts : nullptr,
+                         c->dflags, c->work,
                          traverse_group(c), c->off, segs_of(c), s);
     }
     FF_LAUNCHED(c);
     c->tree_valid = true;
-    c->counts_valid = c->p.count_interactions != 0;
+    c->counts_valid = c->p.count_interactions != 0 || force_counts;
     return FF_OK;
 }
 
@@ -428,7 +444,9 @@ void free_all(ff_ctx* c)
                     c->scan_tmp, c->bbox, c->cell, c->mom, c->lo, c->sum, c->sum_hi, c->mom_hi, c->parent,
                     c->arrive, c->h, c->f, c->esr, c->counts, c->work, c->partials, c->obs, c->obs_step, c->dstep, c->sys_of_pos, c->sys_start, c->sys_h, c->sys_lo,
                     c->sys_hi, c->sys_acc,
-                    c->dflags, c->staging};
+                    c->dflags, c->staging, c->e_cnt, c->e_base, c->e_total, c->g_pos, c->g_u,
+                    c->e_keys[0], c->e_keys[1], c->e_vals[0], c->e_vals[1], c->e_tmp, c->s_beg,
+                    c->s_end, c->s_G, c->s_Q};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int k = 0; k < 2; ++k) {
@@ -657,6 +675,102 @@ ff_status energy(ff_ctx* c, ff_energy_t* out)
     return FF_OK;
 }
 
+// (Re)allocates a device array of count elements; callers track capacity.
+template <typename T>
+ff_status grow(ff_ctx* c, T** p, size_t count)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(c, FF_ENOMEM, "device allocation for the gradient failed: %s", cudaGetErrorString(e));
+    }
+    return FF_OK;
+}
+
+// Energy -1/2 sum u.h (FP64) and its gradient with the opening decisions of
+// this evaluation frozen (k_grad.cu), in sorted order in g_pos, g_u.
+template <typename R>
+ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy)
+{
+    const int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    ff_status st;
+    if (!c->e_cnt) {
+        if ((st = grow(c, &c->e_cnt, n)) != FF_OK) return st;
+        if ((st = grow(c, &c->e_base, n + 1)) != FF_OK) return st;
+        if ((st = grow(c, &c->e_total, 1)) != FF_OK) return st;
+        if ((st = grow(c, reinterpret_cast<char**>(&c->g_pos), c->rec * n)) != FF_OK) return st;
+        if ((st = grow(c, reinterpret_cast<char**>(&c->g_u), c->rec * n)) != FF_OK) return st;
+    }
+    if (algo == FF_ALGO_AP) {
+        if ((st = eval_ap<R>(c, 0)) != FF_OK) return st;
+        ffk::grad_from_field<R>(V<R>(c->h), V<R>(c->f), n, V<R>(c->g_pos), V<R>(c->g_u), s);
+        FF_LAUNCHED(c);
+    } else {
+        if ((st = eval_bh<R>(c, theta, 0, true)) != FF_OK) return st;
+        int ncells_h = 0;
+        FF_CUDA(c, cudaMemsetAsync(c->e_total, 0, sizeof(unsigned long long), s));
+        ffk::grad_entry_counts(c->counts, n, c->e_cnt, c->e_total, s);
+        ffk::scan_exclusive(c->e_cnt, c->e_base, n, c->scan_tmp, s);
+        FF_LAUNCHED(c);
+        unsigned long long total = 0;
+        FF_CUDA(c, cudaMemcpyAsync(&total, c->e_total, sizeof(total), cudaMemcpyDeviceToHost, s));
+        FF_CUDA(c, cudaMemcpyAsync(&ncells_h, c->off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if ((st = sync_and_check(c)) != FF_OK) return st;
+        if (total >= 0xffffffffull)
+            return fail(c, FF_EINVAL, "too many interactions (%llu) for one gradient pass", total);
+        const int64_t ne = (int64_t)total;
+        const int64_t ncells = ncells_h;
+        const int64_t nsrc = ncells + n;
+        if (ne > c->e_cap) {
+            const int64_t cap = ne + ne / 8 + 1024;
+            for (int k = 0; k < 2; ++k) {
+                if ((st = grow(c, &c->e_keys[k], cap)) != FF_OK) return st;
+                if ((st = grow(c, &c->e_vals[k], cap)) != FF_OK) return st;
+            }
+            if ((st = grow(c, &c->e_tmp, ffk::radix_tmp_words(cap))) != FF_OK) return st;
+            c->e_cap = cap;
+        }
+        if (nsrc > c->s_cap) {
+            const int64_t cap = nsrc + nsrc / 8 + 1024;
+            if ((st = grow(c, &c->s_beg, cap)) != FF_OK) return st;
+            if ((st = grow(c, &c->s_end, cap)) != FF_OK) return st;
+            if ((st = grow(c, &c->s_G, 3 * cap)) != FF_OK) return st;
+            if ((st = grow(c, &c->s_Q, 3 * cap)) != FF_OK) return st;
+            c->s_cap = cap;
+        }
+        Buffers& a = c->st[c->cur];
+        ffk::Tree<R> t = tree_of<R>(c);
+        ffk::bh_record<R>(V<R>(a.pos), n, t, field_params<R>(c, theta, 0), c->e_base,
+                          c->e_keys[0], c->e_vals[0], c->dflags, c->off, segs_of(c), s);
+        int passes = 1;
+        while (passes < 8 && ((uint64_t)nsrc >> (8 * passes)) != 0) ++passes;
+        const bool in1 = ffk::radix_sort_pairs_passes(c->e_keys[0], c->e_vals[0], c->e_keys[1],
+                                                      c->e_vals[1], ne, c->e_tmp, passes, s);
+        const uint64_t* keys = c->e_keys[in1 ? 1 : 0];
+        const uint32_t* vals = c->e_vals[in1 ? 1 : 0];
+        ffk::grad_segments(keys, ne, nsrc, c->s_beg, c->s_end, s);
+        ffk::grad_source_sums<R>(V<R>(a.pos), V<R>(a.u), t, ncells, n, vals, c->s_beg, c->s_end,
+                                 c->s_G, c->s_Q, s);
+        ffk::grad_finish<R>(t, ncells, n, c->s_G, c->s_Q, V<R>(c->h), V<R>(c->f),
+                            (R)c->p.dip_scale, V<R>(c->g_pos), V<R>(c->g_u), s);
+        FF_LAUNCHED(c);
+    }
+    Buffers& a = c->st[c->cur];
+    ffk::observables<R>(n, V<R>(a.pos), V<R>(a.vel), V<R>(a.u), V<R>(a.om), V<R>(c->h),
+                        static_cast<R*>(c->esr), dyn_params<R>(c), c->partials, s);
+    ffk::reduce_partials(c->partials, ffk::integrate_blocks(n), 1.0 / (double)n,
+                         0.5 * c->p.inertia, c->obs, s);
+    FF_LAUNCHED(c);
+    FF_CUDA(c, cudaMemcpyAsync(c->hobs, c->obs, sizeof(double) * ffk::kObs, cudaMemcpyDeviceToHost,
+                               s));
+    if ((st = sync_and_check(c)) != FF_OK) return st;
+    if (energy) *energy = c->hobs[0];
+    return FF_OK;
+}
+
 }  // namespace
 
 namespace {
@@ -862,6 +976,30 @@ ff_status ff_dipolar_field(ff_ctx* c, int32_t algo, double theta, int32_t includ
     if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
     return c->fp64 ? dipolar_field<double>(c, algo, theta, include_sr, h_out, f_out, dtype, loc)
                    : dipolar_field<float>(c, algo, theta, include_sr, h_out, f_out, dtype, loc);
+}
+
+ff_status ff_energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy, void* grad_pos,
+                         void* grad_u, int32_t dtype, int32_t loc)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (algo != FF_ALGO_BH && algo != FF_ALGO_AP) return fail(c, FF_EINVAL, "bad algo");
+    if (algo == FF_ALGO_AP && c->nsys > 0) return fail(c, FF_EINVAL, "all-pairs is not available for batched systems");
+    if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(c, FF_EINVAL, "theta must be finite and >= 0");
+    if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
+    s = c->fp64 ? energy_grad<double>(c, algo, theta, energy)
+                : energy_grad<float>(c, algo, theta, energy);
+    if (s != FF_OK) return s;
+    const uint32_t* id = c->st[c->cur].id;
+    if (c->fp64) {
+        if ((s = store_array<double>(c, c->g_pos, id, grad_pos, dtype, loc, 0)) != FF_OK) return s;
+        if ((s = store_array<double>(c, c->g_u, id, grad_u, dtype, loc, 1)) != FF_OK) return s;
+    } else {
+        if ((s = store_array<float>(c, c->g_pos, id, grad_pos, dtype, loc, 0)) != FF_OK) return s;
+        if ((s = store_array<float>(c, c->g_u, id, grad_u, dtype, loc, 1)) != FF_OK) return s;
+    }
+    return sync_and_check(c);
 }
 
 ff_status ff_step(ff_ctx* c, int64_t nsteps)

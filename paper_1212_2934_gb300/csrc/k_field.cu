@@ -13,6 +13,7 @@
 // pointers replace a stack.  Every lane's nxt strictly increases, so the
 // loop ends after at most ncells visits per group.
 #include "ffk.cuh"
+#include "dipole.cuh"
 
 namespace ffk {
 
@@ -20,42 +21,12 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
-
-// Reduced dipolar field of u_j and force on u_k at separation r = rho_k - rho_j
-// (Sec. 2, reduced Eqs. h_dip and f_dip), accumulated:
-//   h += [3 r (u_j.r) - u_j r^2] / r^5
-//   f += 3 [r (u_j.u_k) + u_k (u_j.r) + u_j (u_k.r)] / r^5 - 15 r (u_k.r)(u_j.r) / r^7
-template <typename R>
-__device__ __forceinline__ void dipole(R rx, R ry, R rz, R r2, R ukx, R uky, R ukz, R ujx, R ujy,
-                                       R ujz, R& hx, R& hy, R& hz, R& fx, R& fy, R& fz)
-{
-    const R ir = rsq(r2);
-    const R ir2 = ir * ir;
-    const R ir3 = ir2 * ir;
-    const R ir5 = ir3 * ir2;
-    const R ir7 = ir5 * ir2;
-    const R bj = ujx * rx + ujy * ry + ujz * rz;
-    const R bk = ukx * rx + uky * ry + ukz * rz;
-    const R a = ujx * ukx + ujy * uky + ujz * ukz;
-    const R t = R(3) * bj * ir5;
-    hx += rx * t - ujx * ir3;
-    hy += ry * t - ujy * ir3;
-    hz += rz * t - ujz * ir3;
-    const R s3 = R(3) * ir5;
-    const R cr = s3 * a - R(15) * bk * bj * ir7;
-    const R cuk = s3 * bj, cuj = s3 * bk;
-    fx += rx * cr + ukx * cuk + ujx * cuj;
-    fy += ry * cr + uky * cuk + ujy * cuj;
-    fz += rz * cr + ukz * cuk + ujz * cuj;
-}
 
 // Knuth's TwoSum: s + e == a + b exactly (no fused or reordered operations).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
@@ -398,6 +369,71 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
     if (COUNT) counts[k] = make_int4(nacc, npair, nopen, 0);
 }
 
+// Source lists for the energy gradient: the walk of bh_task1, making the same
+// decisions in the same order, writes one entry per source instead of
+// summing.  key = the source: a cell (accepted, or a one-particle leaf summed
+// exactly) or ncells + the position of a particle of an opened multi-particle
+// leaf; value = the particle.  base[k] .. base[k + 1] is the particle's slot,
+// sized from the counted walk (accepted cells + exact pairs); a walk that
+// does not fill it exactly raises the traversal flag.
+template <typename R>
+__global__ void __launch_bounds__(128) k_bh_record(const vec4<R>* __restrict__ pos, int n,
+                                                   Tree<R> t, FieldParams<R> fp,
+                                                   const uint32_t* __restrict__ base,
+                                                   uint64_t* __restrict__ keys,
+                                                   uint32_t* __restrict__ vals, int* flags,
+                                                   const uint32_t* __restrict__ off, Segs sg)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (*flags & FLAG_CAPACITY) return;
+    const unsigned ncells = (unsigned)*t.ncells;
+    const vec4<R> xk = pos[k];
+    unsigned i = 0, end = ncells;
+    if (sg.of_pos) {
+        const int sys = (int)sg.of_pos[k];
+        i = off[sg.start[sys]];
+        end = off[sg.start[sys + 1]];
+    }
+    uint32_t w = base[k];
+    const uint32_t wend = base[k + 1];
+    while (i < end) {
+        const Cell<R> cl = t.cell[i];
+        const int4 nd = cl.node;
+        const bool inside = nd.x <= k && k < nd.y;
+        const bool leaf = (nd.w >> 8) != 0;
+        const bool single = leaf && (nd.y - nd.x == 1);
+        const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i);
+        unsigned nxt = i + 1;
+        if (acc || (single && !inside)) {
+            if (w < wend) {
+                keys[w] = i;
+                vals[w] = (uint32_t)k;
+            }
+            ++w;
+            nxt = (unsigned)nd.z;
+        } else if (leaf) {
+            if (!single) {
+                for (int s = nd.x; s < nd.y; ++s) {
+                    if (s == k) continue;
+                    if (w < wend) {
+                        keys[w] = (uint64_t)ncells + (uint64_t)s;
+                        vals[w] = (uint32_t)k;
+                    }
+                    ++w;
+                }
+            }
+            nxt = (unsigned)nd.z;
+        }
+        if (nxt <= i) {
+            atomicOr(flags, FLAG_TRAVERSE);
+            break;
+        }
+        i = nxt;
+    }
+    if (w != wend) atomicOr(flags, FLAG_TRAVERSE);
+}
+
 // Persistent traversal: the key order is cut into nseg contiguous segments of
 // 32-particle tasks; a warp takes tasks from the segment of the SM it runs on
 // (so warps sharing an L1 cache walk neighbouring parts of the tree) and then
@@ -583,5 +619,24 @@ template void ap_field<float>(const float4*, const float4*, int64_t, FieldParams
                               float4*, float*, cudaStream_t);
 template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<double>, dvec4*,
                                dvec4*, double*, cudaStream_t);
+
+
+template <typename R>
+void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
+               uint64_t* keys, uint32_t* vals, int* flags, const uint32_t* off, Segs sg,
+               cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_bh_record<R><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(pos, (int)n, t, fp, base, keys,
+                                                               vals, flags, off, sg);
+    counted();
+}
+
+template void bh_record<float>(const float4*, int64_t, Tree<float>, FieldParams<float>,
+                               const uint32_t*, uint64_t*, uint32_t*, int*, const uint32_t*,
+                               Segs, cudaStream_t);
+template void bh_record<double>(const dvec4*, int64_t, Tree<double>, FieldParams<double>,
+                                const uint32_t*, uint64_t*, uint32_t*, int*, const uint32_t*,
+                                Segs, cudaStream_t);
 
 }  // namespace ffk

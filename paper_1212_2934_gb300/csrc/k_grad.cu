@@ -1,0 +1,239 @@
+// Gradient of the Barnes-Hut dipolar energy E = -1/2 sum_m u_m . h_m with
+// the opening decisions frozen (Sec. 3.2 traversal, Sec. 5 energy).
+//
+// With phi(r; a, b) = a . T(r) b and h_m = sum over m's sources s of
+// T(rho_m - x_s) w_s (cells: centre and moment sum; exact pairs: particles):
+//   dE/du_k   = -1/2 [ h_k + ds sum over (m, s), k in s, of T(rho_m - x_s) u_m ]
+//   dE/drho_k = -1/2 [ f_k - ds sum over (m, s), k in s, of
+//                      grad phi(rho_m - x_s; w_s, u_m) / n_s ]
+// h and f are the dipolar field and force of the same traversal (ds
+// included).  The reverse sums are formed without atomics: the traversal
+// records every (source, target) entry, a stable radix sort on the source
+// groups them, one warp per source sums its entries in a fixed order, and each
+// leaf adds the sums of its ancestor cells for its particles.
+#include "dipole.cuh"
+#include "ffk.cuh"
+
+namespace ffk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kGradThreads = 256;
+// per-lane single-precision partial sums are added to the FP64 totals after
+// this many entries, so their rounding stays that of short sums
+constexpr int kFlushEvery = 64;
+
+__global__ void k_entry_counts(const int4* __restrict__ counts, int64_t n,
+                               uint32_t* __restrict__ out, unsigned long long* total)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < n) {
+        const int4 c = counts[i];
+        v = (unsigned long long)(unsigned)c.x + (unsigned long long)(unsigned)c.y;
+        out[i] = (uint32_t)v;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+}
+
+// (keys outside 0 .. nsrc - 1 can only come from a recording walk that
+// raised its flag; they are skipped)
+__global__ void k_segments(const uint64_t* __restrict__ keys, int64_t ne, int64_t nsrc,
+                           uint32_t* beg, uint32_t* end)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const uint64_t k = keys[i];
+    if (k >= (uint64_t)nsrc) return;
+    if (i == 0 || keys[i - 1] != k) beg[k] = (uint32_t)i;
+    if (i == ne - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// One warp per source.
+template <typename R>
+__global__ void __launch_bounds__(kGradThreads) k_source_sums(
+    const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u, Tree<R> t, int64_t ncells,
+    int64_t nsrc, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ beg,
+    const uint32_t* __restrict__ end, double* __restrict__ G, double* __restrict__ Q)
+{
+    const int64_t s = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= nsrc) return;
+    vec4<R> x, w;
+    R ns = R(1);
+    if (s < ncells) {
+        const Cell<R> cl = t.cell[s];
+        x = cl.cen;
+        w = t.mom[s];
+        ns = (R)(cl.node.y - cl.node.x);
+    } else {
+        x = pos[s - ncells];
+        w = u[s - ncells];
+    }
+    const uint32_t b = beg[s], e = end[s];
+    double g[3] = {0.0, 0.0, 0.0}, q[3] = {0.0, 0.0, 0.0};
+    R gx = 0, gy = 0, gz = 0, qx = 0, qy = 0, qz = 0;
+    int since = 0;
+    for (uint32_t k = b + lane; k < e; k += 32) {
+        const uint32_t m = vals[k];
+        if (m >= (uint32_t)(nsrc - ncells)) continue;  // only after a flagged recording walk
+        const vec4<R> xm = pos[m], um = u[m];
+        const R rx = xm.x - x.x, ry = xm.y - x.y, rz = xm.z - x.z;
+        const R r2 = rx * rx + ry * ry + rz * rz;
+        // T(r) u_m (field of u_m) and grad phi(r; w_s, u_m) (force on w_s)
+        if (r2 > R(0)) dipole<R>(rx, ry, rz, r2, w.x, w.y, w.z, um.x, um.y, um.z, gx, gy, gz, qx, qy, qz);
+        if (++since == kFlushEvery) {
+            g[0] += gx; g[1] += gy; g[2] += gz;
+            q[0] += qx; q[1] += qy; q[2] += qz;
+            gx = gy = gz = qx = qy = qz = R(0);
+            since = 0;
+        }
+    }
+    g[0] += gx; g[1] += gy; g[2] += gz;
+    q[0] += qx; q[1] += qy; q[2] += qz;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        g[a] = warp_sum(g[a]);
+        q[a] = warp_sum(q[a]);
+    }
+    if (lane == 0) {
+        const double inv = 1.0 / (double)ns;
+        G[3 * s] = g[0];
+        G[3 * s + 1] = g[1];
+        G[3 * s + 2] = g[2];
+        Q[3 * s] = q[0] * inv;
+        Q[3 * s + 1] = q[1] * inv;
+        Q[3 * s + 2] = q[2] * inv;
+    }
+}
+
+// One thread per cell; a leaf adds up its ancestors' sums and finishes the
+// gradient of each of its particles.
+template <typename R>
+__global__ void k_grad_finish(Tree<R> t, int64_t ncells, int64_t n, const double* __restrict__ G,
+                              const double* __restrict__ Q, const vec4<R>* __restrict__ h,
+                              const vec4<R>* __restrict__ f, R ds, vec4<R>* __restrict__ gp,
+                              vec4<R>* __restrict__ gu)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const int4 nd = t.cell[c].node;
+    if ((nd.w >> 8) == 0) return;
+    double dg[3] = {0.0, 0.0, 0.0}, dq[3] = {0.0, 0.0, 0.0};
+    int a = (int)c;
+    for (int level = 0; a >= 0 && level <= kMaxLevel; ++level) {
+        for (int d = 0; d < 3; ++d) {
+            dg[d] += G[3 * (int64_t)a + d];
+            dq[d] += Q[3 * (int64_t)a + d];
+        }
+        a = t.parent[a];
+    }
+    const double sc = (double)ds;
+    for (int p = nd.x; p < nd.y; ++p) {
+        const double* gs = G + 3 * (ncells + p);
+        const double* qs = Q + 3 * (ncells + p);
+        const vec4<R> hp = h[p], fp = f[p];
+        vec4<R> ou, op;
+        ou.x = (R)(-0.5 * ((double)hp.x + sc * (dg[0] + gs[0])));
+        ou.y = (R)(-0.5 * ((double)hp.y + sc * (dg[1] + gs[1])));
+        ou.z = (R)(-0.5 * ((double)hp.z + sc * (dg[2] + gs[2])));
+        ou.w = R(0);
+        op.x = (R)(-0.5 * ((double)fp.x - sc * (dq[0] + qs[0])));
+        op.y = (R)(-0.5 * ((double)fp.y - sc * (dq[1] + qs[1])));
+        op.z = (R)(-0.5 * ((double)fp.z - sc * (dq[2] + qs[2])));
+        op.w = R(0);
+        gu[p] = ou;
+        gp[p] = op;
+    }
+}
+
+template <typename R>
+__global__ void k_grad_from_field(const vec4<R>* __restrict__ h, const vec4<R>* __restrict__ f,
+                                  int64_t n, vec4<R>* __restrict__ gp, vec4<R>* __restrict__ gu)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    vec4<R> a = h[i], b = f[i];
+    a.x = -a.x; a.y = -a.y; a.z = -a.z;
+    b.x = -b.x; b.y = -b.y; b.z = -b.z;
+    gu[i] = a;
+    gp[i] = b;
+}
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void grad_entry_counts(const int4* counts, int64_t n, uint32_t* out, unsigned long long* total64,
+                       cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_entry_counts<<<blocks(n, kGradThreads), kGradThreads, 0, s>>>(counts, n, out, total64);
+    counted();
+}
+
+void grad_segments(const uint64_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg, uint32_t* end,
+                   cudaStream_t s)
+{
+    cudaMemsetAsync(beg, 0, sizeof(uint32_t) * nsrc, s);
+    cudaMemsetAsync(end, 0, sizeof(uint32_t) * nsrc, s);
+    if (ne <= 0) return;
+    k_segments<<<blocks(ne, kGradThreads), kGradThreads, 0, s>>>(keys, ne, nsrc, beg, end);
+    counted();
+}
+
+template <typename R>
+void grad_source_sums(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64_t ncells, int64_t n,
+                      const uint32_t* vals, const uint32_t* beg, const uint32_t* end, double* G,
+                      double* Q, cudaStream_t s)
+{
+    const int64_t nsrc = ncells + n;
+    if (nsrc <= 0) return;
+    k_source_sums<R><<<blocks(nsrc * 32, kGradThreads), kGradThreads, 0, s>>>(
+        pos, u, t, ncells, nsrc, vals, beg, end, G, Q);
+    counted();
+}
+
+template <typename R>
+void grad_finish(Tree<R> t, int64_t ncells, int64_t n, const double* G, const double* Q,
+                 const vec4<R>* h, const vec4<R>* f, R ds, vec4<R>* grad_pos, vec4<R>* grad_u,
+                 cudaStream_t s)
+{
+    if (ncells <= 0) return;
+    k_grad_finish<R><<<blocks(ncells, kGradThreads), kGradThreads, 0, s>>>(
+        t, ncells, n, G, Q, h, f, ds, grad_pos, grad_u);
+    counted();
+}
+
+template <typename R>
+void grad_from_field(const vec4<R>* h, const vec4<R>* f, int64_t n, vec4<R>* grad_pos,
+                     vec4<R>* grad_u, cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_grad_from_field<R><<<blocks(n, kGradThreads), kGradThreads, 0, s>>>(h, f, n, grad_pos,
+                                                                          grad_u);
+    counted();
+}
+
+#define FFK_GRAD_INST(R)                                                                          \
+    template void grad_from_field<R>(const vec4<R>*, const vec4<R>*, int64_t, vec4<R>*, vec4<R>*, \
+                                     cudaStream_t);                                               \
+    template void grad_source_sums<R>(const vec4<R>*, const vec4<R>*, Tree<R>, int64_t, int64_t,  \
+                                      const uint32_t*, const uint32_t*, const uint32_t*, double*, \
+                                      double*, cudaStream_t);                                    \
+    template void grad_finish<R>(Tree<R>, int64_t, int64_t, const double*, const double*,         \
+                                 const vec4<R>*, const vec4<R>*, R, vec4<R>*, vec4<R>*,           \
+                                 cudaStream_t);
+FFK_GRAD_INST(float)
+FFK_GRAD_INST(double)
+#undef FFK_GRAD_INST
+
+}  // namespace ffk

@@ -662,6 +662,32 @@ size_t radix_tmp_words(int64_t n)
     return (size_t)(h + (h + 1) + scan_tmp_words(h));
 }
 
+bool radix_sort_pairs_passes(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                             uint32_t* tmp, int passes, cudaStream_t s)
+{
+    if (n <= 1) return false;
+    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    const int64_t h = (int64_t)kRadixBins * nb;
+    uint32_t* hist = tmp;
+    uint32_t* offs = tmp + h;
+    uint32_t* stmp = offs + h + 1;
+    uint64_t* ka = k0;
+    uint32_t* va = v0;
+    uint64_t* kb = k1;
+    uint32_t* vb = v1;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * kRadixBits;
+        k_radix_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, n, shift, hist, nb);
+        scan_exclusive(hist, offs, h, stmp, s);
+        k_radix_scatter<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, kb, vb, n, shift,
+                                                                offs, nb);
+        counted(2);
+        uint64_t* tk = ka; ka = kb; kb = tk;
+        uint32_t* tv = va; va = vb; vb = tv;
+    }
+    return (passes & 1) != 0;
+}
+
 void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
                       uint32_t* tmp, cudaStream_t s)
 {

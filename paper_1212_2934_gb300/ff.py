@@ -89,6 +89,8 @@ _SIGS = {
     "ff_set_systems": (_st, [_vp, C.c_int32, _vp, _vp, _vp, _vp]),
     "ff_system_moments": (_st, [_vp, _vp, C.POINTER(C.c_int64), C.c_int32]),
     "ff_tune_traversal": (_st, [_vp, _vp, C.c_int32, C.c_int32, C.POINTER(C.c_int32), _vp]),
+    "ff_energy_grad": (_st, [_vp, C.c_int32, C.c_double, C.POINTER(C.c_double), _vp, _vp,
+                             C.c_int32, C.c_int32]),
     "ff_profile": (_st, [_vp, C.c_int32]),
     "ff_profile_read": (_st, [_vp, C.POINTER(ff_profile_t)]),
     "ff_morton_order_noalloc": (_st, [_vp, C.c_int64, _vp, _vp, _vp]),
@@ -251,6 +253,59 @@ def ff_dipolar_field(ctx, algo=FF_ALGO_BH, theta=0.5, include_sr=True, h_out=Non
     _check(ctx.handle, lib().ff_dipolar_field(ctx.handle, int(algo), float(theta),
                                               int(bool(include_sr)), ph[0], pf[0], ref[1], ref[2]))
     return h_out, f_out
+
+
+def ff_energy_grad(ctx, algo=FF_ALGO_BH, theta=0.5, dtype=np.float64, device_like=None):
+    """(E, dE/dpos, dE/du) of the dipolar energy E = -1/2 sum u.h of the current state; the
+    Barnes-Hut gradient is exact with this evaluation's opening decisions frozen.  Gradients
+    are numpy arrays unless device_like is a CUDA tensor."""
+    gp = _alloc_out(ctx.n, dtype, device_like)
+    gu = _alloc_out(ctx.n, dtype, device_like)
+    pp, pu = _out_pair(gp, ctx.n), _out_pair(gu, ctx.n)
+    e = C.c_double()
+    _check(ctx.handle, lib().ff_energy_grad(ctx.handle, int(algo), float(theta), C.byref(e),
+                                            pp[0], pu[0], pp[1], pp[2]))
+    return e.value, gp, gu
+
+
+def dipolar_energy(pos, u, ctx, algo=FF_ALGO_BH, theta=0.5):
+    """Differentiable dipolar energy of (pos, u) (CUDA tensors of shape (n, 3) in the
+    context's precision) under torch.autograd.  The context's state is replaced by (pos, u)
+    with zero velocities; the gradient comes from ff_energy_grad."""
+    return _energy_fn().apply(pos, u, ctx, int(algo), float(theta))
+
+
+_ENERGY_FN = None
+
+
+def _energy_fn():
+    global _ENERGY_FN
+    if _ENERGY_FN is None:
+        import torch
+
+        class DipolarEnergy(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, pos, u, ctx, algo, theta):
+                ff_set_particles(ctx, pos.detach(), u.detach())
+                e, gp, gu = ff_energy_grad(ctx, algo, theta, dtype=_np_dtype(pos),
+                                           device_like=pos)
+                fctx.save_for_backward(gp, gu)
+                return torch.tensor(e, dtype=torch.float64, device=pos.device)
+
+            @staticmethod
+            def backward(fctx, grad_e):
+                gp, gu = fctx.saved_tensors
+                g = grad_e.to(gp.dtype)
+                return g * gp, g * gu, None, None, None
+
+        _ENERGY_FN = DipolarEnergy
+    return _ENERGY_FN
+
+
+def _np_dtype(t):
+    import torch
+
+    return np.float64 if t.dtype == torch.float64 else np.float32
 
 
 def ff_step(ctx, nsteps=1):

@@ -43,6 +43,14 @@ def test_energy_is_that_of_the_bh_field(ora, prec, leaf_max):
     # a single-precision tree places its pseudo-particles at the rounded centres; the energy
     # being differentiated uses the exact means (the smooth function), one rounding apart
     assert e == pytest.approx(-0.5 * np.sum(u * r["h"]), rel=1e-12 if prec == "f64" else 1e-6)
+    # with the tree's own centres the energy is the field's exactly (same sources, same order
+    # of the pair kernel), and the gradient moves by rounding only
+    e1, gp1, gu1 = ora.bh_energy_grad(pos, u, 0.5, leaf_max, prec, dip_scale=0.7, lj_eps=1.0,
+                                      tree_centres=True)
+    assert e1 == pytest.approx(-0.5 * np.sum(u * r["h"]), rel=1e-13)
+    tol = 1e-12 if prec == "f64" else 1e-4
+    assert np.abs(gu1 - gu).max() <= tol * np.abs(gu).max()
+    assert np.abs(gp1 - gp).max() <= tol * np.abs(gp).max()
     # at theta > 0 the gradient is not simply -h: the reverse sums matter
     assert np.abs(gu + r["h"]).max() > 1e-6 * np.abs(r["h"]).max()
 
