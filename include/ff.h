@@ -239,7 +239,7 @@ ff_status ff_tune_traversal(ff_ctx *ctx, const int32_t *groups, int32_t ngroups,
  * order); *energy (may be NULL) receives E in FP64; grad_pos and grad_u (may
  * be NULL) receive n x 3 values in the caller's order, dtype/loc as in
  * ff_get_particles.  The Barnes-Hut gradient records one entry per
- * interaction (12 bytes x 2 buffers; about 1000 interactions per particle
+ * interaction (8 bytes x 2 buffers; about 1000 interactions per particle
  * at theta = 0.5), allocated on first use and grown as needed; more than
  * 2^32 - 1 interactions is FF_EINVAL.  Waits.
  */

@@ -88,7 +88,7 @@ struct ff_ctx {
     unsigned long long* e_total = nullptr;
     void* g_pos = nullptr;       // gradients in sorted order (records)
     void* g_u = nullptr;
-    uint64_t* e_keys[2] = {nullptr, nullptr};
+    uint32_t* e_keys[2] = {nullptr, nullptr};
     uint32_t* e_vals[2] = {nullptr, nullptr};
     uint32_t* e_tmp = nullptr;
     int64_t e_cap = 0;           // entries the buffers hold
@@ -96,7 +96,12 @@ struct ff_ctx {
     uint32_t* s_end = nullptr;
     double* s_G = nullptr;       // per source: 3 + 3 sums
     double* s_Q = nullptr;
+    uint32_t* s_items = nullptr; // per source: work items of its entry list
+    uint32_t* s_item_off = nullptr;
+    uint32_t* s_scan = nullptr;
     int64_t s_cap = 0;           // sources the buffers hold
+    double* i_part = nullptr;    // per work item: six partial sums
+    int64_t i_cap = 0;
     bool tree_valid = false;     // a Barnes-Hut tree of some state exists
     bool counts_valid = false;
 
@@ -446,7 +451,7 @@ void free_all(ff_ctx* c)
                     c->sys_hi, c->sys_acc,
                     c->dflags, c->staging, c->e_cnt, c->e_base, c->e_total, c->g_pos, c->g_u,
                     c->e_keys[0], c->e_keys[1], c->e_vals[0], c->e_vals[1], c->e_tmp, c->s_beg,
-                    c->s_end, c->s_G, c->s_Q};
+                    c->s_end, c->s_G, c->s_Q, c->s_items, c->s_item_off, c->s_scan, c->i_part};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int k = 0; k < 2; ++k) {
@@ -739,20 +744,30 @@ ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy)
             if ((st = grow(c, &c->s_end, cap)) != FF_OK) return st;
             if ((st = grow(c, &c->s_G, 3 * cap)) != FF_OK) return st;
             if ((st = grow(c, &c->s_Q, 3 * cap)) != FF_OK) return st;
+            if ((st = grow(c, &c->s_items, cap)) != FF_OK) return st;
+            if ((st = grow(c, &c->s_item_off, cap + 1)) != FF_OK) return st;
+            if ((st = grow(c, &c->s_scan, ffk::scan_tmp_words(cap))) != FF_OK) return st;
             c->s_cap = cap;
+        }
+        const int64_t max_items = nsrc + ne / ffk::kGradItemEntries + 1;
+        if (max_items > c->i_cap) {
+            const int64_t cap = max_items + max_items / 8 + 1024;
+            if ((st = grow(c, &c->i_part, 6 * cap)) != FF_OK) return st;
+            c->i_cap = cap;
         }
         Buffers& a = c->st[c->cur];
         ffk::Tree<R> t = tree_of<R>(c);
         ffk::bh_record<R>(V<R>(a.pos), n, t, field_params<R>(c, theta, 0), c->e_base,
-                          c->e_keys[0], c->e_vals[0], c->dflags, c->off, segs_of(c), s);
+                          c->e_keys[0], c->e_vals[0], c->dflags, c->work, c->off, segs_of(c), s);
         int passes = 1;
         while (passes < 8 && ((uint64_t)nsrc >> (8 * passes)) != 0) ++passes;
-        const bool in1 = ffk::radix_sort_pairs_passes(c->e_keys[0], c->e_vals[0], c->e_keys[1],
-                                                      c->e_vals[1], ne, c->e_tmp, passes, s);
-        const uint64_t* keys = c->e_keys[in1 ? 1 : 0];
+        const bool in1 = ffk::radix_sort_pairs_passes<uint32_t>(
+            c->e_keys[0], c->e_vals[0], c->e_keys[1], c->e_vals[1], ne, c->e_tmp, passes, s);
+        const uint32_t* keys = c->e_keys[in1 ? 1 : 0];
         const uint32_t* vals = c->e_vals[in1 ? 1 : 0];
         ffk::grad_segments(keys, ne, nsrc, c->s_beg, c->s_end, s);
         ffk::grad_source_sums<R>(V<R>(a.pos), V<R>(a.u), t, ncells, n, vals, c->s_beg, c->s_end,
+                                 c->s_items, c->s_item_off, c->s_scan, c->i_part, max_items,
                                  c->s_G, c->s_Q, s);
         ffk::grad_finish<R>(t, ncells, n, c->s_G, c->s_Q, V<R>(c->h), V<R>(c->f),
                             (R)c->p.dip_scale, V<R>(c->g_pos), V<R>(c->g_u), s);

@@ -128,10 +128,11 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
 size_t radix_tmp_words(int64_t n);
 void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
                       uint32_t* tmp, cudaStream_t s);
-// The same on the low 8 * passes bits only; returns true when the sorted data
-// ended in (k1, v1) (an odd number of passes).
-bool radix_sort_pairs_passes(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
-                             uint32_t* tmp, int passes, cudaStream_t s);
+// The same on the low 8 * passes bits only (K = uint64_t or uint32_t keys);
+// returns true when the sorted data ended in (k1, v1) (an odd number of passes).
+template <typename K>
+bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
+                             int passes, cudaStream_t s);
 
 // bb holds one root cube per system.
 template <typename R>
@@ -166,7 +167,7 @@ void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint3
 // base[k] .. base[k + 1] of (source, k) in the order of its walk.
 template <typename R>
 void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
-               uint64_t* keys, uint32_t* vals, int* flags, const uint32_t* off, Segs sg,
+               uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off, Segs sg,
                cudaStream_t s);
 
 // ------------------------------------------------ energy gradient (k_grad.cu)
@@ -176,14 +177,18 @@ void grad_entry_counts(const int4* counts, int64_t n, uint32_t* out,
                        unsigned long long* total64, cudaStream_t s);
 // first and one-past-last entry of every source in the sorted keys (arrays of
 // nsrc, zeroed here)
-void grad_segments(const uint64_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg, uint32_t* end,
+void grad_segments(const uint32_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg, uint32_t* end,
                    cudaStream_t s);
 // per source s: G_s = sum over its entries of T(r) u_m and Q_s = sum of
-// grad phi(r; w_s, u_m) / n_s, r = rho_m - x_s (FP64 results, 3 per source)
+// grad phi(r; w_s, u_m) / n_s, r = rho_m - x_s (FP64 results, 3 per source).
+// Scratch: items/item_off (nsrc, nsrc + 1 words), scan_tmp for nsrc, part
+// (6 doubles per item; max_items >= nsrc + entries / kGradItemEntries + 1).
+constexpr int64_t kGradItemEntries = 1024;
 template <typename R>
 void grad_source_sums(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64_t ncells, int64_t n,
-                      const uint32_t* vals, const uint32_t* beg, const uint32_t* end, double* G,
-                      double* Q, cudaStream_t s);
+                      const uint32_t* vals, const uint32_t* beg, const uint32_t* end,
+                      uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
+                      int64_t max_items, double* G, double* Q, cudaStream_t s);
 // per particle p: g_p, q_p = the sums of every cell containing p plus its own
 // particle-source sums, then grad_u = -1/2 (h + ds g), grad_pos = -1/2 (f - ds q)
 template <typename R>

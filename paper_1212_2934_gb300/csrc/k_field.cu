@@ -377,17 +377,15 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
 // sized from the counted walk (accepted cells + exact pairs); a walk that
 // does not fill it exactly raises the traversal flag.
 template <typename R>
-__global__ void __launch_bounds__(128) k_bh_record(const vec4<R>* __restrict__ pos, int n,
-                                                   Tree<R> t, FieldParams<R> fp,
-                                                   const uint32_t* __restrict__ base,
-                                                   uint64_t* __restrict__ keys,
-                                                   uint32_t* __restrict__ vals, int* flags,
-                                                   const uint32_t* __restrict__ off, Segs sg)
+__device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict__ pos, int n,
+                                            const Tree<R>& t, const FieldParams<R>& fp,
+                                            unsigned ncells, const uint32_t* __restrict__ base,
+                                            uint32_t* __restrict__ keys,
+                                            uint32_t* __restrict__ vals, int* flags,
+                                            const uint32_t* __restrict__ off, const Segs& sg)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = task * 32 + (threadIdx.x & 31);
     if (k >= n) return;
-    if (*flags & FLAG_CAPACITY) return;
-    const unsigned ncells = (unsigned)*t.ncells;
     const vec4<R> xk = pos[k];
     unsigned i = 0, end = ncells;
     if (sg.of_pos) {
@@ -417,7 +415,7 @@ __global__ void __launch_bounds__(128) k_bh_record(const vec4<R>* __restrict__ p
                 for (int s = nd.x; s < nd.y; ++s) {
                     if (s == k) continue;
                     if (w < wend) {
-                        keys[w] = (uint64_t)ncells + (uint64_t)s;
+                        keys[w] = ncells + (uint32_t)s;
                         vals[w] = (uint32_t)k;
                     }
                     ++w;
@@ -432,6 +430,36 @@ __global__ void __launch_bounds__(128) k_bh_record(const vec4<R>* __restrict__ p
         i = nxt;
     }
     if (w != wend) atomicOr(flags, FLAG_TRAVERSE);
+}
+
+// The recording walk on the traversal's schedule: warps take 32-particle tasks
+// from their SM's Morton segment first (see k_bh).
+template <typename R>
+__global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
+    const vec4<R>* __restrict__ pos, int n, Tree<R> t, FieldParams<R> fp,
+    const uint32_t* __restrict__ base, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+    int* flags, int* __restrict__ work, int nseg, const uint32_t* __restrict__ off, Segs sg)
+{
+    if (*flags & FLAG_CAPACITY) return;
+    const unsigned ncells = (unsigned)*t.ncells;
+    const int ntask = (n + 31) / 32;
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    const int home = (int)(smid % (unsigned)nseg);
+    const int lane = threadIdx.x & 31;
+    for (int probe = 0; probe < nseg; ++probe) {
+        const int ws = (home + probe) % nseg;
+        const int t0 = (int)((int64_t)ntask * ws / nseg);
+        const int t1 = (int)((int64_t)ntask * (ws + 1) / nseg);
+        for (;;) {
+            int got = 0;
+            if (lane == 0) got = atomicAdd(&work[ws], 1);
+            got = __shfl_sync(kFull, got, 0);
+            const int task = t0 + got;
+            if (task >= t1) break;
+            record_task<R>(task, pos, n, t, fp, ncells, base, keys, vals, flags, off, sg);
+        }
+    }
 }
 
 // Persistent traversal: the key order is cut into nseg contiguous segments of
@@ -623,20 +651,35 @@ template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<
 
 template <typename R>
 void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
-               uint64_t* keys, uint32_t* vals, int* flags, const uint32_t* off, Segs sg,
+               uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off, Segs sg,
                cudaStream_t s)
 {
     if (n <= 0) return;
-    k_bh_record<R><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(pos, (int)n, t, fp, base, keys,
-                                                               vals, flags, off, sg);
+    static int blocks = 0, nsm = 0;
+    if (blocks == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_bh_record<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             kTraverseCarveout);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_record<R>, kBhThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (nsm < 1) nsm = 1;
+        if (nsm > kWorkSegments) nsm = kWorkSegments;
+        blocks = per_sm * nsm;
+    }
+    cudaMemsetAsync(work, 0, sizeof(int) * nsm, s);
+    k_bh_record<R><<<blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, keys, vals, flags, work,
+                                                 nsm, off, sg);
     counted();
 }
 
 template void bh_record<float>(const float4*, int64_t, Tree<float>, FieldParams<float>,
-                               const uint32_t*, uint64_t*, uint32_t*, int*, const uint32_t*,
+                               const uint32_t*, uint32_t*, uint32_t*, int*, int*, const uint32_t*,
                                Segs, cudaStream_t);
 template void bh_record<double>(const dvec4*, int64_t, Tree<double>, FieldParams<double>,
-                                const uint32_t*, uint64_t*, uint32_t*, int*, const uint32_t*,
-                                Segs, cudaStream_t);
+                                const uint32_t*, uint32_t*, uint32_t*, int*, int*,
+                                const uint32_t*, Segs, cudaStream_t);
 
 }  // namespace ffk

@@ -20,9 +20,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGradThreads = 256;
-// per-lane single-precision partial sums are added to the FP64 totals after
-// this many entries, so their rounding stays that of short sums
-constexpr int kFlushEvery = 64;
 
 __global__ void k_entry_counts(const int4* __restrict__ counts, int64_t n,
                                uint32_t* __restrict__ out, unsigned long long* total)
@@ -40,78 +37,108 @@ __global__ void k_entry_counts(const int4* __restrict__ counts, int64_t n,
 
 // (keys outside 0 .. nsrc - 1 can only come from a recording walk that
 // raised its flag; they are skipped)
-__global__ void k_segments(const uint64_t* __restrict__ keys, int64_t ne, int64_t nsrc,
+__global__ void k_segments(const uint32_t* __restrict__ keys, int64_t ne, int64_t nsrc,
                            uint32_t* beg, uint32_t* end)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
-    const uint64_t k = keys[i];
-    if (k >= (uint64_t)nsrc) return;
+    const uint32_t k = keys[i];
+    if ((int64_t)k >= nsrc) return;
     if (i == 0 || keys[i - 1] != k) beg[k] = (uint32_t)i;
     if (i == ne - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
 }
 
-__device__ __forceinline__ double warp_sum(double v)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
-// One warp per source.
+// Work items: every source's entry list is cut into pieces of at most
+// kGradItemEntries entries, so no warp is left alone with a top-level cell that
+// most particles accept.
+__global__ void k_item_counts(const uint32_t* __restrict__ beg, const uint32_t* __restrict__ end,
+                              int64_t nsrc, uint32_t* __restrict__ items)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsrc) return;
+    items[s] = (uint32_t)((end[s] - beg[s] + kGradItemEntries - 1) / kGradItemEntries);
+}
+
+// One warp per item: the terms of its entries summed in single precision (at
+// most 32 per lane, then across the warp), written as six FP64 partials.
 template <typename R>
-__global__ void __launch_bounds__(kGradThreads) k_source_sums(
+__global__ void __launch_bounds__(kGradThreads) k_item_sums(
     const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u, Tree<R> t, int64_t ncells,
     int64_t nsrc, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ beg,
-    const uint32_t* __restrict__ end, double* __restrict__ G, double* __restrict__ Q)
+    const uint32_t* __restrict__ end, const uint32_t* __restrict__ item_off,
+    double* __restrict__ part)
 {
-    const int64_t s = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
+    const int64_t it = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (s >= nsrc) return;
+    if (it >= (int64_t)item_off[nsrc]) return;
+    // the source owning this item: the last s with item_off[s] <= it
+    int64_t lo = 0, hi = nsrc;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)item_off[mid] <= it) lo = mid; else hi = mid;
+    }
+    const int64_t s = lo;
     vec4<R> x, w;
-    R ns = R(1);
     if (s < ncells) {
-        const Cell<R> cl = t.cell[s];
-        x = cl.cen;
+        x = t.cell[s].cen;
         w = t.mom[s];
-        ns = (R)(cl.node.y - cl.node.x);
     } else {
         x = pos[s - ncells];
         w = u[s - ncells];
     }
-    const uint32_t b = beg[s], e = end[s];
-    double g[3] = {0.0, 0.0, 0.0}, q[3] = {0.0, 0.0, 0.0};
+    const uint32_t b = beg[s] + (uint32_t)(it - item_off[s]) * (uint32_t)kGradItemEntries;
+    const uint32_t e = min(end[s], b + (uint32_t)kGradItemEntries);
+    const uint32_t np = (uint32_t)(nsrc - ncells);
     R gx = 0, gy = 0, gz = 0, qx = 0, qy = 0, qz = 0;
-    int since = 0;
     for (uint32_t k = b + lane; k < e; k += 32) {
         const uint32_t m = vals[k];
-        if (m >= (uint32_t)(nsrc - ncells)) continue;  // only after a flagged recording walk
+        if (m >= np) continue;  // only after a flagged recording walk
         const vec4<R> xm = pos[m], um = u[m];
         const R rx = xm.x - x.x, ry = xm.y - x.y, rz = xm.z - x.z;
         const R r2 = rx * rx + ry * ry + rz * rz;
         // T(r) u_m (field of u_m) and grad phi(r; w_s, u_m) (force on w_s)
-        if (r2 > R(0)) dipole<R>(rx, ry, rz, r2, w.x, w.y, w.z, um.x, um.y, um.z, gx, gy, gz, qx, qy, qz);
-        if (++since == kFlushEvery) {
-            g[0] += gx; g[1] += gy; g[2] += gz;
-            q[0] += qx; q[1] += qy; q[2] += qz;
-            gx = gy = gz = qx = qy = qz = R(0);
-            since = 0;
-        }
+        if (r2 > R(0))
+            dipole<R>(rx, ry, rz, r2, w.x, w.y, w.z, um.x, um.y, um.z, gx, gy, gz, qx, qy, qz);
     }
-    g[0] += gx; g[1] += gy; g[2] += gz;
-    q[0] += qx; q[1] += qy; q[2] += qz;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        g[a] = warp_sum(g[a]);
-        q[a] = warp_sum(q[a]);
-    }
+    gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz);
+    qx = warp_sum(qx); qy = warp_sum(qy); qz = warp_sum(qz);
     if (lane == 0) {
-        const double inv = 1.0 / (double)ns;
-        G[3 * s] = g[0];
-        G[3 * s + 1] = g[1];
-        G[3 * s + 2] = g[2];
-        Q[3 * s] = q[0] * inv;
-        Q[3 * s + 1] = q[1] * inv;
-        Q[3 * s + 2] = q[2] * inv;
+        double* o = part + 6 * it;
+        o[0] = gx; o[1] = gy; o[2] = gz;
+        o[3] = qx; o[4] = qy; o[5] = qz;
+    }
+}
+
+// One thread per source: its items' partials added in order in FP64.
+template <typename R>
+__global__ void k_item_reduce(Tree<R> t, int64_t ncells, int64_t nsrc,
+                              const uint32_t* __restrict__ item_off,
+                              const double* __restrict__ part, double* __restrict__ G,
+                              double* __restrict__ Q)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsrc) return;
+    double g[3] = {0.0, 0.0, 0.0}, q[3] = {0.0, 0.0, 0.0};
+    for (uint32_t it = item_off[s]; it < item_off[s + 1]; ++it) {
+        const double* o = part + 6 * (int64_t)it;
+        g[0] += o[0]; g[1] += o[1]; g[2] += o[2];
+        q[0] += o[3]; q[1] += o[4]; q[2] += o[5];
+    }
+    double ns = 1.0;
+    if (s < ncells) {
+        const int4 nd = t.cell[s].node;
+        ns = (double)(nd.y - nd.x);
+    }
+    for (int a = 0; a < 3; ++a) {
+        G[3 * s + a] = g[a];
+        Q[3 * s + a] = q[a] / ns;
     }
 }
 
@@ -180,7 +207,7 @@ void grad_entry_counts(const int4* counts, int64_t n, uint32_t* out, unsigned lo
     counted();
 }
 
-void grad_segments(const uint64_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg, uint32_t* end,
+void grad_segments(const uint32_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg, uint32_t* end,
                    cudaStream_t s)
 {
     cudaMemsetAsync(beg, 0, sizeof(uint32_t) * nsrc, s);
@@ -192,14 +219,19 @@ void grad_segments(const uint64_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg
 
 template <typename R>
 void grad_source_sums(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64_t ncells, int64_t n,
-                      const uint32_t* vals, const uint32_t* beg, const uint32_t* end, double* G,
-                      double* Q, cudaStream_t s)
+                      const uint32_t* vals, const uint32_t* beg, const uint32_t* end,
+                      uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
+                      int64_t max_items, double* G, double* Q, cudaStream_t s)
 {
     const int64_t nsrc = ncells + n;
     if (nsrc <= 0) return;
-    k_source_sums<R><<<blocks(nsrc * 32, kGradThreads), kGradThreads, 0, s>>>(
-        pos, u, t, ncells, nsrc, vals, beg, end, G, Q);
-    counted();
+    k_item_counts<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(beg, end, nsrc, items);
+    scan_exclusive(items, item_off, nsrc, scan_tmp, s);
+    k_item_sums<R><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
+        pos, u, t, ncells, nsrc, vals, beg, end, item_off, part);
+    k_item_reduce<R><<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(t, ncells, nsrc, item_off,
+                                                                       part, G, Q);
+    counted(3);
 }
 
 template <typename R>
@@ -227,7 +259,8 @@ void grad_from_field(const vec4<R>* h, const vec4<R>* f, int64_t n, vec4<R>* gra
     template void grad_from_field<R>(const vec4<R>*, const vec4<R>*, int64_t, vec4<R>*, vec4<R>*, \
                                      cudaStream_t);                                               \
     template void grad_source_sums<R>(const vec4<R>*, const vec4<R>*, Tree<R>, int64_t, int64_t,  \
-                                      const uint32_t*, const uint32_t*, const uint32_t*, double*, \
+                                      const uint32_t*, const uint32_t*, const uint32_t*,          \
+                                      uint32_t*, uint32_t*, uint32_t*, double*, int64_t, double*, \
                                       double*, cudaStream_t);                                    \
     template void grad_finish<R>(Tree<R>, int64_t, int64_t, const double*, const double*,         \
                                  const vec4<R>*, const vec4<R>*, R, vec4<R>*, vec4<R>*,           \

@@ -114,7 +114,8 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t n,
 // ------------------------------------------------------------ radix sort
 // Digit of element i: bits [shift, shift + 8) of its key or, in a system pass
 // (sys != null), of the system that owned the element's pre-sort position.
-__device__ __forceinline__ uint32_t radix_digit(const uint64_t* __restrict__ keys,
+template <typename K>
+__device__ __forceinline__ uint32_t radix_digit(const K* __restrict__ keys,
                                                 const uint32_t* __restrict__ vals,
                                                 const uint32_t* __restrict__ sys, int64_t i,
                                                 int shift)
@@ -123,7 +124,8 @@ __device__ __forceinline__ uint32_t radix_digit(const uint64_t* __restrict__ key
     return (uint32_t)((keys[i] >> shift) & (kRadixBins - 1));
 }
 
-__global__ void k_radix_hist(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+template <typename K>
+__global__ void k_radix_hist(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
                              const uint32_t* __restrict__ sys, int64_t n, int shift,
                              uint32_t* __restrict__ hist, int64_t nb)
 {
@@ -141,45 +143,77 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, const uint32_t* 
 }
 
 // Stable scatter: within a tile, keys keep their index order; ranks among
-// equal digits come from warp match masks and per-warp digit counts.
-__global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                const uint32_t* __restrict__ sys, uint64_t* __restrict__ kout,
+// equal digits come from warp match masks and per-warp digit counts.  The tile
+// is first placed in shared memory in digit order, then written out so that
+// consecutive threads store consecutive elements of one bucket (coalesced).
+template <typename K>
+__global__ void k_radix_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                const uint32_t* __restrict__ sys, K* __restrict__ kout,
                                 uint32_t* __restrict__ vout, int64_t n, int shift,
+                                const uint32_t* __restrict__ hist,
                                 const uint32_t* __restrict__ offs, int64_t nb)
 {
-    __shared__ uint32_t s_base[kRadixBins];
+    __shared__ K s_key[kSortTile];
+    __shared__ uint32_t s_val[kSortTile];
+    __shared__ uint32_t s_glob[kRadixBins];  // where this tile's digit-d run starts globally
+    __shared__ uint32_t s_loc[kRadixBins];   // where it starts in the tile's digit order
+    __shared__ uint32_t s_run[kRadixBins];   // next free local slot of digit d
     __shared__ uint32_t s_w[kSortThreads / 32][kRadixBins];
+    __shared__ uint32_t s_wsum[kSortThreads / 32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    s_base[t] = offs[(int64_t)t * nb + blockIdx.x];
+    s_glob[t] = offs[(int64_t)t * nb + blockIdx.x];
+    // local starts: exclusive scan of this tile's digit counts
+    const uint32_t cnt = hist[(int64_t)t * nb + blockIdx.x];
+    uint32_t inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_wsum[w] = inc;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int ww = 0; ww < w; ++ww) before += s_wsum[ww];
+    s_loc[t] = before + inc - cnt;
+    s_run[t] = before + inc - cnt;
     const uint32_t lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const int tile_n = (int)min((int64_t)kSortTile, n - base);
     for (int r = 0; r < kSortItems; ++r) {
 #pragma unroll
         for (int j = 0; j < kRadixBins / 32; ++j) s_w[w][lane + 32 * j] = 0;
         __syncthreads();
         const int64_t i = base + r * kSortThreads + t;
         const bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0ull;
+        K key = valid ? kin[i] : K(0);
         uint32_t d = valid ? radix_digit(kin, vin, sys, i, shift) : (uint32_t)kRadixBins;
         const uint32_t peers = __match_any_sync(kFull, d);
         const uint32_t rank = __popc(peers & lt);
         if (valid && rank == 0) s_w[w][d] = __popc(peers);
         __syncthreads();
-        uint32_t run = s_base[t];
+        uint32_t run = s_run[t];
 #pragma unroll
         for (int ww = 0; ww < kSortThreads / 32; ++ww) {
             uint32_t c = s_w[ww][t];
             s_w[ww][t] = run;
             run += c;
         }
-        s_base[t] = run;
+        s_run[t] = run;
         __syncthreads();
         if (valid) {
-            const uint32_t pos = s_w[w][d] + rank;
-            kout[pos] = key;
-            vout[pos] = vin[i];
+            const uint32_t lp = s_w[w][d] + rank;
+            s_key[lp] = key;
+            s_val[lp] = vin[i];
         }
         __syncthreads();
+    }
+    for (int j = t; j < tile_n; j += kSortThreads) {
+        const K key = s_key[j];
+        const uint32_t val = s_val[j];
+        const uint32_t d = sys ? ((sys[val] >> shift) & (kRadixBins - 1))
+                               : (uint32_t)((key >> shift) & (kRadixBins - 1));
+        const uint32_t g = s_glob[d] + ((uint32_t)j - s_loc[d]);
+        kout[g] = key;
+        vout[g] = val;
     }
 }
 
@@ -662,8 +696,9 @@ size_t radix_tmp_words(int64_t n)
     return (size_t)(h + (h + 1) + scan_tmp_words(h));
 }
 
-bool radix_sort_pairs_passes(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
-                             uint32_t* tmp, int passes, cudaStream_t s)
+template <typename K>
+bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
+                             int passes, cudaStream_t s)
 {
     if (n <= 1) return false;
     const int64_t nb = (n + kSortTile - 1) / kSortTile;
@@ -671,22 +706,26 @@ bool radix_sort_pairs_passes(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t*
     uint32_t* hist = tmp;
     uint32_t* offs = tmp + h;
     uint32_t* stmp = offs + h + 1;
-    uint64_t* ka = k0;
+    K* ka = k0;
     uint32_t* va = v0;
-    uint64_t* kb = k1;
+    K* kb = k1;
     uint32_t* vb = v1;
     for (int p = 0; p < passes; ++p) {
         const int shift = p * kRadixBits;
-        k_radix_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, n, shift, hist, nb);
+        k_radix_hist<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, n, shift, hist, nb);
         scan_exclusive(hist, offs, h, stmp, s);
-        k_radix_scatter<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, kb, vb, n, shift,
-                                                                offs, nb);
+        k_radix_scatter<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, kb, vb, n,
+                                                                   shift, hist, offs, nb);
         counted(2);
-        uint64_t* tk = ka; ka = kb; kb = tk;
+        K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
     return (passes & 1) != 0;
 }
+template bool radix_sort_pairs_passes<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, int64_t,
+                                                uint32_t*, int, cudaStream_t);
+template bool radix_sort_pairs_passes<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t,
+                                                uint32_t*, int, cudaStream_t);
 
 void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
                       uint32_t* tmp, cudaStream_t s)
@@ -702,10 +741,11 @@ void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, in
     uint64_t* kb = k1;
     uint32_t* vb = v1;
     for (int shift = 0; shift < 64; shift += kRadixBits) {
-        k_radix_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, n, shift, hist, nb);
+        k_radix_hist<uint64_t><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, n, shift,
+                                                                     hist, nb);
         scan_exclusive(hist, offs, h, stmp, s);
-        k_radix_scatter<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, kb, vb, n, shift,
-                                                                offs, nb);
+        k_radix_scatter<uint64_t><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, kb, vb, n,
+                                                                          shift, hist, offs, nb);
         counted(2);
         uint64_t* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
@@ -733,10 +773,11 @@ void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, 
     uint32_t* vb = v1;
     for (int p = 0; p < passes; ++p) {
         const int shift = p * kRadixBits;
-        k_radix_hist<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, sg.of_pos, n, shift, hist, nb);
+        k_radix_hist<uint64_t><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, sg.of_pos, n, shift,
+                                                                     hist, nb);
         scan_exclusive(hist, offs, h, stmp, s);
-        k_radix_scatter<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, sg.of_pos, kb, vb, n, shift,
-                                                                offs, nb);
+        k_radix_scatter<uint64_t><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, sg.of_pos, kb, vb, n, shift,
+                                                                hist, offs, nb);
         counted(2);
         uint64_t* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
