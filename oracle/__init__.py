@@ -62,6 +62,11 @@ def lib():
         L.ora_bh_energy_grad.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p,
                                          C.c_int32, _dp, _dp]
         L.ora_bh_energy_grad.restype = C.c_double
+        L.ora_bh_vjp.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p, C.c_int32,
+                                 _dp, _dp, _dp, _dp, C.c_void_p, C.c_void_p]
+        L.ora_mz_grad.argtypes = [_i64, _dp, _dp, _dp, _dp, C.POINTER(Dyn), C.POINTER(BHParams),
+                                  _i64, _dp]
+        L.ora_mz_grad.restype = C.c_double
         L.ora_morton.argtypes = [_i64, _dp, C.c_int32, _u64p, _dp]
         L.ora_tree.argtypes = [_i64, _dp, _dp, C.c_int32, C.c_int32, _u64p, _i64p, _dp, _i64,
                                _i32p, _i32p, _i64p, _i64p, _i64p, _dp, _dp, _dp, _dp, _dp]
@@ -246,6 +251,39 @@ def bh_energy_grad(pos, u, theta, leaf_max=1, prec="f64", dip_scale=1.0, lj_eps=
                                  None if keep is None else C.c_void_p(keep.ctypes.data),
                                  int(bool(tree_centres)), gp, gu)
     return float(e), gp, gu
+
+
+def bh_vjp(pos, u, abar, bbar, theta, leaf_max=1, prec="f64", dip_scale=1.0, lj_eps=0.0,
+           lj_sigma=1.0, lj_rcut=2.5, include_sr=True, pos_dec=None, tree_centres=False):
+    """Vector-Jacobian product of the Barnes-Hut field h and force f (decisions of pos_dec,
+    default pos, frozen): for L = sum abar.h + bbar.f returns (dL/dpos, dL/du, h, f), with h
+    and f of the same frozen evaluation."""
+    pos, u, abar, bbar = _vec3(pos), _vec3(u), _vec3(abar), _vec3(bbar)
+    n = pos.shape[0]
+    p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec),
+                 dip_scale=float(dip_scale), lj_eps=float(lj_eps), lj_sigma=float(lj_sigma),
+                 lj_rcut=float(lj_rcut), include_sr=int(bool(include_sr)), pad=0)
+    dp, du, h, f = (np.zeros((n, 3)) for _ in range(4))
+    keep = None if pos_dec is None else _vec3(pos_dec)
+    lib().ora_bh_vjp(n, pos, u, C.byref(p), None if keep is None else C.c_void_p(keep.ctypes.data),
+                     int(bool(tree_centres)), abar, bbar, dp, du, C.c_void_p(h.ctypes.data),
+                     C.c_void_p(f.ctypes.data))
+    return dp, du, h, f
+
+
+def mz_grad(state, dyn, nsteps, theta=0.5, leaf_max=1, prec="f64", dip_scale=1.0, lj_eps=1.0,
+            lj_sigma=1.0, lj_rcut=2.5, include_sr=True):
+    """Mean magnetisation <M_z> over nsteps steps from `state` (pos, vel, u, om; ids 0..n-1,
+    Philox steps 0..nsteps-1) and its derivative with respect to h_ext by reverse mode.
+    Returns (Mz, dMz/dh_ext[3])."""
+    pos, vel, u, om = (_vec3(state[k]) for k in ("pos", "vel", "u", "om"))
+    n = pos.shape[0]
+    p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec),
+                 dip_scale=float(dip_scale), lj_eps=float(lj_eps), lj_sigma=float(lj_sigma),
+                 lj_rcut=float(lj_rcut), include_sr=int(bool(include_sr)), pad=0)
+    g = np.zeros(3)
+    mz = lib().ora_mz_grad(n, pos, vel, u, om, C.byref(dyn), C.byref(p), int(nsteps), g)
+    return float(mz), g
 
 
 def philox4x32_10(ctr, key):

@@ -1144,3 +1144,397 @@ void ora_energy(int64_t n, const double *pos, const double *vel, const double *u
     for (int a = 0; a < 3; ++a) out[6 + a] /= (double)n;
     out[9] /= (double)n;
 }
+
+/* ------------------------------------------------------------------------ */
+/* reverse mode: field and force VJP, Euler-Maruyama adjoint, d<M_z>/dh      */
+/* ------------------------------------------------------------------------ */
+/*
+ * Hessian of phi(r; a, b) = a . T(r) b applied to v, i.e. the derivative along
+ * v of the printed force 3[a(b.r) + b(a.r) + r(a.b)]/r^5 - 15 r(a.r)(b.r)/r^7:
+ *   3[(a.v) b + (b.v) a + (a.b) v]/r^5
+ *   - 15 [r((a.v)(b.r) + (b.v)(a.r) + (r.v)(a.b)) + v (a.r)(b.r) + (r.v)(a (b.r) + b (a.r))]/r^7
+ *   + 105 r (r.v)(a.r)(b.r)/r^9
+ */
+static void phi_hess(const double r[3], const double a[3], const double b[3], const double v[3],
+                     double out[3])
+{
+    double r2 = dot3(r, r);
+    double ir = 1.0 / sqrt(r2);
+    double ir2 = ir * ir;
+    double ir5 = ir2 * ir2 * ir;
+    double ir7 = ir5 * ir2;
+    double ir9 = ir7 * ir2;
+    double ar = dot3(a, r), br = dot3(b, r), rv = dot3(r, v);
+    double av = dot3(a, v), bv = dot3(b, v), ab = dot3(a, b);
+    for (int c = 0; c < 3; ++c)
+        out[c] = 3.0 * (av * b[c] + bv * a[c] + ab * v[c]) * ir5
+               - 15.0 * (r[c] * (av * br + bv * ar + rv * ab) + v[c] * ar * br
+                         + rv * (a[c] * br + b[c] * ar)) * ir7
+               + 105.0 * r[c] * rv * ar * br * ir9;
+}
+
+typedef struct {
+    const bh_ctx *g;
+    const double *pos_dec;
+    const double *cc, *uc;        /* current centre and moment sum of every cell */
+    const double *abar, *bbar;    /* cotangents of h and f, n x 3 */
+    double *acc;                  /* this thread's source sums: dL/dw_s, dL/dx_s (6 per source) */
+    int lj;
+    double hk[3], fk[3], dx[3], du[3];
+} vjp_ctx;
+
+/*
+ * One interaction of target m with source s (position xs, moment sum ws),
+ * r = rho_m - xs, for L = sum_m abar_m . h_m + bbar_m . f_m with
+ * h_m += ds T(r) ws and f_m += ds grad phi(r; u_m, ws):
+ *   dL/du_m  += ds grad phi(r; bbar_m, ws)
+ *   dL/drho_m += ds [grad phi(r; abar_m, ws) + H phi(r; u_m, ws) bbar_m] = g
+ *   dL/dws   += ds [T(r) abar_m + grad phi(r; bbar_m, u_m)]
+ *   dL/dxs   -= g
+ * (the r-Jacobian of T(r) w is symmetric, so its product with a vector is
+ * grad phi of that vector).
+ */
+static void vjp_term(vjp_ctx *q, int64_t m, const double *xs, const double *ws, double *src6)
+{
+    const bh_ctx *g = q->g;
+    const double ds = g->p->dip_scale;
+    const double *xm = &g->pos[3 * m], *um = &g->u[3 * m];
+    const double *a = &q->abar[3 * m], *b = &q->bbar[3 * m];
+    double r[3], hp[3], fp[3], t1[3], t2[3], t3[3], t4[3], t5[3], dummy[3];
+    for (int c = 0; c < 3; ++c) r[c] = xm[c] - xs[c];
+    if (dot3(r, r) == 0.0) return;
+    ora_pair_dipole(r, um, ws, hp, fp);    /* forward: T(r) ws, grad phi(r; u_m, ws) */
+    ora_pair_dipole(r, b, ws, dummy, t1);  /* grad phi(r; bbar, ws) */
+    ora_pair_dipole(r, a, ws, dummy, t2);  /* grad phi(r; abar, ws) */
+    phi_hess(r, um, ws, b, t3);
+    ora_pair_dipole(r, um, a, t4, dummy);  /* T(r) abar */
+    ora_pair_dipole(r, b, um, dummy, t5);  /* grad phi(r; bbar, u_m) */
+    for (int c = 0; c < 3; ++c) {
+        q->hk[c] += ds * hp[c];
+        q->fk[c] += ds * fp[c];
+        q->du[c] += ds * t1[c];
+        double gc = ds * (t2[c] + t3[c]);
+        q->dx[c] += gc;
+        src6[c] += ds * (t4[c] + t5[c]);
+        src6[3 + c] -= gc;
+    }
+}
+
+/*
+ * LJ pair (Eq. LJ) of target m with particle j inside the cut: f_m += c r,
+ * c = 24 eps (s^12 - s^6) / r^2 with s = sigma / r.  The pair enters
+ * L through bbar_m . c r + bbar_j . c (-r) = c (bbar_m - bbar_j) . r, whose
+ * derivative in rho_m is c db + 2 c'(r^2) (db . r) r, db = bbar_m - bbar_j,
+ * c' = dc / d(r^2) = 24 eps (-7 s^12 + 4 s^6) / r^4.  Every pair inside the cut
+ * is summed exactly by both of its particles, so each adds its own derivative.
+ */
+static void vjp_lj(vjp_ctx *q, int64_t m, int64_t j)
+{
+    const bh_ctx *g = q->g;
+    const double *xm = &g->pos[3 * m], *xj = &g->pos[3 * j];
+    double r[3], db[3];
+    for (int c = 0; c < 3; ++c) {
+        r[c] = xm[c] - xj[c];
+        db[c] = q->bbar[3 * m + c] - q->bbar[3 * j + c];
+    }
+    double r2 = dot3(r, r);
+    double s2 = g->p->lj_sigma * g->p->lj_sigma / r2;
+    double s6 = s2 * s2 * s2;
+    double eps24 = 24.0 * g->p->lj_eps;
+    double cc = eps24 * (s6 * s6 - s6) / r2;
+    double dc = eps24 * (-7.0 * s6 * s6 + 4.0 * s6) / (r2 * r2);
+    double dbr = dot3(db, r);
+    for (int c = 0; c < 3; ++c) {
+        q->fk[c] += cc * r[c];
+        q->dx[c] += cc * db[c] + 2.0 * dc * dbr * r[c];
+    }
+}
+
+static void vjp_visit(vjp_ctx *q, int64_t m, int64_t sm, int64_t c)
+{
+    const bh_ctx *g = q->g;
+    const ora_tree_t *t = g->t;
+    const double *xd = &q->pos_dec[3 * m];
+    int inside = (t->pbegin[c] <= sm && sm < t->pend[c]);
+    int ok = 0;
+    if (!inside) {
+        if (g->p->prec != 1) {
+            float xf[3], cf[3], lof[3];
+            for (int a = 0; a < 3; ++a) {
+                xf[a] = (float)xd[a];
+                cf[a] = (float)t->cen[3 * c + a];
+                lof[a] = (float)t->lo[3 * c + a];
+            }
+            ok = accept_f(xf, cf, (float)t->side[c], lof, g->theta2_f, g->use_rcut, g->rcut2_f);
+        } else {
+            ok = accept_d(xd, &t->cen[3 * c], t->side[c], &t->lo[3 * c], g->theta2_d,
+                          g->use_rcut, g->rcut2_d);
+        }
+    }
+    if (ok) {
+        vjp_term(q, m, &q->cc[3 * c], &q->uc[3 * c], &q->acc[6 * c]);
+        return;
+    }
+    if (t->leaf[c]) {
+        for (int64_t s = t->pbegin[c]; s < t->pend[c]; ++s) {
+            if (s == sm) continue;
+            int64_t j = g->order[s];
+            vjp_term(q, m, &g->pos[3 * j], &g->u[3 * j], &q->acc[6 * (t->n + j)]);
+            if (q->lj && lj_inside(&g->pos[3 * m], &g->pos[3 * j], g->p->lj_rcut, g->p->prec))
+                vjp_lj(q, m, j);
+        }
+        return;
+    }
+    int64_t ch = c + 1;
+    while (ch < t->skip[c]) {
+        vjp_visit(q, m, sm, ch);
+        ch = t->skip[ch];
+    }
+}
+
+/*
+ * Vector-Jacobian product of the Barnes-Hut field and force (Sec. 3.2, the
+ * decisions of pos_dec frozen, as ora_bh_energy_grad): for
+ * L = sum_m abar_m . h_m + bbar_m . f_m, with h the dipolar field and f the
+ * dipolar force plus, when p->include_sr, the LJ force, writes dL/dpos and
+ * dL/du (n x 3).  h_out and f_out (may be NULL) receive the field and force
+ * of the same frozen evaluation.
+ */
+void ora_bh_vjp(int64_t n, const double *pos, const double *u, const ora_bh_params *p,
+                const double *pos_dec, int32_t tree_centres, const double *abar,
+                const double *bbar, double *dpos, double *du, double *h_out, double *f_out)
+{
+    if (!pos_dec) pos_dec = pos;
+    uint64_t *skeys = malloc(n * sizeof(uint64_t));
+    int64_t *order = malloc(n * sizeof(int64_t));
+    int64_t *rank = malloc(n * sizeof(int64_t));
+    double root[4];
+    ora_tree_t t;
+    tree_build(n, pos_dec, u, p->prec, p->leaf_max, skeys, order, root, &t);
+    for (int64_t s = 0; s < n; ++s) rank[order[s]] = s;
+    const int64_t nc = t.n;
+    double *cc = calloc(3 * nc, sizeof(double));
+    double *uc = calloc(3 * nc, sizeof(double));
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int64_t s = t.pbegin[c]; s < t.pend[c]; ++s) {
+            int64_t j = order[s];
+            for (int a = 0; a < 3; ++a) {
+                cc[3 * c + a] += pos[3 * j + a];
+                uc[3 * c + a] += u[3 * j + a];
+            }
+        }
+        double cnt = (double)(t.pend[c] - t.pbegin[c]);
+        for (int a = 0; a < 3; ++a)
+            cc[3 * c + a] = tree_centres ? t.cen[3 * c + a] : cc[3 * c + a] / cnt;
+    }
+    bh_ctx g;
+    g.t = &t;
+    g.order = order;
+    g.pos = pos;
+    g.u = u;
+    g.p = p;
+    g.use_rcut = (p->lj_eps != 0.0 && p->lj_rcut > 0.0);
+    g.theta2_d = p->theta * p->theta;
+    g.theta2_f = (float)g.theta2_d;
+    g.rcut2_d = g.use_rcut ? p->lj_rcut * p->lj_rcut : 0.0;
+    g.rcut2_f = (float)g.rcut2_d;
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    const int64_t nsrc = nc + n;
+    double *acc = calloc((size_t)nthr * 6 * nsrc, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < n; ++m) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        vjp_ctx q;
+        memset(&q, 0, sizeof(q));
+        q.g = &g;
+        q.pos_dec = pos_dec;
+        q.cc = cc;
+        q.uc = uc;
+        q.abar = abar;
+        q.bbar = bbar;
+        q.acc = acc + (size_t)tid * 6 * nsrc;
+        q.lj = g.use_rcut && p->include_sr;
+        vjp_visit(&q, m, rank[m], 0);
+        for (int a = 0; a < 3; ++a) {
+            dpos[3 * m + a] = q.dx[a];
+            du[3 * m + a] = q.du[a];
+            if (h_out) h_out[3 * m + a] = q.hk[a];
+            if (f_out) f_out[3 * m + a] = q.fk[a];
+        }
+    }
+    for (int th = 1; th < nthr; ++th)
+        for (int64_t i = 0; i < 6 * nsrc; ++i) acc[i] += acc[(size_t)th * 6 * nsrc + i];
+    for (int64_t c = 0; c < nc; ++c) {
+        double cnt = (double)(t.pend[c] - t.pbegin[c]);
+        for (int64_t s = t.pbegin[c]; s < t.pend[c]; ++s) {
+            int64_t k = order[s];
+            for (int a = 0; a < 3; ++a) {
+                du[3 * k + a] += acc[6 * c + a];
+                dpos[3 * k + a] += acc[6 * c + 3 + a] / cnt;
+            }
+        }
+    }
+    for (int64_t k = 0; k < n; ++k)
+        for (int a = 0; a < 3; ++a) {
+            du[3 * k + a] += acc[6 * (nc + k) + a];
+            dpos[3 * k + a] += acc[6 * (nc + k) + 3 + a];
+        }
+    free(acc); free(cc); free(uc);
+    tree_free(&t);
+    free(skeys); free(order); free(rank);
+}
+
+/* dF/dw of the wall force F(w) = 24 eps (s^12 - s^6) / w, s = sigma_w / w; zero
+   where the force is cut (w >= sigma_w) or w is clamped */
+static double wall_df(double w, double eps)
+{
+    if (!(w < ORA_WALL_SIGMA)) return 0.0;
+    if (w < ORA_WALL_WMIN) return 0.0;
+    double s = ORA_WALL_SIGMA / w;
+    double s2 = s * s;
+    double s6 = s2 * s2 * s2;
+    return 24.0 * eps * (-13.0 * s6 * s6 + 7.0 * s6) / (w * w);
+}
+
+/*
+ * Adjoint of one Euler-Maruyama step of ora_em_step for one particle.
+ * In: the step-n state (x, v, u, w), the dipolar field hdip and interaction
+ * force fint of that state, and the adjoints of the step's outputs in
+ * (xb, vb, ub, wb), which are replaced by the adjoints of its inputs
+ * (without the field's and force's own dependence on x and u).  Out: the
+ * cotangents of hdip (abar) and fint (bbar), and the cotangent of the applied
+ * field accumulated into hb[3].
+ *   u' = a / |a|, a = u + dt w x u:   abar_a = (ub' - u'(u'.ub')) / |a|
+ *       ub = abar_a - dt w x abar_a;  wb = dt u x abar_a
+ *   w' = w + dt (u x h - Gr w) / I:   wb += (1 - dt Gr / I) wb';  ub += dt/I h x wb'
+ *       hbar = dt/I wb' x u (cotangent of h = hdip + h_ext)
+ *   v' = v + dt (f - Gt v):          vb = (1 - dt Gt) vb';  fbar = dt vb'
+ *   x' = x + dt v:                    xb = xb' + walls' dF/dx fbar;  vb += dt xb'
+ */
+static void em_step_vjp1(const double x[3], const double u[3], const double w[3],
+                         const double hdip[3], const ora_dyn *d, double xb[3], double vb[3],
+                         double ub[3], double wb[3], double abar[3], double bbar[3], double hb[3])
+{
+    const double dt = d->dt;
+    double h[3], a[3], wxu[3], un[3];
+    for (int c = 0; c < 3; ++c) h[c] = hdip[c] + d->h_ext[c];
+    wxu[0] = w[1] * u[2] - w[2] * u[1];
+    wxu[1] = w[2] * u[0] - w[0] * u[2];
+    wxu[2] = w[0] * u[1] - w[1] * u[0];
+    for (int c = 0; c < 3; ++c) a[c] = u[c] + dt * wxu[c];
+    double l = sqrt(dot3(a, a));
+    for (int c = 0; c < 3; ++c) un[c] = a[c] / l;
+    double p = dot3(un, ub);
+    double aa[3];
+    for (int c = 0; c < 3; ++c) aa[c] = (ub[c] - un[c] * p) / l;
+    double nub[3], nwb[3], nvb[3], nxb[3];
+    /* ub = aa - dt w x aa; wb = dt u x aa */
+    nub[0] = aa[0] - dt * (w[1] * aa[2] - w[2] * aa[1]);
+    nub[1] = aa[1] - dt * (w[2] * aa[0] - w[0] * aa[2]);
+    nub[2] = aa[2] - dt * (w[0] * aa[1] - w[1] * aa[0]);
+    nwb[0] = dt * (u[1] * aa[2] - u[2] * aa[1]);
+    nwb[1] = dt * (u[2] * aa[0] - u[0] * aa[2]);
+    nwb[2] = dt * (u[0] * aa[1] - u[1] * aa[0]);
+    const double ci = dt / d->inertia;
+    for (int c = 0; c < 3; ++c) nwb[c] += (1.0 - ci * d->gamma_r) * wb[c];
+    /* ub += dt/I h x wb';  hbar = dt/I wb' x u */
+    nub[0] += ci * (h[1] * wb[2] - h[2] * wb[1]);
+    nub[1] += ci * (h[2] * wb[0] - h[0] * wb[2]);
+    nub[2] += ci * (h[0] * wb[1] - h[1] * wb[0]);
+    abar[0] = ci * (wb[1] * u[2] - wb[2] * u[1]);
+    abar[1] = ci * (wb[2] * u[0] - wb[0] * u[2]);
+    abar[2] = ci * (wb[0] * u[1] - wb[1] * u[0]);
+    for (int c = 0; c < 3; ++c) {
+        hb[c] += abar[c];
+        nvb[c] = (1.0 - dt * d->gamma_t) * vb[c] + dt * xb[c];
+        bbar[c] = dt * vb[c];
+        nxb[c] = xb[c];
+    }
+    if (d->walls)
+        for (int c = 0; c < 3; ++c) {
+            double dfl = wall_df(x[c] - (d->box_lo[c] - 0.5), d->wall_eps);
+            double dfu = wall_df((d->box_hi[c] + 0.5) - x[c], d->wall_eps);
+            nxb[c] += bbar[c] * (dfl + dfu);
+        }
+    for (int c = 0; c < 3; ++c) {
+        xb[c] = nxb[c];
+        vb[c] = nvb[c];
+        ub[c] = nub[c];
+        wb[c] = nwb[c];
+    }
+}
+
+/*
+ * Sensitivity of the mean magnetisation to the applied field (Sec. 5): runs
+ * nsteps steps of ora_em_step from the given state (particle ids 0..n-1,
+ * Philox steps 0..nsteps-1) with the Barnes-Hut (or, at theta = 0, exact)
+ * field and force of p, and returns
+ *   Mz = 1/nsteps sum_{t=1..nsteps} 1/n sum_k u_z,k(t)
+ * with its derivative with respect to h_ext in dmz_dh[3], by reverse mode
+ * through every step (the decisions of each step frozen; noise is additive
+ * and keyed by (seed, step, id), so it does not depend on h_ext).  The input
+ * state is left unchanged.
+ */
+double ora_mz_grad(int64_t n, const double *pos0, const double *vel0, const double *u0,
+                   const double *om0, const ora_dyn *d, const ora_bh_params *p, int64_t nsteps,
+                   double dmz_dh[3])
+{
+    const size_t sz = 3 * (size_t)n;
+    double *X = malloc(sizeof(double) * sz * (nsteps + 1));
+    double *V = malloc(sizeof(double) * sz * (nsteps + 1));
+    double *U = malloc(sizeof(double) * sz * (nsteps + 1));
+    double *W = malloc(sizeof(double) * sz * (nsteps + 1));
+    double *Hd = malloc(sizeof(double) * sz * (nsteps > 0 ? nsteps : 1));
+    int64_t *ids = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; ++k) ids[k] = k;
+    memcpy(X, pos0, sizeof(double) * sz);
+    memcpy(V, vel0, sizeof(double) * sz);
+    memcpy(U, u0, sizeof(double) * sz);
+    memcpy(W, om0, sizeof(double) * sz);
+    double *f = malloc(sizeof(double) * sz);
+    double *esr = malloc(sizeof(double) * (n > 0 ? n : 1));
+    double mz = 0.0;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        double *x = X + sz * s, *v = V + sz * s, *u = U + sz * s, *w = W + sz * s;
+        double *h = Hd + sz * s;
+        ora_bh(n, x, u, p, NULL, 0, h, f, esr, NULL, NULL, NULL, NULL, NULL, NULL);
+        memcpy(x + sz, x, sizeof(double) * sz);
+        memcpy(v + sz, v, sizeof(double) * sz);
+        memcpy(u + sz, u, sizeof(double) * sz);
+        memcpy(w + sz, w, sizeof(double) * sz);
+        ora_em_step(n, x + sz, v + sz, u + sz, w + sz, ids, h, f, d, (uint64_t)s);
+        double m = 0.0;
+        for (int64_t k = 0; k < n; ++k) m += (u + sz)[3 * k + 2];
+        mz += m / (double)n;
+    }
+    mz /= (double)(nsteps > 0 ? nsteps : 1);
+
+    double *xb = calloc(sz, sizeof(double)), *vb = calloc(sz, sizeof(double));
+    double *ub = calloc(sz, sizeof(double)), *wb = calloc(sz, sizeof(double));
+    double *ab = calloc(sz, sizeof(double)), *bb = calloc(sz, sizeof(double));
+    double *dx = calloc(sz, sizeof(double)), *du = calloc(sz, sizeof(double));
+    double hb[3] = {0.0, 0.0, 0.0};
+    const double w_obs = 1.0 / ((double)n * (double)(nsteps > 0 ? nsteps : 1));
+    for (int64_t s = nsteps - 1; s >= 0; --s) {
+        for (int64_t k = 0; k < n; ++k) ub[3 * k + 2] += w_obs;  /* M_z of state s + 1 */
+        const double *x = X + sz * s, *u = U + sz * s, *w = W + sz * s, *h = Hd + sz * s;
+        for (int64_t k = 0; k < n; ++k)
+            em_step_vjp1(&x[3 * k], &u[3 * k], &w[3 * k], &h[3 * k], d, &xb[3 * k], &vb[3 * k],
+                         &ub[3 * k], &wb[3 * k], &ab[3 * k], &bb[3 * k], hb);
+        ora_bh_vjp(n, x, u, p, NULL, 1, ab, bb, dx, du, NULL, NULL);
+        for (size_t i = 0; i < sz; ++i) {
+            xb[i] += dx[i];
+            ub[i] += du[i];
+        }
+    }
+    for (int c = 0; c < 3; ++c) dmz_dh[c] = hb[c];
+    free(X); free(V); free(U); free(W); free(Hd); free(ids); free(f); free(esr);
+    free(xb); free(vb); free(ub); free(wb); free(ab); free(bb); free(dx); free(du);
+    return mz;
+}
