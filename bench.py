@@ -912,6 +912,38 @@ def run_grad(args):
         e2e_once()
     barrier()
     e2e_s = time.perf_counter() - t0
+    # d<M_z>/dh_ext through a 200-step unroll saved every 20 steps, next to the same 200
+    # steps without the derivative (a fresh context each, from the same state)
+    sens = None
+    if not args.no_extras:
+        def fresh():
+            c2 = ff.ff_create(ff.ff_params_default(n=n, precision="f32", theta=args.theta,
+                                                   leaf_max=args.leaf_max, device=dev,
+                                                   stream=stream.cuda_stream, h_ext=(0, 0, 1.0)))
+            ff.ff_set_particles(c2, pos_d, u_d)
+            return c2
+
+        c2 = fresh()
+        ff.ff_step(c2, 3)
+        barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c2 = fresh()
+        s0.record(stream)
+        ff.ff_step(c2, 200)
+        s1.record(stream)
+        barrier()
+        fwd_ms = s0.elapsed_time(s1)
+        c2 = fresh()
+        barrier()
+        t0 = time.perf_counter()
+        mzv, gv = ff.ff_mz_sensitivity(c2, 200, 20)
+        barrier()
+        sens_ms = 1e3 * (time.perf_counter() - t0)
+        sens = {"steps": 200, "checkpoint_every": 20, "ms": sens_ms, "forward_200_steps_ms": fwd_ms,
+                "ratio_to_forward": sens_ms / fwd_ms, "mz": mzv, "dmz_dh": list(gv),
+                "note": "wall clock of ff_mz_sensitivity (forward with checkpoints, segment "
+                        "recomputation, adjoint of every step) vs CUDA-event time of 200 plain steps"}
+        del c2
     line = {
         "metric": GRAD_METRIC, "value": value, "unit": "particle-gradients/s", "n_gpus": world,
         "steps": K, "warmup": W, "ms_per_step": max_ms / K, "higher_is_better": True,
@@ -926,7 +958,7 @@ def run_grad(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "paths": {"field_only_ms": field_ms, "gradient_over_field": (max_ms / K) / field_ms,
-                  "energy": e},
+                  "energy": e, "mz_sensitivity": sens},
         "e2e": {"value": whole_job_rate(n, K, world, max_over_ranks(e2e_s, "cuda")),
                 "unit": "particle-gradients/s", "h2d_bytes_per_step": 2 * n * 3 * 4,
                 "d2h_bytes_per_step": 2 * n * 3 * 4,

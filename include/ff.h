@@ -246,6 +246,23 @@ ff_status ff_tune_traversal(ff_ctx *ctx, const int32_t *groups, int32_t ngroups,
 ff_status ff_energy_grad(ff_ctx *ctx, int32_t algo, double theta, double *energy, void *grad_pos,
                          void *grad_u, int32_t dtype, int32_t loc);
 
+/*
+ * Sensitivity of the mean magnetisation to the applied field (Sec. 5):
+ * advances the state by nsteps steps (as ff_step) and returns
+ *   Mz = 1/nsteps sum over the nsteps new states of 1/n sum_k u_z,k
+ * in *mz and dMz/dh_ext (3 components) in dmz_dh, by reverse mode through
+ * every step: the Euler-Maruyama update (Sec. 4, torque, friction and the
+ * renormalisation of u; walls), the Barnes-Hut field and force (Sec. 3.2)
+ * with each step's opening decisions frozen, and the LJ forces.  The state
+ * is saved every `every` steps and each stretch is recomputed on the way
+ * back (memory: about nsteps / every + every state copies).  Noise is
+ * additive and keyed by (seed, step, particle), so it does not depend on
+ * h_ext and the recomputation reproduces it.  Single-system Barnes-Hut
+ * contexts; the context ends at the advanced state.  Waits.
+ */
+ff_status ff_mz_sensitivity(ff_ctx *ctx, int64_t nsteps, int64_t every, double *mz,
+                            double *dmz_dh);
+
 /* Waits for the context's stream and reports any error flag raised on the GPU. */
 ff_status ff_synchronize(ff_ctx *ctx);
 

@@ -37,4 +37,80 @@ __device__ __forceinline__ void dipole(R rx, R ry, R rz, R r2, R ukx, R uky, R u
     fz += rz * cr + ukz * cuk + ujz * cuj;
 }
 
+
+// Inverse powers of r shared by the derivative terms below.
+template <typename R>
+struct PairGeo {
+    R rx, ry, rz, ir3, ir5, ir7, ir9;
+};
+
+template <typename R>
+__device__ __forceinline__ PairGeo<R> pair_geo(R rx, R ry, R rz, R r2)
+{
+    PairGeo<R> g;
+    g.rx = rx;
+    g.ry = ry;
+    g.rz = rz;
+    const R ir = dip_rsqrt(r2);
+    const R ir2 = ir * ir;
+    g.ir3 = ir2 * ir;
+    g.ir5 = g.ir3 * ir2;
+    g.ir7 = g.ir5 * ir2;
+    g.ir9 = g.ir7 * ir2;
+    return g;
+}
+
+// grad phi(r; p, q) with phi = p . T(r) q (the printed force with u_k = p,
+// u_j = q): 3[p (q.r) + q (p.r) + r (p.q)]/r^5 - 15 r (p.r)(q.r)/r^7, added.
+template <typename R>
+__device__ __forceinline__ void grad_phi_add(const PairGeo<R>& g, R px, R py, R pz, R qx, R qy,
+                                             R qz, R s, R& ox, R& oy, R& oz)
+{
+    const R pr = px * g.rx + py * g.ry + pz * g.rz;
+    const R qr = qx * g.rx + qy * g.ry + qz * g.rz;
+    const R pq = px * qx + py * qy + pz * qz;
+    const R a = R(3) * g.ir5 * s;
+    const R c = (R(3) * pq * g.ir5 - R(15) * pr * qr * g.ir7) * s;
+    ox += a * (px * qr + qx * pr) + c * g.rx;
+    oy += a * (py * qr + qy * pr) + c * g.ry;
+    oz += a * (pz * qr + qz * pr) + c * g.rz;
+}
+
+// T(r) p = [3 r (p.r) - p r^2]/r^5, scaled by s and added.
+template <typename R>
+__device__ __forceinline__ void t_apply_add(const PairGeo<R>& g, R px, R py, R pz, R s, R& ox,
+                                            R& oy, R& oz)
+{
+    const R pr = px * g.rx + py * g.ry + pz * g.rz;
+    const R a = R(3) * pr * g.ir5 * s, b = g.ir3 * s;
+    ox += a * g.rx - b * px;
+    oy += a * g.ry - b * py;
+    oz += a * g.rz - b * pz;
+}
+
+// H phi(r; p, q) v, the derivative of grad phi(r; p, q) along v:
+//   3[(p.v) q + (q.v) p + (p.q) v]/r^5
+//   - 15 [r((p.v)(q.r) + (q.v)(p.r) + (r.v)(p.q)) + v (p.r)(q.r) + (r.v)(p (q.r) + q (p.r))]/r^7
+//   + 105 r (r.v)(p.r)(q.r)/r^9,   scaled by s and added.
+template <typename R>
+__device__ __forceinline__ void hess_phi_add(const PairGeo<R>& g, R px, R py, R pz, R qx, R qy,
+                                             R qz, R vx, R vy, R vz, R s, R& ox, R& oy, R& oz)
+{
+    const R pr = px * g.rx + py * g.ry + pz * g.rz;
+    const R qr = qx * g.rx + qy * g.ry + qz * g.rz;
+    const R rv = g.rx * vx + g.ry * vy + g.rz * vz;
+    const R pv = px * vx + py * vy + pz * vz;
+    const R qv = qx * vx + qy * vy + qz * vz;
+    const R pq = px * qx + py * qy + pz * qz;
+    const R a5 = R(3) * g.ir5 * s;
+    const R a7 = R(15) * g.ir7 * s;
+    const R cr = -a7 * (pv * qr + qv * pr + rv * pq) + R(105) * rv * pr * qr * g.ir9 * s;
+    const R cv = a5 * pq - a7 * pr * qr;
+    const R cp = a5 * qv - a7 * rv * qr;
+    const R cq = a5 * pv - a7 * rv * pr;
+    ox += cr * g.rx + cv * vx + cp * px + cq * qx;
+    oy += cr * g.ry + cv * vy + cp * py + cq * qy;
+    oz += cr * g.rz + cv * vz + cp * pz + cq * qz;
+}
+
 }  // namespace ffk

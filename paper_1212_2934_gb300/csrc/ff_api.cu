@@ -14,6 +14,8 @@
 #include <new>
 #include <vector>
 
+#include <algorithm>
+#include <vector>
 #include "ff.h"
 #include "ffk.cuh"
 
@@ -694,10 +696,9 @@ ff_status grow(ff_ctx* c, T** p, size_t count)
     return FF_OK;
 }
 
-// Energy -1/2 sum u.h (FP64) and its gradient with the opening decisions of
-// this evaluation frozen (k_grad.cu), in sorted order in g_pos, g_u.
-template <typename R>
-ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy)
+// After a counted Barnes-Hut evaluation: scans the per-particle interaction
+// counts into entry slots and sizes every buffer the recorded entries need.
+ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64_t* max_items_out)
 {
     const int64_t n = c->n;
     cudaStream_t s = c->stream;
@@ -706,6 +707,74 @@ ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy)
         if ((st = grow(c, &c->e_cnt, n)) != FF_OK) return st;
         if ((st = grow(c, &c->e_base, n + 1)) != FF_OK) return st;
         if ((st = grow(c, &c->e_total, 1)) != FF_OK) return st;
+    }
+    int ncells_h = 0;
+    FF_CUDA(c, cudaMemsetAsync(c->e_total, 0, sizeof(unsigned long long), s));
+    ffk::grad_entry_counts(c->counts, n, c->e_cnt, c->e_total, s);
+    ffk::scan_exclusive(c->e_cnt, c->e_base, n, c->scan_tmp, s);
+    FF_LAUNCHED(c);
+    unsigned long long total = 0;
+    FF_CUDA(c, cudaMemcpyAsync(&total, c->e_total, sizeof(total), cudaMemcpyDeviceToHost, s));
+    FF_CUDA(c, cudaMemcpyAsync(&ncells_h, c->off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if ((st = sync_and_check(c)) != FF_OK) return st;
+    if (total >= 0xffffffffull)
+        return fail(c, FF_EINVAL, "too many interactions (%llu) for one gradient pass", total);
+    const int64_t ne = (int64_t)total;
+    const int64_t ncells = ncells_h;
+    const int64_t nsrc = ncells + n;
+    if (ne > c->e_cap) {
+        const int64_t cap = ne + ne / 8 + 1024;
+        for (int k = 0; k < 2; ++k) {
+            if ((st = grow(c, &c->e_keys[k], cap)) != FF_OK) return st;
+            if ((st = grow(c, &c->e_vals[k], cap)) != FF_OK) return st;
+        }
+        if ((st = grow(c, &c->e_tmp, ffk::radix_tmp_words(cap))) != FF_OK) return st;
+        c->e_cap = cap;
+    }
+    if (nsrc > c->s_cap) {
+        const int64_t cap = nsrc + nsrc / 8 + 1024;
+        if ((st = grow(c, &c->s_beg, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->s_end, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->s_G, 3 * cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->s_Q, 3 * cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->s_items, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->s_item_off, cap + 1)) != FF_OK) return st;
+        if ((st = grow(c, &c->s_scan, ffk::scan_tmp_words(cap))) != FF_OK) return st;
+        c->s_cap = cap;
+    }
+    const int64_t max_items = nsrc + ne / ffk::kGradItemEntries + 1;
+    if (max_items > c->i_cap) {
+        const int64_t cap = max_items + max_items / 8 + 1024;
+        if ((st = grow(c, &c->i_part, 6 * cap)) != FF_OK) return st;
+        c->i_cap = cap;
+    }
+    *ne_out = ne;
+    *ncells_out = ncells;
+    *max_items_out = max_items;
+    return FF_OK;
+}
+
+// Sorts the recorded entries by source; returns the sorted arrays.
+void sort_entries(ff_ctx* c, int64_t ne, int64_t nsrc, const uint32_t** keys,
+                  const uint32_t** vals)
+{
+    int passes = 1;
+    while (passes < 4 && ((uint64_t)nsrc >> (8 * passes)) != 0) ++passes;
+    const bool in1 = ffk::radix_sort_pairs_passes<uint32_t>(
+        c->e_keys[0], c->e_vals[0], c->e_keys[1], c->e_vals[1], ne, c->e_tmp, passes, c->stream);
+    *keys = c->e_keys[in1 ? 1 : 0];
+    *vals = c->e_vals[in1 ? 1 : 0];
+}
+
+// Energy -1/2 sum u.h (FP64) and its gradient with the opening decisions of
+// this evaluation frozen (k_grad.cu), in sorted order in g_pos, g_u.
+template <typename R>
+ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy)
+{
+    const int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    ff_status st;
+    if (!c->g_pos) {
         if ((st = grow(c, reinterpret_cast<char**>(&c->g_pos), c->rec * n)) != FF_OK) return st;
         if ((st = grow(c, reinterpret_cast<char**>(&c->g_u), c->rec * n)) != FF_OK) return st;
     }
@@ -715,56 +784,16 @@ ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy)
         FF_LAUNCHED(c);
     } else {
         if ((st = eval_bh<R>(c, theta, 0, true)) != FF_OK) return st;
-        int ncells_h = 0;
-        FF_CUDA(c, cudaMemsetAsync(c->e_total, 0, sizeof(unsigned long long), s));
-        ffk::grad_entry_counts(c->counts, n, c->e_cnt, c->e_total, s);
-        ffk::scan_exclusive(c->e_cnt, c->e_base, n, c->scan_tmp, s);
-        FF_LAUNCHED(c);
-        unsigned long long total = 0;
-        FF_CUDA(c, cudaMemcpyAsync(&total, c->e_total, sizeof(total), cudaMemcpyDeviceToHost, s));
-        FF_CUDA(c, cudaMemcpyAsync(&ncells_h, c->off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-        if ((st = sync_and_check(c)) != FF_OK) return st;
-        if (total >= 0xffffffffull)
-            return fail(c, FF_EINVAL, "too many interactions (%llu) for one gradient pass", total);
-        const int64_t ne = (int64_t)total;
-        const int64_t ncells = ncells_h;
+        int64_t ne = 0, ncells = 0, max_items = 0;
+        if ((st = prepare_entries(c, &ne, &ncells, &max_items)) != FF_OK) return st;
         const int64_t nsrc = ncells + n;
-        if (ne > c->e_cap) {
-            const int64_t cap = ne + ne / 8 + 1024;
-            for (int k = 0; k < 2; ++k) {
-                if ((st = grow(c, &c->e_keys[k], cap)) != FF_OK) return st;
-                if ((st = grow(c, &c->e_vals[k], cap)) != FF_OK) return st;
-            }
-            if ((st = grow(c, &c->e_tmp, ffk::radix_tmp_words(cap))) != FF_OK) return st;
-            c->e_cap = cap;
-        }
-        if (nsrc > c->s_cap) {
-            const int64_t cap = nsrc + nsrc / 8 + 1024;
-            if ((st = grow(c, &c->s_beg, cap)) != FF_OK) return st;
-            if ((st = grow(c, &c->s_end, cap)) != FF_OK) return st;
-            if ((st = grow(c, &c->s_G, 3 * cap)) != FF_OK) return st;
-            if ((st = grow(c, &c->s_Q, 3 * cap)) != FF_OK) return st;
-            if ((st = grow(c, &c->s_items, cap)) != FF_OK) return st;
-            if ((st = grow(c, &c->s_item_off, cap + 1)) != FF_OK) return st;
-            if ((st = grow(c, &c->s_scan, ffk::scan_tmp_words(cap))) != FF_OK) return st;
-            c->s_cap = cap;
-        }
-        const int64_t max_items = nsrc + ne / ffk::kGradItemEntries + 1;
-        if (max_items > c->i_cap) {
-            const int64_t cap = max_items + max_items / 8 + 1024;
-            if ((st = grow(c, &c->i_part, 6 * cap)) != FF_OK) return st;
-            c->i_cap = cap;
-        }
         Buffers& a = c->st[c->cur];
         ffk::Tree<R> t = tree_of<R>(c);
         ffk::bh_record<R>(V<R>(a.pos), n, t, field_params<R>(c, theta, 0), c->e_base,
                           c->e_keys[0], c->e_vals[0], c->dflags, c->work, c->off, segs_of(c), s);
-        int passes = 1;
-        while (passes < 8 && ((uint64_t)nsrc >> (8 * passes)) != 0) ++passes;
-        const bool in1 = ffk::radix_sort_pairs_passes<uint32_t>(
-            c->e_keys[0], c->e_vals[0], c->e_keys[1], c->e_vals[1], ne, c->e_tmp, passes, s);
-        const uint32_t* keys = c->e_keys[in1 ? 1 : 0];
-        const uint32_t* vals = c->e_vals[in1 ? 1 : 0];
+        const uint32_t* keys = nullptr;
+        const uint32_t* vals = nullptr;
+        sort_entries(c, ne, nsrc, &keys, &vals);
         ffk::grad_segments(keys, ne, nsrc, c->s_beg, c->s_end, s);
         ffk::grad_source_sums<R>(V<R>(a.pos), V<R>(a.u), t, ncells, n, vals, c->s_beg, c->s_end,
                                  c->s_items, c->s_item_off, c->s_scan, c->i_part, max_items,
@@ -839,6 +868,168 @@ ff_status tune_traversal(ff_ctx* c, const int32_t* groups, int ng, int reps, flo
         }
     }
     return s;
+}
+
+// Sensitivity of the mean magnetisation over nsteps steps to the applied
+// field, by reverse mode through every step (k_step.cu em_adjoint, the field
+// and force VJP of k_field.cu / k_grad.cu), with the state saved every
+// `every` steps and each segment recomputed on the way back.
+template <typename R>
+ff_status mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz_out, double* g_out)
+{
+    const int64_t n = c->n;
+    cudaStream_t s = c->stream;
+    const size_t rb = c->rec * (size_t)n;
+    const size_t ib = sizeof(uint32_t) * (size_t)n;
+    const int64_t ncp = (nsteps + every - 1) / every;
+    struct Scratch {
+        std::vector<void*> dev;
+        double* host = nullptr;
+        ~Scratch()
+        {
+            for (void* q : dev) cudaFree(q);
+            if (host) cudaFreeHost(host);
+        }
+    } sc;
+    bool oom = false;
+    auto alloc = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes ? bytes : 1) != cudaSuccess) {
+            oom = true;
+            return nullptr;
+        }
+        sc.dev.push_back(q);
+        return q;
+    };
+    struct Snap {
+        void* a[4];
+        uint32_t* id;
+        int64_t step;
+    };
+    auto new_snap = [&](Snap& d) {
+        for (int q = 0; q < 4; ++q) d.a[q] = alloc(rb);
+        d.id = static_cast<uint32_t*>(alloc(ib));
+        d.step = 0;
+    };
+    std::vector<Snap> cps((size_t)ncp), seg((size_t)(every < nsteps ? every : nsteps));
+    Snap fin;
+    for (auto& d : cps) new_snap(d);
+    for (auto& d : seg) new_snap(d);
+    new_snap(fin);
+    R* adj[4];
+    R* tmp[4];
+    for (int q = 0; q < 4; ++q) {
+        adj[q] = static_cast<R*>(alloc(rb));
+        tmp[q] = static_cast<R*>(alloc(rb));
+    }
+    R* abar = static_cast<R*>(alloc(rb));
+    R* bbar = static_cast<R*>(alloc(rb));
+    R* dxt = static_cast<R*>(alloc(rb));
+    R* dut = static_cast<R*>(alloc(rb));
+    const int nb = ffk::integrate_blocks(n);
+    double* hpart = static_cast<double*>(alloc(sizeof(double) * 3 * nb));
+    double* mzs = static_cast<double*>(alloc(sizeof(double) * nsteps));
+    double* sumtmp = static_cast<double*>(alloc(sizeof(double) * ffk::sum_tmp_words(n)));
+    if (oom) return fail(c, FF_ENOMEM, "device allocation for the sensitivity failed");
+    if (cudaMallocHost(reinterpret_cast<void**>(&sc.host), sizeof(double) * (3 * nb + nsteps)) !=
+        cudaSuccess)
+        return fail(c, FF_ENOMEM, "pinned host allocation for the sensitivity failed");
+    double* hp_host = sc.host;
+    double* mz_host = sc.host + 3 * nb;
+
+    auto save = [&](Snap& d) -> ff_status {
+        Buffers& b = c->st[c->cur];
+        void* src[4] = {b.pos, b.vel, b.u, b.om};
+        for (int q = 0; q < 4; ++q)
+            FF_CUDA(c, cudaMemcpyAsync(d.a[q], src[q], rb, cudaMemcpyDeviceToDevice, s));
+        FF_CUDA(c, cudaMemcpyAsync(d.id, b.id, ib, cudaMemcpyDeviceToDevice, s));
+        d.step = c->step;
+        return FF_OK;
+    };
+    auto load = [&](const Snap& d) -> ff_status {
+        Buffers& b = c->st[c->cur];
+        void* dst[4] = {b.pos, b.vel, b.u, b.om};
+        for (int q = 0; q < 4; ++q)
+            FF_CUDA(c, cudaMemcpyAsync(dst[q], d.a[q], rb, cudaMemcpyDeviceToDevice, s));
+        FF_CUDA(c, cudaMemcpyAsync(b.id, d.id, ib, cudaMemcpyDeviceToDevice, s));
+        c->step = d.step;
+        ffk::step_set(c->dstep, (unsigned long long)d.step, s);
+        return FF_OK;
+    };
+
+    // forward, saving the state every `every` steps; M_z of every new state
+    ff_status st;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        if (t % every == 0 && (st = save(cps[(size_t)(t / every)])) != FF_OK) return st;
+        if ((st = do_step<R>(c)) != FF_OK) return st;
+        ffk::sum_z<R>(V<R>(c->st[c->cur].u), n, sumtmp, mzs + t, s);
+        FF_LAUNCHED(c);
+    }
+    if ((st = save(fin)) != FF_OK) return st;
+    FF_CUDA(c, cudaMemcpyAsync(mz_host, mzs, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, s));
+    if ((st = sync_and_check(c)) != FF_OK) return st;
+    double mz = 0.0;
+    for (int64_t t = 0; t < nsteps; ++t) mz += mz_host[t];
+    mz /= (double)n * (double)nsteps;
+
+    // backward, one segment at a time from the last
+    for (int q = 0; q < 4; ++q) FF_CUDA(c, cudaMemsetAsync(adj[q], 0, rb, s));
+    double hsum[3] = {0.0, 0.0, 0.0};
+    const R add_uz = (R)(1.0 / ((double)n * (double)nsteps));
+    const double theta = c->p.theta;
+    for (int64_t cp = ncp - 1; cp >= 0; --cp) {
+        const int64_t t0 = cp * every, t1 = std::min(nsteps, t0 + every);
+        if ((st = load(cps[(size_t)cp])) != FF_OK) return st;
+        for (int64_t t = t0; t < t1; ++t) {
+            if ((st = save(seg[(size_t)(t - t0)])) != FF_OK) return st;
+            if ((st = do_step<R>(c)) != FF_OK) return st;
+        }
+        for (int64_t t = t1 - 1; t >= t0; --t) {
+            if ((st = load(seg[(size_t)(t - t0)])) != FF_OK) return st;
+            // the step's tree, decisions, field and force (the state is sorted)
+            if ((st = eval_bh<R>(c, theta, 1, true)) != FF_OK) return st;
+            Buffers& a = c->st[c->cur];
+            const uint32_t* perm = c->vals[0];
+            ffk::em_adjoint<R>(n, V<R>(a.pos), V<R>(a.u), V<R>(a.om), V<R>(c->h), dyn_params<R>(c),
+                               add_uz, V<R>(adj[0]), V<R>(adj[1]), V<R>(adj[2]), V<R>(adj[3]),
+                               V<R>(abar), V<R>(bbar), hpart, s);
+            FF_LAUNCHED(c);
+            FF_CUDA(c, cudaMemcpyAsync(hp_host, hpart, sizeof(double) * 3 * nb,
+                                       cudaMemcpyDeviceToHost, s));
+            int64_t ne = 0, ncells = 0, max_items = 0;
+            if ((st = prepare_entries(c, &ne, &ncells, &max_items)) != FF_OK) return st;
+            for (int b = 0; b < nb; ++b)
+                for (int q = 0; q < 3; ++q) hsum[q] += hp_host[3 * b + q];
+            const int64_t nsrc = ncells + n;
+            ffk::Tree<R> tr = tree_of<R>(c);
+            ffk::bh_record_vjp<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar), n, tr,
+                                  field_params<R>(c, theta, 1), c->e_base, c->e_keys[0],
+                                  c->e_vals[0], c->dflags, c->work, c->off, segs_of(c), V<R>(dxt),
+                                  V<R>(dut), s);
+            const uint32_t* keys = nullptr;
+            const uint32_t* vals = nullptr;
+            sort_entries(c, ne, nsrc, &keys, &vals);
+            ffk::grad_segments(keys, ne, nsrc, c->s_beg, c->s_end, s);
+            ffk::vjp_source_sums<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar),
+                                    (R)c->p.dip_scale, tr, ncells, n, vals, c->s_beg, c->s_end,
+                                    c->s_items, c->s_item_off, c->s_scan, c->i_part, max_items,
+                                    c->s_G, c->s_Q, s);
+            ffk::vjp_finish<R>(tr, ncells, n, c->s_G, c->s_Q, V<R>(dxt), V<R>(dut), V<R>(adj[0]),
+                               V<R>(adj[2]), s);
+            // carry the adjoints back through the step's gather into the state's order
+            for (int q = 0; q < 4; ++q) {
+                ffk::scatter_records<R>(perm, n, V<R>(adj[q]), V<R>(tmp[q]), s);
+                std::swap(adj[q], tmp[q]);
+            }
+            FF_LAUNCHED(c);
+        }
+    }
+    if ((st = load(fin)) != FF_OK) return st;
+    if ((st = sync_and_check(c)) != FF_OK) return st;
+    if (mz_out) *mz_out = mz;
+    if (g_out)
+        for (int q = 0; q < 3; ++q) g_out[q] = hsum[q];
+    return FF_OK;
 }
 
 }  // namespace
@@ -1015,6 +1206,19 @@ ff_status ff_energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy, 
         if ((s = store_array<float>(c, c->g_u, id, grad_u, dtype, loc, 1)) != FF_OK) return s;
     }
     return sync_and_check(c);
+}
+
+ff_status ff_mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz, double* dmz_dh)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (nsteps < 1) return fail(c, FF_EINVAL, "nsteps must be >= 1");
+    if (every < 1) return fail(c, FF_EINVAL, "every must be >= 1");
+    if (c->nsys > 0) return fail(c, FF_EINVAL, "the sensitivity is for a single system");
+    if (c->p.algo != FF_ALGO_BH) return fail(c, FF_EINVAL, "the context does not use Barnes-Hut");
+    return c->fp64 ? mz_sensitivity<double>(c, nsteps, every, mz, dmz_dh)
+                   : mz_sensitivity<float>(c, nsteps, every, mz, dmz_dh);
 }
 
 ff_status ff_step(ff_ctx* c, int64_t nsteps)

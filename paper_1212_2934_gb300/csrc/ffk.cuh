@@ -170,6 +170,14 @@ void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, cons
                uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off, Segs sg,
                cudaStream_t s);
 
+// The same walk for a vector-Jacobian product of h and f with cotangents
+// abar, bbar: also writes each particle's target-side terms to dxt, dut.
+template <typename R>
+void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
+                   const vec4<R>* bbar, int64_t n, Tree<R> t, FieldParams<R> fp,
+                   const uint32_t* base, uint32_t* keys, uint32_t* vals, int* flags, int* work,
+                   const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s);
+
 // ------------------------------------------------ energy gradient (k_grad.cu)
 // entries per particle (accepted cells + exact pairs) as uint32; *total64
 // (zeroed by the caller) receives their sum in 64 bits
@@ -195,6 +203,31 @@ template <typename R>
 void grad_finish(Tree<R> t, int64_t ncells, int64_t n, const double* G, const double* Q,
                  const vec4<R>* h, const vec4<R>* f, R ds, vec4<R>* grad_pos, vec4<R>* grad_u,
                  cudaStream_t s);
+
+// Vector-Jacobian product of h and f, source side: per source s,
+// G_s = ds sum [T(r) abar_m + grad phi(r; bbar_m, u_m)] (dL/dw_s) and
+// Q_s = -ds sum [grad phi(r; abar_m, w_s) + H phi(r; u_m, w_s) bbar_m] / n_s
+// (dL/dx_s per member), same scratch as grad_source_sums.
+template <typename R>
+void vjp_source_sums(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
+                     const vec4<R>* bbar, R ds, Tree<R> t, int64_t ncells, int64_t n,
+                     const uint32_t* vals, const uint32_t* beg, const uint32_t* end,
+                     uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
+                     int64_t max_items, double* G, double* Q, cudaStream_t s);
+// dx_p += dxt_p + sum of Q over the cells holding p (and p's own particle
+// source), du_p += dut_p + the same for G (accumulated into dx, du).
+template <typename R>
+void vjp_finish(Tree<R> t, int64_t ncells, int64_t n, const double* G, const double* Q,
+                const vec4<R>* dxt, const vec4<R>* dut, vec4<R>* dx, vec4<R>* du, cudaStream_t s);
+// out[perm[i]] = in[i] for n records (carries adjoints back through a gather)
+template <typename R>
+void scatter_records(const uint32_t* perm, int64_t n, const vec4<R>* in, vec4<R>* out,
+                     cudaStream_t s);
+// sum over n records of component z into *out (FP64, deterministic; tmp holds
+// sum_tmp_words(n) doubles)
+size_t sum_tmp_words(int64_t n);
+template <typename R>
+void sum_z(const vec4<R>* v, int64_t n, double* tmp, double* out, cudaStream_t s);
 
 // all pairs exact: the gradient is the negated field and force
 template <typename R>
@@ -227,6 +260,16 @@ void integrate(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R>*
                const R* esr, DynParams<R> dp, vec4<R>* pos2, vec4<R>* vel2, vec4<R>* u2,
                vec4<R>* om2, uint32_t* id2, double* partials, cudaStream_t s);
 
+// Adjoint of one integrate step (see k_step.cu): adjoints of the outputs in
+// xb, vb, ub, wb are replaced by those of the inputs (add_uz first added to
+// ub.z); writes the cotangents abar (of h_dip) and bbar (of the interaction
+// force) and per-block sums of abar (3 doubles per integrate_blocks(n) block).
+template <typename R>
+void em_adjoint(int64_t n, const vec4<R>* pos, const vec4<R>* u, const vec4<R>* om,
+                const vec4<R>* hdip, DynParams<R> dp, R add_uz, vec4<R>* xb, vec4<R>* vb,
+                vec4<R>* ub, vec4<R>* wb, vec4<R>* abar, vec4<R>* bbar, double* partials,
+                cudaStream_t s);
+
 // Observables of the state without stepping (per-block partials).
 template <typename R>
 void observables(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R>* u,
@@ -236,6 +279,8 @@ void reduce_partials(const double* partials, int nblocks, double inv_n, double i
                      double* out, cudaStream_t s);
 // Advances the device step counter by one.
 void step_advance(unsigned long long* step, cudaStream_t s);
+// sets the device step counter (restoring a saved state)
+void step_set(unsigned long long* step, unsigned long long v, cudaStream_t s);
 
 // Layout conversion between caller arrays (n x 3, float or double) and
 // records; scatter/gather through the particle ids.

@@ -95,6 +95,30 @@ __device__ __forceinline__ void lj(const FieldParams<R>& fp, R rx, R ry, R rz, R
     e += R(0.5) * (fp.lj_e2 * s6 * s6 - fp.lj_e4 * s6 - fp.lj_shift);
 }
 
+// Derivative terms of one LJ pair for a vector-Jacobian product: the pair
+// enters L = sum bbar . f through c (bbar_k - bbar_j) . r with c = 24 eps
+// (s^12 - s^6) / r^2, whose r-derivative is c db + 2 c'(r^2) (db . r) r,
+// c' = 24 eps s^6 (4 - 7 s^6) / r^4 (the same cut and bracket as lj()).
+template <typename R>
+__device__ __forceinline__ void lj_vjp(const FieldParams<R>& fp, R rx, R ry, R rz, R r2, R dbx,
+                                       R dby, R dbz, R& dx, R& dy, R& dz)
+{
+    if (!(r2 < fp.lj_rcut2_hi)) return;
+    const R r2e = radd(radd(rmul(rx, rx), rmul(ry, ry)), rmul(rz, rz));
+    if (!(r2e < fp.lj_rcut2 && r2e > R(0))) return;
+    const R ir2 = R(1) / r2e;
+    const R s2m1 = sigma2_minus_r2(fp, rx, ry, rz) * ir2;
+    const R s2 = R(1) + s2m1;
+    const R s6 = s2 * s2 * s2;
+    const R s6m1 = s2m1 * (s2 * s2 + s2 + R(1));
+    const R c = fp.lj_eps24 * (s6 * s6m1) * ir2;
+    const R cp = fp.lj_eps24 * s6 * (R(4) - R(7) * s6) * ir2 * ir2;
+    const R k = R(2) * cp * (dbx * rx + dby * ry + dbz * rz);
+    dx += c * dbx + k * rx;
+    dy += c * dby + k * ry;
+    dz += c * dbz + k * rz;
+}
+
 // Opening test in the tree precision, each operation rounded once:
 // side^2 < theta^2 ((dx dx + dy dy) + dz dz), and with LJ on, the distance
 // from the particle to the cell's cube is at least rcut.
@@ -376,17 +400,56 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
 // leaf; value = the particle.  base[k] .. base[k + 1] is the particle's slot,
 // sized from the counted walk (accepted cells + exact pairs); a walk that
 // does not fill it exactly raises the traversal flag.
+// With VJP, the walk also sums the target-side terms of a vector-Jacobian
+// product of h and f (cotangents abar, bbar) for L = sum abar . h + bbar . f:
+//   dL/du_k   += ds grad phi(r; bbar_k, w_s)
+//   dL/drho_k += ds [grad phi(r; abar_k, w_s) + H phi(r; u_k, w_s) bbar_k] + LJ terms
+// written to dxt, dut (the source-side terms come from the recorded entries).
 template <typename R>
+struct VjpIn {
+    const vec4<R>* u;
+    const vec4<R>* abar;
+    const vec4<R>* bbar;
+    vec4<R>* dxt;
+    vec4<R>* dut;
+};
+
+template <typename R>
+__device__ __forceinline__ void vjp_target(const FieldParams<R>& fp, const vec4<R>& xk,
+                                           const vec4<R>& uk, const vec4<R>& ak,
+                                           const vec4<R>& bk, const vec4<R>& xs,
+                                           const vec4<R>& ws, R& dx, R& dy, R& dz, R& ux, R& uy,
+                                           R& uz)
+{
+    const R rx = xk.x - xs.x, ry = xk.y - xs.y, rz = xk.z - xs.z;
+    const R r2 = rx * rx + ry * ry + rz * rz;
+    if (!(r2 > R(0))) return;
+    const PairGeo<R> g = pair_geo<R>(rx, ry, rz, r2);
+    const R ds = fp.dip_scale;
+    grad_phi_add<R>(g, bk.x, bk.y, bk.z, ws.x, ws.y, ws.z, ds, ux, uy, uz);
+    grad_phi_add<R>(g, ak.x, ak.y, ak.z, ws.x, ws.y, ws.z, ds, dx, dy, dz);
+    hess_phi_add<R>(g, uk.x, uk.y, uk.z, ws.x, ws.y, ws.z, bk.x, bk.y, bk.z, ds, dx, dy, dz);
+}
+
+template <typename R, bool VJP>
 __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict__ pos, int n,
                                             const Tree<R>& t, const FieldParams<R>& fp,
                                             unsigned ncells, const uint32_t* __restrict__ base,
                                             uint32_t* __restrict__ keys,
                                             uint32_t* __restrict__ vals, int* flags,
-                                            const uint32_t* __restrict__ off, const Segs& sg)
+                                            const uint32_t* __restrict__ off, const Segs& sg,
+                                            const VjpIn<R>& vj)
 {
     const int k = task * 32 + (threadIdx.x & 31);
     if (k >= n) return;
     const vec4<R> xk = pos[k];
+    vec4<R> uk, ak, bk;
+    R dx = 0, dy = 0, dz = 0, ux = 0, uy = 0, uz = 0;
+    if (VJP) {
+        uk = vj.u[k];
+        ak = vj.abar[k];
+        bk = vj.bbar[k];
+    }
     unsigned i = 0, end = ncells;
     if (sg.of_pos) {
         const int sys = (int)sg.of_pos[k];
@@ -409,6 +472,16 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
                 vals[w] = (uint32_t)k;
             }
             ++w;
+            if (VJP) {
+                const vec4<R> ws = t.mom[i];
+                vjp_target<R>(fp, xk, uk, ak, bk, cl.cen, ws, dx, dy, dz, ux, uy, uz);
+                if (!acc && fp.include_sr) {
+                    const vec4<R> bj = vj.bbar[nd.x];
+                    const R rx = xk.x - cl.cen.x, ry = xk.y - cl.cen.y, rz = xk.z - cl.cen.z;
+                    lj_vjp<R>(fp, rx, ry, rz, rx * rx + ry * ry + rz * rz, bk.x - bj.x,
+                              bk.y - bj.y, bk.z - bj.z, dx, dy, dz);
+                }
+            }
             nxt = (unsigned)nd.z;
         } else if (leaf) {
             if (!single) {
@@ -419,6 +492,17 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
                         vals[w] = (uint32_t)k;
                     }
                     ++w;
+                    if (VJP) {
+                        const vec4<R> xj = pos[s], uj = vj.u[s], bj = vj.bbar[s];
+                        vjp_target<R>(fp, xk, uk, ak, bk, xj, uj, dx, dy, dz, ux, uy, uz);
+                        if (fp.include_sr) {
+                            const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
+                            const R r2 = rx * rx + ry * ry + rz * rz;
+                            if (r2 > R(0))
+                                lj_vjp<R>(fp, rx, ry, rz, r2, bk.x - bj.x, bk.y - bj.y,
+                                          bk.z - bj.z, dx, dy, dz);
+                        }
+                    }
                 }
             }
             nxt = (unsigned)nd.z;
@@ -430,15 +514,23 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         i = nxt;
     }
     if (w != wend) atomicOr(flags, FLAG_TRAVERSE);
+    if (VJP) {
+        vec4<R> o;
+        o.x = dx; o.y = dy; o.z = dz; o.w = R(0);
+        vj.dxt[k] = o;
+        o.x = ux; o.y = uy; o.z = uz;
+        vj.dut[k] = o;
+    }
 }
 
 // The recording walk on the traversal's schedule: warps take 32-particle tasks
 // from their SM's Morton segment first (see k_bh).
-template <typename R>
+template <typename R, bool VJP>
 __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
     const vec4<R>* __restrict__ pos, int n, Tree<R> t, FieldParams<R> fp,
     const uint32_t* __restrict__ base, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-    int* flags, int* __restrict__ work, int nseg, const uint32_t* __restrict__ off, Segs sg)
+    int* flags, int* __restrict__ work, int nseg, const uint32_t* __restrict__ off, Segs sg,
+    VjpIn<R> vj)
 {
     if (*flags & FLAG_CAPACITY) return;
     const unsigned ncells = (unsigned)*t.ncells;
@@ -457,7 +549,8 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
             got = __shfl_sync(kFull, got, 0);
             const int task = t0 + got;
             if (task >= t1) break;
-            record_task<R>(task, pos, n, t, fp, ncells, base, keys, vals, flags, off, sg);
+            record_task<R, VJP>(task, pos, n, t, fp, ncells, base, keys, vals, flags, off, sg,
+                                vj);
         }
     }
 }
@@ -649,30 +742,54 @@ template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<
                                dvec4*, double*, cudaStream_t);
 
 
-template <typename R>
-void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
-               uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off, Segs sg,
-               cudaStream_t s)
+template <typename R, bool VJP>
+void bh_record_g(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
+                 uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off,
+                 Segs sg, VjpIn<R> vj, cudaStream_t s)
 {
-    if (n <= 0) return;
     static int blocks = 0, nsm = 0;
     if (blocks == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_bh_record<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_bh_record<R, VJP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              kTraverseCarveout);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_record<R>, kBhThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_record<R, VJP>, kBhThreads, 0);
         if (per_sm < 1) per_sm = 1;
         if (nsm < 1) nsm = 1;
         if (nsm > kWorkSegments) nsm = kWorkSegments;
         blocks = per_sm * nsm;
     }
     cudaMemsetAsync(work, 0, sizeof(int) * nsm, s);
-    k_bh_record<R><<<blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, keys, vals, flags, work,
-                                                 nsm, off, sg);
+    k_bh_record<R, VJP><<<blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, keys, vals, flags,
+                                                      work, nsm, off, sg, vj);
     counted();
+}
+
+template <typename R>
+void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
+               uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off, Segs sg,
+               cudaStream_t s)
+{
+    if (n <= 0) return;
+    bh_record_g<R, false>(pos, n, t, fp, base, keys, vals, flags, work, off, sg, VjpIn<R>{}, s);
+}
+
+template <typename R>
+void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
+                   const vec4<R>* bbar, int64_t n, Tree<R> t, FieldParams<R> fp,
+                   const uint32_t* base, uint32_t* keys, uint32_t* vals, int* flags, int* work,
+                   const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s)
+{
+    if (n <= 0) return;
+    VjpIn<R> vj;
+    vj.u = u;
+    vj.abar = abar;
+    vj.bbar = bbar;
+    vj.dxt = dxt;
+    vj.dut = dut;
+    bh_record_g<R, true>(pos, n, t, fp, base, keys, vals, flags, work, off, sg, vj, s);
 }
 
 template void bh_record<float>(const float4*, int64_t, Tree<float>, FieldParams<float>,
@@ -681,5 +798,13 @@ template void bh_record<float>(const float4*, int64_t, Tree<float>, FieldParams<
 template void bh_record<double>(const dvec4*, int64_t, Tree<double>, FieldParams<double>,
                                 const uint32_t*, uint32_t*, uint32_t*, int*, int*,
                                 const uint32_t*, Segs, cudaStream_t);
+template void bh_record_vjp<float>(const float4*, const float4*, const float4*, const float4*,
+                                   int64_t, Tree<float>, FieldParams<float>, const uint32_t*,
+                                   uint32_t*, uint32_t*, int*, int*, const uint32_t*, Segs,
+                                   float4*, float4*, cudaStream_t);
+template void bh_record_vjp<double>(const dvec4*, const dvec4*, const dvec4*, const dvec4*,
+                                    int64_t, Tree<double>, FieldParams<double>, const uint32_t*,
+                                    uint32_t*, uint32_t*, int*, int*, const uint32_t*, Segs,
+                                    dvec4*, dvec4*, cudaStream_t);
 
 }  // namespace ffk

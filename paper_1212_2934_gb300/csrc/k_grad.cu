@@ -142,6 +142,137 @@ __global__ void k_item_reduce(Tree<R> t, int64_t ncells, int64_t nsrc,
     }
 }
 
+// One warp per item of the general vector-Jacobian product (see
+// vjp_source_sums): six single-precision sums per item, written in FP64.
+template <typename R>
+__global__ void __launch_bounds__(kGradThreads) k_vjp_item_sums(
+    const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u,
+    const vec4<R>* __restrict__ abar, const vec4<R>* __restrict__ bbar, R ds, Tree<R> t,
+    int64_t ncells, int64_t nsrc, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ beg, const uint32_t* __restrict__ end,
+    const uint32_t* __restrict__ item_off, double* __restrict__ part)
+{
+    const int64_t it = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (it >= (int64_t)item_off[nsrc]) return;
+    int64_t lo = 0, hi = nsrc;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)item_off[mid] <= it) lo = mid; else hi = mid;
+    }
+    const int64_t s = lo;
+    vec4<R> x, w;
+    if (s < ncells) {
+        x = t.cell[s].cen;
+        w = t.mom[s];
+    } else {
+        x = pos[s - ncells];
+        w = u[s - ncells];
+    }
+    const uint32_t b = beg[s] + (uint32_t)(it - item_off[s]) * (uint32_t)kGradItemEntries;
+    const uint32_t e = min(end[s], b + (uint32_t)kGradItemEntries);
+    const uint32_t np = (uint32_t)(nsrc - ncells);
+    R gx = 0, gy = 0, gz = 0, qx = 0, qy = 0, qz = 0;
+    for (uint32_t k = b + lane; k < e; k += 32) {
+        const uint32_t m = vals[k];
+        if (m >= np) continue;  // only after a flagged recording walk
+        const vec4<R> xm = pos[m], um = u[m], am = abar[m], bm = bbar[m];
+        const R rx = xm.x - x.x, ry = xm.y - x.y, rz = xm.z - x.z;
+        const R r2 = rx * rx + ry * ry + rz * rz;
+        if (!(r2 > R(0))) continue;
+        const PairGeo<R> g = pair_geo<R>(rx, ry, rz, r2);
+        // dL/dw_s: T(r) abar_m + grad phi(r; bbar_m, u_m)
+        t_apply_add<R>(g, am.x, am.y, am.z, R(1), gx, gy, gz);
+        grad_phi_add<R>(g, bm.x, bm.y, bm.z, um.x, um.y, um.z, R(1), gx, gy, gz);
+        // dL/dx_s: -(grad phi(r; abar_m, w_s) + H phi(r; u_m, w_s) bbar_m)
+        grad_phi_add<R>(g, am.x, am.y, am.z, w.x, w.y, w.z, R(-1), qx, qy, qz);
+        hess_phi_add<R>(g, um.x, um.y, um.z, w.x, w.y, w.z, bm.x, bm.y, bm.z, R(-1), qx, qy, qz);
+    }
+    gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz);
+    qx = warp_sum(qx); qy = warp_sum(qy); qz = warp_sum(qz);
+    if (lane == 0) {
+        double* o = part + 6 * it;
+        o[0] = (double)gx * (double)ds; o[1] = (double)gy * (double)ds; o[2] = (double)gz * (double)ds;
+        o[3] = (double)qx * (double)ds; o[4] = (double)qy * (double)ds; o[5] = (double)qz * (double)ds;
+    }
+}
+
+// One thread per cell; a leaf adds up its ancestors' source sums for each of
+// its particles and adds the target-side terms.
+template <typename R>
+__global__ void k_vjp_finish(Tree<R> t, int64_t ncells, int64_t n, const double* __restrict__ G,
+                             const double* __restrict__ Q, const vec4<R>* __restrict__ dxt,
+                             const vec4<R>* __restrict__ dut, vec4<R>* __restrict__ dx,
+                             vec4<R>* __restrict__ du)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const int4 nd = t.cell[c].node;
+    if ((nd.w >> 8) == 0) return;
+    double dg[3] = {0.0, 0.0, 0.0}, dq[3] = {0.0, 0.0, 0.0};
+    int a = (int)c;
+    for (int level = 0; a >= 0 && level <= kMaxLevel; ++level) {
+        for (int d = 0; d < 3; ++d) {
+            dg[d] += G[3 * (int64_t)a + d];
+            dq[d] += Q[3 * (int64_t)a + d];
+        }
+        a = t.parent[a];
+    }
+    for (int p = nd.x; p < nd.y; ++p) {
+        const double* gs = G + 3 * (ncells + p);
+        const double* qs = Q + 3 * (ncells + p);
+        const vec4<R> xt = dxt[p], ut = dut[p];
+        vec4<R> ox = dx[p], ou = du[p];
+        ox.x = (R)((double)ox.x + (double)xt.x + dq[0] + qs[0]);
+        ox.y = (R)((double)ox.y + (double)xt.y + dq[1] + qs[1]);
+        ox.z = (R)((double)ox.z + (double)xt.z + dq[2] + qs[2]);
+        ou.x = (R)((double)ou.x + (double)ut.x + dg[0] + gs[0]);
+        ou.y = (R)((double)ou.y + (double)ut.y + dg[1] + gs[1]);
+        ou.z = (R)((double)ou.z + (double)ut.z + dg[2] + gs[2]);
+        dx[p] = ox;
+        du[p] = ou;
+    }
+}
+
+template <typename R>
+__global__ void k_scatter_records(const uint32_t* __restrict__ perm, int64_t n,
+                                  const vec4<R>* __restrict__ in, vec4<R>* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[perm[i]] = in[i];
+}
+
+// per-block FP64 sums of the z components, then one block adds them in order
+template <typename R>
+__global__ void k_sum_z_blocks(const vec4<R>* __restrict__ v, int64_t n, double* __restrict__ tmp)
+{
+    __shared__ double sh[kGradThreads / 32];
+    const int64_t i = (int64_t)blockIdx.x * kGradThreads + threadIdx.x;
+    double x = i < n ? (double)v[i].z : 0.0;
+    x = warp_sum(x);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kGradThreads / 32; ++w) s += sh[w];
+        tmp[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sum_final(const double* __restrict__ tmp, int64_t nb, double* out)
+{
+    __shared__ double sh[kGradThreads];
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < nb; b += kGradThreads) s += tmp[b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kGradThreads; ++k) t += sh[k];
+        *out = t;
+    }
+}
+
 // One thread per cell; a leaf adds up its ancestors' sums and finishes the
 // gradient of each of its particles.
 template <typename R>
@@ -255,7 +386,65 @@ void grad_from_field(const vec4<R>* h, const vec4<R>* f, int64_t n, vec4<R>* gra
     counted();
 }
 
+template <typename R>
+void vjp_source_sums(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
+                     const vec4<R>* bbar, R ds, Tree<R> t, int64_t ncells, int64_t n,
+                     const uint32_t* vals, const uint32_t* beg, const uint32_t* end,
+                     uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
+                     int64_t max_items, double* G, double* Q, cudaStream_t s)
+{
+    const int64_t nsrc = ncells + n;
+    if (nsrc <= 0) return;
+    k_item_counts<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(beg, end, nsrc, items);
+    scan_exclusive(items, item_off, nsrc, scan_tmp, s);
+    k_vjp_item_sums<R><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
+        pos, u, abar, bbar, ds, t, ncells, nsrc, vals, beg, end, item_off, part);
+    k_item_reduce<R><<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(t, ncells, nsrc, item_off,
+                                                                       part, G, Q);
+    counted(3);
+}
+
+template <typename R>
+void vjp_finish(Tree<R> t, int64_t ncells, int64_t n, const double* G, const double* Q,
+                const vec4<R>* dxt, const vec4<R>* dut, vec4<R>* dx, vec4<R>* du, cudaStream_t s)
+{
+    if (ncells <= 0) return;
+    k_vjp_finish<R><<<blocks(ncells, kGradThreads), kGradThreads, 0, s>>>(t, ncells, n, G, Q, dxt,
+                                                                         dut, dx, du);
+    counted();
+}
+
+template <typename R>
+void scatter_records(const uint32_t* perm, int64_t n, const vec4<R>* in, vec4<R>* out,
+                     cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_scatter_records<R><<<blocks(n, kGradThreads), kGradThreads, 0, s>>>(perm, n, in, out);
+    counted();
+}
+
+size_t sum_tmp_words(int64_t n) { return (size_t)((n + kGradThreads - 1) / kGradThreads) + 1; }
+
+template <typename R>
+void sum_z(const vec4<R>* v, int64_t n, double* tmp, double* out, cudaStream_t s)
+{
+    const int64_t nb = (n + kGradThreads - 1) / kGradThreads;
+    if (nb > 0) k_sum_z_blocks<R><<<(unsigned)nb, kGradThreads, 0, s>>>(v, n, tmp);
+    k_sum_final<<<1, kGradThreads, 0, s>>>(tmp, nb, out);
+    counted(nb > 0 ? 2 : 1);
+}
+
 #define FFK_GRAD_INST(R)                                                                          \
+    template void vjp_source_sums<R>(const vec4<R>*, const vec4<R>*, const vec4<R>*,              \
+                                     const vec4<R>*, R, Tree<R>, int64_t, int64_t,               \
+                                     const uint32_t*, const uint32_t*, const uint32_t*,           \
+                                     uint32_t*, uint32_t*, uint32_t*, double*, int64_t, double*,  \
+                                     double*, cudaStream_t);                                     \
+    template void vjp_finish<R>(Tree<R>, int64_t, int64_t, const double*, const double*,          \
+                                const vec4<R>*, const vec4<R>*, vec4<R>*, vec4<R>*, cudaStream_t);\
+    template void scatter_records<R>(const uint32_t*, int64_t, const vec4<R>*, vec4<R>*,          \
+                                     cudaStream_t);                                               \
+    template void sum_z<R>(const vec4<R>*, int64_t, double*, double*, cudaStream_t);              \
     template void grad_from_field<R>(const vec4<R>*, const vec4<R>*, int64_t, vec4<R>*, vec4<R>*, \
                                      cudaStream_t);                                               \
     template void grad_source_sums<R>(const vec4<R>*, const vec4<R>*, Tree<R>, int64_t, int64_t,  \

@@ -346,6 +346,112 @@ __global__ void k_scatter_counts(const int4* __restrict__ in, const uint32_t* __
     if (o) o[d] = v.z;
 }
 
+// dF/dw of wall_force (zero where the force is cut or w is clamped)
+template <typename R>
+__device__ __forceinline__ R wall_dforce(R w, const DynParams<R>& dp)
+{
+    if (!(w < R(0.5))) return R(0);
+    if (w < R(0.01)) return R(0);
+    const R s = R(0.5) / w;
+    const R s2 = s * s;
+    const R s6 = s2 * s2 * s2;
+    return dp.wall_eps24 * (R(7) * s6 - R(13) * s6 * s6) / (w * w);
+}
+
+// Adjoint of one step of k_integrate for each particle.  In: the step's input
+// state, its dipolar field, and the adjoints of the step's outputs in
+// xb, vb, ub, wb (add_uz is first added to ub.z: the mean-magnetisation term
+// of the output state).  Out: the adjoints of the inputs, without the field's
+// and force's own dependence on positions and moments; the cotangents abar of
+// h_dip and bbar of the interaction force; per-block FP64 sums of abar (the
+// cotangent of the applied field) in partials[3 * block + q].
+//   u' = a / |a|, a = u + dt w x u:  aa = (ub' - u'(u'.ub')) / |a|
+//        ub = aa - dt w x aa;  wb = dt u x aa
+//   w' = w + dt (u x h - Gr w) / I:  wb += (1 - dt Gr / I) wb';  ub += dt/I h x wb'
+//        abar = dt/I wb' x u
+//   v' = v + dt (f - Gt v):         vb = (1 - dt Gt) vb' + dt xb';  bbar = dt vb'
+//   x' = x + dt v:                   xb = xb' + bbar . (walls' dF/dx)
+template <typename R>
+__global__ void __launch_bounds__(kStepThreads) k_em_adjoint(
+    int64_t n, const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u,
+    const vec4<R>* __restrict__ om, const vec4<R>* __restrict__ hdip, DynParams<R> dp, R add_uz,
+    vec4<R>* __restrict__ xb, vec4<R>* __restrict__ vb, vec4<R>* __restrict__ ub,
+    vec4<R>* __restrict__ wb, vec4<R>* __restrict__ abar, vec4<R>* __restrict__ bbar,
+    double* __restrict__ partials)
+{
+    __shared__ double sh[kStepThreads / 32][3];
+    R hs[3] = {R(0), R(0), R(0)};
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const vec4<R> x = pos[s], uu = u[s], w = om[s], hd = hdip[s];
+        const Local<R> L = local_of<R>(dp, s);
+        const R hx = hd.x + L.hx, hy = hd.y + L.hy, hz = hd.z + L.hz;
+        const vec4<R> X = xb[s], V = vb[s], W = wb[s];
+        vec4<R> U = ub[s];
+        U.z += add_uz;
+        const R dt = dp.dt;
+        const R cx = w.y * uu.z - w.z * uu.y, cy = w.z * uu.x - w.x * uu.z,
+                cz = w.x * uu.y - w.y * uu.x;
+        const R ax = uu.x + dt * cx, ay = uu.y + dt * cy, az = uu.z + dt * cz;
+        const R il = R(1) / sqrt(ax * ax + ay * ay + az * az);
+        const R nx = ax * il, ny = ay * il, nz = az * il;
+        const R pr = nx * U.x + ny * U.y + nz * U.z;
+        const R qx = (U.x - nx * pr) * il, qy = (U.y - ny * pr) * il, qz = (U.z - nz * pr) * il;
+        const R ci = dt * dp.inv_inertia;
+        vec4<R> oX, oV, oU, oW, oa, ob;
+        oU.x = qx - dt * (w.y * qz - w.z * qy) + ci * (hy * W.z - hz * W.y);
+        oU.y = qy - dt * (w.z * qx - w.x * qz) + ci * (hz * W.x - hx * W.z);
+        oU.z = qz - dt * (w.x * qy - w.y * qx) + ci * (hx * W.y - hy * W.x);
+        oU.w = R(0);
+        const R fr = R(1) - ci * dp.gamma_r;
+        oW.x = dt * (uu.y * qz - uu.z * qy) + fr * W.x;
+        oW.y = dt * (uu.z * qx - uu.x * qz) + fr * W.y;
+        oW.z = dt * (uu.x * qy - uu.y * qx) + fr * W.z;
+        oW.w = R(0);
+        oa.x = ci * (W.y * uu.z - W.z * uu.y);
+        oa.y = ci * (W.z * uu.x - W.x * uu.z);
+        oa.z = ci * (W.x * uu.y - W.y * uu.x);
+        oa.w = R(0);
+        const R ft = R(1) - dt * dp.gamma_t;
+        oV.x = ft * V.x + dt * X.x;
+        oV.y = ft * V.y + dt * X.y;
+        oV.z = ft * V.z + dt * X.z;
+        oV.w = R(0);
+        ob.x = dt * V.x;
+        ob.y = dt * V.y;
+        ob.z = dt * V.z;
+        ob.w = R(0);
+        oX = X;
+        if (dp.walls) {
+            oX.x += ob.x * (wall_dforce<R>(x.x - L.lo[0], dp) + wall_dforce<R>(L.hi[0] - x.x, dp));
+            oX.y += ob.y * (wall_dforce<R>(x.y - L.lo[1], dp) + wall_dforce<R>(L.hi[1] - x.y, dp));
+            oX.z += ob.z * (wall_dforce<R>(x.z - L.lo[2], dp) + wall_dforce<R>(L.hi[2] - x.z, dp));
+        }
+        xb[s] = oX;
+        vb[s] = oV;
+        ub[s] = oU;
+        wb[s] = oW;
+        abar[s] = oa;
+        bbar[s] = ob;
+        hs[0] += oa.x;
+        hs[1] += oa.y;
+        hs[2] += oa.z;
+    }
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        double v = (double)hs[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) sh[wi][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int k = 0; k < kStepThreads / 32; ++k) t += sh[k][threadIdx.x];
+        partials[3 * (int64_t)blockIdx.x + threadIdx.x] = t;
+    }
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -376,6 +482,18 @@ void integrate(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R>*
 }
 
 template <typename R>
+void em_adjoint(int64_t n, const vec4<R>* pos, const vec4<R>* u, const vec4<R>* om,
+                const vec4<R>* hdip, DynParams<R> dp, R add_uz, vec4<R>* xb, vec4<R>* vb,
+                vec4<R>* ub, vec4<R>* wb, vec4<R>* abar, vec4<R>* bbar, double* partials,
+                cudaStream_t s)
+{
+    k_em_adjoint<R><<<integrate_blocks(n), kStepThreads, 0, s>>>(n, pos, u, om, hdip, dp, add_uz,
+                                                                 xb, vb, ub, wb, abar, bbar,
+                                                                 partials);
+    counted();
+}
+
+template <typename R>
 void observables(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R>* u,
                  const vec4<R>* om, const vec4<R>* h, const R* esr, DynParams<R> dp,
                  double* partials, cudaStream_t s)
@@ -395,6 +513,16 @@ void reduce_partials(const double* partials, int nblocks, double inv_n, double i
 void step_advance(unsigned long long* step, cudaStream_t s)
 {
     k_step_advance<<<1, 1, 0, s>>>(step);
+    counted();
+}
+
+namespace {
+__global__ void k_step_set(unsigned long long* step, unsigned long long v) { *step = v; }
+}  // namespace
+
+void step_set(unsigned long long* step, unsigned long long v, cudaStream_t s)
+{
+    k_step_set<<<1, 1, 0, s>>>(step, v);
     counted();
 }
 
@@ -438,6 +566,9 @@ void scatter_counts(const int4* in, const uint32_t* id, int64_t n, int32_t* a, i
                                const vec4<R>*, const uint32_t*, const vec4<R>*, const vec4<R>*,  \
                                const R*, DynParams<R>, vec4<R>*, vec4<R>*, vec4<R>*, vec4<R>*,   \
                                uint32_t*, double*, cudaStream_t);                               \
+    template void em_adjoint<R>(int64_t, const vec4<R>*, const vec4<R>*, const vec4<R>*,          \
+                                const vec4<R>*, DynParams<R>, R, vec4<R>*, vec4<R>*, vec4<R>*,    \
+                                vec4<R>*, vec4<R>*, vec4<R>*, double*, cudaStream_t);            \
     template void observables<R>(int64_t, const vec4<R>*, const vec4<R>*, const vec4<R>*,        \
                                  const vec4<R>*, const vec4<R>*, const R*, DynParams<R>,         \
                                  double*, cudaStream_t);                                        \

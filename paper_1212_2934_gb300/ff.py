@@ -91,6 +91,7 @@ _SIGS = {
     "ff_tune_traversal": (_st, [_vp, _vp, C.c_int32, C.c_int32, C.POINTER(C.c_int32), _vp]),
     "ff_energy_grad": (_st, [_vp, C.c_int32, C.c_double, C.POINTER(C.c_double), _vp, _vp,
                              C.c_int32, C.c_int32]),
+    "ff_mz_sensitivity": (_st, [_vp, C.c_int64, C.c_int64, C.POINTER(C.c_double), _vp]),
     "ff_profile": (_st, [_vp, C.c_int32]),
     "ff_profile_read": (_st, [_vp, C.POINTER(ff_profile_t)]),
     "ff_morton_order_noalloc": (_st, [_vp, C.c_int64, _vp, _vp, _vp]),
@@ -266,6 +267,16 @@ def ff_energy_grad(ctx, algo=FF_ALGO_BH, theta=0.5, dtype=np.float64, device_lik
     _check(ctx.handle, lib().ff_energy_grad(ctx.handle, int(algo), float(theta), C.byref(e),
                                             pp[0], pu[0], pp[1], pp[2]))
     return e.value, gp, gu
+
+
+def ff_mz_sensitivity(ctx, nsteps, every=20):
+    """Advances nsteps steps and returns (<M_z>, d<M_z>/dh_ext[3]) by checkpointed reverse
+    mode (the state is saved every `every` steps)."""
+    mz = C.c_double()
+    g = np.zeros(3)
+    _check(ctx.handle, lib().ff_mz_sensitivity(ctx.handle, int(nsteps), int(every), C.byref(mz),
+                                               C.c_void_p(g.ctypes.data)))
+    return mz.value, g
 
 
 def dipolar_energy(pos, u, ctx, algo=FF_ALGO_BH, theta=0.5):
