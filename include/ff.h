@@ -93,7 +93,13 @@ typedef struct {
     int32_t traverse_group;  /* lanes walking the cell list together: 1,2,4,8,16,32; 0 = default.
                                 Results do not depend on it (every lane decides for itself). */
     void *stream;          /* cudaStream_t to run on; NULL: the context creates one */
+    int32_t rotation;      /* FF_ROT_VECTOR (default): rigid rotor I w' = u x h - G_r w + noise,
+                              u' = w x u; FF_ROT_PRINTED: the printed reduced angle equations
+                              (theta, phi and their rates; the rates kept in w_x, w_y), which
+                              do not relax toward the Boltzmann distribution (Sec. 2) */
 } ff_params;
+
+enum { FF_ROT_VECTOR = 0, FF_ROT_PRINTED = 1 };
 
 /* Energies and observables returned by ff_energy (FP64). */
 typedef struct {

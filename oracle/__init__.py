@@ -42,7 +42,7 @@ class Dyn(C.Structure):
     _fields_ = [("dt", C.c_double), ("gamma_t", C.c_double), ("gamma_r", C.c_double),
                 ("inertia", C.c_double), ("kT", C.c_double), ("rot_noise", C.c_double),
                 ("h_ext", C.c_double * 3), ("box_lo", C.c_double * 3),
-                ("box_hi", C.c_double * 3), ("walls", C.c_int32), ("pad", C.c_int32),
+                ("box_hi", C.c_double * 3), ("walls", C.c_int32), ("literal", C.c_int32),
                 ("wall_eps", C.c_double), ("seed", C.c_uint64)]
 
 
@@ -276,6 +276,8 @@ def mz_grad(state, dyn, nsteps, theta=0.5, leaf_max=1, prec="f64", dip_scale=1.0
     """Mean magnetisation <M_z> over nsteps steps from `state` (pos, vel, u, om; ids 0..n-1,
     Philox steps 0..nsteps-1) and its derivative with respect to h_ext by reverse mode.
     Returns (Mz, dMz/dh_ext[3])."""
+    if dyn.literal:
+        raise ValueError("the sensitivity is defined for the vector rotor form only")
     pos, vel, u, om = (_vec3(state[k]) for k in ("pos", "vel", "u", "om"))
     n = pos.shape[0]
     p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec),
@@ -307,7 +309,7 @@ def normals(seed, step, ids):
 
 def make_dyn(dt=1e-3, gamma_t=0.1, gamma_r=0.1, inertia=0.4, kT=1.0, rot_noise=2.0,
              h_ext=(0.0, 0.0, 0.0), box_lo=(0.0, 0.0, 0.0), box_hi=(0.0, 0.0, 0.0),
-             walls=False, wall_eps=1.0, seed=1):
+             walls=False, wall_eps=1.0, seed=1, literal=False):
     d = Dyn()
     d.dt, d.gamma_t, d.gamma_r, d.inertia, d.kT, d.rot_noise = (
         float(dt), float(gamma_t), float(gamma_r), float(inertia), float(kT), float(rot_noise))
@@ -316,7 +318,7 @@ def make_dyn(dt=1e-3, gamma_t=0.1, gamma_r=0.1, inertia=0.4, kT=1.0, rot_noise=2
         d.box_lo[a] = float(box_lo[a])
         d.box_hi[a] = float(box_hi[a])
     d.walls = int(bool(walls))
-    d.pad = 0
+    d.literal = int(bool(literal))
     d.wall_eps = float(wall_eps)
     d.seed = int(seed)
     return d

@@ -1026,7 +1026,7 @@ typedef struct {
     double h_ext[3];
     double box_lo[3], box_hi[3];
     int32_t walls;
-    int32_t pad;
+    int32_t literal;       /* 1: the printed angle equations (see ora_em_step) */
     double wall_eps;
     uint64_t seed;
 } ora_dyn;
@@ -1078,6 +1078,18 @@ void ora_wall(const double x[3], const ora_dyn *d, double fw[3], double *ew)
  * all right-hand sides from the step-n state; xi_t = normals 0..2 and
  * xi_r = normals 3..5 of (seed, step, id).  Arrays are n x 3, updated in
  * place.
+ *
+ * With d->literal = 1 the rotation follows the printed reduced angle
+ * equations instead (Sec. 2, reduced Eqs. for theta and phi, as printed):
+ * theta = acos(u_z), phi = atan2(u_y, u_x), the rates (theta', phi') are kept
+ * in w_x, w_y (w_z = 0), and
+ *   theta'' I = (u_x h_y - u_y h_x) - G_r theta' + noise
+ *   phi''   I = -(u_y h_z - u_z h_y) sin phi + (u_z h_x - u_x h_z) cos phi - G_r phi' + noise
+ * stepped like the vector form (angles by their rates, rates by the torques,
+ * all from the step-n state, noise normals 3 and 4), then
+ * u = (sin theta cos phi, sin theta sin phi, cos theta).  Kept to document
+ * that these equations do not relax toward the Boltzmann distribution (a
+ * field along z exerts no torque on theta).
  */
 void ora_em_step(int64_t n, double *pos, double *vel, double *u, double *om,
                  const int64_t *ids, const double *hdip, const double *fint,
@@ -1107,11 +1119,26 @@ void ora_em_step(int64_t n, double *pos, double *vel, double *u, double *om,
             un[a] = uu[a] + d->dt * wxu[a];
         }
         double nrm = sqrt(dot3(un, un));
+        for (int a = 0; a < 3; ++a) un[a] /= nrm;
+        if (d->literal) {
+            double uz = uu[2] < -1.0 ? -1.0 : (uu[2] > 1.0 ? 1.0 : uu[2]);
+            double th = acos(uz), ph = atan2(uu[1], uu[0]);
+            double tt = uu[0] * h[1] - uu[1] * h[0];
+            double tp = -(uu[1] * h[2] - uu[2] * h[1]) * sin(ph)
+                        + (uu[2] * h[0] - uu[0] * h[2]) * cos(ph);
+            double th2 = th + d->dt * w[0], ph2 = ph + d->dt * w[1];
+            wn[0] = w[0] + d->dt * (tt - d->gamma_r * w[0]) / d->inertia + sr * z[3];
+            wn[1] = w[1] + d->dt * (tp - d->gamma_r * w[1]) / d->inertia + sr * z[4];
+            wn[2] = 0.0;
+            un[0] = sin(th2) * cos(ph2);
+            un[1] = sin(th2) * sin(ph2);
+            un[2] = cos(th2);
+        }
         for (int a = 0; a < 3; ++a) {
             x[a] = xn[a];
             v[a] = vn[a];
             w[a] = wn[a];
-            uu[a] = un[a] / nrm;
+            uu[a] = un[a];
         }
     }
 }
@@ -1479,7 +1506,7 @@ static void em_step_vjp1(const double x[3], const double u[3], const double w[3]
  * with its derivative with respect to h_ext in dmz_dh[3], by reverse mode
  * through every step (the decisions of each step frozen; noise is additive
  * and keyed by (seed, step, id), so it does not depend on h_ext).  The input
- * state is left unchanged.
+ * state is left unchanged.  Vector rotor form only (d->literal = 0).
  */
 double ora_mz_grad(int64_t n, const double *pos0, const double *vel0, const double *u0,
                    const double *om0, const ora_dyn *d, const ora_bh_params *p, int64_t nsteps,

@@ -267,6 +267,7 @@ ffk::DynParams<R> dyn_params(const ff_ctx* c)
     d.wall_e2 = (R)(2.0 * p.wall_eps);
     d.wall_e4 = (R)(4.0 * p.wall_eps);
     d.walls = p.walls ? 1 : 0;
+    d.printed_angles = p.rotation == FF_ROT_PRINTED ? 1 : 0;
     d.key0 = (uint32_t)p.seed;
     d.key1 = (uint32_t)(p.seed >> 32);
     d.step = c->dstep;
@@ -544,6 +545,7 @@ const char* check_params(const ff_params* p)
     if (p->n < 1 || p->n > kMaxN) return "n out of range (1 .. 2^27)";
     if (p->precision != FF_FP32 && p->precision != FF_FP64 && p->precision != FF_MIXED)
         return "bad precision";
+    if (p->rotation != FF_ROT_VECTOR && p->rotation != FF_ROT_PRINTED) return "bad rotation";
     if (p->algo != FF_ALGO_BH && p->algo != FF_ALGO_AP) return "bad algo";
     if (p->leaf_max < 1 || p->leaf_max > ffk::kMaxLeaf) return "leaf_max out of range (1 .. 64)";
     if (!(p->theta >= 0.0) || !std::isfinite(p->theta)) return "theta must be finite and >= 0";
@@ -1213,6 +1215,7 @@ ff_status ff_mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz
     LaunchTally tally_(c);
     ff_status s = usable(c, true);
     if (s != FF_OK) return s;
+    if (c->p.rotation != FF_ROT_VECTOR) return fail(c, FF_EINVAL, "the sensitivity is defined for the vector rotor");
     if (nsteps < 1) return fail(c, FF_EINVAL, "nsteps must be >= 1");
     if (every < 1) return fail(c, FF_EINVAL, "every must be >= 1");
     if (c->nsys > 0) return fail(c, FF_EINVAL, "the sensitivity is for a single system");

@@ -85,6 +85,7 @@ struct DynParams {
     R lo[3], hi[3];
     R wall_eps24, wall_e2, wall_e4;
     int walls;
+    int printed_angles;                  // 1: the printed angle equations (see k_step.cu)
     uint32_t key0, key1;                 // Philox key (seed)
     const unsigned long long* step;      // device word: the step counter
     // batched ensembles (null for a single system): per-system applied field

@@ -233,6 +233,21 @@ __global__ void __launch_bounds__(kStepThreads) k_integrate(
         un.y = ay * inv;
         un.z = az * inv;
         un.w = R(0);
+        if (dp.printed_angles) {
+            // the printed reduced angle equations: theta, phi from u, their rates in
+            // w_x, w_y; angles moved by the rates, rates by the printed torques
+            const R uz = uu.z < R(-1) ? R(-1) : (uu.z > R(1) ? R(1) : uu.z);
+            const R th = acos(uz), ph = atan2(uu.y, uu.x);
+            const R tt = uu.x * hy - uu.y * hx;
+            const R tp = -(uu.y * hz - uu.z * hy) * sin(ph) + (uu.z * hx - uu.x * hz) * cos(ph);
+            const R th2 = th + dp.dt * w.x, ph2 = ph + dp.dt * w.y;
+            wn.x = w.x + dp.dt * (tt - dp.gamma_r * w.x) * dp.inv_inertia + dp.sig_r * z[3];
+            wn.y = w.y + dp.dt * (tp - dp.gamma_r * w.y) * dp.inv_inertia + dp.sig_r * z[4];
+            wn.z = R(0);
+            un.x = sin(th2) * cos(ph2);
+            un.y = sin(th2) * sin(ph2);
+            un.z = cos(th2);
+        }
         pos2[s] = xn;
         vel2[s] = vn;
         u2[s] = un;

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libff.so")
 
 FF_OK, FF_EINVAL, FF_ENOMEM, FF_ECUDA, FF_EDEVICE, FF_ENONFINITE, FF_ESTATE = range(7)
 FF_FP32, FF_FP64, FF_MIXED = 0, 1, 2
+FF_ROT_VECTOR, FF_ROT_PRINTED = 0, 1
 FF_ALGO_BH, FF_ALGO_AP = 0, 1
 FF_DTYPE_F32, FF_DTYPE_F64 = 0, 1
 FF_HOST, FF_DEVICE = 0, 1
@@ -41,7 +42,7 @@ class ff_params(C.Structure):
                 ("box_hi", C.c_double * 3), ("walls", C.c_int32), ("device", C.c_int32),
                 ("wall_eps", C.c_double), ("seed", C.c_uint64),
                 ("count_interactions", C.c_int32), ("traverse_group", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("rotation", C.c_int32)]
 
 
 class ff_energy_t(C.Structure):

@@ -25,8 +25,8 @@ import math
 import numpy as np
 
 __all__ = ["box_side_for_fraction", "isotropic_moments", "rsa_cube", "dense_cube",
-           "uniform_cube", "chains_cube", "batched_sizes", "batched_ensembles", "Ensemble",
-           "make_ensemble"]
+           "uniform_cube", "chains_cube", "slab_monolayer", "batched_sizes", "batched_ensembles",
+           "Ensemble", "make_ensemble"]
 
 
 def box_side_for_fraction(n: int, phi: float, diameter: float = 1.0) -> float:
@@ -236,6 +236,43 @@ def chains_cube(nchains: int, length: int, side: float, seed: int,
     pos = np.concatenate(placed)
     u = np.concatenate(placed_u)
     return pos, u
+
+
+def slab_monolayer(n: int, area_fraction: float, seed: int, gap: float = 0.05,
+                   dmin: float = 1.0):
+    """A monolayer between two walls (Sec. 4: a parallelepiped of height 2.1 R as the
+    confinement).  In diameters the wall planes are 2.1 R = 1.05 apart; with planes half a
+    diameter beyond the box (the walls' convention) the centres lie in z in [0, gap],
+    gap = 0.05.  In the plane: random sequential addition in a square of side
+    sqrt(n (pi/4) / area_fraction), centres >= dmin apart (3-d distances).
+    Returns (pos, side)."""
+    from scipy.spatial import cKDTree
+
+    side = math.sqrt(n * (math.pi / 4.0) / area_fraction)
+    rng = np.random.default_rng([seed, 0x51AB])
+    placed = np.empty((0, 3))
+    tree = None
+    idle = 0
+    while placed.shape[0] < n:
+        if idle > 200:
+            raise RuntimeError("slab_monolayer jammed at %d of %d" % (placed.shape[0], n))
+        m = max(1024, 2 * (n - placed.shape[0]))
+        cand = np.column_stack([rng.uniform(0.0, side, m), rng.uniform(0.0, side, m),
+                                rng.uniform(0.0, gap, m)])
+        ok = np.ones(m, dtype=bool)
+        if tree is not None:
+            d, _ = tree.query(cand, k=1, distance_upper_bound=dmin)
+            ok &= ~(d < dmin)
+        idx = np.nonzero(ok)[0]
+        if idx.size:
+            idx = idx[_drop_later_conflicts(cand[idx], dmin)][: n - placed.shape[0]]
+        if idx.size == 0:
+            idle += 1
+            continue
+        idle = 0
+        placed = np.concatenate([placed, cand[idx]])
+        tree = cKDTree(placed)
+    return placed, side
 
 
 def batched_sizes(nsys: int = 256, nmin: int = 1024, nmax: int = 65536):

@@ -170,3 +170,55 @@ def test_walls_hold_particles(ff):
     assert np.isfinite(x).all()
     assert x.min() > -0.6 and x.max() < e["side"] + 0.6
     np.testing.assert_allclose(np.linalg.norm(u, axis=1), 1.0, atol=1e-5)
+
+
+def test_printed_angle_equations_match_oracle(ff, ora):
+    """rotation = FF_ROT_PRINTED: the printed reduced angle equations, FP64, 40 steps of the
+    dense cube with the field tilted off z, against the oracle's literal mode."""
+    from paper_1212_2934_gb300 import synth
+
+    e = synth.make_ensemble("dense4096")
+    e["h_ext"] = (0.4, -0.3, 0.8)
+    steps = 40
+    s = dict(pos=e["pos"].copy(), vel=np.zeros_like(e["pos"]), u=e["u"].copy(),
+             om=np.zeros_like(e["pos"]), id=np.arange(e["n"], dtype=np.int64))
+    dyn = _odyn(ora, e, literal=True)
+    kw = dict(theta=e["theta"], leaf_max=e["leaf_max"], prec="f64", dip_scale=e["dip_scale"],
+              lj_eps=e["lj_eps"], lj_sigma=e["lj_sigma"], lj_rcut=e["lj_rcut"])
+    for k in range(steps):
+        ora.run(s, 1, dyn, "bh", k, **kw)
+    ctx = ff.ff_create(_params(ff, e, "f64", rotation=ff.FF_ROT_PRINTED))
+    ff.ff_set_particles(ctx, e["pos"], e["u"])
+    ff.ff_step(ctx, steps)
+    x, u, v, w = ff.ff_get_particles(ctx)
+    assert np.abs(x - s["pos"]).max() <= 1e-9 * np.abs(s["pos"]).max()
+    assert np.abs(u - s["u"]).max() <= 1e-9
+    assert rel_err(w, s["om"]).max() <= 1e-9
+    assert np.all(w[:, 2] == 0.0)  # the rates live in w_x, w_y
+
+
+@pytest.mark.slow
+def test_printed_angle_equations_do_not_magnetise(ff, ora):
+    """The documented bias on the GPU: non-interacting moments in h = 3 z under the printed
+    angle equations keep <u_z> near 0, while the vector rotor follows L(3) = 0.672."""
+    n = 4000
+    rng = np.random.default_rng(11)
+    pos = rng.uniform(0, 200, (n, 3))
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    out = {}
+    for rot in (ff.FF_ROT_VECTOR, ff.FF_ROT_PRINTED):
+        p = ff.ff_params_default(n=n, precision="f32", algo="ap", dip_scale=0.0, lj_eps=0.0,
+                                 gamma_t=1.0, gamma_r=1.0, kT=1.0, h_ext=(0, 0, 3.0), seed=3,
+                                 rotation=rot)
+        ctx = ff.ff_create(p)
+        ff.ff_set_particles(ctx, pos.astype(np.float32), u.astype(np.float32))
+        ff.ff_step(ctx, 3000)
+        acc = 0.0
+        for _ in range(20):
+            ff.ff_step(ctx, 100)
+            acc += ff.ff_get_particles(ctx)[1][:, 2].mean()
+        out[rot] = acc / 20
+    L3 = float(ora.langevin(np.array([3.0]))[0])
+    assert abs(out[ff.FF_ROT_VECTOR] - L3) < 0.05
+    assert abs(out[ff.FF_ROT_PRINTED]) < 0.1

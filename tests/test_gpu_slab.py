@@ -1,0 +1,83 @@
+"""The monolayer confinement of Sec. 4 (a parallelepiped of height 2.1 R).
+
+In diameters the wall planes are 1.05 apart; with the walls' convention (planes
+half a diameter beyond the box) the box is [0, L]^2 x [0, 0.05].  The tree is
+then nearly flat (a quadtree inside the root cube).  Checked: the Barnes-Hut
+field and force against the oracle (FP32 1e-5; forces against the term
+magnitudes, which cancel between close neighbours), an FP64 trajectory with
+the slab walls against the oracle, and that the walls hold the monolayer.
+"""
+import numpy as np
+import pytest
+
+from conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ff():
+    from paper_1212_2934_gb300 import _build, ff
+
+    _build.build()
+    ff.lib()
+    return ff
+
+
+def _slab(n, seed):
+    from paper_1212_2934_gb300 import synth
+
+    pos, side = synth.slab_monolayer(n, 0.3, seed)
+    u = synth.isotropic_moments(n, seed + 1)
+    return pos, u, side
+
+
+def _params(ff, n, side, prec, **kw):
+    base = dict(n=n, precision=prec, walls=1, box_lo=(0, 0, 0), box_hi=(side, side, 0.05),
+                h_ext=(0.0, 0.0, 0.0), gamma_t=0.5, gamma_r=0.5, seed=4)
+    base.update(kw)
+    return ff.ff_params_default(**base)
+
+
+def test_slab_field_matches_oracle(ff, ora):
+    pos, u, side = _slab(6000, 3)
+    pos32 = pos.astype(np.float32).astype(np.float64)
+    u32 = u.astype(np.float32).astype(np.float64)
+    ctx = ff.ff_create(_params(ff, len(pos), side, "f32", count_interactions=1))
+    ff.ff_set_particles(ctx, pos32.astype(np.float32), u32.astype(np.float32))
+    h, f = ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, 0.5, True)
+    ref = ora.bh(pos32, u32, 0.5, 1, "f32", 1.0, 1.0, 1.0, 2.5, True)
+    assert rel_err(h, ref["h"]).max() <= 1e-5
+    assert rel_err(f, ref["f"], scale=ref["fabs"]).max() <= 1e-5
+    acc, pairs, opened = ff.ff_get_counts(ctx)
+    assert np.array_equal(acc, ref["nacc"]) and np.array_equal(pairs, ref["npair"])
+
+
+def test_slab_trajectory_matches_oracle(ff, ora):
+    pos, u, side = _slab(1500, 5)
+    steps = 30
+    s = dict(pos=pos.copy(), vel=np.zeros_like(pos), u=u.copy(), om=np.zeros_like(pos),
+             id=np.arange(len(pos), dtype=np.int64))
+    dyn = ora.make_dyn(gamma_t=0.5, gamma_r=0.5, kT=1.0, box_lo=(0, 0, 0),
+                       box_hi=(side, side, 0.05), walls=True, seed=4)
+    for k in range(steps):
+        ora.run(s, 1, dyn, "bh", k, theta=0.5, leaf_max=1, prec="f64", dip_scale=1.0,
+                lj_eps=1.0, lj_sigma=1.0, lj_rcut=2.5)
+    ctx = ff.ff_create(_params(ff, len(pos), side, "f64"))
+    ff.ff_set_particles(ctx, pos, u)
+    ff.ff_step(ctx, steps)
+    x, uu, v, w = ff.ff_get_particles(ctx)
+    assert np.abs(x - s["pos"]).max() <= 1e-9 * np.abs(s["pos"]).max()
+    assert np.abs(uu - s["u"]).max() <= 1e-9
+    assert rel_err(v, s["vel"]).max() <= 1e-9
+
+
+def test_walls_hold_the_monolayer(ff):
+    pos, u, side = _slab(4000, 7)
+    ctx = ff.ff_create(_params(ff, len(pos), side, "f32"))
+    ff.ff_set_particles(ctx, pos.astype(np.float32), u.astype(np.float32))
+    ff.ff_step(ctx, 500)
+    x = ff.ff_get_particles(ctx)[0]
+    # centres never reach the wall planes at -0.5 and 0.55
+    assert x[:, 2].min() > -0.5 and x[:, 2].max() < 0.55
+    assert np.isfinite(x).all()

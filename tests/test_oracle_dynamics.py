@@ -185,3 +185,48 @@ def test_langevin_function(ora):
     L = ora.langevin(a)
     np.testing.assert_allclose(L[1:], 1 / np.tanh(a[1:]) - 1 / a[1:], rtol=1e-14)
     assert L[0] == pytest.approx(a[0] / 3)
+
+
+# ------------------------------------------- the printed angle equations (documented bias)
+
+
+def test_literal_angle_step_by_hand(ora):
+    """The printed reduced angle equations on one noise-free particle: u = x (theta = pi/2,
+    phi = 0) in h = (0, 1, 0): the theta torque u_x h_y - u_y h_x = 1 and the phi torque
+    -(u_y h_z - u_z h_y) sin phi + (u_z h_x - u_x h_z) cos phi = 0; the first step changes
+    only the rates, the second moves theta by dt times the new rate."""
+    s = dict(pos=np.zeros((1, 3)), vel=np.zeros((1, 3)), u=np.array([[1.0, 0, 0]]),
+             om=np.zeros((1, 3)), id=np.zeros(1, dtype=np.int64))
+    dt, g, inertia = 1e-3, 0.1, 0.4
+    dyn = ora.make_dyn(dt=dt, gamma_r=g, inertia=inertia, kT=0.0, h_ext=(0, 1.0, 0),
+                       literal=True)
+    zero = np.zeros((1, 3))
+    ora.em_step(s, zero, zero, dyn, 0)
+    rate = dt * 1.0 / inertia
+    np.testing.assert_allclose(s["om"][0], [rate, 0.0, 0.0], atol=1e-15)
+    np.testing.assert_allclose(s["u"][0], [1.0, 0.0, 0.0], atol=1e-15)
+    # second step: theta = pi/2 + dt * rate (the torque is now cos(theta') in x-y terms)
+    ora.em_step(s, zero, zero, dyn, 1)
+    th = np.pi / 2 + dt * rate
+    np.testing.assert_allclose(s["u"][0], [np.sin(th), 0.0, np.cos(th)], atol=1e-14)
+    tq = np.sin(np.pi / 2) * 1.0  # u_x h_y at the second step's start (u_x = sin(pi/2) = 1)
+    np.testing.assert_allclose(s["om"][0, 0], rate + dt * (tq - g * rate) / inertia, rtol=1e-13)
+
+
+@pytest.mark.slow
+def test_literal_angles_do_not_magnetise(ora):
+    """The documented bias of the printed angle equations: a field along z exerts no torque on
+    theta, so a non-interacting ensemble does not magnetise (<u_z> stays near 0), where the
+    vector rigid rotor gives L(alpha) (test_langevin_magnetisation)."""
+    n = 2000
+    s = _state(n, 3)
+    dyn = ora.make_dyn(gamma_t=1.0, gamma_r=1.0, kT=1.0, h_ext=(0, 0, 3.0), seed=7, literal=True)
+    zero = np.zeros((n, 3))
+    acc, cnt = 0.0, 0
+    for k in range(5000):
+        ora.em_step(s, zero, zero, dyn, k)
+        if k >= 3000 and k % 50 == 0:
+            acc += s["u"][:, 2].mean()
+            cnt += 1
+    L3 = float(ora.langevin(np.array([3.0]))[0])
+    assert abs(acc / cnt) < 0.1 < L3 - 0.5

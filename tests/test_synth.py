@@ -53,3 +53,12 @@ def test_rsa_and_batched_shapes():
     b = synth.batched_ensembles(8, 0.02, 5.0, 2)
     assert b["pos"].shape[0] == int(b["sizes"].sum())
     assert sorted(b["fields"][:, 2].tolist()) == pytest.approx(list(5.0 * np.arange(8) / 7))
+
+
+def test_slab_monolayer():
+    pos, side = synth.slab_monolayer(1500, 0.3, 2)
+    assert pos.shape == (1500, 3)
+    assert pos[:, 2].min() >= 0.0 and pos[:, 2].max() <= 0.05
+    assert pos[:, :2].min() >= 0.0 and pos[:, :2].max() <= side
+    assert len(cKDTree(pos).query_pairs(1.0 - 1e-9)) == 0
+    assert 1500 * np.pi / 4 / side ** 2 == pytest.approx(0.3)
