@@ -35,7 +35,7 @@ _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
 class BHParams(C.Structure):
     _fields_ = [("theta", C.c_double), ("leaf_max", C.c_int32), ("prec", C.c_int32),
                 ("dip_scale", C.c_double), ("lj_eps", C.c_double), ("lj_sigma", C.c_double),
-                ("lj_rcut", C.c_double), ("include_sr", C.c_int32), ("pad", C.c_int32)]
+                ("lj_rcut", C.c_double), ("include_sr", C.c_int32), ("quad", C.c_int32)]
 
 
 class Dyn(C.Structure):
@@ -196,19 +196,19 @@ def tree(pos, u, prec="f32", leaf_max=1):
 
 
 def bh(pos, u, theta, leaf_max=1, prec="f32", dip_scale=1.0, lj_eps=0.0, lj_sigma=1.0,
-       lj_rcut=2.5, include_sr=True, only=None):
+       lj_rcut=2.5, include_sr=True, only=None, quad=False):
     """Barnes-Hut field and force (Sec. 3.2) with the opening rule stated in ora.c.
 
     Returns a dict with h, f, e_sr (n x 3 / n, FP64, input order), nacc, npair,
     nopen, ncover (per-particle counts), habs, fabs (sums of the magnitudes of the
     terms summed into h and f) and ncells.  With ``only`` (indices), rows of other
-    particles are zero.
+    particles are zero.  quad: add each accepted cell's dipole-position term.
     """
     pos, u = _vec3(pos), _vec3(u)
     n = pos.shape[0]
     p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec),
                  dip_scale=float(dip_scale), lj_eps=float(lj_eps), lj_sigma=float(lj_sigma),
-                 lj_rcut=float(lj_rcut), include_sr=int(bool(include_sr)), pad=0)
+                 lj_rcut=float(lj_rcut), include_sr=int(bool(include_sr)), quad=int(bool(quad)))
     h = np.zeros((n, 3))
     f = np.zeros((n, 3))
     e = np.zeros(n)
@@ -239,7 +239,7 @@ def bh_energy_grad(pos, u, theta, leaf_max=1, prec="f64", dip_scale=1.0, lj_eps=
     n = pos.shape[0]
     p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec),
                  dip_scale=float(dip_scale), lj_eps=float(lj_eps), lj_sigma=float(lj_sigma),
-                 lj_rcut=float(lj_rcut), include_sr=0, pad=0)
+                 lj_rcut=float(lj_rcut), include_sr=0, quad=0)
     gp = np.zeros((n, 3))
     gu = np.zeros((n, 3))
     keep = None
@@ -262,7 +262,7 @@ def bh_vjp(pos, u, abar, bbar, theta, leaf_max=1, prec="f64", dip_scale=1.0, lj_
     n = pos.shape[0]
     p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec),
                  dip_scale=float(dip_scale), lj_eps=float(lj_eps), lj_sigma=float(lj_sigma),
-                 lj_rcut=float(lj_rcut), include_sr=int(bool(include_sr)), pad=0)
+                 lj_rcut=float(lj_rcut), include_sr=int(bool(include_sr)), quad=0)
     dp, du, h, f = (np.zeros((n, 3)) for _ in range(4))
     keep = None if pos_dec is None else _vec3(pos_dec)
     lib().ora_bh_vjp(n, pos, u, C.byref(p), None if keep is None else C.c_void_p(keep.ctypes.data),
@@ -282,7 +282,7 @@ def mz_grad(state, dyn, nsteps, theta=0.5, leaf_max=1, prec="f64", dip_scale=1.0
     n = pos.shape[0]
     p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec),
                  dip_scale=float(dip_scale), lj_eps=float(lj_eps), lj_sigma=float(lj_sigma),
-                 lj_rcut=float(lj_rcut), include_sr=int(bool(include_sr)), pad=0)
+                 lj_rcut=float(lj_rcut), include_sr=int(bool(include_sr)), quad=0)
     g = np.zeros(3)
     mz = lib().ora_mz_grad(n, pos, vel, u, om, C.byref(dyn), C.byref(p), int(nsteps), g)
     return float(mz), g

@@ -549,7 +549,7 @@ typedef struct {
     double dip_scale;
     double lj_eps, lj_sigma, lj_rcut;
     int32_t include_sr;
-    int32_t pad;
+    int32_t quad;          /* 1: add each accepted cell's dipole-position (quadrupole) term */
 } ora_bh_params;
 
 /*
@@ -622,7 +622,46 @@ typedef struct {
     int use_rcut;
     float theta2_f, rcut2_f;
     double theta2_d, rcut2_d;
+    const double *quad;   /* 7 per cell: S_xx, S_yy, S_zz, S_xy, S_xz, S_yz, m (p->quad only) */
 } bh_ctx;
+
+/*
+ * Next term of the pseudo-particle expansion (an accuracy extension beyond
+ * the paper's pseudo-particles).  A cell's particles sit at rho_i = c + d_i
+ * with moments u_i; the field at r from the centre c is
+ *   sum_i T(r - d_i) u_i = T(r) U - grad Phi(r) + O(d^2),
+ *   Phi(r) = sum_i d_i . T(r) u_i = (3 r.S.r - m r^2) / r^5,
+ * with S the symmetric part of M = sum_i d_i (x) u_i and m its trace.  The
+ * force on a dipole u_k is the gradient of u_k . h, so its correction is
+ * -H Phi u_k:
+ *   grad Phi  = 6 S r / r^5 - 15 (r.S.r) r / r^7 + 3 m r / r^5
+ *   H Phi v   = 6 S v / r^5 - 30 (r.v) S r / r^7 - 30 (S r.v) r / r^7 - 15 (r.S.r) v / r^7
+ *             + 105 (r.S.r)(r.v) r / r^9 + 3 m v / r^5 - 15 m (r.v) r / r^7
+ * q7 = (S_xx, S_yy, S_zz, S_xy, S_xz, S_yz, m).  Adds the corrections to h, f.
+ */
+static void quad_correction(const double r[3], const double q7[7], const double uk[3],
+                            double h[3], double f[3])
+{
+    double r2 = dot3(r, r);
+    double ir = 1.0 / sqrt(r2);
+    double ir2 = ir * ir, ir5 = ir2 * ir2 * ir, ir7 = ir5 * ir2, ir9 = ir7 * ir2;
+    double S[3][3] = {{q7[0], q7[3], q7[4]}, {q7[3], q7[1], q7[5]}, {q7[4], q7[5], q7[2]}};
+    double m = q7[6];
+    double Sr[3], Su[3];
+    for (int a = 0; a < 3; ++a) {
+        Sr[a] = S[a][0] * r[0] + S[a][1] * r[1] + S[a][2] * r[2];
+        Su[a] = S[a][0] * uk[0] + S[a][1] * uk[1] + S[a][2] * uk[2];
+    }
+    double q = dot3(r, Sr), ru = dot3(r, uk), sru = dot3(Sr, uk);
+    for (int a = 0; a < 3; ++a) {
+        double gp = 6.0 * Sr[a] * ir5 - 15.0 * q * r[a] * ir7 + 3.0 * m * r[a] * ir5;
+        double hp = 6.0 * Su[a] * ir5 - 30.0 * ru * Sr[a] * ir7 - 30.0 * sru * r[a] * ir7
+                  - 15.0 * q * uk[a] * ir7 + 105.0 * q * ru * r[a] * ir9 + 3.0 * m * uk[a] * ir5
+                  - 15.0 * m * ru * r[a] * ir7;
+        h[a] -= gp;
+        f[a] -= hp;
+    }
+}
 
 typedef struct {
     double h[3], fd[3], fs[3], e_sr;
@@ -658,6 +697,7 @@ static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *
         for (int a = 0; a < 3; ++a) r[a] = xk[a] - t->cen[3 * c + a];
         if (dot3(r, r) > 0.0) {
             ora_pair_dipole(r, uk, &t->U64[3 * c], hp, fp);
+            if (g->quad) quad_correction(r, &g->quad[7 * c], uk, hp, fp);
             for (int a = 0; a < 3; ++a) { acc->h[a] += hp[a]; acc->fd[a] += fp[a]; }
             acc->habs += sqrt(dot3(hp, hp));
             acc->fdabs += sqrt(dot3(fp, fp));
@@ -732,6 +772,29 @@ int64_t ora_bh(int64_t n, const double *pos, const double *u, const ora_bh_param
     g.theta2_f = (float)g.theta2_d;
     g.rcut2_d = g.use_rcut ? p->lj_rcut * p->lj_rcut : 0.0;
     g.rcut2_f = (float)g.rcut2_d;
+    g.quad = NULL;
+    double *quad = NULL;
+    if (p->quad) {
+        /* S and m of every cell about its pseudo-particle position, from its particles */
+        quad = calloc(7 * t.n, sizeof(double));
+        for (int64_t c = 0; c < t.n; ++c) {
+            double *q7 = &quad[7 * c];
+            for (int64_t s = t.pbegin[c]; s < t.pend[c]; ++s) {
+                int64_t j = order[s];
+                double d[3];
+                for (int a = 0; a < 3; ++a) d[a] = pos[3 * j + a] - t.cen[3 * c + a];
+                const double *uj = &u[3 * j];
+                q7[0] += d[0] * uj[0];
+                q7[1] += d[1] * uj[1];
+                q7[2] += d[2] * uj[2];
+                q7[3] += 0.5 * (d[0] * uj[1] + d[1] * uj[0]);
+                q7[4] += 0.5 * (d[0] * uj[2] + d[2] * uj[0]);
+                q7[5] += 0.5 * (d[1] * uj[2] + d[2] * uj[1]);
+                q7[6] += dot3(d, uj);
+            }
+        }
+        g.quad = quad;
+    }
 
     int64_t cnt = only ? n_only : n;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -753,6 +816,7 @@ int64_t ora_bh(int64_t n, const double *pos, const double *u, const ora_bh_param
         if (fabs_out) fabs_out[k] = fabs(p->dip_scale) * acc.fdabs + acc.fsabs;
     }
     int64_t nc = t.n;
+    free(quad);
     tree_free(&t);
     free(skeys);
     free(order);
@@ -889,6 +953,7 @@ double ora_bh_energy_grad(int64_t n, const double *pos, const double *u, const o
     g.theta2_f = (float)g.theta2_d;
     g.rcut2_d = g.use_rcut ? p->lj_rcut * p->lj_rcut : 0.0;
     g.rcut2_f = (float)g.rcut2_d;
+    g.quad = NULL;  /* the gradients use the paper's pseudo-particles only */
 
     int nthr = 1;
 #ifdef _OPENMP
@@ -1365,6 +1430,7 @@ void ora_bh_vjp(int64_t n, const double *pos, const double *u, const ora_bh_para
     g.theta2_f = (float)g.theta2_d;
     g.rcut2_d = g.use_rcut ? p->lj_rcut * p->lj_rcut : 0.0;
     g.rcut2_f = (float)g.rcut2_d;
+    g.quad = NULL;  /* the gradients use the paper's pseudo-particles only */
     int nthr = 1;
 #ifdef _OPENMP
     nthr = omp_get_max_threads();
