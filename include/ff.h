@@ -97,6 +97,12 @@ typedef struct {
                               u' = w x u; FF_ROT_PRINTED: the printed reduced angle equations
                               (theta, phi and their rates; the rates kept in w_x, w_y), which
                               do not relax toward the Boltzmann distribution (Sec. 2) */
+    int32_t quadrupole;    /* 1: every accepted cell also contributes its dipole-position
+                              (quadrupole) term about the centre, -grad Phi to h and -H Phi u
+                              to f with Phi = (3 r.S.r - m r^2)/r^5, S and m from
+                              sum (rho_i - c) (x) u_i: an accuracy option beyond the paper's
+                              pseudo-particles (error second order in theta).  Barnes-Hut
+                              only; not with ff_energy_grad or ff_mz_sensitivity */
 } ff_params;
 
 enum { FF_ROT_VECTOR = 0, FF_ROT_PRINTED = 1 };

@@ -62,6 +62,8 @@ struct ff_ctx {
     void* lo = nullptr;
     void* sum = nullptr;
     ffk::dvec4* sum_hi = nullptr;  // FP64 cell sums (mixed precision only)
+    void* q1 = nullptr;          // dipole-position terms per cell (quadrupole option only)
+    void* q2 = nullptr;
     ffk::dvec4* mom_hi = nullptr;
     int* parent = nullptr;
     int* arrive = nullptr;
@@ -206,6 +208,8 @@ ffk::Tree<R> tree_of(ff_ctx* c)
     t.arrive = c->arrive;
     t.ncells = reinterpret_cast<int*>(c->off + c->n);
     t.cap = c->cap;
+    t.q1 = static_cast<ffk::vec4<R>*>(c->q1);
+    t.q2 = static_cast<ffk::vec4<R>*>(c->q2);
     return t;
 }
 
@@ -449,7 +453,8 @@ ff_status sync_and_check(ff_ctx* c)
 void free_all(ff_ctx* c)
 {
     void* ptrs[] = {c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->radix_tmp, c->cnt, c->off,
-                    c->scan_tmp, c->bbox, c->cell, c->mom, c->lo, c->sum, c->sum_hi, c->mom_hi, c->parent,
+                    c->scan_tmp, c->bbox, c->cell, c->mom, c->lo, c->sum, c->sum_hi, c->mom_hi,
+                    c->q1, c->q2, c->parent,
                     c->arrive, c->h, c->f, c->esr, c->counts, c->work, c->partials, c->obs, c->obs_step, c->dstep, c->sys_of_pos, c->sys_start, c->sys_h, c->sys_lo,
                     c->sys_hi, c->sys_acc,
                     c->dflags, c->staging, c->e_cnt, c->e_base, c->e_total, c->g_pos, c->g_u,
@@ -515,6 +520,10 @@ ff_status alloc_all(ff_ctx* c)
         A(&c->sum_hi, sizeof(ffk::dvec4) * c->cap);
         A(&c->mom_hi, sizeof(ffk::dvec4) * c->cap);
     }
+    if (c->p.quadrupole) {
+        A(&c->q1, rec * c->cap);
+        A(&c->q2, rec * c->cap);
+    }
     A(&c->parent, sizeof(int) * c->cap);
     A(&c->arrive, sizeof(int) * c->cap);
     A(&c->h, rec * n);
@@ -546,6 +555,7 @@ const char* check_params(const ff_params* p)
     if (p->precision != FF_FP32 && p->precision != FF_FP64 && p->precision != FF_MIXED)
         return "bad precision";
     if (p->rotation != FF_ROT_VECTOR && p->rotation != FF_ROT_PRINTED) return "bad rotation";
+    if (p->quadrupole != 0 && p->quadrupole != 1) return "quadrupole must be 0 or 1";
     if (p->algo != FF_ALGO_BH && p->algo != FF_ALGO_AP) return "bad algo";
     if (p->leaf_max < 1 || p->leaf_max > ffk::kMaxLeaf) return "leaf_max out of range (1 .. 64)";
     if (!(p->theta >= 0.0) || !std::isfinite(p->theta)) return "theta must be finite and >= 0";
@@ -1196,6 +1206,8 @@ ff_status ff_energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy, 
     if (algo == FF_ALGO_AP && c->nsys > 0) return fail(c, FF_EINVAL, "all-pairs is not available for batched systems");
     if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(c, FF_EINVAL, "theta must be finite and >= 0");
     if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
+    if (c->p.quadrupole && algo == FF_ALGO_BH)
+        return fail(c, FF_EINVAL, "the gradient uses the paper's pseudo-particles (quadrupole off)");
     s = c->fp64 ? energy_grad<double>(c, algo, theta, energy)
                 : energy_grad<float>(c, algo, theta, energy);
     if (s != FF_OK) return s;
@@ -1216,6 +1228,7 @@ ff_status ff_mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz
     ff_status s = usable(c, true);
     if (s != FF_OK) return s;
     if (c->p.rotation != FF_ROT_VECTOR) return fail(c, FF_EINVAL, "the sensitivity is defined for the vector rotor");
+    if (c->p.quadrupole) return fail(c, FF_EINVAL, "the sensitivity uses the paper's pseudo-particles (quadrupole off)");
     if (nsteps < 1) return fail(c, FF_EINVAL, "nsteps must be >= 1");
     if (every < 1) return fail(c, FF_EINVAL, "every must be >= 1");
     if (c->nsys > 0) return fail(c, FF_EINVAL, "the sensitivity is for a single system");

@@ -116,6 +116,11 @@ struct Tree {
     int* arrive;         // aggregation arrival counters
     int* ncells;         // device word: number of cells
     int64_t cap;         // allocated cells
+    // dipole-position (quadrupole) terms about the centre, when enabled (else null):
+    // q1 = (S_xx, S_yy, S_zz, S_xy), q2 = (S_xz, S_yz, m, 0), S the symmetric part of
+    // sum (rho_i - c) (x) u_i and m its trace
+    vec4<R>* q1 = nullptr;
+    vec4<R>* q2 = nullptr;
 };
 
 // ---------------------------------------------------------------- launchers

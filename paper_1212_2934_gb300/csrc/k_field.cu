@@ -119,6 +119,43 @@ __device__ __forceinline__ void lj_vjp(const FieldParams<R>& fp, R rx, R ry, R r
     dz += c * dbz + k * rz;
 }
 
+// Dipole-position (quadrupole) term of an accepted cell (an option beyond the
+// paper's pseudo-particles): with S the symmetric part of sum (rho_i - c) (x) u_i
+// and m its trace (q1 = (S_xx, S_yy, S_zz, S_xy), q2 = (S_xz, S_yz, m, 0)) and
+// Phi(r) = (3 r.S.r - m r^2) / r^5, the field gains -grad Phi and the force
+// -H Phi u_k:
+//   grad Phi = 6 S r / r^5 + r (3 m / r^5 - 15 q / r^7),           q = r.S.r
+//   H Phi u  = 6 S u / r^5 - 30 (r.u) S r / r^7
+//            + r (105 q (r.u) / r^9 - 30 (S r.u) / r^7 - 15 m (r.u) / r^7)
+//            + u (3 m / r^5 - 15 q / r^7)
+template <typename R>
+__device__ __forceinline__ void quad_term(R rx, R ry, R rz, R r2, const vec4<R>& q1,
+                                          const vec4<R>& q2, R ux, R uy, R uz, R& hx, R& hy,
+                                          R& hz, R& fx, R& fy, R& fz)
+{
+    const PairGeo<R> g = pair_geo<R>(rx, ry, rz, r2);
+    const R srx = q1.x * rx + q1.w * ry + q2.x * rz;
+    const R sry = q1.w * rx + q1.y * ry + q2.y * rz;
+    const R srz = q2.x * rx + q2.y * ry + q1.z * rz;
+    const R sux = q1.x * ux + q1.w * uy + q2.x * uz;
+    const R suy = q1.w * ux + q1.y * uy + q2.y * uz;
+    const R suz = q2.x * ux + q2.y * uy + q1.z * uz;
+    const R q = rx * srx + ry * sry + rz * srz;
+    const R ru = rx * ux + ry * uy + rz * uz;
+    const R sru = srx * ux + sry * uy + srz * uz;
+    const R m = q2.z;
+    const R c6 = R(6) * g.ir5;
+    const R cmq = R(3) * m * g.ir5 - R(15) * q * g.ir7;
+    hx -= c6 * srx + cmq * rx;
+    hy -= c6 * sry + cmq * ry;
+    hz -= c6 * srz + cmq * rz;
+    const R cs = R(30) * ru * g.ir7;
+    const R cr = R(105) * q * ru * g.ir9 - R(30) * sru * g.ir7 - R(15) * m * ru * g.ir7;
+    fx -= c6 * sux - cs * srx + cr * rx + cmq * ux;
+    fy -= c6 * suy - cs * sry + cr * ry + cmq * uy;
+    fz -= c6 * suz - cs * srz + cr * rz + cmq * uz;
+}
+
 // Opening test in the tree precision, each operation rounded once:
 // side^2 < theta^2 ((dx dx + dy dy) + dz dz), and with LJ on, the distance
 // from the particle to the cell's cube is at least rcut.
@@ -302,7 +339,7 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
 
 // Independent per-lane walk (group size 1): each lane follows its own path
 // through the cell list; no vote or shuffle per visited cell.
-template <typename R, bool COUNT>
+template <typename R, bool COUNT, bool QUAD>
 __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ pos,
                                          const vec4<R>* __restrict__ u, int n, const Tree<R>& t,
                                          const FieldParams<R>& fp, unsigned ncells,
@@ -346,6 +383,9 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
             const R r2 = rx * rx + ry * ry + rz * rz;
             if (r2 > R(0))
                 dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, m.x, m.y, m.z, hx, hy, hz, fx, fy, fz);
+            if (QUAD && acc && r2 > R(0))
+                quad_term<R>(rx, ry, rz, r2, t.q1[i], t.q2[i], uk.x, uk.y, uk.z, hx, hy, hz, fx,
+                             fy, fz);
             if (acc) {
                 if (COUNT) ++nacc;
             } else {
@@ -560,7 +600,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
 // (so warps sharing an L1 cache walk neighbouring parts of the tree) and then
 // from the following segments once its own is used up.  Task counters
 // (work[0..nseg)) start at zero; every task is taken exactly once.
-template <typename R, bool COUNT, int G>
+template <typename R, bool COUNT, int G, bool QUAD>
 __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh(const vec4<R>* __restrict__ pos,
                                             const vec4<R>* __restrict__ u, int n, Tree<R> t,
                                             FieldParams<R> fp, vec4<R>* __restrict__ h,
@@ -587,8 +627,8 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh(const vec4<R>* 
             const int task = t0 + got;
             if (task >= t1) break;
             if (G == 1)
-                bh_task1<R, COUNT>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags, off,
-                                   sg);
+                bh_task1<R, COUNT, QUAD>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags,
+                                         off, sg);
             else
                 bh_task<R, COUNT, G>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags, off,
                                      sg);
@@ -666,7 +706,7 @@ __global__ void __launch_bounds__(kApThreads) k_ap(const vec4<R>* __restrict__ p
 
 }  // namespace
 
-template <typename R, bool COUNT, int G>
+template <typename R, bool COUNT, int G, bool QUAD = false>
 void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
                  vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work,
                  const uint32_t* off, Segs sg, cudaStream_t s)
@@ -678,17 +718,17 @@ void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, Fie
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_bh<R, COUNT, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_bh<R, COUNT, G, QUAD>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              kTraverseCarveout);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G>, kBhThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G, QUAD>, kBhThreads, 0);
         if (per_sm < 1) per_sm = 1;
         if (nsm < 1) nsm = 1;
         if (nsm > kWorkSegments) nsm = kWorkSegments;
         blocks = per_sm * nsm;
     }
     cudaMemsetAsync(work, 0, sizeof(int) * nsm, s);
-    k_bh<R, COUNT, G><<<blocks, kBhThreads, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags, work,
+    k_bh<R, COUNT, G, QUAD><<<blocks, kBhThreads, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags, work,
                                              nsm, off, sg);
 }
 
@@ -697,6 +737,12 @@ void bh_launch(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, Field
                vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
                const uint32_t* off, Segs sg, cudaStream_t s)
 {
+    if (t.q1) {
+        // the dipole-position terms are evaluated by the one-lane walk only
+        bh_launch_g<R, COUNT, 1, true>(pos, u, n, t, fp, h, f, esr, counts, flags, work, off, sg,
+                                       s);
+        return;
+    }
 #define FFK_BH_CASE(G) bh_launch_g<R, COUNT, G>(pos, u, n, t, fp, h, f, esr, counts, flags, work, off, sg, s)
     switch (group) {
         case 1: FFK_BH_CASE(1); break;

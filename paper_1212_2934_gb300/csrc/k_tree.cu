@@ -587,6 +587,20 @@ __device__ __forceinline__ dvec4 ldcg4(const dvec4* p)
     return r;
 }
 
+// Adds the symmetric part of d (x) v and its trace to q (S_xx, S_yy, S_zz,
+// S_xy, S_xz, S_yz, m).
+template <typename R>
+__device__ __forceinline__ void quad_add(R dx, R dy, R dz, R vx, R vy, R vz, R q[7])
+{
+    q[0] += dx * vx;
+    q[1] += dy * vy;
+    q[2] += dz * vz;
+    q[3] += R(0.5) * (dx * vy + dy * vx);
+    q[4] += R(0.5) * (dx * vz + dz * vx);
+    q[5] += R(0.5) * (dy * vz + dz * vy);
+    q[6] += dx * vx + dy * vy + dz * vz;
+}
+
 // Bottom-up aggregation (Eq. magCenter): leaves sum their particles in
 // sorted order; the last child to arrive at a parent sums the parent's
 // children in octant order.  centre = position sum / count.  Sums are formed
@@ -627,6 +641,30 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
         sm.x = sx; sm.y = sy; sm.z = sz; sm.w = A(0);
         mm.x = ux; mm.y = uy; mm.z = uz; mm.w = rn;
         cc.x = (R)rdiv(sx, rn); cc.y = (R)rdiv(sy, rn); cc.z = (R)rdiv(sz, rn); cc.w = t.lo[c].w;
+        if (t.q1) {
+            // S and m about this centre: from the particles of a leaf, else from the
+            // children by the shift M = sum_j [M_j + (c_j - c) (x) U_j]
+            R q[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+            if (nd.w >> 8) {
+                for (int s = nd.x; s < nd.y; ++s) {
+                    const vec4<R> p = pos[s], v = u[s];
+                    quad_add<R>(p.x - cc.x, p.y - cc.y, p.z - cc.z, v.x, v.y, v.z, q);
+                }
+            } else {
+                for (int ch = c + 1, k = 0; ch < nd.z && k < 8; ch = t.cell[ch].node.z, ++k) {
+                    const vec4<R> cj = ldcg4(&t.cell[ch].cen), uj = ldcg4(&t.mom[ch]);
+                    const vec4<R> a = ldcg4(&t.q1[ch]), b = ldcg4(&t.q2[ch]);
+                    q[0] += a.x; q[1] += a.y; q[2] += a.z; q[3] += a.w;
+                    q[4] += b.x; q[5] += b.y; q[6] += b.z;
+                    quad_add<R>(cj.x - cc.x, cj.y - cc.y, cj.z - cc.z, uj.x, uj.y, uj.z, q);
+                }
+            }
+            vec4<R> a, b;
+            a.x = q[0]; a.y = q[1]; a.z = q[2]; a.w = q[3];
+            b.x = q[4]; b.y = q[5]; b.z = q[6]; b.w = R(0);
+            t.q1[c] = a;
+            t.q2[c] = b;
+        }
         ssum[c] = sm;
         smom[c] = mm;
         if (sizeof(A) != sizeof(R)) {

@@ -42,7 +42,7 @@ class ff_params(C.Structure):
                 ("box_hi", C.c_double * 3), ("walls", C.c_int32), ("device", C.c_int32),
                 ("wall_eps", C.c_double), ("seed", C.c_uint64),
                 ("count_interactions", C.c_int32), ("traverse_group", C.c_int32),
-                ("stream", C.c_void_p), ("rotation", C.c_int32)]
+                ("stream", C.c_void_p), ("rotation", C.c_int32), ("quadrupole", C.c_int32)]
 
 
 class ff_energy_t(C.Structure):
