@@ -251,15 +251,19 @@ class Clocks:
                 "power_w_median": float(np.median(power)) if power else None}
 
 
-def traffic_for(kernel_src):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+def traffic_for(kernel_src, n, workload, theta, leaf_max):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source and
+    this workload."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
         d = json.load(open(path))
         sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-        if d.get("source_sha256") == sha:
+        same = (d.get("source_sha256") == sha and d.get("n") == n and
+                d.get("workload_name") == workload and d.get("theta") == theta and
+                d.get("leaf_max") == leaf_max)
+        if same:
             return d.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -610,7 +614,8 @@ def run_ours(args):
     flops = info["interactions"] * FLOPS_PER_INTERACTION
     peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
     achieved = flops / (field_ms / 1e3) / 1e12
-    traffic = traffic_for(os.path.join(ROOT, "paper_1212_2934_gb300", "csrc", "k_field.cu"))
+    traffic = traffic_for(os.path.join(ROOT, "paper_1212_2934_gb300", "csrc", "k_field.cu"), n,
+                          args.workload, args.theta, args.leaf_max)
     stages = {k: v / max(prof["calls"][k], 1) for k, v in prof["ms"].items() if prof["calls"][k]}
 
     extras = {}
