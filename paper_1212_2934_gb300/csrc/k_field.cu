@@ -12,6 +12,8 @@
 // groups waste fewer lane slots on cells only some lanes need.  Skip
 // pointers replace a stack.  Every lane's nxt strictly increases, so the
 // loop ends after at most ncells visits per group.
+#include <mutex>
+
 #include "ffk.cuh"
 #include "dipole.cuh"
 
@@ -704,6 +706,37 @@ __global__ void __launch_bounds__(kApThreads) k_ap(const vec4<R>* __restrict__ p
     if (esr) esr[k] = es;
 }
 
+// Shape of a persistent grid on the current device: one work segment per SM
+// (at most kWorkSegments) and as many blocks as fit at once.  `occupancy`
+// configures the caller's kernel and returns its resident blocks per SM; each
+// kernel instance keeps its own per-device cache, guarded by its own mutex.
+struct PersistentGrid {
+    int blocks = 0;
+    int nseg = 0;
+};
+constexpr int kMaxDevices = 64;
+
+template <typename F>
+PersistentGrid persistent_grid(PersistentGrid* cache, std::mutex& mu, F occupancy)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool cached = dev >= 0 && dev < kMaxDevices;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached && cache[dev].blocks > 0) return cache[dev];
+    PersistentGrid g;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = occupancy();
+    if (per_sm < 1) per_sm = 1;
+    if (nsm < 1) nsm = 1;
+    if (nsm > kWorkSegments) nsm = kWorkSegments;
+    g.nseg = nsm;
+    g.blocks = per_sm * nsm;
+    if (cached) cache[dev] = g;
+    return g;
+}
+
 }  // namespace
 
 template <typename R, bool COUNT, int G, bool QUAD = false>
@@ -713,23 +746,19 @@ void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, Fie
 {
     // persistent grid: as many blocks as fit on the device at once; a small
     // shared-memory carveout (the kernel uses none) leaves the rest to L1
-    static int blocks = 0, nsm = 0;
-    if (blocks == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    static std::mutex mu;
+    static PersistentGrid cache[kMaxDevices];
+    const PersistentGrid g = persistent_grid(cache, mu, [] {
         cudaFuncSetAttribute(k_bh<R, COUNT, G, QUAD>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              kTraverseCarveout);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G, QUAD>, kBhThreads, 0);
-        if (per_sm < 1) per_sm = 1;
-        if (nsm < 1) nsm = 1;
-        if (nsm > kWorkSegments) nsm = kWorkSegments;
-        blocks = per_sm * nsm;
-    }
-    cudaMemsetAsync(work, 0, sizeof(int) * nsm, s);
-    k_bh<R, COUNT, G, QUAD><<<blocks, kBhThreads, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags, work,
-                                             nsm, off, sg);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G, QUAD>, kBhThreads,
+                                                      0);
+        return per_sm;
+    });
+    cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
+    k_bh<R, COUNT, G, QUAD><<<g.blocks, kBhThreads, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts,
+                                                            flags, work, g.nseg, off, sg);
 }
 
 template <typename R, bool COUNT>
@@ -793,23 +822,18 @@ void bh_record_g(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, co
                  uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off,
                  Segs sg, VjpIn<R> vj, cudaStream_t s)
 {
-    static int blocks = 0, nsm = 0;
-    if (blocks == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    static std::mutex mu;
+    static PersistentGrid cache[kMaxDevices];
+    const PersistentGrid g = persistent_grid(cache, mu, [] {
         cudaFuncSetAttribute(k_bh_record<R, VJP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              kTraverseCarveout);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_record<R, VJP>, kBhThreads, 0);
-        if (per_sm < 1) per_sm = 1;
-        if (nsm < 1) nsm = 1;
-        if (nsm > kWorkSegments) nsm = kWorkSegments;
-        blocks = per_sm * nsm;
-    }
-    cudaMemsetAsync(work, 0, sizeof(int) * nsm, s);
-    k_bh_record<R, VJP><<<blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, keys, vals, flags,
-                                                      work, nsm, off, sg, vj);
+        return per_sm;
+    });
+    cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
+    k_bh_record<R, VJP><<<g.blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, keys, vals, flags,
+                                                        work, g.nseg, off, sg, vj);
     counted();
 }
 
