@@ -356,7 +356,8 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = f
     }
     {
         StageTimer st(c, S_SORT);
-        ffk::radix_sort_pairs(c->keys[0], c->vals[0], c->keys[1], c->vals[1], n, c->radix_tmp, s);
+        ffk::radix_sort_pairs(c->keys[0], c->vals[0], c->keys[1], c->vals[1], n, c->radix_tmp,
+                              c->dflags, s);
         ffk::radix_sort_systems(c->keys[0], c->vals[0], c->keys[1], c->vals[1], n, c->radix_tmp,
                                 segs_of(c), s);
     }
@@ -447,6 +448,7 @@ ff_status sync_and_check(ff_ctx* c)
     if (fl & ffk::FLAG_CAPACITY) return fail(c, FF_EDEVICE, "tree needs more cells than allocated");
     if (fl & ffk::FLAG_TRAVERSE) return fail(c, FF_EDEVICE, "traversal guard tripped");
     if (fl & ffk::FLAG_AGGREGATE) return fail(c, FF_EDEVICE, "aggregation guard tripped");
+    if (fl & ffk::FLAG_SORT) return fail(c, FF_EDEVICE, "sort tile timed out waiting for an earlier tile");
     return FF_OK;
 }
 
@@ -773,7 +775,8 @@ void sort_entries(ff_ctx* c, int64_t ne, int64_t nsrc, const uint32_t** keys,
     int passes = 1;
     while (passes < 4 && ((uint64_t)nsrc >> (8 * passes)) != 0) ++passes;
     const bool in1 = ffk::radix_sort_pairs_passes<uint32_t>(
-        c->e_keys[0], c->e_vals[0], c->e_keys[1], c->e_vals[1], ne, c->e_tmp, passes, c->stream);
+        c->e_keys[0], c->e_vals[0], c->e_keys[1], c->e_vals[1], ne, c->e_tmp, passes, c->dflags,
+        c->stream);
     *keys = c->e_keys[in1 ? 1 : 0];
     *vals = c->e_vals[in1 ? 1 : 0];
 }

@@ -38,10 +38,15 @@ constexpr size_t kKeyBytes = align256(sizeof(uint64_t) * kNoAllocMaxN);
 constexpr size_t kValOff = kKeyOff + kKeyBytes;
 constexpr size_t kValBytes = align256(sizeof(uint32_t) * kNoAllocMaxN);
 constexpr size_t kRadixOff = kValOff + kValBytes;
-// radix scratch: 256 x tiles histogram, 256 x tiles + 1 offsets, scan block sums
+// radix scratch: the larger of the one-sweep sort's (pass counts, tile
+// status words, tickets) and the tiled sort's (256 x tiles histogram,
+// 256 x tiles + 1 offsets, scan block sums)
 constexpr int64_t kTiles = (kNoAllocMaxN + ffk::kSortTile - 1) / ffk::kSortTile;
 constexpr int64_t kHist = int64_t(ffk::kRadixBins) * kTiles;
-constexpr size_t kRadixWords = size_t(kHist + kHist + 1 + kHist / 2048 + 2);
+constexpr size_t kTiledWords = size_t(kHist + kHist + 1 + kHist / 2048 + 2);
+constexpr size_t kRadixWords = kTiledWords > ffk::os_tmp_words(kNoAllocMaxN)
+                                   ? kTiledWords
+                                   : ffk::os_tmp_words(kNoAllocMaxN);
 constexpr size_t kRadixBytes = align256(sizeof(uint32_t) * kRadixWords);
 constexpr size_t kBoxOff = kRadixOff + kRadixBytes;
 constexpr size_t kBoxBytes = align256(sizeof(ffk::BBox));
@@ -122,7 +127,7 @@ ff_status ff_morton_order_noalloc(const float* pos, int64_t n, uint64_t* keys_ou
     // keys and values are built directly in the caller's outputs, which the
     // eight-pass sort leaves holding the sorted data
     ffk::morton_keys<float>(rec, n, bb, keys_out, order_out, flags, ffk::Segs(), s);
-    ffk::radix_sort_pairs(keys_out, order_out, k1, v1, n, rtmp, s);
+    ffk::radix_sort_pairs(keys_out, order_out, k1, v1, n, rtmp, flags, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(FF_ECUDA, "kernel launch", e);
     int hflag = 0;

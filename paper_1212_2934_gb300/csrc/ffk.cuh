@@ -32,6 +32,7 @@ enum : int {
     FLAG_TRAVERSE = 2,    // traversal guard tripped (corrupt skip pointers)
     FLAG_CAPACITY = 4,    // more cells than allocated
     FLAG_AGGREGATE = 8,   // aggregation walk exceeded the level bound
+    FLAG_SORT = 16,       // a sort tile waited too long for an earlier tile's counts
 };
 
 constexpr int kMaxLevel = 21;        // 21 bits per axis -> 63-bit Morton keys
@@ -41,6 +42,22 @@ constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kSortThreads = 256;    // = kRadixBins: one digit per thread in the scatter
 constexpr int kSortItems = 8;        // keys per thread per block tile
 constexpr int kSortTile = kSortThreads * kSortItems;
+
+// One-sweep radix sort (one scatter launch per pass, tiles chained by
+// decoupled look-back): tile shape and scratch.  The scratch holds the digit
+// counts of every pass, then two status arrays of one 64-bit word per tile and
+// digit (alternate passes use alternate arrays; each tile clears its words in
+// the other array for the pass after it), then one tile ticket per pass.
+constexpr int kOsThreads = 256;  // = kRadixBins: one digit per thread
+constexpr int kOsItems = 8;      // keys per thread per tile
+constexpr int kOsTile = kOsThreads * kOsItems;
+constexpr int kOsMaxPasses = 8;
+constexpr int64_t os_tiles(int64_t n) { return (n + kOsTile - 1) / kOsTile; }
+constexpr size_t os_tmp_words(int64_t n)
+{
+    return (size_t)kOsMaxPasses * kRadixBins + 4 * (size_t)kRadixBins * (size_t)os_tiles(n) +
+           kOsMaxPasses;
+}
 
 // Root cube, written by the bbox kernels and read by the key kernel.
 // lo/hi hold order-preserving integer encodings of the extrema.
@@ -130,15 +147,18 @@ size_t scan_tmp_words(int64_t n);
 void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs, keys < 2^63, eight passes of
-// eight bits: the sorted data end in (k0, v0); (k1, v1) is scratch.
+// eight bits: the sorted data end in (k0, v0); (k1, v1) is scratch.  tmp must
+// hold radix_tmp_words(n) words, 8-byte aligned.  A tile that gives up waiting
+// for an earlier tile raises FLAG_SORT in flags (the order is then undefined).
 size_t radix_tmp_words(int64_t n);
 void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
-                      uint32_t* tmp, cudaStream_t s);
-// The same on the low 8 * passes bits only (K = uint64_t or uint32_t keys);
-// returns true when the sorted data ended in (k1, v1) (an odd number of passes).
+                      uint32_t* tmp, int* flags, cudaStream_t s);
+// The same on the low 8 * passes bits only (K = uint64_t or uint32_t keys,
+// passes 1 .. 8); returns true when the sorted data ended in (k1, v1) (an odd
+// number of passes).
 template <typename K>
 bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
-                             int passes, cudaStream_t s);
+                             int passes, int* flags, cudaStream_t s);
 
 // bb holds one root cube per system.
 template <typename R>

@@ -217,6 +217,170 @@ __global__ void k_radix_scatter(const K* __restrict__ kin, const uint32_t* __res
     }
 }
 
+// ---------------------------------------------------- one-sweep radix sort
+// Digit counts of every pass in one read of the keys.
+template <typename K>
+__global__ void __launch_bounds__(kOsThreads) k_os_hist(const K* __restrict__ keys, int64_t n,
+                                                        int passes, uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[kOsMaxPasses][kRadixBins];
+    const int t = threadIdx.x;
+    for (int p = 0; p < passes; ++p) h[p][t] = 0;
+    __syncthreads();
+    // keys arrive nearly sorted (the previous step's order), so the high digits
+    // of a warp's 32 keys usually agree: such a digit is added once per warp
+    const int lane = t & 31;
+    for (int64_t i0 = (int64_t)blockIdx.x * kOsThreads; i0 < n; i0 += (int64_t)gridDim.x * kOsThreads) {
+        const int64_t i = i0 + t;
+        const bool valid = i < n;
+        const K key = valid ? keys[i] : K(0);
+        const bool whole = __all_sync(kFull, valid);
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = (uint32_t)(key >> (p * kRadixBits)) & (kRadixBins - 1);
+            if (whole && __all_sync(kFull, d == __shfl_sync(kFull, d, 0))) {
+                if (lane == 0) atomicAdd(&h[p][d], 32u);
+            } else if (valid) {
+                atomicAdd(&h[p][d], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p)
+        if (h[p][t]) atomicAdd(&hist[p * kRadixBins + t], h[p][t]);
+}
+
+// Tile status word of the look-back: the digit's count in the low 32 bits and
+// what it covers in the high bits (0: not yet written).
+constexpr unsigned long long kOsAggregate = 1ull << 32;  // this tile alone
+constexpr unsigned long long kOsPrefix = 2ull << 32;     // this tile and all before it
+constexpr int kOsSpinLimit = 1 << 22;                    // polls before a tile gives up
+constexpr int kOsWindow = 8;                             // status words read per look-back trip
+
+// One stable pass over the digit at `shift`.  Blocks take tiles in ticket
+// order.  Each warp ranks its contiguous share of the tile in rounds of 32
+// (match masks within the round, per-warp digit counters across rounds); the
+// tile's count of each digit is published at once, then the tile sums the
+// counts of the tiles before it (walking back until a tile that has published
+// its inclusive prefix) and publishes its own prefix.  A tile waits only for
+// tiles with earlier tickets, which are already running, and every wait is
+// bounded.  The tile is reordered in shared memory by digit before the look-back
+// and written after it, consecutive threads storing consecutive elements of
+// one run.
+template <typename K>
+__global__ void __launch_bounds__(kOsThreads, 4) k_os_scatter(
+    const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
+    uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
+    unsigned long long* status, unsigned long long* __restrict__ status_next,
+    uint32_t* ticket, int* flags)
+{
+    constexpr int kWarps = kOsThreads / 32;
+    constexpr int kWarpItems = kOsTile / kWarps;
+    static_assert(kWarpItems == 32 * kOsItems, "each warp ranks kOsItems rounds of 32");
+    __shared__ K s_key[kOsTile];
+    __shared__ uint32_t s_val[kOsTile];
+    __shared__ uint32_t s_wcnt[kWarps][kRadixBins];  // per-warp digit counts, then prefixes
+    __shared__ uint32_t s_dstart[kRadixBins];        // where each digit starts in the tile
+    __shared__ uint32_t s_gstart[kRadixBins];        // where this tile's run of it goes
+    __shared__ uint32_t s_tile;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (t == 0) s_tile = atomicAdd(ticket, 1u);
+#pragma unroll
+    for (int j = 0; j < kRadixBins / 32; ++j) s_wcnt[w][lane + 32 * j] = 0;
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kOsTile;
+    const int tile_n = (int)min((int64_t)kOsTile, n - base);
+    // the words of this tile in the array the next pass uses
+    status_next[tile * kRadixBins + t] = 0ull;
+
+    K key[kOsItems];
+    uint32_t val[kOsItems], rank[kOsItems];
+#pragma unroll
+    for (int r = 0; r < kOsItems; ++r) {
+        const int e = w * kWarpItems + r * 32 + lane;
+        if (e < tile_n) {
+            key[r] = kin[base + e];
+            val[r] = vin[base + e];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kOsItems; ++r) {
+        const int e = w * kWarpItems + r * 32 + lane;
+        const bool valid = e < tile_n;
+        const uint32_t d =
+            valid ? ((uint32_t)(key[r] >> shift) & (kRadixBins - 1)) : (uint32_t)kRadixBins;
+        const uint32_t peers = __match_any_sync(kFull, d);
+        const uint32_t before = valid ? s_wcnt[w][d] : 0u;
+        rank[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0) s_wcnt[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread t owns digit t: exclusive prefixes over the warps, the tile's count
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t c = s_wcnt[ww][t];
+        s_wcnt[ww][t] = cnt;
+        cnt += c;
+    }
+    volatile unsigned long long* st = status;
+    st[tile * kRadixBins + t] = (tile == 0 ? kOsPrefix : kOsAggregate) | cnt;
+    uint32_t total;
+    s_dstart[t] = block_exscan(cnt, &total);
+    const uint32_t bucket = block_exscan(hist[t], &total);
+    // the tile in digit order in shared memory (block_exscan ends with a barrier)
+#pragma unroll
+    for (int r = 0; r < kOsItems; ++r) {
+        const int e = w * kWarpItems + r * 32 + lane;
+        if (e < tile_n) {
+            const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
+            const uint32_t lp = s_dstart[d] + s_wcnt[w][d] + rank[r];
+            s_key[lp] = key[r];
+            s_val[lp] = val[r];
+        }
+    }
+    // look back: the counts of the earlier tiles, kOsWindow words per round
+    // trip, nearest first, up to the first inclusive prefix
+    uint32_t excl = 0;
+    bool done = tile == 0;
+    for (int64_t j = tile - 1; !done; j -= kOsWindow) {
+        unsigned long long v[kOsWindow];
+#pragma unroll
+        for (int q = 0; q < kOsWindow; ++q)
+            v[q] = j - q >= 0 ? (unsigned long long)st[(j - q) * kRadixBins + t] : 2ull << 32;
+#pragma unroll
+        for (int q = 0; q < kOsWindow; ++q) {
+            if (!done) {
+                unsigned long long x = v[q];
+                for (int it = 0; (x >> 32) == 0 && it < kOsSpinLimit; ++it) {
+                    __nanosleep(32);
+                    x = st[(j - q) * kRadixBins + t];
+                }
+                if ((x >> 32) == 0) {
+                    atomicOr(flags, FLAG_SORT);
+                    done = true;
+                } else {
+                    excl += (uint32_t)x;
+                    done = (x & kOsPrefix) != 0;
+                }
+            }
+        }
+    }
+    if (tile > 0) st[tile * kRadixBins + t] = kOsPrefix | (unsigned long long)(excl + cnt);
+    s_gstart[t] = bucket + excl;
+    __syncthreads();
+    for (int j = t; j < tile_n; j += kOsThreads) {
+        const K key = s_key[j];
+        const uint32_t d = (uint32_t)(key >> shift) & (kRadixBins - 1);
+        const int64_t g = (int64_t)s_gstart[d] + (j - (int64_t)s_dstart[d]);
+        kout[g] = key;
+        vout[g] = s_val[j];
+    }
+}
+
 // ------------------------------------------------------- bbox and keys
 __device__ __forceinline__ long long enc(float x)
 {
@@ -729,66 +893,59 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
 
 size_t radix_tmp_words(int64_t n)
 {
+    // the tiled passes of radix_sort_systems share this scratch with the
+    // one-sweep passes of the key sort
     const int64_t nb = (n + kSortTile - 1) / kSortTile;
     const int64_t h = (int64_t)kRadixBins * nb;
-    return (size_t)(h + (h + 1) + scan_tmp_words(h));
+    const size_t tiled = (size_t)(h + (h + 1) + scan_tmp_words(h));
+    const size_t os = os_tmp_words(n);
+    return tiled > os ? tiled : os;
 }
 
 template <typename K>
 bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
-                             int passes, cudaStream_t s)
+                             int passes, int* flags, cudaStream_t s)
 {
-    if (n <= 1) return false;
-    const int64_t nb = (n + kSortTile - 1) / kSortTile;
-    const int64_t h = (int64_t)kRadixBins * nb;
+    if (n <= 1 || passes < 1) return false;
+    if (passes > kOsMaxPasses) passes = kOsMaxPasses;
+    if (passes * kRadixBits > (int)(8 * sizeof(K))) passes = (int)(8 * sizeof(K)) / kRadixBits;
+    const int64_t tiles = os_tiles(n);
     uint32_t* hist = tmp;
-    uint32_t* offs = tmp + h;
-    uint32_t* stmp = offs + h + 1;
+    unsigned long long* status[2];
+    status[0] = reinterpret_cast<unsigned long long*>(tmp + kOsMaxPasses * kRadixBins);
+    status[1] = status[0] + kRadixBins * tiles;
+    uint32_t* tickets = reinterpret_cast<uint32_t*>(status[1] + kRadixBins * tiles);
+    // counts and the first pass's status words start at zero; the second
+    // array is cleared tile by tile during the first pass, and so on
+    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kOsMaxPasses * kRadixBins, s);
+    cudaMemsetAsync(status[0], 0, sizeof(unsigned long long) * kRadixBins * tiles, s);
+    cudaMemsetAsync(tickets, 0, sizeof(uint32_t) * kOsMaxPasses, s);
+    const int64_t hb = (n + kOsThreads - 1) / kOsThreads;
+    k_os_hist<K><<<(unsigned)(hb < 1216 ? hb : 1216), kOsThreads, 0, s>>>(k0, n, passes, hist);
     K* ka = k0;
     uint32_t* va = v0;
     K* kb = k1;
     uint32_t* vb = v1;
     for (int p = 0; p < passes; ++p) {
-        const int shift = p * kRadixBits;
-        k_radix_hist<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, n, shift, hist, nb);
-        scan_exclusive(hist, offs, h, stmp, s);
-        k_radix_scatter<K><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, kb, vb, n,
-                                                                   shift, hist, offs, nb);
-        counted(2);
+        k_os_scatter<K><<<(unsigned)tiles, kOsThreads, 0, s>>>(
+            ka, va, kb, vb, n, p * kRadixBits, hist + p * kRadixBins, status[p & 1],
+            status[(p + 1) & 1], tickets + p, flags);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
+    counted(1 + passes);
     return (passes & 1) != 0;
 }
 template bool radix_sort_pairs_passes<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, int64_t,
-                                                uint32_t*, int, cudaStream_t);
+                                                uint32_t*, int, int*, cudaStream_t);
 template bool radix_sort_pairs_passes<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t,
-                                                uint32_t*, int, cudaStream_t);
+                                                uint32_t*, int, int*, cudaStream_t);
 
 void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
-                      uint32_t* tmp, cudaStream_t s)
+                      uint32_t* tmp, int* flags, cudaStream_t s)
 {
-    if (n <= 1) return;
-    const int64_t nb = (n + kSortTile - 1) / kSortTile;
-    const int64_t h = (int64_t)kRadixBins * nb;
-    uint32_t* hist = tmp;
-    uint32_t* offs = tmp + h;
-    uint32_t* stmp = offs + h + 1;
-    uint64_t* ka = k0;
-    uint32_t* va = v0;
-    uint64_t* kb = k1;
-    uint32_t* vb = v1;
-    for (int shift = 0; shift < 64; shift += kRadixBits) {
-        k_radix_hist<uint64_t><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, n, shift,
-                                                                     hist, nb);
-        scan_exclusive(hist, offs, h, stmp, s);
-        k_radix_scatter<uint64_t><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, nullptr, kb, vb, n,
-                                                                          shift, hist, offs, nb);
-        counted(2);
-        uint64_t* tk = ka; ka = kb; kb = tk;
-        uint32_t* tv = va; va = vb; vb = tv;
-    }
     // eight passes: the sorted data are back in (k0, v0)
+    radix_sort_pairs_passes<uint64_t>(k0, v0, k1, v1, n, tmp, 8, flags, s);
 }
 
 void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,

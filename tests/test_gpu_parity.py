@@ -198,6 +198,29 @@ def test_two_dipoles_closed_form(ff):
         np.testing.assert_allclose(f, [[0, 0, 6 / 1.5 ** 4], [0, 0, -6 / 1.5 ** 4]], rtol=1e-14)
 
 
+@pytest.mark.parametrize("n", [3072 * 5, 3072 * 5 + 1, 100003])
+def test_sort_many_tiles_with_repeated_keys(ff, ora, n):
+    """Keys and the stable order (equal keys by input index) over many sort tiles, including
+    an exact multiple of the tile and a ragged last tile: positions drawn with repeats from a
+    small set of lattice points, so most keys occur several times.  The reference is the
+    oracle's keys in input order, ordered by numpy's stable argsort."""
+    from paper_1212_2934_gb300 import synth
+
+    rng = np.random.default_rng(n)
+    pts = rng.integers(0, 64, size=(max(n // 5, 1), 3)).astype(np.float64) * 1.5
+    pos = pts[rng.integers(0, len(pts), size=n)].astype(np.float32)
+    u = synth.isotropic_moments(n, 3).astype(np.float32)
+    ctx = _ctx(ff, n, "f32")
+    ff.ff_set_particles(ctx, pos, u)
+    ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, 0.5, False)
+    g = ff.ff_get_tree(ctx)
+    keys, _ = ora.morton(pos.astype(np.float64), "f32")
+    order = np.argsort(keys, kind="stable")
+    assert len(np.unique(keys)) < n // 2  # the case has many repeated keys
+    assert np.array_equal(g["keys"], keys[order])
+    assert np.array_equal(g["order"].astype(np.int64), order)
+
+
 def test_coincident_particles(ff, ora):
     pos, u, _ = _system(500, 71)
     pos[10] = pos[20]
