@@ -774,9 +774,10 @@ void sort_entries(ff_ctx* c, int64_t ne, int64_t nsrc, const uint32_t** keys,
 {
     int passes = 1;
     while (passes < 4 && ((uint64_t)nsrc >> (8 * passes)) != 0) ++passes;
+    // the particle of each entry comes from the slot offsets e_base
     const bool in1 = ffk::radix_sort_pairs_passes<uint32_t>(
         c->e_keys[0], c->e_vals[0], c->e_keys[1], c->e_vals[1], ne, c->e_tmp, passes, c->dflags,
-        c->stream);
+        c->stream, c->e_base, c->n);
     *keys = c->e_keys[in1 ? 1 : 0];
     *vals = c->e_vals[in1 ? 1 : 0];
 }
@@ -805,7 +806,7 @@ ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy)
         Buffers& a = c->st[c->cur];
         ffk::Tree<R> t = tree_of<R>(c);
         ffk::bh_record<R>(V<R>(a.pos), n, t, field_params<R>(c, theta, 0), c->e_base,
-                          c->e_keys[0], c->e_vals[0], c->dflags, c->work, c->off, segs_of(c), s);
+                          c->e_keys[0], c->dflags, c->work, c->off, segs_of(c), s);
         const uint32_t* keys = nullptr;
         const uint32_t* vals = nullptr;
         sort_entries(c, ne, nsrc, &keys, &vals);
@@ -1019,8 +1020,7 @@ ff_status mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz_ou
             ffk::Tree<R> tr = tree_of<R>(c);
             ffk::bh_record_vjp<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar), n, tr,
                                   field_params<R>(c, theta, 1), c->e_base, c->e_keys[0],
-                                  c->e_vals[0], c->dflags, c->work, c->off, segs_of(c), V<R>(dxt),
-                                  V<R>(dut), s);
+                                  c->dflags, c->work, c->off, segs_of(c), V<R>(dxt), V<R>(dut), s);
             const uint32_t* keys = nullptr;
             const uint32_t* vals = nullptr;
             sort_entries(c, ne, nsrc, &keys, &vals);

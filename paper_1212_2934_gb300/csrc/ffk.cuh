@@ -155,10 +155,13 @@ void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, in
                       uint32_t* tmp, int* flags, cudaStream_t s);
 // The same on the low 8 * passes bits only (K = uint64_t or uint32_t keys,
 // passes 1 .. 8); returns true when the sorted data ended in (k1, v1) (an odd
-// number of passes).
+// number of passes).  With vseg (nseg + 1 nondecreasing offsets, vseg[0] = 0,
+// vseg[nseg] = n) the values are not read from v0: element i enters the sort
+// with the value k of the segment vseg[k] <= i < vseg[k + 1].
 template <typename K>
 bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
-                             int passes, int* flags, cudaStream_t s);
+                             int passes, int* flags, cudaStream_t s,
+                             const uint32_t* vseg = nullptr, int64_t nseg = 0);
 
 // bb holds one root cube per system.
 template <typename R>
@@ -190,10 +193,11 @@ void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint3
                     cudaStream_t s);
 
 // Source lists of the gradient pass (see k_field.cu): per particle k, entries
-// base[k] .. base[k + 1] of (source, k) in the order of its walk.
+// base[k] .. base[k + 1] hold its sources in the order of its walk (the
+// particle of an entry is implied by its slot).
 template <typename R>
 void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
-               uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off, Segs sg,
+               uint32_t* keys, int* flags, int* work, const uint32_t* off, Segs sg,
                cudaStream_t s);
 
 // The same walk for a vector-Jacobian product of h and f with cotangents
@@ -201,7 +205,7 @@ void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, cons
 template <typename R>
 void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
                    const vec4<R>* bbar, int64_t n, Tree<R> t, FieldParams<R> fp,
-                   const uint32_t* base, uint32_t* keys, uint32_t* vals, int* flags, int* work,
+                   const uint32_t* base, uint32_t* keys, int* flags, int* work,
                    const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s);
 
 // ------------------------------------------------ energy gradient (k_grad.cu)

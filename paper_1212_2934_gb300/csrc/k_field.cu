@@ -437,11 +437,12 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
 
 // Source lists for the energy gradient: the walk of bh_task1, making the same
 // decisions in the same order, writes one entry per source instead of
-// summing.  key = the source: a cell (accepted, or a one-particle leaf summed
+// summing: the source, a cell (accepted, or a one-particle leaf summed
 // exactly) or ncells + the position of a particle of an opened multi-particle
-// leaf; value = the particle.  base[k] .. base[k + 1] is the particle's slot,
-// sized from the counted walk (accepted cells + exact pairs); a walk that
-// does not fill it exactly raises the traversal flag.
+// leaf.  base[k] .. base[k + 1] is the particle's slot, sized from the counted
+// walk (accepted cells + exact pairs), so the slot names the particle and only
+// the source is stored; a walk that does not fill its slot exactly raises the
+// traversal flag.
 // With VJP, the walk also sums the target-side terms of a vector-Jacobian
 // product of h and f (cotangents abar, bbar) for L = sum abar . h + bbar . f:
 //   dL/du_k   += ds grad phi(r; bbar_k, w_s)
@@ -477,8 +478,7 @@ template <typename R, bool VJP>
 __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict__ pos, int n,
                                             const Tree<R>& t, const FieldParams<R>& fp,
                                             unsigned ncells, const uint32_t* __restrict__ base,
-                                            uint32_t* __restrict__ keys,
-                                            uint32_t* __restrict__ vals, int* flags,
+                                            uint32_t* __restrict__ keys, int* flags,
                                             const uint32_t* __restrict__ off, const Segs& sg,
                                             const VjpIn<R>& vj)
 {
@@ -509,10 +509,7 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i);
         unsigned nxt = i + 1;
         if (acc || (single && !inside)) {
-            if (w < wend) {
-                keys[w] = i;
-                vals[w] = (uint32_t)k;
-            }
+            if (w < wend) keys[w] = i;
             ++w;
             if (VJP) {
                 const vec4<R> ws = t.mom[i];
@@ -529,10 +526,7 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
             if (!single) {
                 for (int s = nd.x; s < nd.y; ++s) {
                     if (s == k) continue;
-                    if (w < wend) {
-                        keys[w] = ncells + (uint32_t)s;
-                        vals[w] = (uint32_t)k;
-                    }
+                    if (w < wend) keys[w] = ncells + (uint32_t)s;
                     ++w;
                     if (VJP) {
                         const vec4<R> xj = pos[s], uj = vj.u[s], bj = vj.bbar[s];
@@ -570,8 +564,7 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
 template <typename R, bool VJP>
 __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
     const vec4<R>* __restrict__ pos, int n, Tree<R> t, FieldParams<R> fp,
-    const uint32_t* __restrict__ base, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-    int* flags, int* __restrict__ work, int nseg, const uint32_t* __restrict__ off, Segs sg,
+    const uint32_t* __restrict__ base, uint32_t* __restrict__ keys, int* flags, int* __restrict__ work, int nseg, const uint32_t* __restrict__ off, Segs sg,
     VjpIn<R> vj)
 {
     if (*flags & FLAG_CAPACITY) return;
@@ -591,7 +584,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
             got = __shfl_sync(kFull, got, 0);
             const int task = t0 + got;
             if (task >= t1) break;
-            record_task<R, VJP>(task, pos, n, t, fp, ncells, base, keys, vals, flags, off, sg,
+            record_task<R, VJP>(task, pos, n, t, fp, ncells, base, keys, flags, off, sg,
                                 vj);
         }
     }
@@ -819,8 +812,8 @@ template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<
 
 template <typename R, bool VJP>
 void bh_record_g(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
-                 uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off,
-                 Segs sg, VjpIn<R> vj, cudaStream_t s)
+                 uint32_t* keys, int* flags, int* work, const uint32_t* off, Segs sg, VjpIn<R> vj,
+                 cudaStream_t s)
 {
     static std::mutex mu;
     static PersistentGrid cache[kMaxDevices];
@@ -832,24 +825,24 @@ void bh_record_g(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, co
         return per_sm;
     });
     cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
-    k_bh_record<R, VJP><<<g.blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, keys, vals, flags,
+    k_bh_record<R, VJP><<<g.blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, keys, flags,
                                                         work, g.nseg, off, sg, vj);
     counted();
 }
 
 template <typename R>
 void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
-               uint32_t* keys, uint32_t* vals, int* flags, int* work, const uint32_t* off, Segs sg,
+               uint32_t* keys, int* flags, int* work, const uint32_t* off, Segs sg,
                cudaStream_t s)
 {
     if (n <= 0) return;
-    bh_record_g<R, false>(pos, n, t, fp, base, keys, vals, flags, work, off, sg, VjpIn<R>{}, s);
+    bh_record_g<R, false>(pos, n, t, fp, base, keys, flags, work, off, sg, VjpIn<R>{}, s);
 }
 
 template <typename R>
 void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
                    const vec4<R>* bbar, int64_t n, Tree<R> t, FieldParams<R> fp,
-                   const uint32_t* base, uint32_t* keys, uint32_t* vals, int* flags, int* work,
+                   const uint32_t* base, uint32_t* keys, int* flags, int* work,
                    const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s)
 {
     if (n <= 0) return;
@@ -859,22 +852,22 @@ void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
     vj.bbar = bbar;
     vj.dxt = dxt;
     vj.dut = dut;
-    bh_record_g<R, true>(pos, n, t, fp, base, keys, vals, flags, work, off, sg, vj, s);
+    bh_record_g<R, true>(pos, n, t, fp, base, keys, flags, work, off, sg, vj, s);
 }
 
 template void bh_record<float>(const float4*, int64_t, Tree<float>, FieldParams<float>,
-                               const uint32_t*, uint32_t*, uint32_t*, int*, int*, const uint32_t*,
-                               Segs, cudaStream_t);
+                               const uint32_t*, uint32_t*, int*, int*, const uint32_t*, Segs,
+                               cudaStream_t);
 template void bh_record<double>(const dvec4*, int64_t, Tree<double>, FieldParams<double>,
-                                const uint32_t*, uint32_t*, uint32_t*, int*, int*,
-                                const uint32_t*, Segs, cudaStream_t);
+                                const uint32_t*, uint32_t*, int*, int*, const uint32_t*, Segs,
+                                cudaStream_t);
 template void bh_record_vjp<float>(const float4*, const float4*, const float4*, const float4*,
                                    int64_t, Tree<float>, FieldParams<float>, const uint32_t*,
-                                   uint32_t*, uint32_t*, int*, int*, const uint32_t*, Segs,
-                                   float4*, float4*, cudaStream_t);
+                                   uint32_t*, int*, int*, const uint32_t*, Segs, float4*, float4*,
+                                   cudaStream_t);
 template void bh_record_vjp<double>(const dvec4*, const dvec4*, const dvec4*, const dvec4*,
                                     int64_t, Tree<double>, FieldParams<double>, const uint32_t*,
-                                    uint32_t*, uint32_t*, int*, int*, const uint32_t*, Segs,
-                                    dvec4*, dvec4*, cudaStream_t);
+                                    uint32_t*, int*, int*, const uint32_t*, Segs, dvec4*, dvec4*,
+                                    cudaStream_t);
 
 }  // namespace ffk

@@ -2,9 +2,10 @@
 // scheme, redesigned): root cube by reduction, 63-bit Morton keys, a stable
 // LSD radix sort, and a parallel build of the depth-first-preorder octree
 // straight from the sorted keys, followed by one bottom-up aggregation
-// launch.  No kernel here waits on another block: the build needs no locks
-// and the aggregation uses arrival counters (the last child to arrive sums
-// its parent), so every loop is bounded.
+// launch.  The build needs no locks and the aggregation uses arrival counters
+// (the last child to arrive sums its parent).  The only waits on other blocks
+// are the sort's look-back polls, on tiles with earlier tickets (already
+// running), each bounded, so every loop ends.
 #include <climits>
 
 #include "ffk.cuh"
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kOsThreads, 4) k_os_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
     unsigned long long* status, unsigned long long* __restrict__ status_next,
-    uint32_t* ticket, int* flags)
+    uint32_t* ticket, int* flags, const uint32_t* __restrict__ vseg, int64_t nseg)
 {
     constexpr int kWarps = kOsThreads / 32;
     constexpr int kWarpItems = kOsTile / kWarps;
@@ -282,6 +283,7 @@ __global__ void __launch_bounds__(kOsThreads, 4) k_os_scatter(
     __shared__ uint32_t s_dstart[kRadixBins];        // where each digit starts in the tile
     __shared__ uint32_t s_gstart[kRadixBins];        // where this tile's run of it goes
     __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_k0;  // with vseg: the segment of the tile's first element
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     if (t == 0) s_tile = atomicAdd(ticket, 1u);
@@ -293,15 +295,34 @@ __global__ void __launch_bounds__(kOsThreads, 4) k_os_scatter(
     const int tile_n = (int)min((int64_t)kOsTile, n - base);
     // the words of this tile in the array the next pass uses
     status_next[tile * kRadixBins + t] = 0ull;
+    if (vseg) {
+        if (t == 0) {
+            int64_t lo = 0, hi = nseg;  // vseg[lo] <= base < vseg[hi]
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) / 2;
+                if ((int64_t)vseg[mid] <= base) lo = mid;
+                else hi = mid;
+            }
+            s_k0 = (uint32_t)lo;
+        }
+        __syncthreads();
+    }
 
     K key[kOsItems];
     uint32_t val[kOsItems], rank[kOsItems];
+    uint32_t seg = vseg ? s_k0 : 0u;
 #pragma unroll
     for (int r = 0; r < kOsItems; ++r) {
         const int e = w * kWarpItems + r * 32 + lane;
         if (e < tile_n) {
             key[r] = kin[base + e];
-            val[r] = vin[base + e];
+            if (vseg) {
+                // this thread's elements rise with r: the segment only moves on
+                while ((int64_t)vseg[seg + 1] <= base + e) ++seg;
+                val[r] = seg;
+            } else {
+                val[r] = vin[base + e];
+            }
         }
     }
 #pragma unroll
@@ -904,7 +925,8 @@ size_t radix_tmp_words(int64_t n)
 
 template <typename K>
 bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
-                             int passes, int* flags, cudaStream_t s)
+                             int passes, int* flags, cudaStream_t s, const uint32_t* vseg,
+                             int64_t nseg)
 {
     if (n <= 1 || passes < 1) return false;
     if (passes > kOsMaxPasses) passes = kOsMaxPasses;
@@ -929,7 +951,7 @@ bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n
     for (int p = 0; p < passes; ++p) {
         k_os_scatter<K><<<(unsigned)tiles, kOsThreads, 0, s>>>(
             ka, va, kb, vb, n, p * kRadixBits, hist + p * kRadixBins, status[p & 1],
-            status[(p + 1) & 1], tickets + p, flags);
+            status[(p + 1) & 1], tickets + p, flags, p == 0 ? vseg : nullptr, nseg);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
@@ -937,15 +959,17 @@ bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n
     return (passes & 1) != 0;
 }
 template bool radix_sort_pairs_passes<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, int64_t,
-                                                uint32_t*, int, int*, cudaStream_t);
+                                                uint32_t*, int, int*, cudaStream_t,
+                                                const uint32_t*, int64_t);
 template bool radix_sort_pairs_passes<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t,
-                                                uint32_t*, int, int*, cudaStream_t);
+                                                uint32_t*, int, int*, cudaStream_t,
+                                                const uint32_t*, int64_t);
 
 void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
                       uint32_t* tmp, int* flags, cudaStream_t s)
 {
     // eight passes: the sorted data are back in (k0, v0)
-    radix_sort_pairs_passes<uint64_t>(k0, v0, k1, v1, n, tmp, 8, flags, s);
+    radix_sort_pairs_passes<uint64_t>(k0, v0, k1, v1, n, tmp, 8, flags, s, nullptr, 0);
 }
 
 void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
