@@ -49,8 +49,14 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // digit (alternate passes use alternate arrays; each tile clears its words in
 // the other array for the pass after it), then one tile ticket per pass.
 constexpr int kOsThreads = 256;  // = kRadixBins: one digit per thread
-constexpr int kOsItems = 8;      // keys per thread per tile
-constexpr int kOsTile = kOsThreads * kOsItems;
+constexpr int kOsItems = 8;      // keys per thread per tile (64-bit keys)
+constexpr int kOsTile = kOsThreads * kOsItems;  // the smallest tile (sizes the scratch)
+// 32-bit keys take twice as many per thread in the same shared memory, so a
+// tile carries more bytes per look-back and per block-wide scan
+template <typename K>
+constexpr int os_items() { return sizeof(K) == 4 ? 2 * kOsItems : kOsItems; }
+template <typename K>
+constexpr int os_min_blocks() { return sizeof(K) == 4 ? 3 : 4; }
 constexpr int kOsMaxPasses = 8;
 constexpr int64_t os_tiles(int64_t n) { return (n + kOsTile - 1) / kOsTile; }
 constexpr size_t os_tmp_words(int64_t n)

@@ -268,17 +268,19 @@ constexpr int kOsWindow = 8;                             // status words read pe
 // and written after it, consecutive threads storing consecutive elements of
 // one run.
 template <typename K>
-__global__ void __launch_bounds__(kOsThreads, 4) k_os_scatter(
+__global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
     unsigned long long* status, unsigned long long* __restrict__ status_next,
     uint32_t* ticket, int* flags, const uint32_t* __restrict__ vseg, int64_t nseg)
 {
     constexpr int kWarps = kOsThreads / 32;
-    constexpr int kWarpItems = kOsTile / kWarps;
-    static_assert(kWarpItems == 32 * kOsItems, "each warp ranks kOsItems rounds of 32");
-    __shared__ K s_key[kOsTile];
-    __shared__ uint32_t s_val[kOsTile];
+    constexpr int kItems = os_items<K>();
+    constexpr int kTile = kOsThreads * kItems;
+    constexpr int kWarpItems = kTile / kWarps;
+    static_assert(kWarpItems == 32 * kItems, "each warp ranks kItems rounds of 32");
+    __shared__ K s_key[kTile];
+    __shared__ uint32_t s_val[kTile];
     __shared__ uint32_t s_wcnt[kWarps][kRadixBins];  // per-warp digit counts, then prefixes
     __shared__ uint32_t s_dstart[kRadixBins];        // where each digit starts in the tile
     __shared__ uint32_t s_gstart[kRadixBins];        // where this tile's run of it goes
@@ -291,8 +293,8 @@ __global__ void __launch_bounds__(kOsThreads, 4) k_os_scatter(
     for (int j = 0; j < kRadixBins / 32; ++j) s_wcnt[w][lane + 32 * j] = 0;
     __syncthreads();
     const int64_t tile = s_tile;
-    const int64_t base = tile * kOsTile;
-    const int tile_n = (int)min((int64_t)kOsTile, n - base);
+    const int64_t base = tile * kTile;
+    const int tile_n = (int)min((int64_t)kTile, n - base);
     // the words of this tile in the array the next pass uses
     status_next[tile * kRadixBins + t] = 0ull;
     if (vseg) {
@@ -308,11 +310,11 @@ __global__ void __launch_bounds__(kOsThreads, 4) k_os_scatter(
         __syncthreads();
     }
 
-    K key[kOsItems];
-    uint32_t val[kOsItems], rank[kOsItems];
+    K key[kItems];
+    uint32_t val[kItems], rank[kItems];
     uint32_t seg = vseg ? s_k0 : 0u;
 #pragma unroll
-    for (int r = 0; r < kOsItems; ++r) {
+    for (int r = 0; r < kItems; ++r) {
         const int e = w * kWarpItems + r * 32 + lane;
         if (e < tile_n) {
             key[r] = kin[base + e];
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(kOsThreads, 4) k_os_scatter(
         }
     }
 #pragma unroll
-    for (int r = 0; r < kOsItems; ++r) {
+    for (int r = 0; r < kItems; ++r) {
         const int e = w * kWarpItems + r * 32 + lane;
         const bool valid = e < tile_n;
         const uint32_t d =
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(kOsThreads, 4) k_os_scatter(
     const uint32_t bucket = block_exscan(hist[t], &total);
     // the tile in digit order in shared memory (block_exscan ends with a barrier)
 #pragma unroll
-    for (int r = 0; r < kOsItems; ++r) {
+    for (int r = 0; r < kItems; ++r) {
         const int e = w * kWarpItems + r * 32 + lane;
         if (e < tile_n) {
             const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
@@ -931,7 +933,7 @@ bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n
     if (n <= 1 || passes < 1) return false;
     if (passes > kOsMaxPasses) passes = kOsMaxPasses;
     if (passes * kRadixBits > (int)(8 * sizeof(K))) passes = (int)(8 * sizeof(K)) / kRadixBits;
-    const int64_t tiles = os_tiles(n);
+    const int64_t tiles = (n + kOsThreads * os_items<K>() - 1) / (kOsThreads * os_items<K>());
     uint32_t* hist = tmp;
     unsigned long long* status[2];
     status[0] = reinterpret_cast<unsigned long long*>(tmp + kOsMaxPasses * kRadixBins);
