@@ -513,6 +513,9 @@ __global__ void k_bbox(const vec4<R>* __restrict__ pos, int64_t n, BBox* bb, int
         }
     }
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, FLAG_NONFINITE);
+    // warp, then block extrema: six global atomics per block
+    __shared__ long long sl[3][32], sh[3][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -520,13 +523,21 @@ __global__ void k_bbox(const vec4<R>* __restrict__ pos, int64_t n, BBox* bb, int
             lo[a] = min(lo[a], __shfl_xor_sync(kFull, lo[a], o));
             hi[a] = max(hi[a], __shfl_xor_sync(kFull, hi[a], o));
         }
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            atomicMin(&bb->lo[a], lo[a]);
-            atomicMax(&bb->hi[a], hi[a]);
+        if (lane == 0) {
+            sl[a][w] = lo[a];
+            sh[a][w] = hi[a];
         }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int a = threadIdx.x;
+        long long l = LLONG_MAX, h = LLONG_MIN;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
+            l = min(l, sl[a][ww]);
+            h = max(h, sh[a][ww]);
+        }
+        atomicMin(&bb->lo[a], l);
+        atomicMax(&bb->hi[a], h);
     }
 }
 
@@ -705,47 +716,72 @@ __global__ void k_emit(const uint64_t* __restrict__ k, int64_t n, const uint32_t
                        const uint32_t* __restrict__ off, const BBox* __restrict__ bb, Tree<R> t,
                        int* flags, Segs sg)
 {
+    // The 32 particles of a warp start between 0 and 22 cells each (most one);
+    // their cells are dealt out to the lanes in turn, so that a particle that
+    // starts many levels does not hold up the other lanes.
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = (int)cnt[i];
-    if (c == 0) return;
-    const int li = split_level(k, i, n, sg.of_pos);
-    // the positions of i's system: runs and parents never leave them
-    const int sys = sg.of_pos ? (int)sg.of_pos[i] : 0;
-    const int64_t sfirst = sg.of_pos ? sg.start[sys] : 0;
-    const int64_t send = sg.of_pos ? sg.start[sys + 1] : n;
-    const int d = li + c - 1;
-    const int64_t base = off[i];
-    if (base + c > t.cap || (int64_t)off[n] > t.cap) {
-        atomicOr(flags, FLAG_CAPACITY);
-        return;
+    const int lane = threadIdx.x & 31;
+    const int c = i < n ? (int)cnt[i] : 0;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
     }
-    R mn[3], side;
-    root_cube<R>(bb + sys, mn, &side);
-    const uint64_t key = k[i];
-    int64_t pe = i + 1;
-    for (int L = d; L >= li; --L) {
-        const int64_t idx = base + (L - li);
+    const int excl = incl - c;
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    if (c > 0 && ((int64_t)off[i] + c > t.cap || (int64_t)off[n] > t.cap)) atomicOr(flags, FLAG_CAPACITY);
+    if (__any_sync(kFull, c > 0 && ((int64_t)off[i] + c > t.cap || (int64_t)off[n] > t.cap))) return;
+    const int li_own = c > 0 ? split_level(k, i, n, sg.of_pos) : 0;
+    const uint64_t key_own = c > 0 ? k[i] : 0ull;
+    const int64_t base_own = c > 0 ? (int64_t)off[i] : 0;
+    for (int j0 = 0; j0 < total; j0 += 32) {
+        const int j = j0 + lane;
+        // owner: the last lane whose run of cells starts at or before j
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(kFull, excl, o + step);
+            if (e <= j) o += step;
+        }
+        const int oc = __shfl_sync(kFull, c, o);
+        const int oli = __shfl_sync(kFull, li_own, o);
+        const int oex = __shfl_sync(kFull, excl, o);
+        const uint64_t key = __shfl_sync(kFull, key_own, o);
+        const int64_t base = __shfl_sync(kFull, base_own, o);
+        if (j >= total) continue;
+        const int64_t ip = i - lane + o;  // the owner's particle
+        // the positions of its system: runs and parents never leave them
+        const int sys = sg.of_pos ? (int)sg.of_pos[ip] : 0;
+        const int64_t sfirst = sg.of_pos ? sg.start[sys] : 0;
+        const int64_t send = sg.of_pos ? sg.start[sys + 1] : n;
+        const int d = oli + oc - 1;
+        const int L = d - (j - oex);  // the owner's cells, deepest first
+        const int64_t idx = base + (L - oli);
+        R mn[3], side;
+        root_cube<R>(bb + sys, mn, &side);
+        int64_t pe;
         if (L == 0) {
             pe = send;
         } else {
             const int sh = 3 * (kMaxLevel - L);
             const uint64_t bound = ((key >> sh) + 1ull) << sh;
-            pe = gallop_right(k, pe, send, bound);
+            pe = gallop_right(k, ip + 1, send, bound);
         }
         const int skip = (int)off[pe];
         const int leaf = (L == d) ? 1 : 0;
-        t.cell[idx].node = make_int4((int)i, (int)pe, skip, L | (leaf << 8));
+        t.cell[idx].node = make_int4((int)ip, (int)pe, skip, L | (leaf << 8));
         int parent;
         if (L == 0) {
             parent = -1;
-        } else if (L > li) {
+        } else if (L > oli) {
             parent = (int)idx - 1;
         } else {
             const int sh2 = 3 * (kMaxLevel - (L - 1));
             const uint64_t lowb = (key >> sh2) << sh2;
-            const int64_t s = gallop_left(k, i, lowb, sfirst);
-            parent = (int)off[s] + (L - 1 - split_level(k, s, n, sg.of_pos));
+            const int64_t sp = gallop_left(k, ip, lowb, sfirst);
+            parent = (int)off[sp] + (L - 1 - split_level(k, sp, n, sg.of_pos));
         }
         t.parent[idx] = parent;
         t.arrive[idx] = 0;
@@ -759,6 +795,17 @@ __global__ void k_emit(const uint64_t* __restrict__ k, int64_t n, const uint32_t
         lo.w = sL;
         t.lo[idx] = lo;
     }
+}
+
+// Atomic add at device scope with acquire-release ordering: the caller's
+// earlier writes are visible to whoever acquires a later value of *p, and the
+// caller sees the writes released by the additions before its own.
+__device__ __forceinline__ int atomic_add_acq_rel(int* p, int v)
+{
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+                 : "memory");
+    return old;
 }
 
 __device__ __forceinline__ float4 ldcg4(const float4* p) { return __ldcg(p); }
@@ -862,11 +909,11 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
         t.cell[c].cen = cc;
         const int par = t.parent[c];
         if (par < 0) break;
-        __threadfence();
-        const int old = atomicAdd(&t.arrive[par], cntc);
+        // release this cell's sums to the sibling that arrives last, which
+        // acquires all of them with the same operation
+        const int old = atomic_add_acq_rel(&t.arrive[par], cntc);
         const int4 pn = t.cell[par].node;
         if (old + cntc != pn.y - pn.x) break;
-        __threadfence();
         int ch = par + 1;
         vec4<A> a = ldcg4(&ssum[ch]), b = ldcg4(&smom[ch]);
         sx = a.x; sy = a.y; sz = a.z; ux = b.x; uy = b.y; uz = b.z;
@@ -1015,7 +1062,7 @@ void morton_keys(const vec4<R>* pos, int64_t n, BBox* bb, uint64_t* keys, uint32
     } else {
         k_bbox_init<<<1, 1, 0, s>>>(bb);
         unsigned g = nblk(n, 256);
-        if (g > 152u * 8u) g = 152u * 8u;
+        if (g > 152u * 4u) g = 152u * 4u;
         k_bbox<R><<<g, 256, 0, s>>>(pos, n, bb, flags);
         counted(2);
     }
