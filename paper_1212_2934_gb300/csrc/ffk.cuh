@@ -132,7 +132,7 @@ struct alignas(32) Cell {
 template <typename R>
 struct Tree {
     Cell<R>* cell;       // topology + centre
-    vec4<R>* mom;        // moment sum xyz, particle count
+    vec4<R>* mom;        // moment sum xyz; w = reach: largest distance from the centre to the cube
     vec4<R>* lo;         // lower cube corner xyz, cube side
     vec4<R>* sum;        // position sum xyz (aggregation scratch)
     int* parent;         // parent cell (-1 for the root)

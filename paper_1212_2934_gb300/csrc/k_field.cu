@@ -160,20 +160,22 @@ __device__ __forceinline__ void quad_term(R rx, R ry, R rz, R r2, const vec4<R>&
 
 // Opening test in the tree precision, each operation rounded once:
 // side^2 < theta^2 ((dx dx + dy dy) + dz dz), and with LJ on, the distance
-// from the particle to the cell's cube is at least rcut.
+// from the particle to the cell's cube is at least rcut.  reach bounds the
+// distance from the centre to any point of the cube (the aggregation stores
+// one per cell; sqrt(3) side always holds, the centre lying in the cube).
 template <typename R>
 __device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& x, const vec4<R>& c,
-                                       const vec4<R>* __restrict__ lo_arr, int i)
+                                       const vec4<R>* __restrict__ lo_arr, int i, R reach)
 {
     const R dx = rsub(x.x, c.x), dy = rsub(x.y, c.y), dz = rsub(x.z, c.z);
     const R d2 = radd(radd(rmul(dx, dx), rmul(dy, dy)), rmul(dz, dz));
     const R s2 = rmul(c.w, c.w);
     if (!(s2 < rmul(fp.theta2, d2))) return false;
     if (fp.use_rcut) {
-        // The centre lies in the cube, so the cube is at least d - sqrt(3) side
-        // away; beyond rcut + sqrt(3) side (with a margin far above the rounding
-        // of d and of the centre) the exact test below cannot fail.
-        const R far = (fp.rcut + R(1.7320509) * c.w) * R(1.00001) + R(0.01);
+        // The cube is at least d - reach away; beyond rcut + reach (with a
+        // margin far above the rounding of d, of the centre and of reach) the
+        // exact test below cannot fail.
+        const R far = (fp.rcut + reach) * R(1.00001) + R(0.01);
         if (d2 >= far * far) return true;
         const vec4<R> lo = lo_arr[i];
         const R side = lo.w;
@@ -217,11 +219,6 @@ constexpr int kTraverseCarveout = FFK_TRAVERSE_CARVEOUT;
 constexpr int kBhThreads = FFK_BH_THREADS;
 constexpr int kBhMinBlocks = FFK_BH_MIN_BLOCKS;
 static_assert(kBhThreads % 32 == 0, "whole warps");
-
-// 1: the per-lane walk requests a cell's moment sum together with its record.
-#ifndef FFK_HOIST_MOMENT
-#define FFK_HOIST_MOMENT 1
-#endif
 
 // Minimum of v over each aligned group of G lanes.
 template <int G>
@@ -279,7 +276,7 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
             const bool leaf = (nd.w >> 8) != 0;
             const bool single = leaf && (nd.y - nd.x == 1);
             const vec4<R> c = cl.cen;
-            const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i);
+            const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i, R(1.7320509) * c.w);
             if (acc || (single && !inside)) {
                 // the cell's pseudo-particle; for a one-particle leaf it is the
                 // particle itself (centre and moment sum of one term are exact)
@@ -364,25 +361,30 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
     }
     while (i < end) {
         const Cell<R> cl = t.cell[i];
-#if FFK_HOIST_MOMENT
-        // requested with the cell so that one latency covers both loads
+        // requested with the cell so that one latency covers both loads; .w is
+        // the cell's reach for the opening test
         const vec4<R> m = t.mom[i];
-#endif
         const int4 nd = cl.node;
         const bool inside = nd.x <= k && k < nd.y;
         const bool leaf = (nd.w >> 8) != 0;
         const bool single = leaf && (nd.y - nd.x == 1);
         const vec4<R> c = cl.cen;
-        const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i);
+        const R rx = xk.x - c.x, ry = xk.y - c.y, rz = xk.z - c.z;
+        const R r2 = rx * rx + ry * ry + rz * rz;
+        const bool out1 = single && !inside;
+        // A one-particle leaf adds the same dipole term whether accepted or
+        // summed as a pair; the two differ only by the LJ term, which is zero
+        // unless r2 < lj_rcut2_hi, and in the counts.  Outside that range the
+        // plain walk skips the opening test of such a leaf.
+        const bool acc =
+            (!COUNT && !QUAD && out1)
+                ? (fp.include_sr && r2 < fp.lj_rcut2_hi &&
+                   accept<R>(fp, xk, c, t.lo, (int)i, m.w))
+                : (!inside && accept<R>(fp, xk, c, t.lo, (int)i, m.w));
         unsigned nxt = i + 1;
-        if (acc || (single && !inside)) {
+        if (acc || out1) {
             // the cell's pseudo-particle; for a one-particle leaf it is the
             // particle itself (centre and moment sum of one term are exact)
-#if !FFK_HOIST_MOMENT
-            const vec4<R> m = t.mom[i];
-#endif
-            const R rx = xk.x - c.x, ry = xk.y - c.y, rz = xk.z - c.z;
-            const R r2 = rx * rx + ry * ry + rz * rz;
             if (r2 > R(0))
                 dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, m.x, m.y, m.z, hx, hy, hz, fx, fy, fz);
             if (QUAD && acc && r2 > R(0))
@@ -506,7 +508,7 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         const bool inside = nd.x <= k && k < nd.y;
         const bool leaf = (nd.w >> 8) != 0;
         const bool single = leaf && (nd.y - nd.x == 1);
-        const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i);
+        const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i, R(1.7320509) * cl.cen.w);
         unsigned nxt = i + 1;
         if (acc || (single && !inside)) {
             if (w < wend) keys[w] = i;

@@ -841,6 +841,25 @@ __device__ __forceinline__ void quad_add(R dx, R dy, R dz, R vx, R vy, R vz, R q
 // in A and kept in ssum/smom (for A = R these are the tree's own sum and mom
 // arrays); with A wider than R the moment sum and the centre are rounded to R
 // once, from the A sums.
+// Largest distance from the centre c to a point of the cube [lo, lo + side]
+// (side = lo.w; the far corner on each axis), stored with each cell's moment
+// sum for the traversal's opening test: a particle farther than rcut + reach
+// from c is at least rcut from the cube.
+template <typename R>
+__device__ __forceinline__ R cube_reach(const vec4<R>& c, const vec4<R>& lo)
+{
+    const R cs[3] = {c.x, c.y, c.z};
+    const R ls[3] = {lo.x, lo.y, lo.z};
+    R r2 = R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const R hi = radd(ls[a], lo.w);
+        const R e = fmax(fabs(rsub(cs[a], ls[a])), fabs(rsub(hi, cs[a])));
+        r2 = r2 + e * e;
+    }
+    return sqrt(r2);
+}
+
 template <typename R, typename A>
 __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u,
                             int64_t n, const uint32_t* __restrict__ cnt,
@@ -872,9 +891,11 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
         const A rn = (A)cntc;
         vec4<A> sm, mm;
         vec4<R> cc;
+        const vec4<R> lo = t.lo[c];
+        cc.x = (R)rdiv(sx, rn); cc.y = (R)rdiv(sy, rn); cc.z = (R)rdiv(sz, rn); cc.w = lo.w;
+        const R reach = cube_reach<R>(cc, lo);
         sm.x = sx; sm.y = sy; sm.z = sz; sm.w = A(0);
-        mm.x = ux; mm.y = uy; mm.z = uz; mm.w = rn;
-        cc.x = (R)rdiv(sx, rn); cc.y = (R)rdiv(sy, rn); cc.z = (R)rdiv(sz, rn); cc.w = t.lo[c].w;
+        mm.x = ux; mm.y = uy; mm.z = uz; mm.w = (A)reach;
         if (t.q1) {
             // S and m about this centre: from the particles of a leaf, else from the
             // children by the shift M = sum_j [M_j + (c_j - c) (x) U_j]
@@ -903,7 +924,7 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
         smom[c] = mm;
         if (sizeof(A) != sizeof(R)) {
             vec4<R> mr;
-            mr.x = (R)ux; mr.y = (R)uy; mr.z = (R)uz; mr.w = (R)cntc;
+            mr.x = (R)ux; mr.y = (R)uy; mr.z = (R)uz; mr.w = reach;
             t.mom[c] = mr;
         }
         t.cell[c].cen = cc;
