@@ -210,6 +210,9 @@ ffk::Tree<R> tree_of(ff_ctx* c)
     t.cap = c->cap;
     t.q1 = static_cast<ffk::vec4<R>*>(c->q1);
     t.q2 = static_cast<ffk::vec4<R>*>(c->q2);
+    // the same cutoff as field_params' rcut (the opening rule's LJ cut)
+    const bool lj_on = c->p.lj_eps != 0.0 && c->p.lj_rcut > 0.0;
+    t.rcut = lj_on ? (R)c->p.lj_rcut : R(0);
     return t;
 }
 

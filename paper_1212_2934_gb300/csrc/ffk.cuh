@@ -132,7 +132,7 @@ struct alignas(32) Cell {
 template <typename R>
 struct Tree {
     Cell<R>* cell;       // topology + centre
-    vec4<R>* mom;        // moment sum xyz; w = reach: largest distance from the centre to the cube
+    vec4<R>* mom;        // moment sum xyz; w = far2 of the LJ opening test (see k_field.cu)
     vec4<R>* lo;         // lower cube corner xyz, cube side
     vec4<R>* sum;        // position sum xyz (aggregation scratch)
     int* parent;         // parent cell (-1 for the root)
@@ -144,7 +144,19 @@ struct Tree {
     // sum (rho_i - c) (x) u_i and m its trace
     vec4<R>* q1 = nullptr;
     vec4<R>* q2 = nullptr;
+    R rcut = R(0);       // LJ cutoff of the opening rule (0: LJ off)
 };
+
+// Square of the distance from a cell's centre beyond which a particle is
+// surely at least rcut from the cell's cube: (rcut + reach) with a margin far
+// above the rounding of the distance, of the centre and of reach, where
+// reach bounds the distance from the centre to any point of the cube.
+template <typename R>
+__host__ __device__ __forceinline__ R far2_of(R rcut, R reach)
+{
+    const R far = (rcut + reach) * R(1.00001) + R(0.01);
+    return far * far;
+}
 
 // ---------------------------------------------------------------- launchers
 // Scan: exclusive prefix sum of n uint32 values into out[0..n]; out[n] = total.

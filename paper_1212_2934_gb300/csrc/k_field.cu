@@ -160,23 +160,21 @@ __device__ __forceinline__ void quad_term(R rx, R ry, R rz, R r2, const vec4<R>&
 
 // Opening test in the tree precision, each operation rounded once:
 // side^2 < theta^2 ((dx dx + dy dy) + dz dz), and with LJ on, the distance
-// from the particle to the cell's cube is at least rcut.  reach bounds the
-// distance from the centre to any point of the cube (the aggregation stores
-// one per cell; sqrt(3) side always holds, the centre lying in the cube).
+// from the particle to the cell's cube is at least rcut.  Beyond far2 =
+// far2_of(rcut, reach) from the centre the exact test cannot fail; the
+// aggregation stores far2 with each cell's moment sum, and reach = sqrt(3)
+// side always holds (the centre lies in the cube).
 template <typename R>
 __device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& x, const vec4<R>& c,
-                                       const vec4<R>* __restrict__ lo_arr, int i, R reach)
+                                       const vec4<R>* __restrict__ lo_arr, int i, R far2)
 {
     const R dx = rsub(x.x, c.x), dy = rsub(x.y, c.y), dz = rsub(x.z, c.z);
     const R d2 = radd(radd(rmul(dx, dx), rmul(dy, dy)), rmul(dz, dz));
     const R s2 = rmul(c.w, c.w);
     if (!(s2 < rmul(fp.theta2, d2))) return false;
     if (fp.use_rcut) {
-        // The cube is at least d - reach away; beyond rcut + reach (with a
-        // margin far above the rounding of d, of the centre and of reach) the
-        // exact test below cannot fail.
-        const R far = (fp.rcut + reach) * R(1.00001) + R(0.01);
-        if (d2 >= far * far) return true;
+        // the cube is at least d - reach away
+        if (d2 >= far2) return true;
         const vec4<R> lo = lo_arr[i];
         const R side = lo.w;
         R t[3];
@@ -276,7 +274,8 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
             const bool leaf = (nd.w >> 8) != 0;
             const bool single = leaf && (nd.y - nd.x == 1);
             const vec4<R> c = cl.cen;
-            const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i, R(1.7320509) * c.w);
+            const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i,
+                                                    far2_of(fp.rcut, R(1.7320509) * c.w));
             if (acc || (single && !inside)) {
                 // the cell's pseudo-particle; for a one-particle leaf it is the
                 // particle itself (centre and moment sum of one term are exact)
@@ -362,7 +361,7 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
     while (i < end) {
         const Cell<R> cl = t.cell[i];
         // requested with the cell so that one latency covers both loads; .w is
-        // the cell's reach for the opening test
+        // the cell's far2 for the opening test
         const vec4<R> m = t.mom[i];
         const int4 nd = cl.node;
         const bool inside = nd.x <= k && k < nd.y;
@@ -508,7 +507,8 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         const bool inside = nd.x <= k && k < nd.y;
         const bool leaf = (nd.w >> 8) != 0;
         const bool single = leaf && (nd.y - nd.x == 1);
-        const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i, R(1.7320509) * cl.cen.w);
+        const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i,
+                                                    far2_of(fp.rcut, R(1.7320509) * cl.cen.w));
         unsigned nxt = i + 1;
         if (acc || (single && !inside)) {
             if (w < wend) keys[w] = i;

@@ -842,9 +842,9 @@ __device__ __forceinline__ void quad_add(R dx, R dy, R dz, R vx, R vy, R vz, R q
 // arrays); with A wider than R the moment sum and the centre are rounded to R
 // once, from the A sums.
 // Largest distance from the centre c to a point of the cube [lo, lo + side]
-// (side = lo.w; the far corner on each axis), stored with each cell's moment
-// sum for the traversal's opening test: a particle farther than rcut + reach
-// from c is at least rcut from the cube.
+// (side = lo.w; the far corner on each axis): a particle farther than
+// rcut + reach from c is at least rcut from the cube.  The traversal's opening
+// test reads far2_of(rcut, reach), stored with each cell's moment sum.
 template <typename R>
 __device__ __forceinline__ R cube_reach(const vec4<R>& c, const vec4<R>& lo)
 {
@@ -893,9 +893,9 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
         vec4<R> cc;
         const vec4<R> lo = t.lo[c];
         cc.x = (R)rdiv(sx, rn); cc.y = (R)rdiv(sy, rn); cc.z = (R)rdiv(sz, rn); cc.w = lo.w;
-        const R reach = cube_reach<R>(cc, lo);
+        const R far2 = far2_of<R>(t.rcut, cube_reach<R>(cc, lo));
         sm.x = sx; sm.y = sy; sm.z = sz; sm.w = A(0);
-        mm.x = ux; mm.y = uy; mm.z = uz; mm.w = (A)reach;
+        mm.x = ux; mm.y = uy; mm.z = uz; mm.w = (A)far2;
         if (t.q1) {
             // S and m about this centre: from the particles of a leaf, else from the
             // children by the shift M = sum_j [M_j + (c_j - c) (x) U_j]
@@ -924,7 +924,7 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
         smom[c] = mm;
         if (sizeof(A) != sizeof(R)) {
             vec4<R> mr;
-            mr.x = (R)ux; mr.y = (R)uy; mr.z = (R)uz; mr.w = reach;
+            mr.x = (R)ux; mr.y = (R)uy; mr.z = (R)uz; mr.w = far2;
             t.mom[c] = mr;
         }
         t.cell[c].cen = cc;
