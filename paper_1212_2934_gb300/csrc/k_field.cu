@@ -164,11 +164,12 @@ __device__ __forceinline__ void quad_term(R rx, R ry, R rz, R r2, const vec4<R>&
 // far2_of(rcut, reach) from the centre the exact test cannot fail; the
 // aggregation stores far2 with each cell's moment sum, and reach = sqrt(3)
 // side always holds (the centre lies in the cube).
+// (dx, dy, dz) = x - c, each component rounded once.
 template <typename R>
-__device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& x, const vec4<R>& c,
-                                       const vec4<R>* __restrict__ lo_arr, int i, R far2)
+__device__ __forceinline__ bool accept(const FieldParams<R>& fp, R dx, R dy, R dz, const vec4<R>& x,
+                                       const vec4<R>& c, const vec4<R>* __restrict__ lo_arr, int i,
+                                       R far2)
 {
-    const R dx = rsub(x.x, c.x), dy = rsub(x.y, c.y), dz = rsub(x.z, c.z);
     const R d2 = radd(radd(rmul(dx, dx), rmul(dy, dy)), rmul(dz, dz));
     const R s2 = rmul(c.w, c.w);
     if (!(s2 < rmul(fp.theta2, d2))) return false;
@@ -192,6 +193,13 @@ __device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& 
         if (b2 < fp.rcut2) return false;
     }
     return true;
+}
+
+template <typename R>
+__device__ __forceinline__ bool accept(const FieldParams<R>& fp, const vec4<R>& x, const vec4<R>& c,
+                                       const vec4<R>* __restrict__ lo_arr, int i, R far2)
+{
+    return accept<R>(fp, rsub(x.x, c.x), rsub(x.y, c.y), rsub(x.z, c.z), x, c, lo_arr, i, far2);
 }
 
 // Preferred shared-memory share of the traversal (percent of the maximum):
@@ -368,7 +376,9 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
         const bool leaf = (nd.w >> 8) != 0;
         const bool single = leaf && (nd.y - nd.x == 1);
         const vec4<R> c = cl.cen;
-        const R rx = xk.x - c.x, ry = xk.y - c.y, rz = xk.z - c.z;
+        // the separation serves the opening test (each component rounded once
+        // either way) and the pair terms
+        const R rx = rsub(xk.x, c.x), ry = rsub(xk.y, c.y), rz = rsub(xk.z, c.z);
         const R r2 = rx * rx + ry * ry + rz * rz;
         const bool out1 = single && !inside;
         // A one-particle leaf adds the same dipole term whether accepted or
@@ -378,8 +388,8 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
         const bool acc =
             (!COUNT && !QUAD && out1)
                 ? (fp.include_sr && r2 < fp.lj_rcut2_hi &&
-                   accept<R>(fp, xk, c, t.lo, (int)i, m.w))
-                : (!inside && accept<R>(fp, xk, c, t.lo, (int)i, m.w));
+                   accept<R>(fp, rx, ry, rz, xk, c, t.lo, (int)i, m.w))
+                : (!inside && accept<R>(fp, rx, ry, rz, xk, c, t.lo, (int)i, m.w));
         unsigned nxt = i + 1;
         if (acc || out1) {
             // the cell's pseudo-particle; for a one-particle leaf it is the
