@@ -125,7 +125,7 @@ struct DynParams {
 template <typename R>
 struct alignas(32) Cell {
     int4 node;     // pbegin, pend, skip, level | leaf << 8
-    vec4<R> cen;   // geometric centre xyz, cube side
+    vec4<R> cen;   // geometric centre xyz, cube side squared (rounded once)
 };
 
 // Tree arrays (device pointers), cells in depth-first preorder.

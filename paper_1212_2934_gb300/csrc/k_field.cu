@@ -161,9 +161,9 @@ __device__ __forceinline__ void quad_term(R rx, R ry, R rz, R r2, const vec4<R>&
 // Opening test in the tree precision, each operation rounded once:
 // side^2 < theta^2 ((dx dx + dy dy) + dz dz), and with LJ on, the distance
 // from the particle to the cell's cube is at least rcut.  Beyond far2 =
-// far2_of(rcut, reach) from the centre the exact test cannot fail; the
-// aggregation stores far2 with each cell's moment sum, and reach = sqrt(3)
-// side always holds (the centre lies in the cube).
+// far2_of(rcut, reach) from the centre (reach: the largest distance from the
+// centre to a point of the cube) the exact test cannot fail; the aggregation
+// stores far2 with each cell's moment sum.
 // (dx, dy, dz) = x - c, each component rounded once.
 template <typename R>
 __device__ __forceinline__ bool accept(const FieldParams<R>& fp, R dx, R dy, R dz, const vec4<R>& x,
@@ -171,8 +171,8 @@ __device__ __forceinline__ bool accept(const FieldParams<R>& fp, R dx, R dy, R d
                                        R far2)
 {
     const R d2 = radd(radd(rmul(dx, dx), rmul(dy, dy)), rmul(dz, dz));
-    const R s2 = rmul(c.w, c.w);
-    if (!(s2 < rmul(fp.theta2, d2))) return false;
+    // c.w holds side^2, rounded once
+    if (!(c.w < rmul(fp.theta2, d2))) return false;
     if (fp.use_rcut) {
         // the cube is at least d - reach away
         if (d2 >= far2) return true;
@@ -282,12 +282,11 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
             const bool leaf = (nd.w >> 8) != 0;
             const bool single = leaf && (nd.y - nd.x == 1);
             const vec4<R> c = cl.cen;
-            const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i,
-                                                    far2_of(fp.rcut, R(1.7320509) * c.w));
+            const vec4<R> m = t.mom[i];  // .w: the cell's far2
+            const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i, m.w);
             if (acc || (single && !inside)) {
                 // the cell's pseudo-particle; for a one-particle leaf it is the
                 // particle itself (centre and moment sum of one term are exact)
-                const vec4<R> m = t.mom[i];
                 const R rx = xk.x - c.x, ry = xk.y - c.y, rz = xk.z - c.z;
                 const R r2 = rx * rx + ry * ry + rz * rz;
                 if (r2 > R(0))
@@ -517,14 +516,13 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         const bool inside = nd.x <= k && k < nd.y;
         const bool leaf = (nd.w >> 8) != 0;
         const bool single = leaf && (nd.y - nd.x == 1);
-        const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i,
-                                                    far2_of(fp.rcut, R(1.7320509) * cl.cen.w));
+        const vec4<R> ws = t.mom[i];  // moment sum; .w: the cell's far2
+        const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i, ws.w);
         unsigned nxt = i + 1;
         if (acc || (single && !inside)) {
             if (w < wend) keys[w] = i;
             ++w;
             if (VJP) {
-                const vec4<R> ws = t.mom[i];
                 vjp_target<R>(fp, xk, uk, ak, bk, cl.cen, ws, dx, dy, dz, ux, uy, uz);
                 if (!acc && fp.include_sr) {
                     const vec4<R> bj = vj.bbar[nd.x];

@@ -892,8 +892,9 @@ __global__ void k_aggregate(const vec4<R>* __restrict__ pos, const vec4<R>* __re
         vec4<A> sm, mm;
         vec4<R> cc;
         const vec4<R> lo = t.lo[c];
-        cc.x = (R)rdiv(sx, rn); cc.y = (R)rdiv(sy, rn); cc.z = (R)rdiv(sz, rn); cc.w = lo.w;
+        cc.x = (R)rdiv(sx, rn); cc.y = (R)rdiv(sy, rn); cc.z = (R)rdiv(sz, rn);
         const R far2 = far2_of<R>(t.rcut, cube_reach<R>(cc, lo));
+        cc.w = rmul(lo.w, lo.w);  // side^2 for the opening test
         sm.x = sx; sm.y = sy; sm.z = sz; sm.w = A(0);
         mm.x = ux; mm.y = uy; mm.z = uz; mm.w = (A)far2;
         if (t.q1) {
