@@ -25,13 +25,12 @@ __device__ __forceinline__ void dipole(R rx, R ry, R rz, R r2, R ukx, R uky, R u
     const R bj = ujx * rx + ujy * ry + ujz * rz;
     const R bk = ukx * rx + uky * ry + ukz * rz;
     const R a = ujx * ukx + ujy * uky + ujz * ukz;
-    const R t = R(3) * bj * ir5;
-    hx += rx * t - ujx * ir3;
-    hy += ry * t - ujy * ir3;
-    hz += rz * t - ujz * ir3;
     const R s3 = R(3) * ir5;
+    const R cuk = s3 * bj, cuj = s3 * bk;  // cuk = 3 (u_j.r) / r^5 serves h and f
+    hx += rx * cuk - ujx * ir3;
+    hy += ry * cuk - ujy * ir3;
+    hz += rz * cuk - ujz * ir3;
     const R cr = s3 * a - R(15) * bk * bj * ir7;
-    const R cuk = s3 * bj, cuj = s3 * bk;
     fx += rx * cr + ukx * cuk + ujx * cuj;
     fy += ry * cr + uky * cuk + ujy * cuj;
     fz += rz * cr + ukz * cuk + ujz * cuj;

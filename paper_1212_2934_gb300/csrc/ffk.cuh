@@ -124,7 +124,7 @@ struct DynParams {
 // in single precision): topology and the pseudo-particle position.
 template <typename R>
 struct alignas(32) Cell {
-    int4 node;     // pbegin, pend, skip, level | leaf << 8
+    int4 node;     // pbegin, pend, skip, level | leaf << 8 | (one-particle leaf) << 9
     vec4<R> cen;   // geometric centre xyz, cube side squared (rounded once)
 };
 

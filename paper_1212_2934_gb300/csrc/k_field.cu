@@ -280,7 +280,7 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
             const int4 nd = cl.node;
             const bool inside = nd.x <= k && k < nd.y;
             const bool leaf = (nd.w >> 8) != 0;
-            const bool single = leaf && (nd.y - nd.x == 1);
+            const bool single = (nd.w >> 9) != 0;  // a one-particle leaf
             const vec4<R> c = cl.cen;
             const vec4<R> m = t.mom[i];  // .w: the cell's far2
             const bool acc = !inside && accept<R>(fp, xk, c, t.lo, (int)i, m.w);
@@ -373,7 +373,7 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
         const int4 nd = cl.node;
         const bool inside = nd.x <= k && k < nd.y;
         const bool leaf = (nd.w >> 8) != 0;
-        const bool single = leaf && (nd.y - nd.x == 1);
+        const bool single = (nd.w >> 9) != 0;  // a one-particle leaf
         const vec4<R> c = cl.cen;
         // the separation serves the opening test (each component rounded once
         // either way) and the pair terms
@@ -515,7 +515,7 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         const int4 nd = cl.node;
         const bool inside = nd.x <= k && k < nd.y;
         const bool leaf = (nd.w >> 8) != 0;
-        const bool single = leaf && (nd.y - nd.x == 1);
+        const bool single = (nd.w >> 9) != 0;  // a one-particle leaf
         const vec4<R> ws = t.mom[i];  // moment sum; .w: the cell's far2
         const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i, ws.w);
         unsigned nxt = i + 1;

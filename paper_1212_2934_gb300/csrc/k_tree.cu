@@ -771,7 +771,8 @@ __global__ void k_emit(const uint64_t* __restrict__ k, int64_t n, const uint32_t
         }
         const int skip = (int)off[pe];
         const int leaf = (L == d) ? 1 : 0;
-        t.cell[idx].node = make_int4((int)ip, (int)pe, skip, L | (leaf << 8));
+        const int single = (leaf && pe - ip == 1) ? 1 : 0;
+        t.cell[idx].node = make_int4((int)ip, (int)pe, skip, L | (leaf << 8) | (single << 9));
         int parent;
         if (L == 0) {
             parent = -1;
