@@ -77,7 +77,9 @@ __device__ __forceinline__ double sigma2_minus_r2(const FieldParams<double>& fp,
 // that exact value is formed only near the cut.  Near contact (r ~ sigma) the
 // bracket (s/r)^12 - (s/r)^6 is a small difference of two numbers near one, so
 // it is formed as s6 (s6 - 1) with s6 - 1 = (s2 - 1)(s2^2 + s2 + 1) and
-// s2 - 1 = (sigma^2 - r^2) / r^2.
+// s2 - 1 = (sigma^2 - r^2) / r^2, the difference compensated below
+// r^2 = 1.5 sigma^2; beyond, sigma^2 - r^2 is at least a third of r^2 and the
+// plain difference of the rounded r^2 is accurate to a few ulps.
 template <typename R>
 __device__ __forceinline__ void lj(const FieldParams<R>& fp, R rx, R ry, R rz, R r2, R& fx, R& fy,
                                    R& fz, R& e)
@@ -86,7 +88,9 @@ __device__ __forceinline__ void lj(const FieldParams<R>& fp, R rx, R ry, R rz, R
     const R r2e = radd(radd(rmul(rx, rx), rmul(ry, ry)), rmul(rz, rz));
     if (!(r2e < fp.lj_rcut2 && r2e > R(0))) return;
     const R ir2 = R(1) / r2e;
-    const R s2m1 = sigma2_minus_r2(fp, rx, ry, rz) * ir2;
+    const R dsr = r2e < R(1.5) * fp.lj_sigma2 ? sigma2_minus_r2(fp, rx, ry, rz)
+                                              : rsub(fp.lj_sigma2, r2e);
+    const R s2m1 = dsr * ir2;
     const R s2 = R(1) + s2m1;
     const R s6 = s2 * s2 * s2;
     const R s6m1 = s2m1 * (s2 * s2 + s2 + R(1));
