@@ -244,6 +244,8 @@ ffk::FieldParams<R> field_params(const ff_ctx* c, double theta, int include_sr)
     fp.lj_sigma2_lo = (R)(p.lj_sigma * p.lj_sigma - (double)fp.lj_sigma2);
     fp.lj_rcut2 = (R)(p.lj_rcut * p.lj_rcut);
     fp.lj_rcut2_hi = (R)((double)fp.lj_rcut2 * (sizeof(R) == 4 ? 1.0 + 1e-5 : 1.0 + 1e-12));
+    const double rin = (p.lj_rcut - 0.01) * (1.0 - 1e-5);
+    fp.lj_rcut2_lo = (R)(rin > 0.0 ? rin * rin : 0.0);
     fp.lj_e2 = (R)(2.0 * p.lj_eps);
     fp.lj_e4 = (R)(4.0 * p.lj_eps);
     double sc2 = lj_on ? p.lj_sigma * p.lj_sigma / (p.lj_rcut * p.lj_rcut) : 0.0;

@@ -94,6 +94,8 @@ struct FieldParams {
     R lj_sigma2_lo;  // sigma^2 - lj_sigma2 (the FP32 pair's low part; 0 in FP64)
     R lj_rcut2;      // rcut^2: the pair cut (decided on an exactly rounded r^2)
     R lj_rcut2_hi;   // slightly above lj_rcut2: pre-test on a fused r^2
+    R lj_rcut2_lo;   // ((rcut - 0.01)(1 - 1e-5))^2: a particle this close is surely
+                     // within rcut of its own cell's cube
     R lj_e2, lj_e4;  // 2 eps, 4 eps (pair energy)
     R lj_shift;      // pair energy at rcut
     int use_rcut;    // LJ on: cells closer than rcut are always opened

@@ -386,11 +386,13 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
         const bool out1 = single && !inside;
         // A one-particle leaf adds the same dipole term whether accepted or
         // summed as a pair; the two differ only by the LJ term, which is zero
-        // unless r2 < lj_rcut2_hi, and in the counts.  Outside that range the
-        // plain walk skips the opening test of such a leaf.
+        // unless r2 < lj_rcut2_hi, and in the counts.  Below lj_rcut2_lo the
+        // particle, and so its cube, is within rcut (by a margin far above the
+        // rounding of the cube's corners): the opening test fails.  The plain
+        // walk therefore decides such a leaf only in between.
         const bool acc =
             (!COUNT && !QUAD && out1)
-                ? (fp.include_sr && r2 < fp.lj_rcut2_hi &&
+                ? (fp.include_sr && r2 < fp.lj_rcut2_hi && r2 >= fp.lj_rcut2_lo &&
                    accept<R>(fp, rx, ry, rz, xk, c, t.lo, (int)i, m.w))
                 : (!inside && accept<R>(fp, rx, ry, rz, xk, c, t.lo, (int)i, m.w));
         unsigned nxt = i + 1;
