@@ -49,14 +49,17 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 // digit (alternate passes use alternate arrays; each tile clears its words in
 // the other array for the pass after it), then one tile ticket per pass.
 constexpr int kOsThreads = 256;  // = kRadixBins: one digit per thread
-constexpr int kOsItems = 8;      // keys per thread per tile (64-bit keys)
-constexpr int kOsTile = kOsThreads * kOsItems;  // the smallest tile (sizes the scratch)
-// 32-bit keys take twice as many per thread in the same shared memory, so a
-// tile carries more bytes per look-back and per block-wide scan
+constexpr int kOsItems = 16;     // keys per thread per tile
+constexpr int kOsTile = kOsThreads * kOsItems;
+// Large tiles carry many bytes per look-back and per block-wide scan, and
+// keep the look-back chains of a pass short (all tiles of a 1M-key pass run
+// at once).  The tile is staged in dynamic shared memory.
 template <typename K>
-constexpr int os_items() { return sizeof(K) == 4 ? 2 * kOsItems : kOsItems; }
+constexpr int os_items() { return kOsItems; }
 template <typename K>
-constexpr int os_min_blocks() { return sizeof(K) == 4 ? 3 : 4; }
+constexpr int os_min_blocks() { return sizeof(K) == 4 ? 3 : 2; }
+template <typename K>
+constexpr size_t os_dyn_smem() { return (size_t)kOsTile * (sizeof(K) + sizeof(uint32_t)); }
 constexpr int kOsMaxPasses = 8;
 constexpr int64_t os_tiles(int64_t n) { return (n + kOsTile - 1) / kOsTile; }
 constexpr size_t os_tmp_words(int64_t n)

@@ -218,16 +218,26 @@ constexpr int kTraverseCarveout = FFK_TRAVERSE_CARVEOUT;
 // block barrier), so the block size only sets how registers and warps are
 // traded.  Registers are allocated per SM sub-partition (16384 each, a warp
 // taking 32 x its registers), so 128 x 10 allows 48 registers a thread, room
-// for the whole walk without spills; 128 x 12 (48 warps instead of 40) caps
-// it at 40 and spills, which costs more than the extra warps gain.
+// for the whole walk without spills.  The plain FP32 walk is lean enough for
+// 128 x 12 (40 registers, 48 warps) with a few spilled words, and measures
+// slightly faster so; the other walks keep 10 blocks.
 #ifndef FFK_BH_THREADS
 #define FFK_BH_THREADS 128
 #endif
 #ifndef FFK_BH_MIN_BLOCKS
 #define FFK_BH_MIN_BLOCKS 10
 #endif
+#ifndef FFK_BH_MIN_BLOCKS_LEAN
+#define FFK_BH_MIN_BLOCKS_LEAN 12
+#endif
 constexpr int kBhThreads = FFK_BH_THREADS;
 constexpr int kBhMinBlocks = FFK_BH_MIN_BLOCKS;
+
+template <typename R, bool COUNT, bool QUAD>
+constexpr int bh_min_blocks()
+{
+    return (sizeof(R) == 4 && !COUNT && !QUAD) ? FFK_BH_MIN_BLOCKS_LEAN : FFK_BH_MIN_BLOCKS;
+}
 static_assert(kBhThreads % 32 == 0, "whole warps");
 
 // Minimum of v over each aligned group of G lanes.
@@ -612,7 +622,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
 // from the following segments once its own is used up.  Task counters
 // (work[0..nseg)) start at zero; every task is taken exactly once.
 template <typename R, bool COUNT, int G, bool QUAD>
-__global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh(const vec4<R>* __restrict__ pos,
+__global__ void __launch_bounds__(kBhThreads, (bh_min_blocks<R, COUNT, QUAD>())) k_bh(const vec4<R>* __restrict__ pos,
                                             const vec4<R>* __restrict__ u, int n, Tree<R> t,
                                             FieldParams<R> fp, vec4<R>* __restrict__ h,
                                             vec4<R>* __restrict__ f, R* __restrict__ esr,

@@ -7,6 +7,7 @@
 // are the sort's look-back polls, on tiles with earlier tickets (already
 // running), each bounded, so every loop ends.
 #include <climits>
+#include <mutex>
 
 #include "ffk.cuh"
 
@@ -279,8 +280,9 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     constexpr int kTile = kOsThreads * kItems;
     constexpr int kWarpItems = kTile / kWarps;
     static_assert(kWarpItems == 32 * kItems, "each warp ranks kItems rounds of 32");
-    __shared__ K s_key[kTile];
-    __shared__ uint32_t s_val[kTile];
+    extern __shared__ __align__(16) unsigned char os_smem[];  // os_dyn_smem<K>() bytes
+    K* s_key = reinterpret_cast<K*>(os_smem);
+    uint32_t* s_val = reinterpret_cast<uint32_t*>(os_smem + sizeof(K) * kTile);
     __shared__ uint32_t s_wcnt[kWarps][kRadixBins];  // per-warp digit counts, then prefixes
     __shared__ uint32_t s_dstart[kRadixBins];        // where each digit starts in the tile
     __shared__ uint32_t s_gstart[kRadixBins];        // where this tile's run of it goes
@@ -984,6 +986,22 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
     counted(nb > 0 ? 3 : 1);
 }
 
+// The scatter's tile needs more dynamic shared memory than the default limit;
+// the limit is raised once per device.
+template <typename K>
+void os_prepare()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return;
+    cudaFuncSetAttribute(k_os_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)os_dyn_smem<K>());
+    if (dev >= 0 && dev < 64) done[dev] = true;
+}
+
 size_t radix_tmp_words(int64_t n)
 {
     // the tiled passes of radix_sort_systems share this scratch with the
@@ -1020,8 +1038,9 @@ bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n
     uint32_t* va = v0;
     K* kb = k1;
     uint32_t* vb = v1;
+    os_prepare<K>();
     for (int p = 0; p < passes; ++p) {
-        k_os_scatter<K><<<(unsigned)tiles, kOsThreads, 0, s>>>(
+        k_os_scatter<K><<<(unsigned)tiles, kOsThreads, os_dyn_smem<K>(), s>>>(
             ka, va, kb, vb, n, p * kRadixBits, hist + p * kRadixBins, status[p & 1],
             status[(p + 1) & 1], tickets + p, flags, p == 0 ? vseg : nullptr, nseg);
         K* tk = ka; ka = kb; kb = tk;
