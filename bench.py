@@ -759,14 +759,16 @@ def run_ours(args):
 
         ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
 
+        bufs = [hn, outs]
+
         def e2e_step():
-            ff._check(ctxe.handle, lib.ff_set_particles(ctxe.handle, *[ptr(h) for h in hn],
+            src, dst = bufs
+            ff._check(ctxe.handle, lib.ff_set_particles(ctxe.handle, *[ptr(h) for h in src],
                                                         ff.FF_DTYPE_F32, ff.FF_HOST))
             ff._check(ctxe.handle, lib.ff_step(ctxe.handle, 1))
-            ff._check(ctxe.handle, lib.ff_get_particles(ctxe.handle, *[ptr(o) for o in outs],
+            ff._check(ctxe.handle, lib.ff_get_particles(ctxe.handle, *[ptr(o) for o in dst],
                                                         ff.FF_DTYPE_F32, ff.FF_HOST))
-            for h, o in zip(hn, outs):
-                h[...] = o  # the next step starts from the state just read back
+            bufs.reverse()  # the next step starts from the state just read back
 
         for _ in range(max(W, 1)):
             e2e_step()

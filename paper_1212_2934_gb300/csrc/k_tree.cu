@@ -1018,7 +1018,8 @@ bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n
                              int passes, int* flags, cudaStream_t s, const uint32_t* vseg,
                              int64_t nseg)
 {
-    if (n <= 1 || passes < 1) return false;
+    // one element is sorted already, unless its value still has to be formed
+    if (n < 1 || passes < 1 || (n == 1 && !vseg)) return false;
     if (passes > kOsMaxPasses) passes = kOsMaxPasses;
     if (passes * kRadixBits > (int)(8 * sizeof(K))) passes = (int)(8 * sizeof(K)) / kRadixBits;
     const int64_t tiles = (n + kOsThreads * os_items<K>() - 1) / (kOsThreads * os_items<K>());

@@ -106,6 +106,20 @@ def test_bh_gradient_batched_systems(ff, ora):
     assert e == pytest.approx(etot, rel=1e-12)
 
 
+@pytest.mark.parametrize("n", [2, 3])
+def test_bh_gradient_fewest_entries(ff, ora, n):
+    """Two and three particles: the smallest entry lists the source sort sees."""
+    from paper_1212_2934_gb300 import synth
+
+    pos = np.array([[0.0, 0.0, 0.0], [1.5, 0.2, -0.3], [3.1, 1.0, 0.4]])[:n]
+    u = synth.isotropic_moments(n, 4)
+    e, gp, gu = _grad(ff, "f64", pos, u, ff.FF_ALGO_BH, 0.5)
+    e0, gp0, gu0 = ora.bh_energy_grad(pos, u, 0.5, 1, "f64", lj_eps=1.0, tree_centres=True)
+    assert rel_err(gu, gu0).max() <= 1e-10
+    assert rel_err(gp, gp0).max() <= 1e-10
+    assert _energy_ok(e, e0, gu0, 1e-10)
+
+
 def test_autograd_function(ff):
     import torch
 
