@@ -364,7 +364,7 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = f
         ffk::radix_sort_pairs(c->keys[0], c->vals[0], c->keys[1], c->vals[1], n, c->radix_tmp,
                               c->dflags, s);
         ffk::radix_sort_systems(c->keys[0], c->vals[0], c->keys[1], c->vals[1], n, c->radix_tmp,
-                                segs_of(c), s);
+                                segs_of(c), c->dflags, s);
     }
     {
         StageTimer st(c, S_GATHER);

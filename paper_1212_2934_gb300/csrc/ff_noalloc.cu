@@ -38,15 +38,8 @@ constexpr size_t kKeyBytes = align256(sizeof(uint64_t) * kNoAllocMaxN);
 constexpr size_t kValOff = kKeyOff + kKeyBytes;
 constexpr size_t kValBytes = align256(sizeof(uint32_t) * kNoAllocMaxN);
 constexpr size_t kRadixOff = kValOff + kValBytes;
-// radix scratch: the larger of the one-sweep sort's (pass counts, tile
-// status words, tickets) and the tiled sort's (256 x tiles histogram,
-// 256 x tiles + 1 offsets, scan block sums)
-constexpr int64_t kTiles = (kNoAllocMaxN + ffk::kSortTile - 1) / ffk::kSortTile;
-constexpr int64_t kHist = int64_t(ffk::kRadixBins) * kTiles;
-constexpr size_t kTiledWords = size_t(kHist + kHist + 1 + kHist / 2048 + 2);
-constexpr size_t kRadixWords = kTiledWords > ffk::os_tmp_words(kNoAllocMaxN)
-                                   ? kTiledWords
-                                   : ffk::os_tmp_words(kNoAllocMaxN);
+// radix scratch: the one-sweep sort's pass counts, tile status words and tickets
+constexpr size_t kRadixWords = ffk::os_tmp_words(kNoAllocMaxN);
 constexpr size_t kRadixBytes = align256(sizeof(uint32_t) * kRadixWords);
 constexpr size_t kBoxOff = kRadixOff + kRadixBytes;
 constexpr size_t kBoxBytes = align256(sizeof(ffk::BBox));

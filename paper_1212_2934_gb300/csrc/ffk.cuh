@@ -39,9 +39,6 @@ constexpr int kMaxLevel = 21;        // 21 bits per axis -> 63-bit Morton keys
 constexpr int kMaxLeaf = 64;         // largest leaf_max accepted
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
-constexpr int kSortThreads = 256;    // = kRadixBins: one digit per thread in the scatter
-constexpr int kSortItems = 8;        // keys per thread per block tile
-constexpr int kSortTile = kSortThreads * kSortItems;
 
 // One-sweep radix sort (one scatter launch per pass, tiles chained by
 // decoupled look-back): tile shape and scratch.  The scratch holds the digit
@@ -194,7 +191,7 @@ void morton_keys(const vec4<R>* pos, int64_t n, BBox* bb, uint64_t* keys, uint32
 // Stable passes on the system of each element (the element's value is its
 // position before the sort), restoring system-major order after the key passes.
 void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
-                        uint32_t* tmp, Segs sg, cudaStream_t s);
+                        uint32_t* tmp, Segs sg, int* flags, cudaStream_t s);
 
 template <typename R>
 void gather_state(const uint32_t* perm, int64_t n, const vec4<R>* pos, const vec4<R>* vel,

@@ -113,117 +113,25 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t n,
     }
 }
 
-// ------------------------------------------------------------ radix sort
-// Digit of element i: bits [shift, shift + 8) of its key or, in a system pass
-// (sys != null), of the system that owned the element's pre-sort position.
-template <typename K>
-__device__ __forceinline__ uint32_t radix_digit(const K* __restrict__ keys,
-                                                const uint32_t* __restrict__ vals,
-                                                const uint32_t* __restrict__ sys, int64_t i,
-                                                int shift)
-{
-    if (sys) return (sys[vals[i]] >> shift) & (kRadixBins - 1);
-    return (uint32_t)((keys[i] >> shift) & (kRadixBins - 1));
-}
-
-template <typename K>
-__global__ void k_radix_hist(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
-                             const uint32_t* __restrict__ sys, int64_t n, int shift,
-                             uint32_t* __restrict__ hist, int64_t nb)
-{
-    __shared__ uint32_t h[kRadixBins];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const int64_t i = base + r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[radix_digit(keys, vals, sys, i, shift)], 1u);
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
-}
-
-// Stable scatter: within a tile, keys keep their index order; ranks among
-// equal digits come from warp match masks and per-warp digit counts.  The tile
-// is first placed in shared memory in digit order, then written out so that
-// consecutive threads store consecutive elements of one bucket (coalesced).
-template <typename K>
-__global__ void k_radix_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                const uint32_t* __restrict__ sys, K* __restrict__ kout,
-                                uint32_t* __restrict__ vout, int64_t n, int shift,
-                                const uint32_t* __restrict__ hist,
-                                const uint32_t* __restrict__ offs, int64_t nb)
-{
-    __shared__ K s_key[kSortTile];
-    __shared__ uint32_t s_val[kSortTile];
-    __shared__ uint32_t s_glob[kRadixBins];  // where this tile's digit-d run starts globally
-    __shared__ uint32_t s_loc[kRadixBins];   // where it starts in the tile's digit order
-    __shared__ uint32_t s_run[kRadixBins];   // next free local slot of digit d
-    __shared__ uint32_t s_w[kSortThreads / 32][kRadixBins];
-    __shared__ uint32_t s_wsum[kSortThreads / 32];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    s_glob[t] = offs[(int64_t)t * nb + blockIdx.x];
-    // local starts: exclusive scan of this tile's digit counts
-    const uint32_t cnt = hist[(int64_t)t * nb + blockIdx.x];
-    uint32_t inc = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_wsum[w] = inc;
-    __syncthreads();
-    uint32_t before = 0;
-    for (int ww = 0; ww < w; ++ww) before += s_wsum[ww];
-    s_loc[t] = before + inc - cnt;
-    s_run[t] = before + inc - cnt;
-    const uint32_t lt = (1u << lane) - 1u;
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    const int tile_n = (int)min((int64_t)kSortTile, n - base);
-    for (int r = 0; r < kSortItems; ++r) {
-#pragma unroll
-        for (int j = 0; j < kRadixBins / 32; ++j) s_w[w][lane + 32 * j] = 0;
-        __syncthreads();
-        const int64_t i = base + r * kSortThreads + t;
-        const bool valid = i < n;
-        K key = valid ? kin[i] : K(0);
-        uint32_t d = valid ? radix_digit(kin, vin, sys, i, shift) : (uint32_t)kRadixBins;
-        const uint32_t peers = __match_any_sync(kFull, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0) s_w[w][d] = __popc(peers);
-        __syncthreads();
-        uint32_t run = s_run[t];
-#pragma unroll
-        for (int ww = 0; ww < kSortThreads / 32; ++ww) {
-            uint32_t c = s_w[ww][t];
-            s_w[ww][t] = run;
-            run += c;
-        }
-        s_run[t] = run;
-        __syncthreads();
-        if (valid) {
-            const uint32_t lp = s_w[w][d] + rank;
-            s_key[lp] = key;
-            s_val[lp] = vin[i];
-        }
-        __syncthreads();
-    }
-    for (int j = t; j < tile_n; j += kSortThreads) {
-        const K key = s_key[j];
-        const uint32_t val = s_val[j];
-        const uint32_t d = sys ? ((sys[val] >> shift) & (kRadixBins - 1))
-                               : (uint32_t)((key >> shift) & (kRadixBins - 1));
-        const uint32_t g = s_glob[d] + ((uint32_t)j - s_loc[d]);
-        kout[g] = key;
-        vout[g] = val;
-    }
-}
-
 // ---------------------------------------------------- one-sweep radix sort
+// Digit of a sort element: 8 bits of its key at `shift` or, in a system pass
+// (sysd != null), of the system that owned the element's pre-sort position
+// (its value).
+template <typename K>
+__device__ __forceinline__ uint32_t os_digit(K key, uint32_t val, const uint32_t* __restrict__ sysd,
+                                             int shift)
+{
+    return sysd ? (sysd[val] >> shift) & (kRadixBins - 1)
+                : (uint32_t)(key >> shift) & (kRadixBins - 1);
+}
+
 // Digit counts of every pass in one read of the keys.
 template <typename K>
-__global__ void __launch_bounds__(kOsThreads) k_os_hist(const K* __restrict__ keys, int64_t n,
-                                                        int passes, uint32_t* __restrict__ hist)
+__global__ void __launch_bounds__(kOsThreads) k_os_hist(const K* __restrict__ keys,
+                                                        const uint32_t* __restrict__ vals,
+                                                        const uint32_t* __restrict__ sysd,
+                                                        int64_t n, int passes,
+                                                        uint32_t* __restrict__ hist)
 {
     __shared__ uint32_t h[kOsMaxPasses][kRadixBins];
     const int t = threadIdx.x;
@@ -236,9 +144,10 @@ __global__ void __launch_bounds__(kOsThreads) k_os_hist(const K* __restrict__ ke
         const int64_t i = i0 + t;
         const bool valid = i < n;
         const K key = valid ? keys[i] : K(0);
+        const uint32_t val = (valid && sysd) ? vals[i] : 0u;
         const bool whole = __all_sync(kFull, valid);
         for (int p = 0; p < passes; ++p) {
-            const uint32_t d = (uint32_t)(key >> (p * kRadixBits)) & (kRadixBins - 1);
+            const uint32_t d = os_digit<K>(key, val, sysd, p * kRadixBits);
             if (whole && __all_sync(kFull, d == __shfl_sync(kFull, d, 0))) {
                 if (lane == 0) atomicAdd(&h[p][d], 32u);
             } else if (valid) {
@@ -273,7 +182,8 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
     unsigned long long* status, unsigned long long* __restrict__ status_next,
-    uint32_t* ticket, int* flags, const uint32_t* __restrict__ vseg, int64_t nseg)
+    uint32_t* ticket, int* flags, const uint32_t* __restrict__ vseg, int64_t nseg,
+    const uint32_t* __restrict__ sysd)
 {
     constexpr int kWarps = kOsThreads / 32;
     constexpr int kItems = os_items<K>();
@@ -333,8 +243,7 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     for (int r = 0; r < kItems; ++r) {
         const int e = w * kWarpItems + r * 32 + lane;
         const bool valid = e < tile_n;
-        const uint32_t d =
-            valid ? ((uint32_t)(key[r] >> shift) & (kRadixBins - 1)) : (uint32_t)kRadixBins;
+        const uint32_t d = valid ? os_digit<K>(key[r], val[r], sysd, shift) : (uint32_t)kRadixBins;
         const uint32_t peers = __match_any_sync(kFull, d);
         const uint32_t before = valid ? s_wcnt[w][d] : 0u;
         rank[r] = before + __popc(peers & lt);
@@ -361,7 +270,7 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     for (int r = 0; r < kItems; ++r) {
         const int e = w * kWarpItems + r * 32 + lane;
         if (e < tile_n) {
-            const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
+            const uint32_t d = os_digit<K>(key[r], val[r], sysd, shift);
             const uint32_t lp = s_dstart[d] + s_wcnt[w][d] + rank[r];
             s_key[lp] = key[r];
             s_val[lp] = val[r];
@@ -399,10 +308,11 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     __syncthreads();
     for (int j = t; j < tile_n; j += kOsThreads) {
         const K key = s_key[j];
-        const uint32_t d = (uint32_t)(key >> shift) & (kRadixBins - 1);
+        const uint32_t val = s_val[j];
+        const uint32_t d = os_digit<K>(key, val, sysd, shift);
         const int64_t g = (int64_t)s_gstart[d] + (j - (int64_t)s_dstart[d]);
         kout[g] = key;
-        vout[g] = s_val[j];
+        vout[g] = val;
     }
 }
 
@@ -1002,26 +912,18 @@ void os_prepare()
     if (dev >= 0 && dev < 64) done[dev] = true;
 }
 
-size_t radix_tmp_words(int64_t n)
-{
-    // the tiled passes of radix_sort_systems share this scratch with the
-    // one-sweep passes of the key sort
-    const int64_t nb = (n + kSortTile - 1) / kSortTile;
-    const int64_t h = (int64_t)kRadixBins * nb;
-    const size_t tiled = (size_t)(h + (h + 1) + scan_tmp_words(h));
-    const size_t os = os_tmp_words(n);
-    return tiled > os ? tiled : os;
-}
+size_t radix_tmp_words(int64_t n) { return os_tmp_words(n); }
 
+// The passes of a one-sweep LSD sort: digits p * 8 .. p * 8 + 7 of the keys or,
+// with sysd, of the system of each element's value.
 template <typename K>
-bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
-                             int passes, int* flags, cudaStream_t s, const uint32_t* vseg,
-                             int64_t nseg)
+bool os_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp, int passes,
+             int* flags, cudaStream_t s, const uint32_t* vseg, int64_t nseg, const uint32_t* sysd)
 {
     // one element is sorted already, unless its value still has to be formed
     if (n < 1 || passes < 1 || (n == 1 && !vseg)) return false;
     if (passes > kOsMaxPasses) passes = kOsMaxPasses;
-    if (passes * kRadixBits > (int)(8 * sizeof(K))) passes = (int)(8 * sizeof(K)) / kRadixBits;
+    if (!sysd && passes * kRadixBits > (int)(8 * sizeof(K))) passes = (int)(8 * sizeof(K)) / kRadixBits;
     const int64_t tiles = (n + kOsThreads * os_items<K>() - 1) / (kOsThreads * os_items<K>());
     uint32_t* hist = tmp;
     unsigned long long* status[2];
@@ -1034,7 +936,8 @@ bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n
     cudaMemsetAsync(status[0], 0, sizeof(unsigned long long) * kRadixBins * tiles, s);
     cudaMemsetAsync(tickets, 0, sizeof(uint32_t) * kOsMaxPasses, s);
     const int64_t hb = (n + kOsThreads - 1) / kOsThreads;
-    k_os_hist<K><<<(unsigned)(hb < 1216 ? hb : 1216), kOsThreads, 0, s>>>(k0, n, passes, hist);
+    k_os_hist<K><<<(unsigned)(hb < 1216 ? hb : 1216), kOsThreads, 0, s>>>(k0, v0, sysd, n, passes,
+                                                                          hist);
     K* ka = k0;
     uint32_t* va = v0;
     K* kb = k1;
@@ -1043,12 +946,20 @@ bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n
     for (int p = 0; p < passes; ++p) {
         k_os_scatter<K><<<(unsigned)tiles, kOsThreads, os_dyn_smem<K>(), s>>>(
             ka, va, kb, vb, n, p * kRadixBits, hist + p * kRadixBins, status[p & 1],
-            status[(p + 1) & 1], tickets + p, flags, p == 0 ? vseg : nullptr, nseg);
+            status[(p + 1) & 1], tickets + p, flags, p == 0 ? vseg : nullptr, nseg, sysd);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
     counted(1 + passes);
     return (passes & 1) != 0;
+}
+
+template <typename K>
+bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
+                             int passes, int* flags, cudaStream_t s, const uint32_t* vseg,
+                             int64_t nseg)
+{
+    return os_sort<K>(k0, v0, k1, v1, n, tmp, passes, flags, s, vseg, nseg, nullptr);
 }
 template bool radix_sort_pairs_passes<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, int64_t,
                                                 uint32_t*, int, int*, cudaStream_t,
@@ -1061,38 +972,19 @@ void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, in
                       uint32_t* tmp, int* flags, cudaStream_t s)
 {
     // eight passes: the sorted data are back in (k0, v0)
-    radix_sort_pairs_passes<uint64_t>(k0, v0, k1, v1, n, tmp, 8, flags, s, nullptr, 0);
+    os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, 8, flags, s, nullptr, 0, nullptr);
 }
 
 void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
-                        uint32_t* tmp, Segs sg, cudaStream_t s)
+                        uint32_t* tmp, Segs sg, int* flags, cudaStream_t s)
 {
     if (!sg.of_pos || sg.nseg <= 1 || n <= 1) return;
-    const int64_t nb = (n + kSortTile - 1) / kSortTile;
-    const int64_t h = (int64_t)kRadixBins * nb;
-    uint32_t* hist = tmp;
-    uint32_t* offs = tmp + h;
-    uint32_t* stmp = offs + h + 1;
     // an even number of passes leaves the data in (k0, v0); the value of each
     // element stays its pre-sort position, so its system is of_pos[value]
     int passes = 0;
     for (int b = 0; (1 << b) < sg.nseg; b += kRadixBits) ++passes;
     if (passes & 1) ++passes;
-    uint64_t* ka = k0;
-    uint32_t* va = v0;
-    uint64_t* kb = k1;
-    uint32_t* vb = v1;
-    for (int p = 0; p < passes; ++p) {
-        const int shift = p * kRadixBits;
-        k_radix_hist<uint64_t><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, sg.of_pos, n, shift,
-                                                                     hist, nb);
-        scan_exclusive(hist, offs, h, stmp, s);
-        k_radix_scatter<uint64_t><<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, sg.of_pos, kb, vb, n, shift,
-                                                                hist, offs, nb);
-        counted(2);
-        uint64_t* tk = ka; ka = kb; kb = tk;
-        uint32_t* tv = va; va = vb; vb = tv;
-    }
+    os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, passes, flags, s, nullptr, 0, sg.of_pos);
 }
 
 template <typename R>
