@@ -533,18 +533,26 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         const bool leaf = (nd.w >> 8) != 0;
         const bool single = (nd.w >> 9) != 0;  // a one-particle leaf
         const vec4<R> ws = t.mom[i];  // moment sum; .w: the cell's far2
-        const bool acc = !inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i, ws.w);
+        const bool out1 = single && !inside;
+        const R rx = rsub(xk.x, cl.cen.x), ry = rsub(xk.y, cl.cen.y), rz = rsub(xk.z, cl.cen.z);
+        const R r2 = rx * rx + ry * ry + rz * rz;
+        // A one-particle leaf gives the same entry whether accepted or summed as a
+        // pair; only the LJ term of the product differs, and it vanishes outside
+        // [lj_rcut2_lo, lj_rcut2_hi) (see bh_task1), so it is decided only there.
+        const bool acc =
+            out1 ? (VJP && fp.include_sr && r2 < fp.lj_rcut2_hi && r2 >= fp.lj_rcut2_lo &&
+                    accept<R>(fp, rx, ry, rz, xk, cl.cen, t.lo, (int)i, ws.w))
+                 : (!inside && accept<R>(fp, rx, ry, rz, xk, cl.cen, t.lo, (int)i, ws.w));
         unsigned nxt = i + 1;
-        if (acc || (single && !inside)) {
+        if (acc || out1) {
             if (w < wend) keys[w] = i;
             ++w;
             if (VJP) {
                 vjp_target<R>(fp, xk, uk, ak, bk, cl.cen, ws, dx, dy, dz, ux, uy, uz);
                 if (!acc && fp.include_sr) {
                     const vec4<R> bj = vj.bbar[nd.x];
-                    const R rx = xk.x - cl.cen.x, ry = xk.y - cl.cen.y, rz = xk.z - cl.cen.z;
-                    lj_vjp<R>(fp, rx, ry, rz, rx * rx + ry * ry + rz * rz, bk.x - bj.x,
-                              bk.y - bj.y, bk.z - bj.z, dx, dy, dz);
+                    lj_vjp<R>(fp, rx, ry, rz, r2, bk.x - bj.x, bk.y - bj.y, bk.z - bj.z, dx, dy,
+                              dz);
                 }
             }
             nxt = (unsigned)nd.z;
