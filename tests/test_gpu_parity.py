@@ -198,6 +198,47 @@ def test_two_dipoles_closed_form(ff):
         np.testing.assert_allclose(f, [[0, 0, 6 / 1.5 ** 4], [0, 0, -6 / 1.5 ** 4]], rtol=1e-14)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64", "mixed"])
+@pytest.mark.parametrize("leaf_max", [1, 8])
+def test_plain_walk_equals_counting_walk(ff, ora, prec, leaf_max):
+    """The walk without counts (the one every step runs) settles the opening rule lazily where
+    the outcome cannot change a term; its field and force (LJ included) equal the counting
+    walk's bit for bit at every theta, and the oracle's within the bar."""
+    pos, u, _ = _system(6007, 21)
+    pos, u = _cast(prec, pos, u)
+    plain = ff.ff_create(ff.ff_params_default(n=len(pos), precision=prec, leaf_max=leaf_max,
+                                              count_interactions=0))
+    ff.ff_set_particles(plain, pos, u)
+    counted = _ctx(ff, len(pos), prec, leaf_max)
+    ff.ff_set_particles(counted, pos, u)
+    for theta in (0.3, 0.5, 0.7):
+        hp, fp = ff.ff_dipolar_field(plain, ff.FF_ALGO_BH, theta, True)
+        hc, fc = ff.ff_dipolar_field(counted, ff.FF_ALGO_BH, theta, True)
+        assert np.array_equal(hp, hc) and np.array_equal(fp, fc), theta
+    ref = ora.bh(pos.astype(np.float64), u.astype(np.float64), 0.7, leaf_max, prec, 1.0, 1.0,
+                 1.0, 2.5, True)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert rel_err(hp, ref["h"]).max() <= tol
+    assert rel_err(fp, ref["f"]).max() <= tol
+
+
+def test_plain_walk_chains(ff):
+    """Touching chains (every neighbour at contact, LJ bracket near zero): the plain walk still
+    equals the counting walk bit for bit."""
+    from paper_1212_2934_gb300 import synth
+
+    side = synth.box_side_for_fraction(64 * 100, 0.01)
+    pos, u = synth.chains_cube(100, 64, side, 5)
+    pos, u = pos.astype(np.float32), u.astype(np.float32)
+    plain = ff.ff_create(ff.ff_params_default(n=len(pos), precision="f32", count_interactions=0))
+    counted = ff.ff_create(ff.ff_params_default(n=len(pos), precision="f32", count_interactions=1))
+    for c in (plain, counted):
+        ff.ff_set_particles(c, pos, u)
+    hp, fp = ff.ff_dipolar_field(plain, ff.FF_ALGO_BH, 0.5, True)
+    hc, fc = ff.ff_dipolar_field(counted, ff.FF_ALGO_BH, 0.5, True)
+    assert np.array_equal(hp, hc) and np.array_equal(fp, fc)
+
+
 @pytest.mark.parametrize("n", [3072 * 5, 3072 * 5 + 1, 100003])
 def test_sort_many_tiles_with_repeated_keys(ff, ora, n):
     """Keys and the stable order (equal keys by input index) over many sort tiles, including
@@ -260,7 +301,8 @@ def test_errors_reported(ff):
 def test_full_size_sampled(ff, ora):
     """The bench workload (N = 1,048,576, phi = 0.05, FP32, theta = 0.5, leaf_max = 1) in the
     bench's launch configuration: keys bit-exact for every particle; field, force and
-    interaction counts of 3000 sampled particles against the oracle's Barnes-Hut."""
+    interaction counts of 3000 sampled particles against the oracle's Barnes-Hut; the walk
+    without counts equal to the counting walk for every particle."""
     from paper_1212_2934_gb300 import synth
 
     e = synth.make_ensemble("phi05")
@@ -285,3 +327,9 @@ def test_full_size_sampled(ff, ora):
     assert np.array_equal(pairs[idx], ref["npair"][idx])
     assert np.array_equal(opened[idx], ref["nopen"][idx])
     assert ref["ncells"] == ff.ff_tree_info(ctx)["ncells"]
+    # the walk every step runs (no counts) gives the same bits for every particle
+    p.count_interactions = 0
+    plain = ff.ff_create(p)
+    ff.ff_set_particles(plain, pos32, u32)
+    hp, fp = ff.ff_dipolar_field(plain, ff.FF_ALGO_BH, 0.5, True)
+    assert np.array_equal(hp, h) and np.array_equal(fp, f)
