@@ -359,6 +359,24 @@ const char *ff_status_string(ff_status s);
 ff_status ff_morton_order_noalloc(const float *pos, int64_t n, uint64_t *keys_out,
                                   uint32_t *order_out, void *stream);
 
+/*
+ * Self-test of the key sort's only wait on other thread blocks (no
+ * counterpart in the paper).  Each tile of a sort pass adds up the digit
+ * counts that earlier tiles publish, polling each word a bounded number of
+ * times and raising a device error flag when the polls run out (the host then
+ * reports FF_EDEVICE instead of waiting forever).  This call sorts n
+ * synthetic keys in buffers it allocates and frees, with the first tile
+ * withholding its counts and every word polled once, so the second tile's
+ * wait must run out.
+ *
+ * n: 8192 .. 2^24 (at least two tiles).  stream: a cudaStream_t, NULL for
+ * the default stream.  Waits before returning.  FF_OK: the wait ran out and
+ * its flag reached the host.  FF_EDEVICE: it did not.  FF_EINVAL: n out of
+ * range.  FF_ECUDA: a CUDA call failed.  The reason is given by
+ * ff_last_error(NULL).
+ */
+ff_status ff_selftest_sort_wait(int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

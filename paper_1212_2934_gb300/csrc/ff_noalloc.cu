@@ -132,4 +132,51 @@ ff_status ff_morton_order_noalloc(const float* pos, int64_t n, uint64_t* keys_ou
     return FF_OK;
 }
 
+// Self-test of the sort's bounded wait: distinct synthetic keys, values 0..n-1.
+__global__ void k_selftest_keys(uint64_t* __restrict__ k, uint32_t* __restrict__ v, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    k[i] = ((uint64_t)i * 0x9E3779B97F4A7C15ull) >> 1;
+    v[i] = (uint32_t)i;
+}
+
+ff_status ff_selftest_sort_wait(int64_t n, void* stream)
+{
+    if (n < 2 * ffk::kOsTile || n > (int64_t)1 << 24)
+        return noalloc_fail(FF_EINVAL, "n must span at least two sort tiles (8192 .. 2^24)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint64_t* k[2] = {nullptr, nullptr};
+    uint32_t* v[2] = {nullptr, nullptr};
+    uint32_t* tmp = nullptr;
+    int* flags = nullptr;
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        e = cudaMalloc(&k[q], sizeof(uint64_t) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&v[q], sizeof(uint32_t) * n);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(uint32_t) * ffk::radix_tmp_words(n));
+    if (e == cudaSuccess) e = cudaMalloc(&flags, sizeof(int));
+    int hflag = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_selftest_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(k[0], v[0], n);
+        ffk::radix_sort_wait_selftest(k[0], v[0], k[1], v[1], n, tmp, flags, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const cudaError_t e_run = e;
+    for (int q = 0; q < 2; ++q) {
+        cudaFree(k[q]);
+        cudaFree(v[q]);
+    }
+    cudaFree(tmp);
+    cudaFree(flags);
+    if (e_run != cudaSuccess) return noalloc_fail(FF_ECUDA, "sort wait self-test", e_run);
+    if (!(hflag & ffk::FLAG_SORT))
+        return noalloc_fail(FF_EDEVICE, "the sort's look-back wait did not run out with a tile withheld");
+    return FF_OK;
+}
+
 }  // extern "C"

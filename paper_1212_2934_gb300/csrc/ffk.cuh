@@ -183,6 +183,13 @@ bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n
                              int passes, int* flags, cudaStream_t s,
                              const uint32_t* vseg = nullptr, int64_t nseg = 0);
 
+// One pass of the 64-bit key sort in which tile 0 withholds its digit counts
+// and every look-back word is polled once: the bounded wait of tile 1 runs out
+// and raises FLAG_SORT.  The keys are then misplaced (every write stays inside
+// [0, n)); only the self-test calls it, and nothing reads its output.
+void radix_sort_wait_selftest(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                              uint32_t* tmp, int* flags, cudaStream_t s);
+
 // bb holds one root cube per system.
 template <typename R>
 void morton_keys(const vec4<R>* pos, int64_t n, BBox* bb, uint64_t* keys, uint32_t* vals,

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
     unsigned long long* status, unsigned long long* __restrict__ status_next,
     uint32_t* ticket, int* flags, const uint32_t* __restrict__ vseg, int64_t nseg,
-    const uint32_t* __restrict__ sysd)
+    const uint32_t* __restrict__ sysd, int withhold)
 {
     constexpr int kWarps = kOsThreads / 32;
     constexpr int kItems = os_items<K>();
@@ -261,7 +261,10 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
         cnt += c;
     }
     volatile unsigned long long* st = status;
-    st[tile * kRadixBins + t] = (tile == 0 ? kOsPrefix : kOsAggregate) | cnt;
+    // withhold (a self-test of the bounded wait): tile 0 never publishes and each
+    // word is polled once, so the wait of tile 1 runs out
+    if (!(withhold && tile == 0)) st[tile * kRadixBins + t] = (tile == 0 ? kOsPrefix : kOsAggregate) | cnt;
+    const int spin_limit = withhold ? 1 : kOsSpinLimit;
     uint32_t total;
     s_dstart[t] = block_exscan(cnt, &total);
     const uint32_t bucket = block_exscan(hist[t], &total);
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
         for (int q = 0; q < kOsWindow; ++q) {
             if (!done) {
                 unsigned long long x = v[q];
-                for (int it = 0; (x >> 32) == 0 && it < kOsSpinLimit; ++it) {
+                for (int it = 0; (x >> 32) == 0 && it < spin_limit; ++it) {
                     __nanosleep(32);
                     x = st[(j - q) * kRadixBins + t];
                 }
@@ -918,7 +921,8 @@ size_t radix_tmp_words(int64_t n) { return os_tmp_words(n); }
 // with sysd, of the system of each element's value.
 template <typename K>
 bool os_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp, int passes,
-             int* flags, cudaStream_t s, const uint32_t* vseg, int64_t nseg, const uint32_t* sysd)
+             int* flags, cudaStream_t s, const uint32_t* vseg, int64_t nseg, const uint32_t* sysd,
+             int withhold = 0)
 {
     // one element is sorted already, unless its value still has to be formed
     if (n < 1 || passes < 1 || (n == 1 && !vseg)) return false;
@@ -946,7 +950,8 @@ bool os_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
     for (int p = 0; p < passes; ++p) {
         k_os_scatter<K><<<(unsigned)tiles, kOsThreads, os_dyn_smem<K>(), s>>>(
             ka, va, kb, vb, n, p * kRadixBits, hist + p * kRadixBins, status[p & 1],
-            status[(p + 1) & 1], tickets + p, flags, p == 0 ? vseg : nullptr, nseg, sysd);
+            status[(p + 1) & 1], tickets + p, flags, p == 0 ? vseg : nullptr, nseg, sysd,
+            withhold);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
@@ -973,6 +978,12 @@ void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, in
 {
     // eight passes: the sorted data are back in (k0, v0)
     os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, 8, flags, s, nullptr, 0, nullptr);
+}
+
+void radix_sort_wait_selftest(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                              uint32_t* tmp, int* flags, cudaStream_t s)
+{
+    os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, 1, flags, s, nullptr, 0, nullptr, 1);
 }
 
 void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,

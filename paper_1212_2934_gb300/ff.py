@@ -96,6 +96,7 @@ _SIGS = {
     "ff_profile": (_st, [_vp, C.c_int32]),
     "ff_profile_read": (_st, [_vp, C.POINTER(ff_profile_t)]),
     "ff_morton_order_noalloc": (_st, [_vp, C.c_int64, _vp, _vp, _vp]),
+    "ff_selftest_sort_wait": (_st, [C.c_int64, _vp]),
     "ff_last_error": (C.c_char_p, [_vp]),
     "ff_status_string": (C.c_char_p, [C.c_int]),
 }
@@ -451,6 +452,13 @@ def ff_morton_order_noalloc(pos, keys_out, order_out, stream=None):
                                                C.c_void_p(keys_out.data_ptr()),
                                                C.c_void_p(order_out.data_ptr()), sp))
     return keys_out, order_out
+
+
+def ff_selftest_sort_wait(n=20000, stream=None):
+    """Runs the sort with its first tile withholding its counts (include/ff.h); raises FFError
+    unless the bounded wait ran out and reported its flag."""
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(None, lib().ff_selftest_sort_wait(int(n), sp))
 
 
 def ff_last_error(ctx=None):
