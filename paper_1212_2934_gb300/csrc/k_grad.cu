@@ -40,12 +40,30 @@ __global__ void k_entry_counts(const int4* __restrict__ counts, int64_t n,
 __global__ void k_segments(const uint32_t* __restrict__ keys, int64_t ne, int64_t nsrc,
                            uint32_t* beg, uint32_t* end)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne) return;
-    const uint32_t k = keys[i];
-    if ((int64_t)k >= nsrc) return;
-    if (i == 0 || keys[i - 1] != k) beg[k] = (uint32_t)i;
-    if (i == ne - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
+    // four consecutive keys per thread (one 16-byte load; keys is 16-byte
+    // aligned), their neighbours across the group from plain loads
+    const int64_t i0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= ne) return;
+    uint32_t k[4];
+    if (i0 + 4 <= ne) {
+        const uint4 q = *reinterpret_cast<const uint4*>(keys + i0);
+        k[0] = q.x; k[1] = q.y; k[2] = q.z; k[3] = q.w;
+    } else {
+        for (int j = 0; j < 4; ++j) k[j] = i0 + j < ne ? keys[i0 + j] : 0u;
+    }
+    uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t i = i0 + j;
+        if (i >= ne) break;
+        const uint32_t kk = k[j];
+        const uint32_t next = i + 1 < ne ? (j < 3 ? k[j + 1] : keys[i + 1]) : 0u;
+        if ((int64_t)kk < nsrc) {
+            if (i == 0 || prev != kk) beg[kk] = (uint32_t)i;
+            if (i == ne - 1 || next != kk) end[kk] = (uint32_t)(i + 1);
+        }
+        prev = kk;
+    }
 }
 
 template <typename T>
@@ -344,7 +362,8 @@ void grad_segments(const uint32_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg
     cudaMemsetAsync(beg, 0, sizeof(uint32_t) * nsrc, s);
     cudaMemsetAsync(end, 0, sizeof(uint32_t) * nsrc, s);
     if (ne <= 0) return;
-    k_segments<<<blocks(ne, kGradThreads), kGradThreads, 0, s>>>(keys, ne, nsrc, beg, end);
+    k_segments<<<blocks((ne + 3) / 4, kGradThreads), kGradThreads, 0, s>>>(keys, ne, nsrc, beg,
+                                                                          end);
     counted();
 }
 
