@@ -500,6 +500,47 @@ __device__ __forceinline__ void vjp_target(const FieldParams<R>& fp, const vec4<
     hess_phi_add<R>(g, uk.x, uk.y, uk.z, ws.x, ws.y, ws.z, bk.x, bk.y, bk.z, ds, dx, dy, dz);
 }
 
+// The entries of one particle's slot [w, wend), written four at a time (one
+// 16-byte store) from the first 16-byte boundary of the slot on, the entries
+// before it and after the last full group one by one.  Positions at or past
+// wend are never written (a walk that overfills its slot raises the flag).
+struct SlotWriter {
+    uint32_t* keys;
+    uint32_t w, wend, a;  // next position, slot end, first aligned position
+    uint32_t s0, s1, s2;  // the entries of the current group of four so far
+
+    __device__ __forceinline__ SlotWriter(uint32_t* k, uint32_t begin, uint32_t stop)
+        : keys(k), w(begin), wend(stop), a((begin + 3u) & ~3u), s0(0), s1(0), s2(0)
+    {
+    }
+    __device__ __forceinline__ void put(uint32_t key)
+    {
+        const uint32_t q = w & 3u;
+        if (w < a) {
+            if (w < wend) keys[w] = key;
+        } else if (q == 0u) {
+            s0 = key;
+        } else if (q == 1u) {
+            s1 = key;
+        } else if (q == 2u) {
+            s2 = key;
+        } else if (w < wend) {
+            *reinterpret_cast<uint4*>(keys + (w - 3u)) = make_uint4(s0, s1, s2, key);
+        }
+        ++w;
+    }
+    // The entries of the last, incomplete group: positions g .. w - 1.
+    __device__ __forceinline__ void flush()
+    {
+        if (w <= a) return;
+        const uint32_t r = (w - a) & 3u;
+        const uint32_t g = w - r;
+        if (r > 0u && g < wend) keys[g] = s0;
+        if (r > 1u && g + 1u < wend) keys[g + 1u] = s1;
+        if (r > 2u && g + 2u < wend) keys[g + 2u] = s2;
+    }
+};
+
 template <typename R, bool VJP>
 __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict__ pos, int n,
                                             const Tree<R>& t, const FieldParams<R>& fp,
@@ -524,8 +565,7 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         i = off[sg.start[sys]];
         end = off[sg.start[sys + 1]];
     }
-    uint32_t w = base[k];
-    const uint32_t wend = base[k + 1];
+    SlotWriter sw(keys, base[k], base[k + 1]);
     while (i < end) {
         const Cell<R> cl = t.cell[i];
         const int4 nd = cl.node;
@@ -545,8 +585,7 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
                  : (!inside && accept<R>(fp, rx, ry, rz, xk, cl.cen, t.lo, (int)i, ws.w));
         unsigned nxt = i + 1;
         if (acc || out1) {
-            if (w < wend) keys[w] = i;
-            ++w;
+            sw.put(i);
             if (VJP) {
                 vjp_target<R>(fp, xk, uk, ak, bk, cl.cen, ws, dx, dy, dz, ux, uy, uz);
                 if (!acc && fp.include_sr) {
@@ -560,8 +599,7 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
             if (!single) {
                 for (int s = nd.x; s < nd.y; ++s) {
                     if (s == k) continue;
-                    if (w < wend) keys[w] = ncells + (uint32_t)s;
-                    ++w;
+                    sw.put(ncells + (uint32_t)s);
                     if (VJP) {
                         const vec4<R> xj = pos[s], uj = vj.u[s], bj = vj.bbar[s];
                         vjp_target<R>(fp, xk, uk, ak, bk, xj, uj, dx, dy, dz, ux, uy, uz);
@@ -583,7 +621,8 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         }
         i = nxt;
     }
-    if (w != wend) atomicOr(flags, FLAG_TRAVERSE);
+    sw.flush();
+    if (sw.w != sw.wend) atomicOr(flags, FLAG_TRAVERSE);
     if (VJP) {
         vec4<R> o;
         o.x = dx; o.y = dy; o.z = dz; o.w = R(0);
