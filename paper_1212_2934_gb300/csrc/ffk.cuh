@@ -47,16 +47,21 @@ constexpr int kRadixBins = 1 << kRadixBits;
 // the other array for the pass after it), then one tile ticket per pass.
 constexpr int kOsThreads = 256;  // = kRadixBins: one digit per thread
 constexpr int kOsItems = 16;     // keys per thread per tile
-constexpr int kOsTile = kOsThreads * kOsItems;
+constexpr int kOsTile = kOsThreads * kOsItems;  // the smallest tile (sizes the scratch)
 // Large tiles carry many bytes per look-back and per block-wide scan, and
 // keep the look-back chains of a pass short (all tiles of a 1M-key pass run
 // at once).  The tile is staged in dynamic shared memory.
+// 32-bit keys (the gradient's entries, hundreds of millions) take twice as
+// many per thread: 8192-key tiles in the same shared memory.
 template <typename K>
-constexpr int os_items() { return kOsItems; }
+constexpr int os_items() { return sizeof(K) == 4 ? 2 * kOsItems : kOsItems; }
 template <typename K>
-constexpr int os_min_blocks() { return sizeof(K) == 4 ? 3 : 2; }
+constexpr int os_min_blocks() { return 2; }
 template <typename K>
-constexpr size_t os_dyn_smem() { return (size_t)kOsTile * (sizeof(K) + sizeof(uint32_t)); }
+constexpr size_t os_dyn_smem()
+{
+    return (size_t)kOsThreads * os_items<K>() * (sizeof(K) + sizeof(uint32_t));
+}
 constexpr int kOsMaxPasses = 8;
 constexpr int64_t os_tiles(int64_t n) { return (n + kOsTile - 1) / kOsTile; }
 constexpr size_t os_tmp_words(int64_t n)
