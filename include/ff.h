@@ -252,8 +252,8 @@ ff_status ff_tune_traversal(ff_ctx *ctx, const int32_t *groups, int32_t ngroups,
  * be NULL) receive n x 3 values in the caller's order, dtype/loc as in
  * ff_get_particles.  The Barnes-Hut gradient records one entry per
  * interaction (8 bytes x 2 buffers; about 1000 interactions per particle
- * at theta = 0.5), allocated on first use and grown as needed; more than
- * 2^32 - 1 interactions is FF_EINVAL.  Waits.
+ * at theta = 0.5), allocated on first use and grown as needed; 2^32 - 16
+ * interactions or more is FF_EINVAL.  Waits.
  */
 ff_status ff_energy_grad(ff_ctx *ctx, int32_t algo, double theta, double *energy, void *grad_pos,
                          void *grad_u, int32_t dtype, int32_t loc);

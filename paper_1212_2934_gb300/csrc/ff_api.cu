@@ -736,7 +736,8 @@ ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64
     FF_CUDA(c, cudaMemcpyAsync(&total, c->e_total, sizeof(total), cudaMemcpyDeviceToHost, s));
     FF_CUDA(c, cudaMemcpyAsync(&ncells_h, c->off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     if ((st = sync_and_check(c)) != FF_OK) return st;
-    if (total >= 0xffffffffull)
+    // entry positions are 32-bit, with room for the recording walk's 16-byte groups
+    if (total >= 0xfffffff0ull)
         return fail(c, FF_EINVAL, "too many interactions (%llu) for one gradient pass", total);
     const int64_t ne = (int64_t)total;
     const int64_t ncells = ncells_h;
