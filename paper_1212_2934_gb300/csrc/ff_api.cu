@@ -104,7 +104,7 @@ struct ff_ctx {
     uint32_t* s_item_off = nullptr;
     uint32_t* s_scan = nullptr;
     int64_t s_cap = 0;           // sources the buffers hold
-    double* i_part = nullptr;    // per work item: six partial sums
+    double* i_part = nullptr;    // per work item: six partial sums; then each item's source
     int64_t i_cap = 0;
     bool tree_valid = false;     // a Barnes-Hut tree of some state exists
     bool counts_valid = false;
@@ -765,7 +765,8 @@ ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64
     const int64_t max_items = nsrc + ne / ffk::kGradItemEntries + 1;
     if (max_items > c->i_cap) {
         const int64_t cap = max_items + max_items / 8 + 1024;
-        if ((st = grow(c, &c->i_part, 6 * cap)) != FF_OK) return st;
+        // six partial sums per item, then the item -> source map (half a double each)
+        if ((st = grow(c, &c->i_part, 7 * cap)) != FF_OK) return st;
         c->i_cap = cap;
     }
     *ne_out = ne;

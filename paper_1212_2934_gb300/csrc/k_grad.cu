@@ -84,6 +84,15 @@ __global__ void k_item_counts(const uint32_t* __restrict__ beg, const uint32_t* 
     items[s] = (uint32_t)((end[s] - beg[s] + kGradItemEntries - 1) / kGradItemEntries);
 }
 
+// The source of every work item: thread s writes item_off[s] .. item_off[s + 1].
+__global__ void k_item_sources(const uint32_t* __restrict__ item_off, int64_t nsrc,
+                               uint32_t* __restrict__ item_src)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsrc) return;
+    for (uint32_t it = item_off[s]; it < item_off[s + 1]; ++it) item_src[it] = (uint32_t)s;
+}
+
 // One warp per item: the terms of its entries summed in single precision (at
 // most 32 per lane, then across the warp), written as six FP64 partials.
 template <typename R>
@@ -91,18 +100,12 @@ __global__ void __launch_bounds__(kGradThreads) k_item_sums(
     const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u, Tree<R> t, int64_t ncells,
     int64_t nsrc, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ beg,
     const uint32_t* __restrict__ end, const uint32_t* __restrict__ item_off,
-    double* __restrict__ part)
+    const uint32_t* __restrict__ item_src, double* __restrict__ part)
 {
     const int64_t it = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (it >= (int64_t)item_off[nsrc]) return;
-    // the source owning this item: the last s with item_off[s] <= it
-    int64_t lo = 0, hi = nsrc;
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)item_off[mid] <= it) lo = mid; else hi = mid;
-    }
-    const int64_t s = lo;
+    const int64_t s = item_src[it];  // the source owning this item
     vec4<R> x, w;
     if (s < ncells) {
         x = t.cell[s].cen;
@@ -168,17 +171,13 @@ __global__ void __launch_bounds__(kGradThreads) k_vjp_item_sums(
     const vec4<R>* __restrict__ abar, const vec4<R>* __restrict__ bbar, R ds, Tree<R> t,
     int64_t ncells, int64_t nsrc, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ beg, const uint32_t* __restrict__ end,
-    const uint32_t* __restrict__ item_off, double* __restrict__ part)
+    const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ item_src,
+    double* __restrict__ part)
 {
     const int64_t it = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (it >= (int64_t)item_off[nsrc]) return;
-    int64_t lo = 0, hi = nsrc;
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)item_off[mid] <= it) lo = mid; else hi = mid;
-    }
-    const int64_t s = lo;
+    const int64_t s = item_src[it];  // the source owning this item
     vec4<R> x, w;
     if (s < ncells) {
         x = t.cell[s].cen;
@@ -377,11 +376,14 @@ void grad_source_sums(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64_t n
     if (nsrc <= 0) return;
     k_item_counts<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(beg, end, nsrc, items);
     scan_exclusive(items, item_off, nsrc, scan_tmp, s);
+    // part holds 6 partial sums per item, then the item -> source map
+    uint32_t* item_src = reinterpret_cast<uint32_t*>(part + 6 * max_items);
+    k_item_sources<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(item_off, nsrc, item_src);
     k_item_sums<R><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
-        pos, u, t, ncells, nsrc, vals, beg, end, item_off, part);
+        pos, u, t, ncells, nsrc, vals, beg, end, item_off, item_src, part);
     k_item_reduce<R><<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(t, ncells, nsrc, item_off,
                                                                        part, G, Q);
-    counted(3);
+    counted(4);
 }
 
 template <typename R>
@@ -416,11 +418,13 @@ void vjp_source_sums(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
     if (nsrc <= 0) return;
     k_item_counts<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(beg, end, nsrc, items);
     scan_exclusive(items, item_off, nsrc, scan_tmp, s);
+    uint32_t* item_src = reinterpret_cast<uint32_t*>(part + 6 * max_items);
+    k_item_sources<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(item_off, nsrc, item_src);
     k_vjp_item_sums<R><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
-        pos, u, abar, bbar, ds, t, ncells, nsrc, vals, beg, end, item_off, part);
+        pos, u, abar, bbar, ds, t, ncells, nsrc, vals, beg, end, item_off, item_src, part);
     k_item_reduce<R><<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(t, ncells, nsrc, item_off,
                                                                        part, G, Q);
-    counted(3);
+    counted(4);
 }
 
 template <typename R>
