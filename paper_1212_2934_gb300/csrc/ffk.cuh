@@ -66,8 +66,9 @@ constexpr int kOsMaxPasses = 8;
 constexpr int64_t os_tiles(int64_t n) { return (n + kOsTile - 1) / kOsTile; }
 constexpr size_t os_tmp_words(int64_t n)
 {
+    // ... plus, when values come from segment offsets, each tile's first segment
     return (size_t)kOsMaxPasses * kRadixBins + 4 * (size_t)kRadixBins * (size_t)os_tiles(n) +
-           kOsMaxPasses;
+           kOsMaxPasses + (size_t)os_tiles(n);
 }
 
 // Root cube, written by the bbox kernels and read by the key kernel.

@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
     unsigned long long* status, unsigned long long* __restrict__ status_next,
-    uint32_t* ticket, int* flags, const uint32_t* __restrict__ vseg, int64_t nseg,
+    uint32_t* ticket, int* flags, const uint32_t* __restrict__ vseg,
+    const uint32_t* __restrict__ tile_seg,
     const uint32_t* __restrict__ sysd, int withhold)
 {
     constexpr int kWarps = kOsThreads / 32;
@@ -210,15 +211,7 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     // the words of this tile in the array the next pass uses
     status_next[tile * kRadixBins + t] = 0ull;
     if (vseg) {
-        if (t == 0) {
-            int64_t lo = 0, hi = nseg;  // vseg[lo] <= base < vseg[hi]
-            while (hi - lo > 1) {
-                const int64_t mid = (lo + hi) / 2;
-                if ((int64_t)vseg[mid] <= base) lo = mid;
-                else hi = mid;
-            }
-            s_k0 = (uint32_t)lo;
-        }
+        if (t == 0) s_k0 = tile_seg[tile];
         __syncthreads();
     }
 
@@ -899,6 +892,18 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
     counted(nb > 0 ? 3 : 1);
 }
 
+// With values from segment offsets: the segment of each tile's first element,
+// tile_seg[t] = the k with vseg[k] <= t * tile < vseg[k + 1] (thread k writes
+// the tiles that start inside its segment).
+__global__ void k_tile_segments(const uint32_t* __restrict__ vseg, int64_t nseg, int tile,
+                                int64_t tiles, uint32_t* __restrict__ tile_seg)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nseg) return;
+    const int64_t lo = vseg[k], hi = vseg[k + 1];
+    for (int64_t t = (lo + tile - 1) / tile; t * tile < hi && t < tiles; ++t) tile_seg[t] = (uint32_t)k;
+}
+
 // The scatter's tile needs more dynamic shared memory than the default limit;
 // the limit is raised once per device.
 template <typename K>
@@ -934,6 +939,10 @@ bool os_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
     status[0] = reinterpret_cast<unsigned long long*>(tmp + kOsMaxPasses * kRadixBins);
     status[1] = status[0] + kRadixBins * tiles;
     uint32_t* tickets = reinterpret_cast<uint32_t*>(status[1] + kRadixBins * tiles);
+    uint32_t* tile_seg = tickets + kOsMaxPasses;
+    if (vseg)
+        k_tile_segments<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(
+            vseg, nseg, kOsThreads * os_items<K>(), tiles, tile_seg);
     // counts and the first pass's status words start at zero; the second
     // array is cleared tile by tile during the first pass, and so on
     cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kOsMaxPasses * kRadixBins, s);
@@ -950,12 +959,12 @@ bool os_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
     for (int p = 0; p < passes; ++p) {
         k_os_scatter<K><<<(unsigned)tiles, kOsThreads, os_dyn_smem<K>(), s>>>(
             ka, va, kb, vb, n, p * kRadixBits, hist + p * kRadixBins, status[p & 1],
-            status[(p + 1) & 1], tickets + p, flags, p == 0 ? vseg : nullptr, nseg, sysd,
+            status[(p + 1) & 1], tickets + p, flags, p == 0 ? vseg : nullptr, tile_seg, sysd,
             withhold);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
-    counted(1 + passes);
+    counted(1 + passes + (vseg ? 1 : 0));
     return (passes & 1) != 0;
 }
 
