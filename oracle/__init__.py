@@ -49,40 +49,48 @@ class Dyn(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        L.ora_set_threads.argtypes = [C.c_int]
-        L.ora_get_threads.restype = C.c_int
-        L.ora_pair_dipole.argtypes = [_dp, _dp, _dp, _dp, _dp]
-        L.ora_pair_lj.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp]
-        L.ora_pair_lj.restype = C.c_double
-        L.ora_allpairs.argtypes = [_i64, _dp, _dp, C.c_double, C.c_double, C.c_double,
-                                   C.c_double, C.c_int32, C.c_int32, C.c_void_p, _i64, _dp, _dp,
-                                   C.c_void_p]
-        L.ora_bh_energy_grad.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p,
-                                         C.c_int32, _dp, _dp]
-        L.ora_bh_energy_grad.restype = C.c_double
-        L.ora_bh_vjp.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p, C.c_int32,
-                                 _dp, _dp, _dp, _dp, C.c_void_p, C.c_void_p]
-        L.ora_mz_grad.argtypes = [_i64, _dp, _dp, _dp, _dp, C.POINTER(Dyn), C.POINTER(BHParams),
-                                  _i64, _dp]
-        L.ora_mz_grad.restype = C.c_double
-        L.ora_morton.argtypes = [_i64, _dp, C.c_int32, _u64p, _dp]
-        L.ora_tree.argtypes = [_i64, _dp, _dp, C.c_int32, C.c_int32, _u64p, _i64p, _dp, _i64,
-                               _i32p, _i32p, _i64p, _i64p, _i64p, _dp, _dp, _dp, _dp, _dp]
-        L.ora_tree.restype = _i64
-        L.ora_bh.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p, _i64,
-                             _dp, _dp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                             C.c_void_p, _dp, _dp]
-        L.ora_bh.restype = _i64
-        L.ora_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
-        L.ora_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, _dp]
-        L.ora_wall.argtypes = [_dp, C.POINTER(Dyn), _dp, C.POINTER(C.c_double)]
-        L.ora_em_step.argtypes = [_i64, _dp, _dp, _dp, _dp, _i64p, _dp, _dp, C.POINTER(Dyn),
-                                  C.c_uint64]
-        L.ora_energy.argtypes = [_i64, _dp, _dp, _dp, _dp, _dp, C.c_void_p, C.POINTER(Dyn), _dp]
-        _lib = L
+        _lib = bind(_build.build())
     return _lib
+
+
+def bind(path):
+    """Load an oracle library at `path` and declare its functions (the tests also
+    bind deliberately broken copies of the oracle to show that the pins catch them)."""
+    L = C.CDLL(path)
+    L.ora_set_threads.argtypes = [C.c_int]
+    L.ora_get_threads.restype = C.c_int
+    L.ora_pair_dipole.argtypes = [_dp, _dp, _dp, _dp, _dp]
+    L.ora_pair_lj.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp]
+    L.ora_pair_lj.restype = C.c_double
+    L.ora_allpairs.argtypes = [_i64, _dp, _dp, C.c_double, C.c_double, C.c_double,
+                               C.c_double, C.c_int32, C.c_int32, C.c_void_p, _i64, _dp, _dp,
+                               C.c_void_p]
+    L.ora_bh_energy_grad.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p,
+                                     C.c_int32, _dp, _dp]
+    L.ora_bh_energy_grad.restype = C.c_double
+    L.ora_bh_vjp.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p, C.c_int32,
+                             _dp, _dp, _dp, _dp, C.c_void_p, C.c_void_p]
+    L.ora_mz_grad.argtypes = [_i64, _dp, _dp, _dp, _dp, C.POINTER(Dyn), C.POINTER(BHParams),
+                              _i64, _dp]
+    L.ora_mz_grad.restype = C.c_double
+    L.ora_morton.argtypes = [_i64, _dp, C.c_int32, _u64p, _dp]
+    L.ora_tree.argtypes = [_i64, _dp, _dp, C.c_int32, C.c_int32, _u64p, _i64p, _dp, _i64,
+                           _i32p, _i32p, _i64p, _i64p, _i64p, _dp, _dp, _dp, _dp, _dp]
+    L.ora_tree.restype = _i64
+    L.ora_bh.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), C.c_void_p, _i64,
+                         _dp, _dp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                         C.c_void_p, _dp, _dp]
+    L.ora_bh.restype = _i64
+    L.ora_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+    L.ora_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, _dp]
+    L.ora_wall.argtypes = [_dp, C.POINTER(Dyn), _dp, C.POINTER(C.c_double)]
+    L.ora_em_step.argtypes = [_i64, _dp, _dp, _dp, _dp, _i64p, _dp, _dp, C.POINTER(Dyn),
+                              C.c_uint64]
+    L.ora_energy.argtypes = [_i64, _dp, _dp, _dp, _dp, _dp, C.c_void_p, C.POINTER(Dyn), _dp]
+    L.ora_bh_sources.argtypes = [_i64, _dp, _dp, C.POINTER(BHParams), _i64, _i64p, _i64p,
+                                 _i64]
+    L.ora_bh_sources.restype = _i64
+    return L
 
 
 def set_threads(n: int) -> None:
@@ -227,6 +235,33 @@ def bh(pos, u, theta, leaf_max=1, prec="f32", dip_scale=1.0, lj_eps=0.0, lj_sigm
                       _ptr(npair), _ptr(nopen), _ptr(ncover), habs, fabs)
     return dict(h=h, f=f, e_sr=e, nacc=nacc, npair=npair, nopen=nopen, ncover=ncover,
                 habs=habs, fabs=fabs, ncells=int(nc))
+
+
+def bh_sources(pos, u, k, theta, leaf_max=1, prec="f32", lj_eps=0.0, lj_sigma=1.0,
+               lj_rcut=2.5, L=None):
+    """The sources of particle k (input index) in the order the Barnes-Hut traversal of
+    ``bh`` visits them (Sec. 3.2): a list of ("cell", frozenset of input indices) for a
+    cell used as its pseudo-particle and ("pair", frozenset({j})) for a particle summed
+    exactly.  L: an oracle library from ``bind`` (default: the oracle itself)."""
+    L = lib() if L is None else L
+    pos, u = _vec3(pos), _vec3(u)
+    n = pos.shape[0]
+    p = BHParams(theta=float(theta), leaf_max=int(leaf_max), prec=_prec(prec), dip_scale=1.0,
+                 lj_eps=float(lj_eps), lj_sigma=float(lj_sigma), lj_rcut=float(lj_rcut),
+                 include_sr=1, quad=0)
+    order = np.zeros(n, dtype=np.int64)
+    cap = 4 * n + 8
+    while True:
+        src = np.zeros(3 * cap, dtype=np.int64)
+        cnt = int(L.ora_bh_sources(n, pos, u, C.byref(p), int(k), order, src, cap))
+        if cnt <= cap:
+            break
+        cap = cnt
+    out = []
+    for q in range(cnt):
+        kind, a, b = src[3 * q: 3 * q + 3]
+        out.append(("cell" if kind == 0 else "pair", frozenset(int(j) for j in order[a:b])))
+    return out
 
 
 def bh_energy_grad(pos, u, theta, leaf_max=1, prec="f64", dip_scale=1.0, lj_eps=0.0,

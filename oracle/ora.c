@@ -667,7 +667,21 @@ typedef struct {
     double h[3], fd[3], fs[3], e_sr;
     double habs, fdabs, fsabs;   /* sums of the magnitudes of the terms added */
     int64_t nacc, npair, nopen, ncover;
+    /* optional list of the sources in visiting order, three words each:
+       (0, pbegin, pend) for an accepted cell, (1, s, s + 1) for the particle at
+       sorted position s summed exactly; nsrc counts past src_cap */
+    int64_t *src, nsrc, src_cap;
 } bh_acc;
+
+static void rec_src(bh_acc *acc, int64_t kind, int64_t a, int64_t b)
+{
+    if (acc->src && acc->nsrc < acc->src_cap) {
+        acc->src[3 * acc->nsrc] = kind;
+        acc->src[3 * acc->nsrc + 1] = a;
+        acc->src[3 * acc->nsrc + 2] = b;
+    }
+    acc->nsrc++;
+}
 
 /* per-particle recursive visit, children in octant order (Sec. 3.2) */
 static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *acc)
@@ -704,6 +718,7 @@ static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *
         }
         acc->nacc++;
         acc->ncover += t->pend[c] - t->pbegin[c];
+        rec_src(acc, 0, t->pbegin[c], t->pend[c]);
         return;
     }
     if (t->leaf[c]) {
@@ -713,6 +728,7 @@ static void bh_visit(const bh_ctx *g, int64_t k, int64_t sk, int64_t c, bh_acc *
             double r[3], hp[3], fp[3];
             for (int a = 0; a < 3; ++a) r[a] = xk[a] - g->pos[3 * j + a];
             acc->npair++;
+            rec_src(acc, 1, s, s + 1);
             if (dot3(r, r) == 0.0) continue;
             ora_pair_dipole(r, uk, &g->u[3 * j], hp, fp);
             for (int a = 0; a < 3; ++a) { acc->h[a] += hp[a]; acc->fd[a] += fp[a]; }
@@ -822,6 +838,48 @@ int64_t ora_bh(int64_t n, const double *pos, const double *u, const ora_bh_param
     free(order);
     free(rank);
     return nc;
+}
+
+/*
+ * The sources of one particle (input index k) in the order the traversal of
+ * ora_bh visits them: three words per source in src (at most cap sources
+ * stored), (0, pbegin, pend) for a cell accepted as its pseudo-particle and
+ * (1, s, s + 1) for the particle at sorted position s summed exactly; order
+ * (n words) receives the sorted position -> input index map, so a source's
+ * particles are order[pbegin .. pend).  Returns the number of sources (larger
+ * than cap when the list did not fit).  This is ora_bh's own visit, so the
+ * list shows exactly the opening decisions its field sums follow.
+ */
+int64_t ora_bh_sources(int64_t n, const double *pos, const double *u, const ora_bh_params *p,
+                       int64_t k, int64_t *order, int64_t *src, int64_t cap)
+{
+    uint64_t *skeys = malloc(n * sizeof(uint64_t));
+    double root[4];
+    ora_tree_t t;
+    tree_build(n, pos, u, p->prec, p->leaf_max, skeys, order, root, &t);
+    int64_t sk = 0;
+    for (int64_t s = 0; s < n; ++s)
+        if (order[s] == k) sk = s;
+    bh_ctx g;
+    g.t = &t;
+    g.order = order;
+    g.pos = pos;
+    g.u = u;
+    g.p = p;
+    g.use_rcut = (p->lj_eps != 0.0 && p->lj_rcut > 0.0);
+    g.theta2_d = p->theta * p->theta;
+    g.theta2_f = (float)g.theta2_d;
+    g.rcut2_d = g.use_rcut ? p->lj_rcut * p->lj_rcut : 0.0;
+    g.rcut2_f = (float)g.rcut2_d;
+    g.quad = NULL;
+    bh_acc acc;
+    memset(&acc, 0, sizeof(acc));
+    acc.src = src;
+    acc.src_cap = cap;
+    bh_visit(&g, k, sk, 0, &acc);
+    tree_free(&t);
+    free(skeys);
+    return acc.nsrc;
 }
 
 /* ------------------------------------------------------------------------ */
