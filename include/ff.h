@@ -330,11 +330,12 @@ const char *ff_status_string(ff_status s);
 
 /*
  * Allocation-free Morton ordering, for callers that cannot allocate device
- * memory: code running while a CUDA stream is being captured (where
- * cudaMalloc is not allowed), applications whose device memory belongs to
- * their own pool, and loops that cannot stall on an allocation.  The paper
- * has no counterpart; it is the key-sort stage of the Barnes-Hut path
- * packaged without allocation.
+ * memory: applications whose device memory belongs to their own pool or
+ * allocator, and loops that cannot stall on an allocation (cudaMalloc may
+ * synchronise the device).  The paper has no counterpart; it is the key-sort
+ * stage of the Barnes-Hut path packaged without allocation.  The call reads
+ * its error word back to the host and waits for the stream, so it cannot be
+ * issued on a stream that is being captured into a graph.
  *
  * pos: device pointer, n x 3 float, caller's order.  Writes keys_out[n]
  * (device, uint64: the sorted 63-bit Morton keys of the root cube of these
@@ -346,14 +347,17 @@ const char *ff_status_string(ff_status s);
  * Nothing is allocated: besides the caller's buffers the work uses one fixed
  * scratch array inside the library, sized for n <= FF_NOALLOC_MAX_N (about
  * 3.7 MB, held on every GPU that loads the library until the process exits).
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Every call shares the array: calls
- * whose GPU work overlaps (other streams, other host threads on the same
- * device) race and must not be issued.
+ * The first call on a device looks up the array's device address and keeps
+ * it for the life of the process: make that first call before any stream
+ * capture on that device, and do not use the call on a device after
+ * cudaDeviceReset.  Every call shares the array: calls whose GPU work
+ * overlaps (other streams, other host threads on the same device) race and
+ * must not be issued.
  *
  * FF_EINVAL: a NULL pointer, or n outside 1 .. FF_NOALLOC_MAX_N.
- * FF_ENONFINITE: a position is NaN or infinite.  FF_ECUDA: a CUDA call
- * failed.  The reason is given by ff_last_error(NULL).
+ * FF_ENONFINITE: a position is NaN or infinite.  FF_EDEVICE: a sort tile's
+ * bounded wait for an earlier tile ran out (the output is then not sorted).
+ * FF_ECUDA: a CUDA call failed.  The reason is given by ff_last_error(NULL).
  */
 #define FF_NOALLOC_MAX_N 131072
 ff_status ff_morton_order_noalloc(const float *pos, int64_t n, uint64_t *keys_out,

@@ -1,20 +1,24 @@
 // Allocation-free Morton ordering (declared in include/ff.h).
 //
-// Some callers may not allocate device memory at all: code that runs while a
-// stream is being captured (cudaMalloc is not allowed there), applications
-// whose memory is owned by their own pool or allocator, and latency-bound
-// loops that cannot afford an allocation on the way.  For them this entry
-// point computes the root cube, the 63-bit Morton keys and the stable key
-// sort of up to kNoAllocMaxN particles using only the caller's input and
-// output buffers plus one fixed scratch array that lives in this file.
+// Some callers may not allocate device memory at all: applications whose
+// device memory is owned by their own pool or allocator (which must see every
+// byte), and latency-bound loops that cannot afford an allocation on the way
+// (cudaMalloc may synchronise the device).  For them this entry point
+// computes the root cube, the 63-bit Morton keys and the stable key sort of
+// up to kNoAllocMaxN particles using only the caller's input and output
+// buffers plus one fixed scratch array that lives in this file.  The call
+// reads its error word back to the host and waits for the stream, so it
+// cannot be issued while that stream is being captured into a graph.
 //
 // The scratch array is a static device variable: every GPU that loads the
 // library keeps it (about 3.7 MB) until the process exits.  Its name in host
 // code is only a host-side stand-in, so the device address is looked up with
 // cudaGetSymbolAddress, once per device, on the first call made with that
-// device current.  All calls share the array and it keeps the contents of the
-// last call; calls whose GPU work overlaps (different streams, or several host
-// threads on one device) race on it.
+// device current; the address is kept for the life of the process, so the
+// entry point must not be used on a device after cudaDeviceReset.  All calls
+// share the array and it keeps the contents of the last call; calls whose GPU
+// work overlaps (different streams, or several host threads on one device)
+// race on it.
 #include <cstddef>
 #include <cstdio>
 #include <mutex>
@@ -129,6 +133,8 @@ ff_status ff_morton_order_noalloc(const float* pos, int64_t n, uint64_t* keys_ou
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return noalloc_fail(FF_ECUDA, "cudaStreamSynchronize", e);
     if (hflag & ffk::FLAG_NONFINITE) return noalloc_fail(FF_ENONFINITE, "a particle position is NaN or infinite");
+    if (hflag & ffk::FLAG_SORT)
+        return noalloc_fail(FF_EDEVICE, "a sort tile gave up waiting for an earlier tile's counts");
     return FF_OK;
 }
 

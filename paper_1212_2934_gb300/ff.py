@@ -445,8 +445,24 @@ FF_NOALLOC_MAX_N = 131072
 
 def ff_morton_order_noalloc(pos, keys_out, order_out, stream=None):
     """Allocation-free Morton ordering of an (n, 3) float32 CUDA tensor into uint64 keys and
-    int32 order tensors (device); see include/ff.h.  stream: a torch CUDA stream or None."""
+    int32 order tensors (device); see include/ff.h.  stream: a torch CUDA stream or None.
+    The tensors are checked before the call (the library sees only raw pointers)."""
+    def need(ok, what):
+        if not ok:
+            raise ValueError("ff_morton_order_noalloc: " + what)
+
+    import torch
+
+    need(getattr(pos, "is_cuda", False) and pos.dtype == torch.float32 and pos.dim() == 2
+         and pos.shape[1] == 3 and pos.is_contiguous(),
+         "pos must be a contiguous (n, 3) float32 CUDA tensor")
     n = int(pos.shape[0])
+    for t, size, name in ((keys_out, 8, "keys_out"), (order_out, 4, "order_out")):
+        need(getattr(t, "is_cuda", False) and t.is_contiguous() and t.element_size() == size
+             and not t.is_floating_point() and not t.is_complex() and t.numel() >= n
+             and t.device == pos.device,
+             "%s must be a contiguous %d-byte integer CUDA tensor on pos's device with at "
+             "least n elements" % (name, size))
     sp = None if stream is None else C.c_void_p(stream.cuda_stream)
     _check(None, lib().ff_morton_order_noalloc(C.c_void_p(pos.data_ptr()), n,
                                                C.c_void_p(keys_out.data_ptr()),

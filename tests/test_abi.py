@@ -92,3 +92,20 @@ def test_struct_layout_matches_header(libff, tmp_path):
     assert vals == [ctypes.sizeof(P), P.seed.offset, P.stream.offset,
                     ctypes.sizeof(libff.ff_energy_t), ctypes.sizeof(libff.ff_tree_info_t),
                     P.h_ext.offset]
+
+
+def test_noalloc_binding_rejects_bad_tensors(libff):
+    """The allocation-free entry point sees raw pointers only; its binding refuses tensors
+    whose bytes the library would misread (host memory, wrong dtype, shape or length)."""
+    torch = pytest.importorskip("torch")
+    n = 64
+    pos = torch.zeros((n, 3), dtype=torch.float32)
+    keys = torch.zeros(n, dtype=torch.int64)
+    order = torch.zeros(n, dtype=torch.int32)
+    cases = [(pos, keys, order),                      # host tensors
+             (pos.double(), keys, order),
+             (pos[:, :2], keys, order),
+             (pos.t(), keys, order)]
+    for p, k, o in cases:
+        with pytest.raises(ValueError):
+            libff.ff_morton_order_noalloc(p, k, o)
