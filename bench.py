@@ -39,7 +39,37 @@ UNIT = "particle-steps/s"
 # separation 3, r^2 5, rsqrt 1, powers of 1/r 4, three dot products 15,
 # field 14, force 26
 FLOPS_PER_INTERACTION = 68
-SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0  # GB300 unit counts and maximum SM clock
+
+
+def simt_peaks(dev):
+    """FP32 and FP64 fused multiply-add rates of this GPU, measured by the library's FMA-chain
+    microbenchmark (libffpeak.so: every thread runs independent FMA chains; CUDA events; the
+    SM clock read from the SMs' own counters during the run).  The FP32 peak is the larger of
+    the scalar and the paired (two floats per instruction) forms."""
+    import ctypes
+
+    from paper_1212_2934_gb300 import _build
+
+    L = ctypes.CDLL(_build.PEAK_LIB)
+    L.ffp_simt_peak.restype = ctypes.c_int
+    out = {}
+    for kind, name in ((0, "fp32_fma"), (1, "fp32_fma2"), (2, "fp64_fma")):
+        tf, ms, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        rc = L.ffp_simt_peak(kind, int(dev), ctypes.byref(tf), ctypes.byref(ms),
+                             ctypes.byref(mhz))
+        if rc != 0:
+            raise RuntimeError("SIMT peak microbenchmark failed (%s): %d" % (name, rc))
+        out[name] = {"tflops": tf.value, "launch_ms": ms.value, "sm_mhz": mhz.value}
+    out["fp32_tflops"] = max(out["fp32_fma"]["tflops"], out["fp32_fma2"]["tflops"])
+    out["fp64_tflops"] = out["fp64_fma"]["tflops"]
+    return out
+
+
+def peak_note(pk, key):
+    parts = ["%s %.2f TFLOP/s at %.0f MHz" % (k, pk[k]["tflops"], pk[k]["sm_mhz"])
+             for k in (("fp32_fma", "fp32_fma2") if key == "fp32" else ("fp64_fma",))]
+    return ("measured by the FMA-chain microbenchmark (csrc/peak/simt_peak.cu) in this run: "
+            + "; ".join(parts))
 
 
 def parse():
@@ -323,6 +353,57 @@ def cpu_step_sample(pos, u, theta, leaf_max, side, sample, threads=None):
     t_int = t4 - t3
     per_step = t_build + t_int + t_trav * n / len(idx)
     return n / per_step, (t4 - t0), oracle.get_threads(), len(idx)
+
+
+def cpu_allpairs_sample(pos, u, targets, threads=None):
+    """The oracle's FP64 all-pairs field and force (Sec. 3.1) on `targets` sampled target
+    particles against all n sources; returns (particle-steps/s extrapolated to all n targets,
+    seconds, threads)."""
+    import oracle
+
+    if threads:
+        oracle.set_threads(threads)
+    n = pos.shape[0]
+    p64 = pos.astype(np.float32).astype(np.float64)
+    idx = np.sort(np.random.default_rng(6).choice(n, size=min(targets, n), replace=False))
+    t0 = time.perf_counter()
+    oracle.allpairs(p64, np.asarray(u, dtype=np.float64), lj_eps=1.0, only=idx)
+    secs = time.perf_counter() - t0
+    return n / (secs * n / len(idx)), secs, oracle.get_threads()
+
+
+def cpu_baselines(pos, u, theta, leaf_max, side, sample):
+    """The oracle on this host: Barnes-Hut on all cores (the headline CPU figure), Barnes-Hut
+    on one core (the paper's Table 1 convention) and all-pairs on all cores and on one core,
+    each on a bounded sample scaled to one full step."""
+    import oracle
+
+    cores = oracle.get_threads()
+    rate, cpu_s, threads, s = cpu_step_sample(pos, u, theta, leaf_max, side, sample)
+    n = pos.shape[0]
+    out = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": "tree build, aggregation and integration of all %d particles plus "
+                     "traversal of %d sampled particles (%.1f s of CPU work), scaled to one "
+                     "full step" % (n, s, cpu_s)}
+    try:
+        r1, s1, t1, m1 = cpu_step_sample(pos, u, theta, leaf_max, side, max(sample // 32, 1024),
+                                         threads=1)
+        out["single_core"] = {"value": r1, "unit": UNIT, "cores": t1,
+                              "sample": "as above on one core, traversal of %d sampled "
+                                        "particles (%.1f s), scaled to one full step" % (m1, s1)}
+        ra, sa, ta = cpu_allpairs_sample(pos, u, 2048, threads=cores)
+        out["allpairs"] = {"value": ra, "unit": UNIT, "cores": ta,
+                           "sample": "FP64 all-pairs field and force of 2048 sampled targets "
+                                     "against all %d sources (%.1f s), extrapolated to all "
+                                     "targets" % (n, sa)}
+        ra1, sa1, ta1 = cpu_allpairs_sample(pos, u, 128, threads=1)
+        out["allpairs_single_core"] = {
+            "value": ra1, "unit": UNIT, "cores": ta1,
+            "sample": "the same for 128 sampled targets on one core (%.1f s), extrapolated to "
+                      "all targets" % sa1}
+    finally:
+        oracle.set_threads(cores)
+    return out
 
 
 def cpu_batched_sample(batch, theta, leaf_max, stride=8):
@@ -609,10 +690,12 @@ def run_ours(args):
     info = ff.ff_tree_info(ctxc)
     del ctxc, xs, hc
 
-    # roofline of the dominant kernel (the traversal), from this run's events
+    # roofline of the dominant kernel (the traversal), from this run's events, against the
+    # FP32 peak measured on this GPU right after the timed region
     field_ms = prof["ms"]["field"] / max(prof["calls"]["field"], 1)
     flops = info["interactions"] * FLOPS_PER_INTERACTION
-    peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    peaks = simt_peaks(dev)
+    peak = peaks["fp32_tflops"]
     achieved = flops / (field_ms / 1e3) / 1e12
     traffic = traffic_for(os.path.join(ROOT, "paper_1212_2934_gb300", "csrc", "k_field.cu"), n,
                           args.workload, args.theta, args.leaf_max)
@@ -665,7 +748,21 @@ def run_ours(args):
             flush.zero_()
         barrier()
         ms64 = sum(a.elapsed_time(b) for a, b in e64) / k64
+        # the FP64 traversal's own launch time and interaction count, for its roofline
+        ff.ff_profile(ctx64, True)
+        for _ in range(2):
+            ff.ff_step(ctx64, 1)
+            flush.zero_()
+        prof64 = ff.ff_profile_read(ctx64)
         del ctx64
+        field64_ms = prof64["ms"]["field"] / max(prof64["calls"]["field"], 1)
+        ctxc64 = ff.ff_create(params(precision="f64", count_interactions=1))
+        ff.ff_set_particles(ctxc64, pos_d.double(), u_d.double())
+        h64 = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        ff.ff_dipolar_field(ctxc64, ff.FF_ALGO_BH, args.theta, True, h64, torch.empty_like(h64))
+        info64 = ff.ff_tree_info(ctxc64)
+        del ctxc64, h64
+        ach64 = info64["interactions"] * FLOPS_PER_INTERACTION / (field64_ms / 1e3) / 1e12
         # ---- FP32 Barnes-Hut with up to 8 particles per leaf (same theta; near field exact
         # inside leaves) -- a tuning comparison, not the paper's one-particle leaves
         ctx8 = ff.ff_create(params(leaf_max=8, count_interactions=0))
@@ -734,7 +831,14 @@ def run_ours(args):
             "ap_fp32": {"particle_steps_per_s": n / (ms_ap / 1e3), "ms_per_step": ms_ap,
                         "pair_interactions_per_s": n * (n - 1) / (ap_field_ms / 1e3),
                         "field_tflops": n * (n - 1) * FLOPS_PER_INTERACTION / (ap_field_ms / 1e3) / 1e12},
-            "bh_fp64": {"particle_steps_per_s": n / (ms64 / 1e3), "ms_per_step": ms64},
+            "bh_fp64": {"particle_steps_per_s": n / (ms64 / 1e3), "ms_per_step": ms64,
+                        "roofline": {"bound": "alu", "kernel": "k_bh<double> (FP64 traversal)",
+                                     "achieved": ach64, "peak": peaks["fp64_tflops"],
+                                     "unit": "TFLOP/s", "frac": ach64 / peaks["fp64_tflops"],
+                                     "avg_launch_ms": field64_ms,
+                                     "algorithmic_flops_per_launch":
+                                         info64["interactions"] * FLOPS_PER_INTERACTION,
+                                     "peak_note": peak_note(peaks, "fp64")}},
             "bh_fp32_leaf8": {"particle_steps_per_s": n / (ms8 / 1e3), "ms_per_step": ms8,
                               "note": "leaf_max = 8 (the paper's leaves hold one particle)"},
             "accuracy_vs_allpairs": dict(extras_accuracy, note=(
@@ -806,8 +910,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_bh (Barnes-Hut traversal)",
-                     "peak_note": "FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x "
-                                  "2070 MHz (no FP32 SIMT peak in the measured peaks file)",
+                     "peak_note": peak_note(peaks, "fp32"),
+                     "peaks_measured": peaks,
                      "algorithmic_flops_per_launch": flops,
                      "avg_launch_ms": field_ms,
                      "timing": "CUDA events around the traversal launch on the library's stream, "
@@ -824,13 +928,8 @@ def run_ours(args):
     if e2e is not None:
         line["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_extras and batch is None:
-        rate, cpu_s, threads, s = cpu_step_sample(pos, u, args.theta, args.leaf_max, side,
-                                                  262144 if args.workload == "phi05" else 131072)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": "tree build, aggregation and integration of all %d "
-                                          "particles plus traversal of %d sampled particles "
-                                          "(%.1f s of CPU work), scaled to one full step"
-                                          % (n, s, cpu_s)}
+        line["cpu_baseline"] = cpu_baselines(pos, u, args.theta, args.leaf_max, side,
+                                             262144 if args.workload == "phi05" else 131072)
     elif rank == 0 and world == 1 and not args.no_extras:
         rate, cpu_s, threads, nsys_s, m = cpu_batched_sample(batch, args.theta, args.leaf_max)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",

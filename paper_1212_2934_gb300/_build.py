@@ -3,7 +3,9 @@
 The translation units are compiled in parallel for sm_103a only and linked
 with the static CUDA runtime into paper_1212_2934_gb300/libff.so.  Objects go
 to _build/ at the repository root.  A build is skipped when the library is
-newer than every source and header.
+newer than every source and header.  The SIMT peak microbenchmark
+(csrc/peak/simt_peak.cu, the roofline denominators of the arithmetic-bound
+kernels) is built alongside it into libffpeak.so.
 """
 import glob
 import os
@@ -18,6 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libff.so")
 EXPORTS = os.path.join(CSRC, "libff.map")  # linker version script: only ff_* is exported
+PEAK_SRC = os.path.join(CSRC, "peak", "simt_peak.cu")
+PEAK_LIB = os.path.join(PKG, "libffpeak.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -47,9 +51,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
+def _peak_up_to_date() -> bool:
+    return (os.path.exists(PEAK_LIB)
+            and os.path.getmtime(PEAK_LIB) >= max(os.path.getmtime(PEAK_SRC),
+                                                   os.path.getmtime(os.path.abspath(__file__))))
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link libff.so; returns its path."""
+    """Compile and link libff.so (and libffpeak.so); returns the path of libff.so."""
+    peak = None
+    if force or not _peak_up_to_date():
+        peak_tmp = PEAK_LIB + ".tmp%d" % os.getpid()
+        peak = (peak_tmp, subprocess.Popen(
+            [nvcc(), *ARCH, *NVFLAGS, "-shared", "-o", peak_tmp, PEAK_SRC, "-cudart", "static"],
+            stdout=subprocess.PIPE, stderr=subprocess.STDOUT))
     if not force and up_to_date():
+        _finish_peak(peak)
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -73,6 +90,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             failed.append(src)
     if failed:
         raise RuntimeError("nvcc failed on: " + ", ".join(failed))
+    _finish_peak(peak)
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static",
            "-Xlinker", "--version-script=" + EXPORTS]
@@ -81,6 +99,17 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
+
+
+def _finish_peak(peak):
+    if peak is None:
+        return
+    tmp, p = peak
+    out, _ = p.communicate()
+    if p.returncode:
+        sys.stderr.write(out.decode(errors="replace"))
+        raise RuntimeError("nvcc failed on: " + PEAK_SRC)
+    os.replace(tmp, PEAK_LIB)
 
 
 if __name__ == "__main__":
