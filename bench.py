@@ -622,11 +622,15 @@ def run_ours(args):
     ff.ff_set_particles(ctx, pos_d, u_d)
     tuning = None
     if args.group == 0:
-        # the traversal schedule (lanes per walk) is picked by the library's autotuner on this
-        # very workload; every choice gives the same bits, only the speed differs
-        best, tms = ff.ff_tune_traversal(ctx, reps=3)
-        tuning = {"chosen": best, "ms_per_candidate": {str(g): round(m, 4) for g, m in tms.items()}}
-        args.group = best
+        # the traversal's launch schedule (lane group, block shape, blocks per SM) is picked by
+        # the library's autotuner on this very workload; every choice gives the same bits, only
+        # the speed differs
+        scheds = ff.ff_schedules()
+        best, tms = ff.ff_tune_schedule(ctx, reps=3)
+        name = lambda i: "group %d, %d threads x %d blocks/SM" % scheds[i]
+        tuning = {"chosen": name(best),
+                  "ms_per_candidate": {name(i): round(m, 4) for i, m in tms.items()}}
+        args.group = scheds[best][0]
     clocks = Clocks(dev)
     clocks.start()
     for _ in range(W):

@@ -138,7 +138,15 @@ void ff_params_default(ff_params *p);
 
 /*
  * Creates a context for p->n particles on p->device (Sec. 2 model, Sec. 3
- * schemes) and allocates all device memory it will use.  *out receives the
+ * schemes) and allocates its device memory: about 0.5 KB per particle in FP32
+ * and 0.8 KB in FP64 (66 GB and 110 GB at n = 2^27), gradient buffers apart.
+ * The tree's cell arrays start with room for 2 n + 8192 cells (gases, chains
+ * and dense packings use 1.2 to 1.8 cells per particle).  A build that needs
+ * more raises a device flag instead of writing past them; that step and the
+ * ones after it leave the state unchanged, and the next call that waits for
+ * results grows the arrays (to 1.25 x the need, at most 22 n + 1, the most any
+ * tree can have), runs the held-back steps again and completes: results are
+ * those of a context that had the room from the start.  *out receives the
  * context.  FF_EINVAL for out-of-range parameters, FF_ENOMEM, FF_ECUDA;
  * the reason is then given by ff_last_error(NULL).
  */
@@ -239,6 +247,41 @@ ff_status ff_tune_traversal(ff_ctx *ctx, const int32_t *groups, int32_t ngroups,
                             int32_t *best_group, float *ms);
 
 /*
+ * Launch schedules of the traversal (no counterpart in the paper; Sec. 3.2
+ * kernel 5 ran one fixed launch on its GPU).  Schedule i = 1 ..
+ * ff_schedule_count() is a lane group (as traverse_group) with, for the plain
+ * single-precision walk (interaction counting off, no dipole-position terms),
+ * its own compiled block shape: threads per block and the resident blocks per
+ * SM the kernel's register budget is set for; other walks use their group's
+ * default shape.  The traversal is persistent (as many blocks as fit), so the
+ * shape trades registers per thread against resident warps.  Every schedule
+ * gives bit-identical fields and forces (each lane decides and sums for its own
+ * particle in depth-first order).  ff_schedule_info fills the three numbers
+ * (any pointer may be NULL); FF_EINVAL for an index out of range.
+ */
+int32_t ff_schedule_count(void);
+ff_status ff_schedule_info(int32_t index, int32_t *group, int32_t *threads,
+                           int32_t *blocks_per_sm);
+
+/*
+ * Makes schedule `index` (0: traverse_group with its default shape) the
+ * context's traversal launch for later ff_step and ff_dipolar_field calls.
+ * FF_EINVAL for an index out of range.
+ */
+ff_status ff_set_schedule(ff_ctx *ctx, int32_t index);
+
+/*
+ * Schedule autotuner: sorts the current state and builds the tree once (as
+ * ff_dipolar_field with the context's theta, LJ included), times `reps`
+ * traversals (1 .. 100) with every schedule by CUDA events on the context's
+ * stream, and keeps the fastest (minimum over reps; ties to the lower index)
+ * as the context's schedule.  *best_schedule receives it; ms (may be NULL)
+ * receives ff_schedule_count() times in milliseconds, schedule 1 first.
+ * Barnes-Hut contexts only.  Waits.
+ */
+ff_status ff_tune_schedule(ff_ctx *ctx, int32_t reps, int32_t *best_schedule, float *ms);
+
+/*
  * Dipolar energy E = -1/2 sum_k u_k . h_k (Sec. 5; h from algo, LJ excluded)
  * and its gradient with respect to every position and moment.  With
  * FF_ALGO_AP every pair is exact: dE/du = -h and dE/drho = -f (the dipolar
@@ -250,7 +293,8 @@ ff_status ff_tune_traversal(ff_ctx *ctx, const int32_t *groups, int32_t ngroups,
  * The current state is evaluated (and, for Barnes-Hut, sorted into key
  * order); *energy (may be NULL) receives E in FP64; grad_pos and grad_u (may
  * be NULL) receive n x 3 values in the caller's order, dtype/loc as in
- * ff_get_particles.  The Barnes-Hut gradient records one entry per
+ * ff_get_particles.  With both NULL only the field and E are computed (the
+ * cost of one field evaluation).  The Barnes-Hut gradient records one entry per
  * interaction (8 bytes x 2 buffers; about 1000 interactions per particle
  * at theta = 0.5), allocated on first use and grown as needed; 2^32 - 16
  * interactions or more is FF_EINVAL.  Waits.

@@ -118,6 +118,7 @@ struct ff_ctx {
     void* sys_hi = nullptr;          // device: vec4<R>[nsys] upper wall planes
     double* sys_acc = nullptr;       // device: nsys x 4 sums of u and h_dip_z
     int64_t sys_steps = 0;           // steps accumulated in sys_acc
+    int sched = 0;                   // traversal launch schedule (0: traverse_group, default shape)
 
     // stage timing
     struct Mark {
@@ -285,6 +286,7 @@ ffk::DynParams<R> dyn_params(const ff_ctx* c)
     d.sys_hi = static_cast<const ffk::vec4<R>*>(c->sys_hi);
     d.sys_of_pos = c->nsys > 0 ? c->sys_of_pos : nullptr;
     d.sys_acc = c->nsys > 0 ? c->sys_acc : nullptr;
+    d.flags = c->dflags;
     return d;
 }
 
@@ -393,7 +395,7 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = f
                          V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr),
                          (c->p.count_interactions || force_counts) ? c->counts : nullptr,
                          c->dflags, c->work,
-                         traverse_group(c), c->off, segs_of(c), s);
+                         traverse_group(c), c->sched, c->off, segs_of(c), s);
     }
     FF_LAUNCHED(c);
     c->tree_valid = true;
@@ -434,12 +436,28 @@ ff_status do_step(ff_ctx* c)
                           V<R>(b.vel), V<R>(b.u), V<R>(b.om), b.id, c->partials, c->stream);
         ffk::reduce_partials(c->partials, ffk::integrate_blocks(c->n), 1.0 / (double)c->n,
                              0.5 * c->p.inertia, c->obs_step, c->stream);
-        ffk::step_advance(c->dstep, c->stream);
+        ffk::step_advance(c->dstep, c->dflags, c->stream);
     }
     FF_LAUNCHED(c);
     c->cur = 1 - c->cur;
     c->step += 1;
     return FF_OK;
+}
+
+// Internal status: the cell arrays were grown (and skipped steps run again)
+// under the caller, which redoes its work (see retrying).
+constexpr ff_status kRetry = static_cast<ff_status>(-100);
+ff_status recover_cells(ff_ctx* c);
+
+// Runs body again while it reports that the cells were grown under it.
+template <typename F>
+ff_status retrying(ff_ctx* c, F&& body)
+{
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        const ff_status s = body();
+        if (s != kRetry) return s;
+    }
+    return fail(c, FF_EDEVICE, "the tree kept outgrowing its cell arrays");
 }
 
 // Waits for the stream and turns device flags into a status.
@@ -450,10 +468,13 @@ ff_status sync_and_check(ff_ctx* c)
     FF_CUDA(c, cudaStreamSynchronize(c->stream));
     const int fl = *c->hflags;
     if (fl & ffk::FLAG_NONFINITE) return fail(c, FF_ENONFINITE, "a particle position is NaN or infinite");
-    if (fl & ffk::FLAG_CAPACITY) return fail(c, FF_EDEVICE, "tree needs more cells than allocated");
     if (fl & ffk::FLAG_TRAVERSE) return fail(c, FF_EDEVICE, "traversal guard tripped");
     if (fl & ffk::FLAG_AGGREGATE) return fail(c, FF_EDEVICE, "aggregation guard tripped");
     if (fl & ffk::FLAG_SORT) return fail(c, FF_EDEVICE, "sort tile timed out waiting for an earlier tile");
+    if (fl & ffk::FLAG_CAPACITY) {
+        const ff_status s = recover_cells(c);
+        return s == FF_OK ? kRetry : s;
+    }
     return FF_OK;
 }
 
@@ -494,6 +515,56 @@ cudaError_t dalloc(T** p, size_t bytes)
     return cudaMalloc(reinterpret_cast<void**>(p), bytes > 0 ? bytes : 16);
 }
 
+// Cells of the tree.  Every particle starts at most 22 cells (levels 0..21), so
+// 22 n + 1 cells always suffice, but gases, chains and dense packings need 1.2
+// to 1.8 cells per particle: the arrays start at 2 n + 8192 cells and grow when
+// a build needs more (see recover_cells).
+int64_t initial_cells(int64_t n)
+{
+    const int64_t bound = 22 * n + 1;
+    const int64_t start = 2 * n + 8192;
+    return start < bound ? start : bound;
+}
+
+// (Re)allocates every per-cell array for cap cells.
+ff_status alloc_cells(ff_ctx* c, int64_t cap)
+{
+    void* olds[] = {c->cell, c->mom, c->lo, c->sum, c->sum_hi, c->mom_hi, c->q1, c->q2,
+                    c->parent, c->arrive};
+    for (void* q : olds)
+        if (q) cudaFree(q);
+    c->cell = c->mom = c->lo = c->sum = c->q1 = c->q2 = nullptr;
+    c->sum_hi = c->mom_hi = nullptr;
+    c->parent = c->arrive = nullptr;
+    c->cap = 0;
+    const size_t rec = c->rec;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t bytes) {
+        if (e == cudaSuccess) e = dalloc(p, bytes);
+    };
+    A(&c->cell, c->cell_bytes * cap);
+    A(&c->mom, rec * cap);
+    A(&c->lo, rec * cap);
+    A(&c->sum, rec * cap);
+    if (c->mixed) {
+        A(&c->sum_hi, sizeof(ffk::dvec4) * cap);
+        A(&c->mom_hi, sizeof(ffk::dvec4) * cap);
+    }
+    if (c->p.quadrupole) {
+        A(&c->q1, rec * cap);
+        A(&c->q2, rec * cap);
+    }
+    A(&c->parent, sizeof(int) * cap);
+    A(&c->arrive, sizeof(int) * cap);
+    if (e != cudaSuccess)
+        return fail(c, FF_ENOMEM, "device allocation of %lld cells failed: %s", (long long)cap,
+                    cudaGetErrorString(e));
+    c->cap = cap;
+    c->tree_valid = false;
+    c->counts_valid = false;
+    return FF_OK;
+}
+
 ff_status alloc_all(ff_ctx* c)
 {
     const int64_t n = c->n;
@@ -516,23 +587,6 @@ ff_status alloc_all(ff_ctx* c)
     A(&c->off, sizeof(uint32_t) * (n + 1));
     A(&c->scan_tmp, sizeof(uint32_t) * ffk::scan_tmp_words(n));
     A(&c->bbox, sizeof(ffk::BBox));
-    // Every particle starts at most 22 cells (levels 0..21), so 22 n + 1 cells
-    // always suffice.
-    c->cap = 22 * n + 1;
-    A(&c->cell, c->cell_bytes * c->cap);
-    A(&c->mom, rec * c->cap);
-    A(&c->lo, rec * c->cap);
-    A(&c->sum, rec * c->cap);
-    if (c->mixed) {
-        A(&c->sum_hi, sizeof(ffk::dvec4) * c->cap);
-        A(&c->mom_hi, sizeof(ffk::dvec4) * c->cap);
-    }
-    if (c->p.quadrupole) {
-        A(&c->q1, rec * c->cap);
-        A(&c->q2, rec * c->cap);
-    }
-    A(&c->parent, sizeof(int) * c->cap);
-    A(&c->arrive, sizeof(int) * c->cap);
     A(&c->h, rec * n);
     A(&c->f, rec * n);
     A(&c->esr, (c->fp64 ? 8 : 4) * n);
@@ -545,6 +599,8 @@ ff_status alloc_all(ff_ctx* c)
     A(&c->dflags, sizeof(int));
     A(&c->staging, sizeof(double) * 12 * n);
     if (e != cudaSuccess) return fail(c, FF_ENOMEM, "device allocation failed: %s", cudaGetErrorString(e));
+    ff_status st = alloc_cells(c, initial_cells(n));
+    if (st != FF_OK) return st;
     if (cudaMallocHost(reinterpret_cast<void**>(&c->hflags), sizeof(int)) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void**>(&c->hobs), sizeof(double) * ffk::kObs) != cudaSuccess)
         return fail(c, FF_ENOMEM, "pinned host allocation failed");
@@ -619,7 +675,12 @@ ff_status set_particles(ff_ctx* c, const void* pos, const void* u, const void* v
     if ((s = load_array<R>(c, vel, dtype, loc, a.vel, 2)) != FF_OK) return s;
     if ((s = load_array<R>(c, om, dtype, loc, a.om, 3)) != FF_OK) return s;
     ffk::iota32(a.id, c->n, c->stream);
+    // a new state: earlier flags no longer apply, and steps that a too small cell array
+    // held back are dropped with the state they were for (the noise counter follows
+    // the host's step count)
     FF_CUDA(c, cudaMemsetAsync(c->dflags, 0, sizeof(int), c->stream));
+    const unsigned long long v = (unsigned long long)c->step;
+    FF_CUDA(c, cudaMemcpyAsync(c->dstep, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
     FF_LAUNCHED(c);
     FF_CUDA(c, cudaStreamSynchronize(c->stream));
     return FF_OK;
@@ -792,16 +853,20 @@ void sort_entries(ff_ctx* c, int64_t ne, int64_t nsrc, const uint32_t** keys,
 // Energy -1/2 sum u.h (FP64) and its gradient with the opening decisions of
 // this evaluation frozen (k_grad.cu), in sorted order in g_pos, g_u.
 template <typename R>
-ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy)
+ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy, bool grads)
 {
     const int64_t n = c->n;
     cudaStream_t s = c->stream;
     ff_status st;
-    if (!c->g_pos) {
+    if (!grads) {
+        // the energy alone: one field evaluation and the FP64 reduction
+        if ((st = eval_field<R>(c, algo, theta, 0)) != FF_OK) return st;
+    } else if (!c->g_pos) {
         if ((st = grow(c, reinterpret_cast<char**>(&c->g_pos), c->rec * n)) != FF_OK) return st;
         if ((st = grow(c, reinterpret_cast<char**>(&c->g_u), c->rec * n)) != FF_OK) return st;
     }
-    if (algo == FF_ALGO_AP) {
+    if (!grads) {
+    } else if (algo == FF_ALGO_AP) {
         if ((st = eval_ap<R>(c, 0)) != FF_OK) return st;
         ffk::grad_from_field<R>(V<R>(c->h), V<R>(c->f), n, V<R>(c->g_pos), V<R>(c->g_u), s);
         FF_LAUNCHED(c);
@@ -842,10 +907,11 @@ ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy)
 
 namespace {
 
-// Sorts and builds once, then times the traversal for each lane group.
+// Sorts and builds once, then times the traversal for each candidate: lane group
+// groups[i] with launch schedule scheds[i] (scheds may be null: the default shape).
 template <typename R>
-ff_status tune_traversal(ff_ctx* c, const int32_t* groups, int ng, int reps, float* ms_out,
-                         int* best)
+ff_status tune_traversal(ff_ctx* c, const int32_t* groups, const int32_t* scheds, int ng, int reps,
+                         float* ms_out, int* best)
 {
     ff_status s = eval_bh<R>(c, c->p.theta, 1);
     if (s != FF_OK) return s;
@@ -870,13 +936,13 @@ ff_status tune_traversal(ff_ctx* c, const int32_t* groups, int ng, int reps, flo
             cudaEventRecord(e[0], c->stream);
             ffk::bh_field<R>(V<R>(a.pos), V<R>(a.u), c->n, t, fp, V<R>(c->h), V<R>(c->f),
                              static_cast<R*>(c->esr), nullptr, c->dflags, c->work, groups[g],
-                             c->off, segs_of(c), c->stream);
+                             scheds ? scheds[g] : 0, c->off, segs_of(c), c->stream);
             cudaEventRecord(e[1], c->stream);
         }
     FF_LAUNCHED(c);
     s = sync_and_check(c);
     float best_ms = 0.0f;
-    *best = groups[0];
+    *best = 0;
     for (int g = 0; g < ng && s == FF_OK; ++g) {
         float m = 0.0f;
         for (int r = 0; r < reps; ++r) {
@@ -887,7 +953,7 @@ ff_status tune_traversal(ff_ctx* c, const int32_t* groups, int ng, int reps, flo
         if (ms_out) ms_out[g] = m;
         if (g == 0 || m < best_ms) {
             best_ms = m;
-            *best = groups[g];
+            *best = g;
         }
     }
     return s;
@@ -1188,8 +1254,10 @@ ff_status ff_get_particles(ff_ctx* c, void* pos, void* u, void* vel, void* omega
     ff_status s = usable(c, true);
     if (s != FF_OK) return s;
     if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
-    return c->fp64 ? get_particles<double>(c, pos, u, vel, omega, dtype, loc)
-                   : get_particles<float>(c, pos, u, vel, omega, dtype, loc);
+    return retrying(c, [&] {
+        return c->fp64 ? get_particles<double>(c, pos, u, vel, omega, dtype, loc)
+                       : get_particles<float>(c, pos, u, vel, omega, dtype, loc);
+    });
 }
 
 ff_status ff_dipolar_field(ff_ctx* c, int32_t algo, double theta, int32_t include_sr, void* h_out,
@@ -1202,8 +1270,10 @@ ff_status ff_dipolar_field(ff_ctx* c, int32_t algo, double theta, int32_t includ
     if (algo == FF_ALGO_AP && c->nsys > 0) return fail(c, FF_EINVAL, "all-pairs is not available for batched systems");
     if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(c, FF_EINVAL, "theta must be finite and >= 0");
     if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
-    return c->fp64 ? dipolar_field<double>(c, algo, theta, include_sr, h_out, f_out, dtype, loc)
-                   : dipolar_field<float>(c, algo, theta, include_sr, h_out, f_out, dtype, loc);
+    return retrying(c, [&] {
+        return c->fp64 ? dipolar_field<double>(c, algo, theta, include_sr, h_out, f_out, dtype, loc)
+                       : dipolar_field<float>(c, algo, theta, include_sr, h_out, f_out, dtype, loc);
+    });
 }
 
 ff_status ff_energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy, void* grad_pos,
@@ -1218,18 +1288,21 @@ ff_status ff_energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy, 
     if (!valid_dtype_loc(dtype, loc)) return fail(c, FF_EINVAL, "bad dtype or loc");
     if (c->p.quadrupole && algo == FF_ALGO_BH)
         return fail(c, FF_EINVAL, "the gradient uses the paper's pseudo-particles (quadrupole off)");
-    s = c->fp64 ? energy_grad<double>(c, algo, theta, energy)
-                : energy_grad<float>(c, algo, theta, energy);
-    if (s != FF_OK) return s;
-    const uint32_t* id = c->st[c->cur].id;
-    if (c->fp64) {
-        if ((s = store_array<double>(c, c->g_pos, id, grad_pos, dtype, loc, 0)) != FF_OK) return s;
-        if ((s = store_array<double>(c, c->g_u, id, grad_u, dtype, loc, 1)) != FF_OK) return s;
-    } else {
-        if ((s = store_array<float>(c, c->g_pos, id, grad_pos, dtype, loc, 0)) != FF_OK) return s;
-        if ((s = store_array<float>(c, c->g_u, id, grad_u, dtype, loc, 1)) != FF_OK) return s;
-    }
-    return sync_and_check(c);
+    const bool grads = grad_pos != nullptr || grad_u != nullptr;
+    return retrying(c, [&] {
+        ff_status st = c->fp64 ? energy_grad<double>(c, algo, theta, energy, grads)
+                               : energy_grad<float>(c, algo, theta, energy, grads);
+        if (st != FF_OK || !grads) return st;
+        const uint32_t* id = c->st[c->cur].id;
+        if (c->fp64) {
+            if ((st = store_array<double>(c, c->g_pos, id, grad_pos, dtype, loc, 0)) != FF_OK) return st;
+            if ((st = store_array<double>(c, c->g_u, id, grad_u, dtype, loc, 1)) != FF_OK) return st;
+        } else {
+            if ((st = store_array<float>(c, c->g_pos, id, grad_pos, dtype, loc, 0)) != FF_OK) return st;
+            if ((st = store_array<float>(c, c->g_u, id, grad_u, dtype, loc, 1)) != FF_OK) return st;
+        }
+        return sync_and_check(c);
+    });
 }
 
 ff_status ff_mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz, double* dmz_dh)
@@ -1243,17 +1316,25 @@ ff_status ff_mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz
     if (every < 1) return fail(c, FF_EINVAL, "every must be >= 1");
     if (c->nsys > 0) return fail(c, FF_EINVAL, "the sensitivity is for a single system");
     if (c->p.algo != FF_ALGO_BH) return fail(c, FF_EINVAL, "the context does not use Barnes-Hut");
-    return c->fp64 ? mz_sensitivity<double>(c, nsteps, every, mz, dmz_dh)
-                   : mz_sensitivity<float>(c, nsteps, every, mz, dmz_dh);
+    // steps issued before this call are complete (and their trees fitted) first
+    if ((s = retrying(c, [&] { return sync_and_check(c); })) != FF_OK) return s;
+    s = c->fp64 ? mz_sensitivity<double>(c, nsteps, every, mz, dmz_dh)
+                : mz_sensitivity<float>(c, nsteps, every, mz, dmz_dh);
+    if (s == kRetry)
+        return fail(c, FF_EDEVICE, "a tree outgrew the cell arrays during the run; they have been "
+                                   "grown, set the state again and repeat the call");
+    return s;
 }
 
-ff_status ff_step(ff_ctx* c, int64_t nsteps)
+}  // extern "C"
+
+namespace {
+
+// nsteps steps, each one captured CUDA graph launch (eager launches while stage
+// timing is on); asynchronous.
+ff_status run_steps(ff_ctx* c, int64_t nsteps)
 {
-    LaunchTally tally_(c);
-    ff_status s = usable(c, true);
-    if (s != FF_OK) return s;
-    if (nsteps < 0) return fail(c, FF_EINVAL, "nsteps must be >= 0");
-    if (c->p.algo == FF_ALGO_AP && c->nsys > 0) return fail(c, FF_EINVAL, "all-pairs is not available for batched systems");
+    ff_status s = FF_OK;
     if (c->prof) {
         // stage timing needs the events between stages: launch eagerly
         for (int64_t k = 0; k < nsteps; ++k) {
@@ -1299,6 +1380,47 @@ ff_status ff_step(ff_ctx* c, int64_t nsteps)
     return FF_OK;
 }
 
+// A build needed more cells than allocated (FLAG_CAPACITY): that step and every
+// step after it left the state and the step counter unchanged.  Grows the cell
+// arrays to 1.25 x what the current state needs, clears the flag and runs again
+// the steps that were issued since.  The caller then redoes its own work.
+ff_status recover_cells(ff_ctx* c)
+{
+    uint32_t need = 0;
+    unsigned long long dstep = 0;
+    FF_CUDA(c, cudaMemcpy(&need, c->off + c->n, sizeof(need), cudaMemcpyDeviceToHost));
+    FF_CUDA(c, cudaMemcpy(&dstep, c->dstep, sizeof(dstep), cudaMemcpyDeviceToHost));
+    const int64_t bound = 22 * c->n + 1;
+    int64_t want = (int64_t)need + (int64_t)need / 4 + 8192;
+    if (want <= c->cap) want = 2 * c->cap;
+    if (want > bound) want = bound;
+    drop_graphs(c);  // the captured steps use the old arrays
+    ff_status s = alloc_cells(c, want);
+    if (s != FF_OK) return s;
+    FF_CUDA(c, cudaMemsetAsync(c->dflags, 0, sizeof(int), c->stream));
+    const int64_t missing = c->step - (int64_t)dstep;
+    if (missing > 0) {
+        c->step = (int64_t)dstep;
+        if (c->nsys > 0) c->sys_steps -= missing;
+        if ((s = run_steps(c, missing)) != FF_OK) return s;
+    }
+    return FF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ff_status ff_step(ff_ctx* c, int64_t nsteps)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (nsteps < 0) return fail(c, FF_EINVAL, "nsteps must be >= 0");
+    if (c->p.algo == FF_ALGO_AP && c->nsys > 0) return fail(c, FF_EINVAL, "all-pairs is not available for batched systems");
+    return run_steps(c, nsteps);
+}
+
 ff_status ff_energy(ff_ctx* c, ff_energy_t* out)
 {
     LaunchTally tally_(c);
@@ -1306,7 +1428,7 @@ ff_status ff_energy(ff_ctx* c, ff_energy_t* out)
     if (s != FF_OK) return s;
     if (!out) return fail(c, FF_EINVAL, "out is NULL");
     if (c->p.algo == FF_ALGO_AP && c->nsys > 0) return fail(c, FF_EINVAL, "all-pairs is not available for batched systems");
-    return c->fp64 ? energy<double>(c, out) : energy<float>(c, out);
+    return retrying(c, [&] { return c->fp64 ? energy<double>(c, out) : energy<float>(c, out); });
 }
 
 ff_status ff_get_step(const ff_ctx* c, int64_t* step)
@@ -1332,7 +1454,7 @@ ff_status ff_synchronize(ff_ctx* c)
 {
     ff_status s = usable(c, false);
     if (s != FF_OK) return s;
-    return sync_and_check(c);
+    return retrying(c, [&] { return sync_and_check(c); });
 }
 
 ff_status ff_tree_info(ff_ctx* c, ff_tree_info_t* out)
@@ -1341,7 +1463,7 @@ ff_status ff_tree_info(ff_ctx* c, ff_tree_info_t* out)
     if (s != FF_OK) return s;
     if (!out) return fail(c, FF_EINVAL, "out is NULL");
     if (!c->tree_valid) return fail(c, FF_ESTATE, "no Barnes-Hut tree has been built");
-    if ((s = sync_and_check(c)) != FF_OK) return s;
+    if ((s = retrying(c, [&] { return sync_and_check(c); })) != FF_OK) return s;
     std::memset(out, 0, sizeof(*out));
     uint32_t nc = 0;
     FF_CUDA(c, cudaMemcpy(&nc, c->off + c->n, sizeof(uint32_t), cudaMemcpyDeviceToHost));
@@ -1406,7 +1528,7 @@ ff_status ff_get_tree(ff_ctx* c, uint64_t* keys, uint32_t* order, int32_t* pbegi
     if (s != FF_OK) return s;
     if (!c->tree_valid) return fail(c, FF_ESTATE, "no Barnes-Hut tree has been built");
     if (dtype != FF_DTYPE_F32 && dtype != FF_DTYPE_F64) return fail(c, FF_EINVAL, "bad dtype");
-    if ((s = sync_and_check(c)) != FF_OK) return s;
+    if ((s = retrying(c, [&] { return sync_and_check(c); })) != FF_OK) return s;
     const int64_t n = c->n;
     uint32_t nc = 0;
     FF_CUDA(c, cudaMemcpy(&nc, c->off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost));
@@ -1459,7 +1581,7 @@ ff_status ff_get_counts(ff_ctx* c, int32_t* accepted, int32_t* pairs, int32_t* o
     int32_t* stg = static_cast<int32_t*>(c->staging);
     ffk::scatter_counts<float>(c->counts, c->st[c->cur].id, n, stg, stg + n, stg + 2 * n, c->stream);
     FF_LAUNCHED(c);
-    if ((s = sync_and_check(c)) != FF_OK) return s;
+    if ((s = retrying(c, [&] { return sync_and_check(c); })) != FF_OK) return s;
     int32_t* dst[3] = {accepted, pairs, opened};
     for (int q = 0; q < 3; ++q)
         if (dst[q]) FF_CUDA(c, cudaMemcpy(dst[q], stg + q * n, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
@@ -1558,14 +1680,72 @@ ff_status ff_tune_traversal(ff_ctx* c, const int32_t* groups, int32_t ngroups, i
     if (reps < 1 || reps > 100) return fail(c, FF_EINVAL, "reps must be 1 .. 100");
     if (c->p.algo != FF_ALGO_BH) return fail(c, FF_EINVAL, "the context does not use Barnes-Hut");
     int best = 0;
-    s = c->fp64 ? tune_traversal<double>(c, groups, ngroups, reps, ms, &best)
-                : tune_traversal<float>(c, groups, ngroups, reps, ms, &best);
-    if (s != FF_OK) return s;
-    if (c->p.traverse_group != best) {
-        c->p.traverse_group = best;
+    const int sched0 = c->sched;
+    c->sched = 0;  // a group choice replaces a tuned launch schedule
+    s = retrying(c, [&] {
+        return c->fp64 ? tune_traversal<double>(c, groups, nullptr, ngroups, reps, ms, &best)
+                       : tune_traversal<float>(c, groups, nullptr, ngroups, reps, ms, &best);
+    });
+    if (s != FF_OK) {
+        c->sched = sched0;
+        return s;
+    }
+    if (c->p.traverse_group != groups[best] || sched0 != 0) {
+        c->p.traverse_group = groups[best];
         drop_graphs(c);  // the captured step launches the old schedule
     }
-    *best_group = best;
+    *best_group = groups[best];
+    return FF_OK;
+}
+
+int32_t ff_schedule_count(void) { return ffk::kNumSchedules; }
+
+ff_status ff_schedule_info(int32_t index, int32_t* group, int32_t* threads, int32_t* blocks_per_sm)
+{
+    if (index < 1 || index > ffk::kNumSchedules) return FF_EINVAL;
+    const ffk::Schedule& q = ffk::kSchedules[index - 1];
+    if (group) *group = q.group;
+    if (threads) *threads = q.threads;
+    if (blocks_per_sm) *blocks_per_sm = q.blocks_per_sm;
+    return FF_OK;
+}
+
+ff_status ff_set_schedule(ff_ctx* c, int32_t index)
+{
+    if (!c) return FF_EINVAL;
+    if (index < 0 || index > ffk::kNumSchedules)
+        return fail(c, FF_EINVAL, "schedule must be 0 .. %d", ffk::kNumSchedules);
+    if (c->sched != index) {
+        c->sched = index;
+        drop_graphs(c);
+    }
+    return FF_OK;
+}
+
+ff_status ff_tune_schedule(ff_ctx* c, int32_t reps, int32_t* best_schedule, float* ms)
+{
+    LaunchTally tally_(c);
+    ff_status s = usable(c, true);
+    if (s != FF_OK) return s;
+    if (!best_schedule) return fail(c, FF_EINVAL, "best_schedule is required");
+    if (reps < 1 || reps > 100) return fail(c, FF_EINVAL, "reps must be 1 .. 100");
+    if (c->p.algo != FF_ALGO_BH) return fail(c, FF_EINVAL, "the context does not use Barnes-Hut");
+    int32_t groups[ffk::kNumSchedules], scheds[ffk::kNumSchedules];
+    for (int i = 0; i < ffk::kNumSchedules; ++i) {
+        groups[i] = ffk::kSchedules[i].group;
+        scheds[i] = i + 1;
+    }
+    int best = 0;
+    s = retrying(c, [&] {
+        return c->fp64 ? tune_traversal<double>(c, groups, scheds, ffk::kNumSchedules, reps, ms, &best)
+                       : tune_traversal<float>(c, groups, scheds, ffk::kNumSchedules, reps, ms, &best);
+    });
+    if (s != FF_OK) return s;
+    if (c->sched != best + 1) {
+        c->sched = best + 1;
+        drop_graphs(c);
+    }
+    *best_schedule = best + 1;
     return FF_OK;
 }
 
@@ -1574,7 +1754,7 @@ ff_status ff_system_moments(ff_ctx* c, double* out, int64_t* nsteps, int32_t res
     ff_status s = usable(c, false);
     if (s != FF_OK) return s;
     if (c->nsys < 1) return fail(c, FF_ESTATE, "no systems set (ff_set_systems)");
-    if ((s = sync_and_check(c)) != FF_OK) return s;
+    if ((s = retrying(c, [&] { return sync_and_check(c); })) != FF_OK) return s;
     if (out) FF_CUDA(c, cudaMemcpy(out, c->sys_acc, sizeof(double) * 4 * c->nsys, cudaMemcpyDeviceToHost));
     if (nsteps) *nsteps = c->sys_steps;
     if (reset) {

@@ -126,6 +126,9 @@ struct DynParams {
     const vec4<R>* sys_hi;               // nseg records: box_hi + 1/2
     const uint32_t* sys_of_pos;
     double* sys_acc;                     // nseg x 4 (u_x, u_y, u_z, h_dip_z), accumulated
+    // the context's error flags (null: none): a step taken while FLAG_CAPACITY is
+    // raised (its tree did not fit) leaves the state unchanged
+    const int* flags;
 };
 
 // What the traversal reads for every visited cell, in one record (32 bytes
@@ -303,10 +306,21 @@ void grad_from_field(const vec4<R>* h, const vec4<R>* f, int64_t n, vec4<R>* gra
 constexpr int kWorkSegments = 1024;
 // off = the build's cell offsets (the first cell of position p is off[p]);
 // with several systems a particle walks only its own system's cells.
+// sched: 0, or one of the launch schedules below (1 .. kNumSchedules), which sets
+// the group and, for the plain FP32 walk, the block shape.
+struct Schedule {
+    int group;          // lanes walking together
+    int threads;        // threads per block
+    int blocks_per_sm;  // resident blocks the register budget is set for
+};
+constexpr int kNumSchedules = 10;
+constexpr Schedule kSchedules[kNumSchedules] = {
+    {1, 128, 12}, {1, 128, 10}, {1, 128, 8}, {1, 256, 6}, {1, 256, 4},
+    {1, 64, 24},  {1, 64, 16},  {2, 128, 12}, {4, 128, 12}, {8, 128, 12}};
 template <typename R>
 void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
               vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
-              const uint32_t* off, Segs sg, cudaStream_t s);
+              int sched, const uint32_t* off, Segs sg, cudaStream_t s);
 
 // All-pairs sum (Sec. 3.1, Algorithm 1).
 template <typename R>
@@ -340,8 +354,8 @@ void observables(int64_t n, const vec4<R>* pos, const vec4<R>* vel, const vec4<R
                  double* partials, cudaStream_t s);
 void reduce_partials(const double* partials, int nblocks, double inv_n, double inertia_half,
                      double* out, cudaStream_t s);
-// Advances the device step counter by one.
-void step_advance(unsigned long long* step, cudaStream_t s);
+// Advances the device step counter by one (not while FLAG_CAPACITY is raised).
+void step_advance(unsigned long long* step, const int* flags, cudaStream_t s);
 // sets the device step counter (restoring a saved state)
 void step_set(unsigned long long* step, unsigned long long v, cudaStream_t s);
 

@@ -233,10 +233,17 @@ constexpr int kTraverseCarveout = FFK_TRAVERSE_CARVEOUT;
 constexpr int kBhThreads = FFK_BH_THREADS;
 constexpr int kBhMinBlocks = FFK_BH_MIN_BLOCKS;
 
+// FP64 walks hold twice the registers per value.
+#ifndef FFK_BH_MIN_BLOCKS_FP64
+#define FFK_BH_MIN_BLOCKS_FP64 6
+#endif
+
 template <typename R, bool COUNT, bool QUAD>
 constexpr int bh_min_blocks()
 {
-    return (sizeof(R) == 4 && !COUNT && !QUAD) ? FFK_BH_MIN_BLOCKS_LEAN : FFK_BH_MIN_BLOCKS;
+    return sizeof(R) == 8 ? FFK_BH_MIN_BLOCKS_FP64
+           : (!COUNT && !QUAD) ? FFK_BH_MIN_BLOCKS_LEAN
+                               : FFK_BH_MIN_BLOCKS;
 }
 static_assert(kBhThreads % 32 == 0, "whole warps");
 
@@ -270,7 +277,7 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
         xk.x = xk.y = xk.z = xk.w = R(0);
         uk = xk;
     }
-    R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0;
+    R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0, ck = 0;
     int nacc = 0, npair = 0, nopen = 0;
     // the cells of this particle's system: [first, end)
     unsigned first = 0, end = ncells;
@@ -303,9 +310,8 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
                 // particle itself (centre and moment sum of one term are exact)
                 const R rx = xk.x - c.x, ry = xk.y - c.y, rz = xk.z - c.z;
                 const R r2 = rx * rx + ry * ry + rz * rz;
-                if (r2 > R(0))
-                    dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, m.x, m.y, m.z, hx, hy, hz, fx, fy,
-                              fz);
+                walk_pair(rx, ry, rz, r2, uk.x, uk.y, uk.z, m.x, m.y, m.z, hx, hy, hz, fx, fy,
+                              fz, ck);
                 if (acc) {
                     if (COUNT) ++nacc;
                 } else {
@@ -321,8 +327,8 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
                         const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
                         const R r2 = rx * rx + ry * ry + rz * rz;
                         if (r2 > R(0)) {
-                            dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, uj.x, uj.y, uj.z, hx, hy,
-                                      hz, fx, fy, fz);
+                            walk_pair(rx, ry, rz, r2, uk.x, uk.y, uk.z, uj.x, uj.y, uj.z, hx,
+                                          hy, hz, fx, fy, fz, ck);
                             if (fp.include_sr) lj<R>(fp, rx, ry, rz, r2, sx, sy, sz, es);
                         }
                         if (COUNT) ++npair;
@@ -346,9 +352,9 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
     ho.y = fp.dip_scale * hy;
     ho.z = fp.dip_scale * hz;
     ho.w = R(0);
-    fo.x = fp.dip_scale * fx + sx;
-    fo.y = fp.dip_scale * fy + sy;
-    fo.z = fp.dip_scale * fz + sz;
+    fo.x = fp.dip_scale * (fx + uk.x * ck) + sx;
+    fo.y = fp.dip_scale * (fy + uk.y * ck) + sy;
+    fo.z = fp.dip_scale * (fz + uk.z * ck) + sz;
     fo.w = R(0);
     h[k] = ho;
     f[k] = fo;
@@ -370,7 +376,7 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
     const int k = task * 32 + lane;
     if (k >= n) return;
     const vec4<R> xk = pos[k], uk = u[k];
-    R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0;
+    R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0, ck = 0;
     int nacc = 0, npair = 0, nopen = 0;
     // the cells of this particle's system: [i, end)
     unsigned i = 0, end = ncells;
@@ -409,8 +415,8 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
         if (acc || out1) {
             // the cell's pseudo-particle; for a one-particle leaf it is the
             // particle itself (centre and moment sum of one term are exact)
-            if (r2 > R(0))
-                dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, m.x, m.y, m.z, hx, hy, hz, fx, fy, fz);
+            walk_pair(rx, ry, rz, r2, uk.x, uk.y, uk.z, m.x, m.y, m.z, hx, hy, hz, fx, fy, fz,
+                          ck);
             if (QUAD && acc && r2 > R(0))
                 quad_term<R>(rx, ry, rz, r2, t.q1[i], t.q2[i], uk.x, uk.y, uk.z, hx, hy, hz, fx,
                              fy, fz);
@@ -429,8 +435,8 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
                     const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
                     const R r2 = rx * rx + ry * ry + rz * rz;
                     if (r2 > R(0)) {
-                        dipole<R>(rx, ry, rz, r2, uk.x, uk.y, uk.z, uj.x, uj.y, uj.z, hx, hy, hz,
-                                  fx, fy, fz);
+                        walk_pair(rx, ry, rz, r2, uk.x, uk.y, uk.z, uj.x, uj.y, uj.z, hx, hy,
+                                      hz, fx, fy, fz, ck);
                         if (fp.include_sr) lj<R>(fp, rx, ry, rz, r2, sx, sy, sz, es);
                     }
                     if (COUNT) ++npair;
@@ -451,9 +457,9 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
     ho.y = fp.dip_scale * hy;
     ho.z = fp.dip_scale * hz;
     ho.w = R(0);
-    fo.x = fp.dip_scale * fx + sx;
-    fo.y = fp.dip_scale * fy + sy;
-    fo.z = fp.dip_scale * fz + sz;
+    fo.x = fp.dip_scale * (fx + uk.x * ck) + sx;
+    fo.y = fp.dip_scale * (fy + uk.y * ck) + sy;
+    fo.z = fp.dip_scale * (fz + uk.z * ck) + sz;
     fo.w = R(0);
     h[k] = ho;
     f[k] = fo;
@@ -668,8 +674,9 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
 // (so warps sharing an L1 cache walk neighbouring parts of the tree) and then
 // from the following segments once its own is used up.  Task counters
 // (work[0..nseg)) start at zero; every task is taken exactly once.
-template <typename R, bool COUNT, int G, bool QUAD>
-__global__ void __launch_bounds__(kBhThreads, (bh_min_blocks<R, COUNT, QUAD>())) k_bh(const vec4<R>* __restrict__ pos,
+template <typename R, bool COUNT, int G, bool QUAD, int THREADS = kBhThreads,
+          int MINB = bh_min_blocks<R, COUNT, QUAD>()>
+__global__ void __launch_bounds__(THREADS, MINB) k_bh(const vec4<R>* __restrict__ pos,
                                             const vec4<R>* __restrict__ u, int n, Tree<R> t,
                                             FieldParams<R> fp, vec4<R>* __restrict__ h,
                                             vec4<R>* __restrict__ f, R* __restrict__ esr,
@@ -805,7 +812,8 @@ PersistentGrid persistent_grid(PersistentGrid* cache, std::mutex& mu, F occupanc
 
 }  // namespace
 
-template <typename R, bool COUNT, int G, bool QUAD = false>
+template <typename R, bool COUNT, int G, bool QUAD = false, int THREADS = kBhThreads,
+          int MINB = bh_min_blocks<R, COUNT, QUAD>()>
 void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
                  vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work,
                  const uint32_t* off, Segs sg, cudaStream_t s)
@@ -814,24 +822,44 @@ void bh_launch_g(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, Fie
     // shared-memory carveout (the kernel uses none) leaves the rest to L1
     static std::mutex mu;
     static PersistentGrid cache[kMaxDevices];
-    const PersistentGrid g = persistent_grid(cache, mu, [] {
-        cudaFuncSetAttribute(k_bh<R, COUNT, G, QUAD>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    const auto kern = k_bh<R, COUNT, G, QUAD, THREADS, MINB>;
+    const PersistentGrid g = persistent_grid(cache, mu, [kern] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              kTraverseCarveout);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh<R, COUNT, G, QUAD>, kBhThreads,
-                                                      0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0);
         return per_sm;
     });
     cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
-    k_bh<R, COUNT, G, QUAD><<<g.blocks, kBhThreads, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts,
-                                                            flags, work, g.nseg, off, sg);
+    kern<<<g.blocks, THREADS, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags, work,
+                                      g.nseg, off, sg);
 }
 
 template <typename R, bool COUNT>
 void bh_launch(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
                vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
-               const uint32_t* off, Segs sg, cudaStream_t s)
+               int sched, const uint32_t* off, Segs sg, cudaStream_t s)
 {
+    if constexpr (sizeof(R) == 4 && !COUNT) {
+        // a tuned launch schedule of the plain FP32 walk (see kSchedules)
+        if (sched >= 1 && sched <= kNumSchedules && !t.q1) {
+#define FFK_SCHED(G, T, B) bh_launch_g<R, false, G, false, T, B>(pos, u, n, t, fp, h, f, esr, counts, flags, work, off, sg, s)
+            switch (sched) {
+                case 1: FFK_SCHED(1, 128, 12); return;
+                case 2: FFK_SCHED(1, 128, 10); return;
+                case 3: FFK_SCHED(1, 128, 8); return;
+                case 4: FFK_SCHED(1, 256, 6); return;
+                case 5: FFK_SCHED(1, 256, 4); return;
+                case 6: FFK_SCHED(1, 64, 24); return;
+                case 7: FFK_SCHED(1, 64, 16); return;
+                case 8: FFK_SCHED(2, 128, 12); return;
+                case 9: FFK_SCHED(4, 128, 12); return;
+                default: FFK_SCHED(8, 128, 12); return;
+            }
+#undef FFK_SCHED
+        }
+    }
+    if (sched >= 1 && sched <= kNumSchedules) group = kSchedules[sched - 1].group;
     if (t.q1) {
         // the dipole-position terms are evaluated by the one-lane walk only
         bh_launch_g<R, COUNT, 1, true>(pos, u, n, t, fp, h, f, esr, counts, flags, work, off, sg,
@@ -853,12 +881,14 @@ void bh_launch(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, Field
 template <typename R>
 void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
               vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work, int group,
-              const uint32_t* off, Segs sg, cudaStream_t s)
+              int sched, const uint32_t* off, Segs sg, cudaStream_t s)
 {
     if (counts)
-        bh_launch<R, true>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, off, sg, s);
+        bh_launch<R, true>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, sched, off, sg,
+                           s);
     else
-        bh_launch<R, false>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, off, sg, s);
+        bh_launch<R, false>(pos, u, n, t, fp, h, f, esr, counts, flags, work, group, sched, off,
+                            sg, s);
     counted();
 }
 
@@ -873,10 +903,10 @@ void ap_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, FieldParams<R> fp
 
 template void bh_field<float>(const float4*, const float4*, int64_t, Tree<float>,
                               FieldParams<float>, float4*, float4*, float*, int4*, int*, int*,
-                              int, const uint32_t*, Segs, cudaStream_t);
+                              int, int, const uint32_t*, Segs, cudaStream_t);
 template void bh_field<double>(const dvec4*, const dvec4*, int64_t, Tree<double>,
                                FieldParams<double>, dvec4*, dvec4*, double*, int4*, int*, int*,
-                               int, const uint32_t*, Segs, cudaStream_t);
+                               int, int, const uint32_t*, Segs, cudaStream_t);
 template void ap_field<float>(const float4*, const float4*, int64_t, FieldParams<float>, float4*,
                               float4*, float*, cudaStream_t);
 template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<double>, dvec4*,

@@ -200,8 +200,18 @@ __global__ void __launch_bounds__(kStepThreads) k_integrate(
     R v[kObs];
 #pragma unroll
     for (int q = 0; q < kObs; ++q) v[q] = R(0);
+    // the tree of this step did not fit: no field was formed, the state is kept as it is
+    const bool hold = dp.flags && (*dp.flags & FLAG_CAPACITY);
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
+        if (hold) {
+            pos2[s] = pos[s];
+            vel2[s] = vel[s];
+            u2[s] = u[s];
+            om2[s] = om[s];
+            id2[s] = id[s];
+            continue;
+        }
         const vec4<R> x = pos[s], vv = vel[s], uu = u[s], w = om[s], hd = hdip[s], fi = fint[s];
         const uint32_t pid = id[s];
         const Local<R> L = local_of<R>(dp, s);
@@ -305,7 +315,11 @@ __global__ void __launch_bounds__(kStepThreads) k_reduce_partials(
     }
 }
 
-__global__ void k_step_advance(unsigned long long* step) { *step += 1ull; }
+__global__ void k_step_advance(unsigned long long* step, const int* flags)
+{
+    if (flags && (*flags & FLAG_CAPACITY)) return;
+    *step += 1ull;
+}
 
 template <typename R, typename I>
 __global__ void k_load3(const I* __restrict__ in, int64_t n, vec4<R>* __restrict__ out)
@@ -525,9 +539,9 @@ void reduce_partials(const double* partials, int nblocks, double inv_n, double i
     counted();
 }
 
-void step_advance(unsigned long long* step, cudaStream_t s)
+void step_advance(unsigned long long* step, const int* flags, cudaStream_t s)
 {
-    k_step_advance<<<1, 1, 0, s>>>(step);
+    k_step_advance<<<1, 1, 0, s>>>(step, flags);
     counted();
 }
 

@@ -97,6 +97,10 @@ _SIGS = {
     "ff_profile_read": (_st, [_vp, C.POINTER(ff_profile_t)]),
     "ff_morton_order_noalloc": (_st, [_vp, C.c_int64, _vp, _vp, _vp]),
     "ff_selftest_sort_wait": (_st, [C.c_int64, _vp]),
+    "ff_schedule_count": (C.c_int32, []),
+    "ff_schedule_info": (_st, [C.c_int32, _vp, _vp, _vp]),
+    "ff_set_schedule": (_st, [_vp, C.c_int32]),
+    "ff_tune_schedule": (_st, [_vp, C.c_int32, _vp, _vp]),
     "ff_last_error": (C.c_char_p, [_vp]),
     "ff_status_string": (C.c_char_p, [C.c_int]),
 }
@@ -258,10 +262,17 @@ def ff_dipolar_field(ctx, algo=FF_ALGO_BH, theta=0.5, include_sr=True, h_out=Non
     return h_out, f_out
 
 
-def ff_energy_grad(ctx, algo=FF_ALGO_BH, theta=0.5, dtype=np.float64, device_like=None):
+def ff_energy_grad(ctx, algo=FF_ALGO_BH, theta=0.5, dtype=np.float64, device_like=None,
+                   grads=True):
     """(E, dE/dpos, dE/du) of the dipolar energy E = -1/2 sum u.h of the current state; the
     Barnes-Hut gradient is exact with this evaluation's opening decisions frozen.  Gradients
-    are numpy arrays unless device_like is a CUDA tensor."""
+    are numpy arrays unless device_like is a CUDA tensor.  grads=False: (E, None, None) at
+    the cost of one field evaluation."""
+    if not grads:
+        e = C.c_double()
+        _check(ctx.handle, lib().ff_energy_grad(ctx.handle, int(algo), float(theta), C.byref(e),
+                                                None, None, FF_DTYPE_F64, FF_HOST))
+        return e.value, None, None
     gp = _alloc_out(ctx.n, dtype, device_like)
     gu = _alloc_out(ctx.n, dtype, device_like)
     pp, pu = _out_pair(gp, ctx.n), _out_pair(gu, ctx.n)
@@ -284,7 +295,8 @@ def ff_mz_sensitivity(ctx, nsteps, every=20):
 def dipolar_energy(pos, u, ctx, algo=FF_ALGO_BH, theta=0.5):
     """Differentiable dipolar energy of (pos, u) (CUDA tensors of shape (n, 3) in the
     context's precision) under torch.autograd.  The context's state is replaced by (pos, u)
-    with zero velocities; the gradient comes from ff_energy_grad."""
+    with zero velocities.  The forward pass evaluates the field once; backward sets the same
+    state again and takes the gradient from ff_energy_grad."""
     return _energy_fn().apply(pos, u, ctx, int(algo), float(theta))
 
 
@@ -299,15 +311,21 @@ def _energy_fn():
         class DipolarEnergy(torch.autograd.Function):
             @staticmethod
             def forward(fctx, pos, u, ctx, algo, theta):
+                # the energy only; the gradient pass runs in backward, if it is asked for
                 ff_set_particles(ctx, pos.detach(), u.detach())
-                e, gp, gu = ff_energy_grad(ctx, algo, theta, dtype=_np_dtype(pos),
-                                           device_like=pos)
-                fctx.save_for_backward(gp, gu)
+                e, _, _ = ff_energy_grad(ctx, algo, theta, grads=False)
+                fctx.save_for_backward(pos.detach(), u.detach())
+                fctx.args = (ctx, algo, theta)
                 return torch.tensor(e, dtype=torch.float64, device=pos.device)
 
             @staticmethod
             def backward(fctx, grad_e):
-                gp, gu = fctx.saved_tensors
+                pos, u = fctx.saved_tensors
+                ctx, algo, theta = fctx.args
+                # the same state again: the same tree, decisions and energy
+                ff_set_particles(ctx, pos, u)
+                _, gp, gu = ff_energy_grad(ctx, algo, theta, dtype=_np_dtype(pos),
+                                           device_like=pos)
                 g = grad_e.to(gp.dtype)
                 return g * gp, g * gu, None, None, None
 
@@ -410,6 +428,31 @@ def ff_system_moments(ctx, reset=False):
 
 
 TRAVERSE_GROUPS = (1, 2, 4, 8, 16, 32)
+
+
+def ff_schedules():
+    """{index: (group, threads per block, blocks per SM)} of the traversal launch schedules."""
+    out = {}
+    for i in range(1, int(lib().ff_schedule_count()) + 1):
+        g, t, b = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(None, lib().ff_schedule_info(i, C.byref(g), C.byref(t), C.byref(b)))
+        out[i] = (g.value, t.value, b.value)
+    return out
+
+
+def ff_set_schedule(ctx, index):
+    _check(ctx.handle, lib().ff_set_schedule(ctx.handle, int(index)))
+
+
+def ff_tune_schedule(ctx, reps=3):
+    """Times the traversal with every launch schedule, keeps the fastest for the context and
+    returns (best index, {index: ms})."""
+    k = int(lib().ff_schedule_count())
+    ms = np.zeros(k, dtype=np.float32)
+    best = C.c_int32()
+    _check(ctx.handle, lib().ff_tune_schedule(ctx.handle, int(reps), C.byref(best),
+                                              C.c_void_p(ms.ctypes.data)))
+    return best.value, {i + 1: float(m) for i, m in enumerate(ms)}
 
 
 def ff_tune_traversal(ctx, groups=None, reps=3):

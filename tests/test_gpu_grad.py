@@ -127,11 +127,17 @@ def test_autograd_function(ff):
     p = torch.tensor(pos, dtype=torch.float64, device="cuda", requires_grad=True)
     q = torch.tensor(u, dtype=torch.float64, device="cuda", requires_grad=True)
     ctx = ff.ff_create(ff.ff_params_default(n=2000, precision="f64"))
+    l0 = ff.ff_profile_read(ctx)["launches"]
     e = ff.dipolar_energy(p, q, ctx, ff.FF_ALGO_BH, 0.5)
+    l_forward = ff.ff_profile_read(ctx)["launches"] - l0
     (3.0 * e).backward()
     ctx2 = ff.ff_create(ff.ff_params_default(n=2000, precision="f64"))
     ff.ff_set_particles(ctx2, pos, u)
+    l1 = ff.ff_profile_read(ctx2)["launches"]
     e2, gp, gu = ff.ff_energy_grad(ctx2, ff.FF_ALGO_BH, 0.5)
+    l_grad = ff.ff_profile_read(ctx2)["launches"] - l1
+    # the forward pass evaluates the field only; the gradient pass waits for backward
+    assert l_forward < l_grad
     assert float(e) == pytest.approx(e2, rel=1e-14)
     assert np.array_equal(p.grad.cpu().numpy(), 3.0 * gp)
     assert np.array_equal(q.grad.cpu().numpy(), 3.0 * gu)

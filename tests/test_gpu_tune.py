@@ -92,3 +92,33 @@ def test_tuner_rejects_bad_input(ff):
     # the context stays usable after rejected calls
     best, _ = ff.ff_tune_traversal(ctx, [2], reps=1)
     assert best == 2
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_every_schedule_gives_the_same_bits(ff, prec):
+    """The launch schedules (block shapes of the plain FP32 walk, lane groups) change speed
+    only: fields, forces and steps are bit-identical, and the tuner keeps the fastest."""
+    pos, u, side = _gas(30000, 5)
+    dt = np.float32 if prec == "f32" else np.float64
+    P, U = pos.astype(dt), u.astype(dt)
+    kw = dict(n=len(P), precision=prec, walls=1, box_lo=(0, 0, 0), box_hi=(side,) * 3, seed=6)
+    ctx = ff.ff_create(ff.ff_params_default(**kw))
+    ff.ff_set_particles(ctx, P, U)
+    h0, f0 = ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, 0.5, True)
+    scheds = ff.ff_schedules()
+    assert len(scheds) >= 8 and all(g in ff.TRAVERSE_GROUPS for g, _, _ in scheds.values())
+    for i in scheds:
+        ff.ff_set_schedule(ctx, i)
+        h, f = ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, 0.5, True)
+        assert np.array_equal(h, h0) and np.array_equal(f, f0), i
+    best, ms = ff.ff_tune_schedule(ctx, reps=2)
+    assert best in scheds and ms[best] == min(ms.values())
+    ref = ff.ff_create(ff.ff_params_default(traverse_group=1, **kw))
+    ff.ff_set_particles(ref, P, U)
+    ff.ff_dipolar_field(ref, ff.FF_ALGO_BH, 0.5, True)
+    ff.ff_step(ctx, 4)
+    ff.ff_step(ref, 4)
+    for a, b in zip(ff.ff_get_particles(ctx), ff.ff_get_particles(ref)):
+        assert np.array_equal(a, b)
+    with pytest.raises(ff.FFError):
+        ff.ff_set_schedule(ctx, len(scheds) + 1)
