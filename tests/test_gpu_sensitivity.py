@@ -148,3 +148,40 @@ def test_full_size_200_step_unroll_central_differences(ff):
     mz, g = ff.ff_mz_sensitivity(ctx(1.0), 200, 20)
     assert mz == pytest.approx(mean_mz(1.0), rel=1e-10, abs=1e-13)
     assert g[2] == pytest.approx((mean_mz(1.0 + 1e-3) - mean_mz(1.0 - 1e-3)) / 2e-3, rel=1e-4)
+
+
+@pytest.mark.slow
+def test_full_size_fp32_against_fp64(ff):
+    """N = 262,144 at volume fraction 0.05: the FP32 d<M_z>/dh_ext through a 200-step unroll
+    saved every 20 steps against the FP64 one and against central differences (h = 1e-3) of
+    FP64 trajectories (measured on GB300: 8e-7 relative for the z component)."""
+    from paper_1212_2934_gb300 import synth
+
+    n = 262144
+    side = synth.box_side_for_fraction(n, 0.05)
+    pos = synth.rsa_cube(n, side, 3).astype(np.float32)
+    u = synth.isotropic_moments(n, 4).astype(np.float32)
+
+    def ctx(hz, prec):
+        p = ff.ff_params_default(n=n, precision=prec, walls=1, box_lo=(0, 0, 0),
+                                 box_hi=(side, side, side), h_ext=(0.0, 0.0, hz), seed=1)
+        c = ff.ff_create(p)
+        dt = np.float64 if prec == "f64" else np.float32
+        ff.ff_set_particles(c, pos.astype(dt), u.astype(dt))
+        return c
+
+    def mean_mz(hz):
+        c = ctx(hz, "f64")
+        acc = 0.0
+        for _ in range(200):
+            ff.ff_step(c, 1)
+            acc += ff.ff_get_particles(c)[1][:, 2].mean()
+        return acc / 200
+
+    mz32, g32 = ff.ff_mz_sensitivity(ctx(1.0, "f32"), 200, 20)
+    mz64, g64 = ff.ff_mz_sensitivity(ctx(1.0, "f64"), 200, 20)
+    cd = (mean_mz(1.0 + 1e-3) - mean_mz(1.0 - 1e-3)) / 2e-3
+    assert mz32 == pytest.approx(mz64, rel=1e-5)
+    assert g32[2] == pytest.approx(g64[2], rel=1e-5)
+    assert g32[2] == pytest.approx(cd, rel=1e-5)
+    np.testing.assert_allclose(g32, g64, rtol=1e-4, atol=1e-5 * abs(g64[2]))
