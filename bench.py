@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--group", type=int, default=0,
                     help="lanes walking the cell list together (0: picked by the library's "
                          "autotuner on the workload before warm-up)")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="traversal launch schedule (ff_schedule_info index); 0: tuned on the "
+                         "workload before warm-up unless --group is given")
     ap.add_argument("--workload", default="phi05", choices=["phi05", "batched", "chains", "grad"],
                     help="phi05: one system of --n particles (default); batched: 256 independent "
                          "dilute systems of log-uniform sizes 1,024..65,536 at fields 0..5; "
@@ -621,7 +624,12 @@ def run_ours(args):
     ctx = create(params(count_interactions=0))
     ff.ff_set_particles(ctx, pos_d, u_d)
     tuning = None
-    if args.group == 0:
+    if args.schedule > 0:
+        ff.ff_set_schedule(ctx, args.schedule)
+        args.group = ff.ff_schedules()[args.schedule][0]
+        tuning = {"chosen": "group %d, %d threads x %d blocks/SM (fixed by --schedule)"
+                            % ff.ff_schedules()[args.schedule]}
+    elif args.group == 0:
         # the traversal's launch schedule (lane group, block shape, blocks per SM) is picked by
         # the library's autotuner on this very workload; every choice gives the same bits, only
         # the speed differs
