@@ -284,9 +284,9 @@ class Clocks:
                 "power_w_median": float(np.median(power)) if power else None}
 
 
-def traffic_for(kernel_src, n, workload, theta, leaf_max):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source and
-    this workload."""
+def traffic_for(kernel_src, n, workload, theta, leaf_max, schedule):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source,
+    this workload and this traversal launch schedule."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -295,7 +295,7 @@ def traffic_for(kernel_src, n, workload, theta, leaf_max):
         sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
         same = (d.get("source_sha256") == sha and d.get("n") == n and
                 d.get("workload_name") == workload and d.get("theta") == theta and
-                d.get("leaf_max") == leaf_max)
+                d.get("leaf_max") == leaf_max and d.get("schedule") == schedule)
         if same:
             return d.get("dram_bytes_per_launch")
     except (OSError, ValueError):
@@ -639,6 +639,7 @@ def run_ours(args):
         tuning = {"chosen": name(best),
                   "ms_per_candidate": {name(i): round(m, 4) for i, m in tms.items()}}
         args.group = scheds[best][0]
+        args.schedule = best
     clocks = Clocks(dev)
     clocks.start()
     for _ in range(W):
@@ -710,7 +711,7 @@ def run_ours(args):
     peak = peaks["fp32_tflops"]
     achieved = flops / (field_ms / 1e3) / 1e12
     traffic = traffic_for(os.path.join(ROOT, "paper_1212_2934_gb300", "csrc", "k_field.cu"), n,
-                          args.workload, args.theta, args.leaf_max)
+                          args.workload, args.theta, args.leaf_max, args.schedule)
     stages = {k: v / max(prof["calls"][k], 1) for k, v in prof["ms"].items() if prof["calls"][k]}
 
     extras = {}
