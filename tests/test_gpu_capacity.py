@@ -76,3 +76,48 @@ def test_held_back_steps_run_again(ff):
     ff.ff_step(grown, 2)
     for x, y in zip(ff.ff_get_particles(fresh), ff.ff_get_particles(grown)):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_growth_in_double_and_mixed_precision(ff, ora, prec):
+    pos, u = _close_pairs(1500, seed=6)
+    n = pos.shape[0]
+    dt = np.float64 if prec == "f64" else np.float32
+    ctx = ff.ff_create(ff.ff_params_default(n=n, precision=prec, count_interactions=1))
+    ff.ff_set_particles(ctx, pos.astype(dt), u.astype(dt))
+    ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, 0.5, True)
+    assert ff.ff_tree_info(ctx)["ncells"] > 2 * n + 8192
+    g = ff.ff_get_tree(ctx)
+    t = ora.tree(pos.astype(np.float64), u.astype(np.float64), prec, 1)
+    for k in ("pbegin", "pend", "skip", "level", "leaf"):
+        assert np.array_equal(g[k].astype(np.int64), t[k].astype(np.int64)), k
+
+
+def test_growth_with_batched_systems(ff):
+    """Systems of close pairs next to a plain gas: the forest grows; every system's field
+    equals that of a context that had room from the start."""
+    from paper_1212_2934_gb300 import synth
+
+    a, ua = _close_pairs(2500, seed=7)
+    m = 4000
+    side = synth.box_side_for_fraction(m, 0.05)
+    b = synth.rsa_cube(m, side, 8).astype(np.float32)
+    ub = synth.isotropic_moments(m, 9).astype(np.float32)
+    P = np.concatenate([a, b])
+    U = np.concatenate([ua, ub])
+    sizes = [a.shape[0], m]
+    fresh = ff.ff_create(ff.ff_params_default(n=len(P)))
+    ff.ff_set_systems(fresh, sizes)
+    ff.ff_set_particles(fresh, P, U)
+    h1, f1 = ff.ff_dipolar_field(fresh, ff.FF_ALGO_BH, 0.5, True)
+    assert ff.ff_tree_info(fresh)["ncells"] > 2 * len(P) + 8192
+    again = ff.ff_dipolar_field(fresh, ff.FF_ALGO_BH, 0.5, True)
+    assert np.array_equal(again[0], h1) and np.array_equal(again[1], f1)
+    # each system alone (its own context) gives the same bits
+    off = 0
+    for i, k in enumerate(sizes):
+        one = ff.ff_create(ff.ff_params_default(n=k))
+        ff.ff_set_particles(one, P[off:off + k], U[off:off + k])
+        h, f = ff.ff_dipolar_field(one, ff.FF_ALGO_BH, 0.5, True)
+        assert np.array_equal(h, h1[off:off + k]) and np.array_equal(f, f1[off:off + k]), i
+        off += k

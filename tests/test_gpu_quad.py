@@ -47,7 +47,7 @@ def test_quadrupole_matches_oracle(ff, ora, prec, leaf_max):
         assert rel_err(f, ref["f"]).max() <= 1e-10
     else:
         assert rel_err(h, ref["h"]).max() <= 1e-5
-        assert rel_err(f, ref["f"], scale=ref["fabs"]).max() <= 1e-5
+        assert rel_err(f, ref["f"]).max() <= 1e-5  # the plain bar (7.5e-6 measured on GB300)
     acc, pairs, opened = ff.ff_get_counts(ctx)
     assert np.array_equal(acc, ref["nacc"]) and np.array_equal(opened, ref["nopen"])
 

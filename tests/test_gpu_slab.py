@@ -48,7 +48,7 @@ def test_slab_field_matches_oracle(ff, ora):
     h, f = ff.ff_dipolar_field(ctx, ff.FF_ALGO_BH, 0.5, True)
     ref = ora.bh(pos32, u32, 0.5, 1, "f32", 1.0, 1.0, 1.0, 2.5, True)
     assert rel_err(h, ref["h"]).max() <= 1e-5
-    assert rel_err(f, ref["f"], scale=ref["fabs"]).max() <= 1e-5
+    assert rel_err(f, ref["f"]).max() <= 1e-5  # the plain bar (6.3e-6 measured on GB300)
     acc, pairs, opened = ff.ff_get_counts(ctx)
     assert np.array_equal(acc, ref["nacc"]) and np.array_equal(pairs, ref["npair"])
 
