@@ -109,15 +109,17 @@ def test_growth_with_batched_systems(ff):
     fresh = ff.ff_create(ff.ff_params_default(n=len(P)))
     ff.ff_set_systems(fresh, sizes)
     ff.ff_set_particles(fresh, P, U)
-    h1, f1 = ff.ff_dipolar_field(fresh, ff.FF_ALGO_BH, 0.5, True)
+    # the LJ force of pairs 1e-4 apart overflows single precision: dipolar terms only
+    h1, f1 = ff.ff_dipolar_field(fresh, ff.FF_ALGO_BH, 0.5, False)
+    assert np.isfinite(h1).all() and np.isfinite(f1).all()
     assert ff.ff_tree_info(fresh)["ncells"] > 2 * len(P) + 8192
-    again = ff.ff_dipolar_field(fresh, ff.FF_ALGO_BH, 0.5, True)
+    again = ff.ff_dipolar_field(fresh, ff.FF_ALGO_BH, 0.5, False)
     assert np.array_equal(again[0], h1) and np.array_equal(again[1], f1)
     # each system alone (its own context) gives the same bits
     off = 0
     for i, k in enumerate(sizes):
         one = ff.ff_create(ff.ff_params_default(n=k))
         ff.ff_set_particles(one, P[off:off + k], U[off:off + k])
-        h, f = ff.ff_dipolar_field(one, ff.FF_ALGO_BH, 0.5, True)
+        h, f = ff.ff_dipolar_field(one, ff.FF_ALGO_BH, 0.5, False)
         assert np.array_equal(h, h1[off:off + k]) and np.array_equal(f, f1[off:off + k]), i
         off += k
