@@ -821,7 +821,7 @@ def run_ours(args):
         for q in (0, 1):
             ctxq = ff.ff_create(params(count_interactions=0, quadrupole=q))
             ff.ff_set_particles(ctxq, pos_d, u_d)
-            for th in (0.5, 0.7):
+            for th in (0.3, 0.5, 0.7):
                 ff.ff_dipolar_field(ctxq, ff.FF_ALGO_BH, th, False, hb, fb)
                 q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 q0.record(stream)
