@@ -106,6 +106,18 @@ struct ff_ctx {
     int64_t s_cap = 0;           // sources the buffers hold
     double* i_part = nullptr;    // per work item: six partial sums; then each item's source
     int64_t i_cap = 0;
+    // records of the group walk (one per task and source taken by some lane of the task)
+    uint32_t* t_cnt = nullptr;   // per task: its records (ntask)
+    uint32_t* t_off = nullptr;   // their exclusive scan (ntask + 1)
+    uint32_t* s_rbeg = nullptr;  // per source: its first sorted record (s_cap)
+    uint32_t* r_key = nullptr;   // packed in task order: the source
+    uint32_t* r_idx = nullptr;   //   the packed index (sort value)
+    uint2* r_rec = nullptr;      //   (task, lane mask)
+    uint2* r_srec = nullptr;     // sorted by source
+    uint32_t* r_cnt = nullptr;   //   entries of each sorted record
+    uint32_t* r_E = nullptr;     //   their exclusive scan (+1)
+    uint32_t* r_scan = nullptr;
+    int64_t r_cap = 0;
     bool tree_valid = false;     // a Barnes-Hut tree of some state exists
     bool counts_valid = false;
 
@@ -487,7 +499,9 @@ void free_all(ff_ctx* c)
                     c->sys_hi, c->sys_acc,
                     c->dflags, c->staging, c->e_cnt, c->e_base, c->e_total, c->g_pos, c->g_u,
                     c->e_keys[0], c->e_keys[1], c->e_vals[0], c->e_vals[1], c->e_tmp, c->s_beg,
-                    c->s_end, c->s_G, c->s_Q, c->s_items, c->s_item_off, c->s_scan, c->i_part};
+                    c->s_end, c->s_G, c->s_Q, c->s_items, c->s_item_off, c->s_scan, c->i_part,
+                    c->t_cnt, c->t_off, c->s_rbeg, c->r_key, c->r_idx, c->r_rec, c->r_srec,
+                    c->r_cnt, c->r_E, c->r_scan};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int k = 0; k < 2; ++k) {
@@ -821,6 +835,7 @@ ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64
         if ((st = grow(c, &c->s_items, cap)) != FF_OK) return st;
         if ((st = grow(c, &c->s_item_off, cap + 1)) != FF_OK) return st;
         if ((st = grow(c, &c->s_scan, ffk::scan_tmp_words(cap))) != FF_OK) return st;
+        if ((st = grow(c, &c->s_rbeg, cap)) != FF_OK) return st;
         c->s_cap = cap;
     }
     const int64_t max_items = nsrc + ne / ffk::kGradItemEntries + 1;
@@ -850,6 +865,60 @@ void sort_entries(ff_ctx* c, int64_t ne, int64_t nsrc, const uint32_t** keys,
     *vals = c->e_vals[in1 ? 1 : 0];
 }
 
+// After prepare_entries: the group walk's records, packed, sorted by source and
+// scanned into entry offsets (k_field.cu group_record_task, k_grad.cu).  Waits
+// for the walk to read the number of records.
+template <typename R>
+ff_status record_sources(ff_ctx* c, double theta, int64_t nsrc, int64_t* nrec_out)
+{
+    const int64_t n = c->n;
+    const int64_t ntask = (n + 31) / 32;
+    cudaStream_t s = c->stream;
+    ff_status st;
+    if (!c->t_cnt) {
+        if ((st = grow(c, &c->t_cnt, ntask)) != FF_OK) return st;
+        if ((st = grow(c, &c->t_off, ntask + 1)) != FF_OK) return st;
+    }
+    Buffers& a = c->st[c->cur];
+    // the records of task T go to the slots of its particles (e_keys[0], e_vals[0])
+    ffk::bh_group_record<R>(V<R>(a.pos), n, tree_of<R>(c), field_params<R>(c, theta, 0), c->e_base,
+                            c->e_keys[0], c->e_vals[0], c->t_cnt, c->dflags, c->work, c->off,
+                            segs_of(c), s);
+    ffk::scan_exclusive(c->t_cnt, c->t_off, ntask, c->scan_tmp, s);
+    FF_LAUNCHED(c);
+    uint32_t total = 0;
+    FF_CUDA(c, cudaMemcpyAsync(&total, c->t_off + ntask, sizeof(total), cudaMemcpyDeviceToHost, s));
+    if ((st = sync_and_check(c)) != FF_OK) return st;
+    const int64_t nrec = total;
+    if (nrec > c->r_cap) {
+        const int64_t cap = nrec + nrec / 8 + 1024;
+        if ((st = grow(c, &c->r_key, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->r_idx, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->r_rec, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->r_srec, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->r_cnt, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->r_E, cap + 1)) != FF_OK) return st;
+        if ((st = grow(c, &c->r_scan, ffk::scan_tmp_words(cap))) != FF_OK) return st;
+        c->r_cap = cap;
+    }
+    ffk::grad_pack_records(c->t_cnt, c->t_off, ntask, c->e_base, c->e_keys[0], c->e_vals[0],
+                           c->r_key, c->r_idx, c->r_rec, s);
+    int passes = 1;
+    while (passes < 4 && ((uint64_t)nsrc >> (8 * passes)) != 0) ++passes;
+    // the records, in task order, sorted stably by source (e_keys[0], e_vals[0]
+    // are free again and serve as the other buffer pair)
+    const bool in1 = ffk::radix_sort_pairs_passes<uint32_t>(
+        c->r_key, c->r_idx, c->e_keys[0], c->e_vals[0], nrec, c->e_tmp, passes, c->dflags, s,
+        nullptr, 0);
+    const uint32_t* skey = in1 ? c->e_keys[0] : c->r_key;
+    const uint32_t* sidx = in1 ? c->e_vals[0] : c->r_idx;
+    ffk::grad_record_sources(skey, sidx, nrec, c->r_rec, nsrc, c->r_srec, c->r_cnt, c->r_E,
+                             c->r_scan, c->s_rbeg, c->s_beg, c->s_end, s);
+    FF_LAUNCHED(c);
+    *nrec_out = nrec;
+    return FF_OK;
+}
+
 // Energy -1/2 sum u.h (FP64) and its gradient with the opening decisions of
 // this evaluation frozen (k_grad.cu), in sorted order in g_pos, g_u.
 template <typename R>
@@ -877,15 +946,12 @@ ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy, boo
         const int64_t nsrc = ncells + n;
         Buffers& a = c->st[c->cur];
         ffk::Tree<R> t = tree_of<R>(c);
-        ffk::bh_record<R>(V<R>(a.pos), n, t, field_params<R>(c, theta, 0), c->e_base,
-                          c->e_keys[0], c->dflags, c->work, c->off, segs_of(c), s);
-        const uint32_t* keys = nullptr;
-        const uint32_t* vals = nullptr;
-        sort_entries(c, ne, nsrc, &keys, &vals);
-        ffk::grad_segments(keys, ne, nsrc, c->s_beg, c->s_end, s);
-        ffk::grad_source_sums<R>(V<R>(a.pos), V<R>(a.u), t, ncells, n, vals, c->s_beg, c->s_end,
-                                 c->s_items, c->s_item_off, c->s_scan, c->i_part, max_items,
-                                 c->s_G, c->s_Q, s);
+        int64_t nrec = 0;
+        if ((st = record_sources<R>(c, theta, nsrc, &nrec)) != FF_OK) return st;
+        ffk::grad_source_sums_rec<R>(V<R>(a.pos), V<R>(a.u), t, ncells, n, c->r_srec, c->r_E,
+                                     nrec, c->s_rbeg, c->s_beg, c->s_end, c->s_items,
+                                     c->s_item_off, c->s_scan, c->i_part, max_items, c->s_G,
+                                     c->s_Q, s);
         ffk::grad_finish<R>(t, ncells, n, c->s_G, c->s_Q, V<R>(c->h), V<R>(c->f),
                             (R)c->p.dip_scale, V<R>(c->g_pos), V<R>(c->g_u), s);
         FF_LAUNCHED(c);

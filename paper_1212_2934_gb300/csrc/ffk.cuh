@@ -228,21 +228,24 @@ void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint3
                     const uint32_t* off, Tree<R> t, vec4<A>* ssum, vec4<A>* smom, int* flags,
                     cudaStream_t s);
 
-// Source lists of the gradient pass (see k_field.cu): per particle k, entries
-// base[k] .. base[k + 1] hold its sources in the order of its walk (the
-// particle of an entry is implied by its slot).
-template <typename R>
-void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
-               uint32_t* keys, int* flags, int* work, const uint32_t* off, Segs sg,
-               cudaStream_t s);
-
-// The same walk for a vector-Jacobian product of h and f with cotangents
-// abar, bbar: also writes each particle's target-side terms to dxt, dut.
+// Source lists of a vector-Jacobian product of h and f with cotangents abar,
+// bbar (see k_field.cu): per particle k, entries base[k] .. base[k + 1] hold
+// its sources in the order of its walk (the particle of an entry is implied by
+// its slot); each particle's target-side terms go to dxt, dut.
 template <typename R>
 void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
                    const vec4<R>* bbar, int64_t n, Tree<R> t, FieldParams<R> fp,
                    const uint32_t* base, uint32_t* keys, int* flags, int* work,
                    const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s);
+
+// Source records of the gradient pass (see k_field.cu): one warp per task of 32
+// particles walks the union of their cell lists; every source some lane takes
+// is written once, with the mask of those lanes, to rkeys/rmask from
+// base[32 task] on, and the task's number of records to tcount[task].
+template <typename R>
+void bh_group_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp,
+                     const uint32_t* base, uint32_t* rkeys, uint32_t* rmask, uint32_t* tcount,
+                     int* flags, int* work, const uint32_t* off, Segs sg, cudaStream_t s);
 
 // ------------------------------------------------ energy gradient (k_grad.cu)
 // entries per particle (accepted cells + exact pairs) as uint32; *total64
@@ -253,16 +256,35 @@ void grad_entry_counts(const int4* counts, int64_t n, uint32_t* out,
 // nsrc, zeroed here)
 void grad_segments(const uint32_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg, uint32_t* end,
                    cudaStream_t s);
+// Records of the group walk: the ntask tasks' records (tcount each, from
+// base[32 task] in rkeys/rmask; toff = exclusive scan of tcount) packed in task
+// order: ckey (the source), cidx[r] = r, crec[r] = (task, lane mask).
+void grad_pack_records(const uint32_t* tcount, const uint32_t* toff, int64_t ntask,
+                       const uint32_t* base, const uint32_t* rkeys, const uint32_t* rmask,
+                       uint32_t* ckey, uint32_t* cidx, uint2* crec, cudaStream_t s);
+// After the records are sorted by source (skey, sidx = their packed index):
+// srec[i] = crec[sidx[i]], recE[i] = entries before record i (recE[nrec] =
+// entries), and per source its first record rbeg, and the entry range beg, end
+// (nsrc each, zeroed here).  cnt: nrec words of scratch, scan_tmp for nrec.
+void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
+                         const uint2* crec, int64_t nsrc, uint2* srec, uint32_t* cnt,
+                         uint32_t* recE, uint32_t* scan_tmp, uint32_t* rbeg, uint32_t* beg,
+                         uint32_t* end, cudaStream_t s);
 // per source s: G_s = sum over its entries of T(r) u_m and Q_s = sum of
 // grad phi(r; w_s, u_m) / n_s, r = rho_m - x_s (FP64 results, 3 per source).
+// Entry e of source s (beg[s] <= e < end[s]) is particle 32 task + lane of the
+// sorted record holding it (recE[r] <= e < recE[r + 1]), its lanes taken in
+// rising order.  Each source's entries are cut into items of kGradItemEntries,
+// summed one warp each in single precision, the items then added in FP64.
 // Scratch: items/item_off (nsrc, nsrc + 1 words), scan_tmp for nsrc, part
 // (6 doubles per item; max_items >= nsrc + entries / kGradItemEntries + 1).
 constexpr int64_t kGradItemEntries = 1024;
 template <typename R>
-void grad_source_sums(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64_t ncells, int64_t n,
-                      const uint32_t* vals, const uint32_t* beg, const uint32_t* end,
-                      uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
-                      int64_t max_items, double* G, double* Q, cudaStream_t s);
+void grad_source_sums_rec(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64_t ncells,
+                          int64_t n, const uint2* srec, const uint32_t* recE, int64_t nrec,
+                          const uint32_t* rbeg, const uint32_t* beg, const uint32_t* end,
+                          uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
+                          int64_t max_items, double* G, double* Q, cudaStream_t s);
 // per particle p: g_p, q_p = the sums of every cell containing p plus its own
 // particle-source sums, then grad_u = -1/2 (h + ds g), grad_pos = -1/2 (f - ds q)
 template <typename R>
@@ -273,7 +295,8 @@ void grad_finish(Tree<R> t, int64_t ncells, int64_t n, const double* G, const do
 // Vector-Jacobian product of h and f, source side: per source s,
 // G_s = ds sum [T(r) abar_m + grad phi(r; bbar_m, u_m)] (dL/dw_s) and
 // Q_s = -ds sum [grad phi(r; abar_m, w_s) + H phi(r; u_m, w_s) bbar_m] / n_s
-// (dL/dx_s per member), same scratch as grad_source_sums.
+// (dL/dx_s per member), from the sorted entries vals (targets), beg and end
+// (grad_segments); same items, order and scratch as grad_source_sums_rec.
 template <typename R>
 void vjp_source_sums(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
                      const vec4<R>* bbar, R ds, Tree<R> t, int64_t ncells, int64_t n,

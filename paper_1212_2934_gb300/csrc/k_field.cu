@@ -669,6 +669,128 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
     }
 }
 
+// Source records for the energy gradient, one warp per 32-particle task: the
+// lanes walk the union of their cell lists in order (the lane-group walk with
+// G = 32), each lane deciding its own cells exactly as record_task does, and
+// each source that at least one lane takes is written once, with the mask of
+// the lanes that take it.  Sources are numbered as in record_task; within a
+// task each source occurs once.  The records of a task go to rkeys/rmask from
+// base[32 task] on (a task has at most as many records as entries, so they fit
+// in the task's slots) and their number to tcount[task].  Expanding the records
+// lane by lane gives every entry of the task, so after a stable sort on the
+// source the entries come out in the order of the per-lane slots.
+template <typename R>
+__device__ __forceinline__ void group_record_task(int task, const vec4<R>* __restrict__ pos, int n,
+                                                  const Tree<R>& t, const FieldParams<R>& fp,
+                                                  unsigned ncells,
+                                                  const uint32_t* __restrict__ base,
+                                                  uint32_t* __restrict__ rkeys,
+                                                  uint32_t* __restrict__ rmask,
+                                                  uint32_t* __restrict__ tcount, int* flags,
+                                                  const uint32_t* __restrict__ off, const Segs& sg)
+{
+    const int lane = threadIdx.x & 31;
+    const int k0 = task * 32;
+    const int k = k0 + lane;
+    const bool active = k < n;
+    vec4<R> xk;
+    if (active) {
+        xk = pos[k];
+    } else {
+        xk.x = xk.y = xk.z = xk.w = R(0);
+    }
+    unsigned first = 0, end = ncells;
+    if (sg.of_pos && active) {
+        const int sys = (int)sg.of_pos[k];
+        first = off[sg.start[sys]];
+        end = off[sg.start[sys + 1]];
+    }
+    unsigned nxt = active && first < end ? first : 0xffffffffu;
+    const uint32_t w0 = base[k0];
+    const uint32_t wend = base[min(k0 + 32, n)];
+    uint32_t w = w0;
+    for (;;) {
+        const unsigned i = __reduce_min_sync(kFull, nxt);
+        if (i >= ncells) break;
+        // one address for the whole warp: a single transaction
+        const Cell<R> cl = t.cell[i];
+        const int4 nd = cl.node;
+        bool take = false, pairs = false;
+        if (nxt == i) {
+            const bool inside = nd.x <= k && k < nd.y;
+            const bool leaf = (nd.w >> 8) != 0;
+            const bool single = (nd.w >> 9) != 0;  // a one-particle leaf
+            // a one-particle leaf outside is recorded as the cell whether accepted
+            // or summed as a pair (the same entry)
+            take = (single && !inside) ||
+                   (!inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i, t.mom[i].w));
+            pairs = !take && leaf && !single;
+            unsigned nx = (take || leaf) ? (unsigned)nd.z : i + 1;
+            if (nx <= i) {  // skip pointers must move forward
+                atomicOr(flags, FLAG_TRAVERSE);
+                nx = 0xffffffffu;
+            }
+            nxt = nx >= end ? 0xffffffffu : nx;
+        }
+        const uint32_t mt = __ballot_sync(kFull, take);
+        if (mt) {
+            if (lane == 0 && w < wend) {
+                rkeys[w] = i;
+                rmask[w] = mt;
+            }
+            ++w;
+        }
+        const uint32_t mp = __ballot_sync(kFull, pairs);
+        if (mp) {
+            // the particles of an opened multi-particle leaf, each but the lane's own
+            for (int s = nd.x; s < nd.y; ++s) {
+                const uint32_t m = (s >= k0 && s < k0 + 32) ? mp & ~(1u << (s - k0)) : mp;
+                if (m) {
+                    if (lane == 0 && w < wend) {
+                        rkeys[w] = ncells + (uint32_t)s;
+                        rmask[w] = m;
+                    }
+                    ++w;
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        tcount[task] = w - w0;
+        if (w > wend) atomicOr(flags, FLAG_TRAVERSE);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_group_record(
+    const vec4<R>* __restrict__ pos, int n, Tree<R> t, FieldParams<R> fp,
+    const uint32_t* __restrict__ base, uint32_t* __restrict__ rkeys, uint32_t* __restrict__ rmask,
+    uint32_t* __restrict__ tcount, int* flags, int* __restrict__ work, int nseg,
+    const uint32_t* __restrict__ off, Segs sg)
+{
+    if (*flags & FLAG_CAPACITY) return;
+    const unsigned ncells = (unsigned)*t.ncells;
+    const int ntask = (n + 31) / 32;
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    const int home = (int)(smid % (unsigned)nseg);
+    const int lane = threadIdx.x & 31;
+    for (int probe = 0; probe < nseg; ++probe) {
+        const int ws = (home + probe) % nseg;
+        const int t0 = (int)((int64_t)ntask * ws / nseg);
+        const int t1 = (int)((int64_t)ntask * (ws + 1) / nseg);
+        for (;;) {
+            int got = 0;
+            if (lane == 0) got = atomicAdd(&work[ws], 1);
+            got = __shfl_sync(kFull, got, 0);
+            const int task = t0 + got;
+            if (task >= t1) break;
+            group_record_task<R>(task, pos, n, t, fp, ncells, base, rkeys, rmask, tcount, flags,
+                                 off, sg);
+        }
+    }
+}
+
 // Persistent traversal: the key order is cut into nseg contiguous segments of
 // 32-particle tasks; a warp takes tasks from the segment of the SM it runs on
 // (so warps sharing an L1 cache walk neighbouring parts of the tree) and then
@@ -934,15 +1056,6 @@ void bh_record_g(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, co
 }
 
 template <typename R>
-void bh_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
-               uint32_t* keys, int* flags, int* work, const uint32_t* off, Segs sg,
-               cudaStream_t s)
-{
-    if (n <= 0) return;
-    bh_record_g<R, false>(pos, n, t, fp, base, keys, flags, work, off, sg, VjpIn<R>{}, s);
-}
-
-template <typename R>
 void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
                    const vec4<R>* bbar, int64_t n, Tree<R> t, FieldParams<R> fp,
                    const uint32_t* base, uint32_t* keys, int* flags, int* work,
@@ -958,12 +1071,34 @@ void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
     bh_record_g<R, true>(pos, n, t, fp, base, keys, flags, work, off, sg, vj, s);
 }
 
-template void bh_record<float>(const float4*, int64_t, Tree<float>, FieldParams<float>,
-                               const uint32_t*, uint32_t*, int*, int*, const uint32_t*, Segs,
-                               cudaStream_t);
-template void bh_record<double>(const dvec4*, int64_t, Tree<double>, FieldParams<double>,
-                                const uint32_t*, uint32_t*, int*, int*, const uint32_t*, Segs,
-                                cudaStream_t);
+template <typename R>
+void bh_group_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp,
+                     const uint32_t* base, uint32_t* rkeys, uint32_t* rmask, uint32_t* tcount,
+                     int* flags, int* work, const uint32_t* off, Segs sg, cudaStream_t s)
+{
+    if (n <= 0) return;
+    static std::mutex mu;
+    static PersistentGrid cache[kMaxDevices];
+    const PersistentGrid g = persistent_grid(cache, mu, [] {
+        cudaFuncSetAttribute(k_bh_group_record<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             kTraverseCarveout);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_group_record<R>, kBhThreads,
+                                                      0);
+        return per_sm;
+    });
+    cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
+    k_bh_group_record<R><<<g.blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, rkeys, rmask,
+                                                         tcount, flags, work, g.nseg, off, sg);
+    counted();
+}
+
+template void bh_group_record<float>(const float4*, int64_t, Tree<float>, FieldParams<float>,
+                                     const uint32_t*, uint32_t*, uint32_t*, uint32_t*, int*, int*,
+                                     const uint32_t*, Segs, cudaStream_t);
+template void bh_group_record<double>(const dvec4*, int64_t, Tree<double>, FieldParams<double>,
+                                      const uint32_t*, uint32_t*, uint32_t*, uint32_t*, int*,
+                                      int*, const uint32_t*, Segs, cudaStream_t);
 template void bh_record_vjp<float>(const float4*, const float4*, const float4*, const float4*,
                                    int64_t, Tree<float>, FieldParams<float>, const uint32_t*,
                                    uint32_t*, int*, int*, const uint32_t*, Segs, float4*, float4*,

@@ -7,10 +7,16 @@
 //   dE/drho_k = -1/2 [ f_k - ds sum over (m, s), k in s, of
 //                      grad phi(rho_m - x_s; w_s, u_m) / n_s ]
 // h and f are the dipolar field and force of the same traversal (ds
-// included).  The reverse sums are formed without atomics: the traversal
-// records every (source, target) entry, a stable radix sort on the source
-// groups them, one warp per source sums its entries in a fixed order, and each
-// leaf adds the sums of its ancestor cells for its particles.
+// included).  The reverse sums are formed without atomics.  One warp per task
+// of 32 consecutive particles walks the union of their cell lists and writes,
+// per source some lane takes, one record (source, task, lane mask); the records
+// (about a tenth as many as the (source, target) entries) are packed in task
+// order and sorted stably by source, so each source's entries, expanded lane
+// by lane, come out in target order.  Each source's entries are summed in a
+// fixed order (pieces of at most 1024 entries one warp each, the pieces added
+// in FP64), and each leaf adds the sums of its ancestor cells for its
+// particles.  The vector-Jacobian product keeps per-target entries: its walk
+// also sums target-side terms lane by lane.
 #include "dipole.cuh"
 #include "ffk.cuh"
 
@@ -93,12 +99,82 @@ __global__ void k_item_sources(const uint32_t* __restrict__ item_off, int64_t ns
     for (uint32_t it = item_off[s]; it < item_off[s + 1]; ++it) item_src[it] = (uint32_t)s;
 }
 
-// One warp per item: the terms of its entries summed in single precision (at
-// most 32 per lane, then across the warp), written as six FP64 partials.
+// ------------------------------------------------- records of the group walk
+// One block per task: its records, packed in task order.
+__global__ void k_pack_records(const uint32_t* __restrict__ tcount,
+                               const uint32_t* __restrict__ toff, int64_t ntask,
+                               const uint32_t* __restrict__ base,
+                               const uint32_t* __restrict__ rkeys,
+                               const uint32_t* __restrict__ rmask, uint32_t* __restrict__ ckey,
+                               uint32_t* __restrict__ cidx, uint2* __restrict__ crec)
+{
+    for (int64_t task = blockIdx.x; task < ntask; task += gridDim.x) {
+        const uint32_t cnt = tcount[task], dst = toff[task], src = base[32 * task];
+        for (uint32_t r = threadIdx.x; r < cnt; r += blockDim.x) {
+            ckey[dst + r] = rkeys[src + r];
+            cidx[dst + r] = dst + r;
+            crec[dst + r] = make_uint2((uint32_t)task, rmask[src + r]);
+        }
+    }
+}
+
+// The sorted records and their entry counts.
+__global__ void k_record_gather(const uint32_t* __restrict__ sidx, int64_t nrec,
+                                const uint2* __restrict__ crec, uint2* __restrict__ srec,
+                                uint32_t* __restrict__ cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrec) return;
+    const uint2 r = crec[sidx[i]];
+    srec[i] = r;
+    cnt[i] = (uint32_t)__popc(r.y);
+}
+
+// Per source: its first sorted record and its entry range (keys outside
+// 0 .. nsrc - 1 can only come from a walk that raised its flag; skipped).
+__global__ void k_record_segments(const uint32_t* __restrict__ keys, int64_t nrec, int64_t nsrc,
+                                  const uint32_t* __restrict__ recE, uint32_t* __restrict__ rbeg,
+                                  uint32_t* __restrict__ beg, uint32_t* __restrict__ end)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrec) return;
+    const uint32_t kk = keys[i];
+    if ((int64_t)kk >= nsrc) return;
+    if (i == 0 || keys[i - 1] != kk) {
+        rbeg[kk] = (uint32_t)i;
+        beg[kk] = recE[i];
+    }
+    if (i == nrec - 1 || keys[i + 1] != kk) end[kk] = recE[i + 1];
+}
+
+// Position of the set bit of m that has j set bits below it (m has more than j).
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t j)
+{
+    uint32_t p = 0;
+#pragma unroll
+    for (uint32_t h = 16; h > 0; h >>= 1) {
+        const uint32_t c = (uint32_t)__popc(m & ((1u << h) - 1u));
+        if (j >= c) {
+            j -= c;
+            m >>= h;
+            p += h;
+        }
+    }
+    return p;
+}
+
+// k_item_sums with the entries read from the sorted records: the item's
+// entries are taken 32 at a time, lane j holding entry c0 + j, so each lane
+// sums the same entries in the same order as there.  The records overlapping
+// a group of 32 entries are at most 32 consecutive ones (each holds at least
+// one entry): lane l reads record r + l, the lanes whose record starts inside
+// the group mark its offset, and lane j's record is the last marked one at or
+// before j.
 template <typename R>
-__global__ void __launch_bounds__(kGradThreads) k_item_sums(
+__global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
     const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u, Tree<R> t, int64_t ncells,
-    int64_t nsrc, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ beg,
+    int64_t nsrc, const uint2* __restrict__ srec, const uint32_t* __restrict__ recE, int64_t nrec,
+    const uint32_t* __restrict__ rbeg, const uint32_t* __restrict__ beg,
     const uint32_t* __restrict__ end, const uint32_t* __restrict__ item_off,
     const uint32_t* __restrict__ item_src, double* __restrict__ part)
 {
@@ -114,19 +190,52 @@ __global__ void __launch_bounds__(kGradThreads) k_item_sums(
         x = pos[s - ncells];
         w = u[s - ncells];
     }
-    const uint32_t b = beg[s] + (uint32_t)(it - item_off[s]) * (uint32_t)kGradItemEntries;
+    const uint32_t bs = beg[s];
+    const uint32_t b = bs + (uint32_t)(it - item_off[s]) * (uint32_t)kGradItemEntries;
     const uint32_t e = min(end[s], b + (uint32_t)kGradItemEntries);
     const uint32_t np = (uint32_t)(nsrc - ncells);
+    // the record holding entry b: the last r with recE[r] <= b, among the
+    // source's first b - bs + 1 records
+    uint32_t lo = rbeg[s];
+    uint32_t hi = (uint32_t)min(nrec, (int64_t)lo + (int64_t)(b - bs) + 1);
+    while (hi - lo > 1u) {
+        const uint32_t mid = lo + (hi - lo) / 2u;
+        if (recE[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    uint32_t r = lo;
     R gx = 0, gy = 0, gz = 0, qx = 0, qy = 0, qz = 0;
-    for (uint32_t k = b + lane; k < e; k += 32) {
-        const uint32_t m = vals[k];
-        if (m >= np) continue;  // only after a flagged recording walk
-        const vec4<R> xm = pos[m], um = u[m];
-        const R rx = xm.x - x.x, ry = xm.y - x.y, rz = xm.z - x.z;
-        const R r2 = rx * rx + ry * ry + rz * rz;
-        // T(r) u_m (field of u_m) and grad phi(r; w_s, u_m) (force on w_s)
-        if (r2 > R(0))
-            dipole<R>(rx, ry, rz, r2, w.x, w.y, w.z, um.x, um.y, um.z, gx, gy, gz, qx, qy, qz);
+    for (uint32_t c0 = b; c0 < e; c0 += 32u) {
+        const uint32_t rr = r + (uint32_t)lane;
+        const bool have = (int64_t)rr < nrec;
+        const uint32_t E = have ? recE[rr] : 0xffffffffu;
+        const uint2 rec = have ? srec[rr] : make_uint2(0u, 0u);
+        const uint32_t d = E - c0;  // where record rr starts in the group
+        const uint32_t mark = lane == 0 ? 1u : (have && d < 32u ? 1u << d : 0u);
+        const uint32_t starts = __reduce_or_sync(kFull, mark);
+        const uint32_t upto = lane == 31 ? starts : starts & ((2u << lane) - 1u);
+        const int q = __popc(upto) - 1;
+        const uint32_t Eq = __shfl_sync(kFull, E, q);
+        const uint32_t mq = __shfl_sync(kFull, rec.y, q);
+        const uint32_t tq = __shfl_sync(kFull, rec.x, q);
+        const uint32_t k = c0 + (uint32_t)lane;
+        if (k < e) {
+            const uint32_t m = tq * 32u + nth_set_bit(mq, k - Eq);
+            if (m < np) {
+                const vec4<R> xm = pos[m], um = u[m];
+                const R rx = xm.x - x.x, ry = xm.y - x.y, rz = xm.z - x.z;
+                const R r2 = rx * rx + ry * ry + rz * rz;
+                // T(r) u_m (field of u_m) and grad phi(r; w_s, u_m) (force on w_s)
+                if (r2 > R(0))
+                    dipole<R>(rx, ry, rz, r2, w.x, w.y, w.z, um.x, um.y, um.z, gx, gy, gz, qx,
+                              qy, qz);
+            }
+        }
+        // the record holding entry c0 + 32: the group's last record, or the next
+        const int ql = __popc(starts) - 1;
+        const uint32_t El = __shfl_sync(kFull, E, ql);
+        const uint32_t ml = __shfl_sync(kFull, rec.y, ql);
+        r += (uint32_t)ql + (El + (uint32_t)__popc(ml) == c0 + 32u ? 1u : 0u);
     }
     gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz);
     qx = warp_sum(qx); qy = warp_sum(qy); qz = warp_sum(qz);
@@ -366,21 +475,48 @@ void grad_segments(const uint32_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg
     counted();
 }
 
+void grad_pack_records(const uint32_t* tcount, const uint32_t* toff, int64_t ntask,
+                       const uint32_t* base, const uint32_t* rkeys, const uint32_t* rmask,
+                       uint32_t* ckey, uint32_t* cidx, uint2* crec, cudaStream_t s)
+{
+    if (ntask <= 0) return;
+    const int64_t g = ntask < (1 << 20) ? ntask : (1 << 20);
+    k_pack_records<<<(unsigned)g, kGradThreads, 0, s>>>(tcount, toff, ntask, base, rkeys, rmask,
+                                                        ckey, cidx, crec);
+    counted();
+}
+
+void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
+                         const uint2* crec, int64_t nsrc, uint2* srec, uint32_t* cnt,
+                         uint32_t* recE, uint32_t* scan_tmp, uint32_t* rbeg, uint32_t* beg,
+                         uint32_t* end, cudaStream_t s)
+{
+    cudaMemsetAsync(beg, 0, sizeof(uint32_t) * nsrc, s);
+    cudaMemsetAsync(end, 0, sizeof(uint32_t) * nsrc, s);
+    if (nrec <= 0) return;
+    k_record_gather<<<blocks(nrec, kGradThreads), kGradThreads, 0, s>>>(sidx, nrec, crec, srec,
+                                                                       cnt);
+    scan_exclusive(cnt, recE, nrec, scan_tmp, s);
+    k_record_segments<<<blocks(nrec, kGradThreads), kGradThreads, 0, s>>>(skey, nrec, nsrc, recE,
+                                                                         rbeg, beg, end);
+    counted(2);
+}
+
 template <typename R>
-void grad_source_sums(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64_t ncells, int64_t n,
-                      const uint32_t* vals, const uint32_t* beg, const uint32_t* end,
-                      uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
-                      int64_t max_items, double* G, double* Q, cudaStream_t s)
+void grad_source_sums_rec(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64_t ncells,
+                          int64_t n, const uint2* srec, const uint32_t* recE, int64_t nrec,
+                          const uint32_t* rbeg, const uint32_t* beg, const uint32_t* end,
+                          uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
+                          int64_t max_items, double* G, double* Q, cudaStream_t s)
 {
     const int64_t nsrc = ncells + n;
     if (nsrc <= 0) return;
     k_item_counts<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(beg, end, nsrc, items);
     scan_exclusive(items, item_off, nsrc, scan_tmp, s);
-    // part holds 6 partial sums per item, then the item -> source map
     uint32_t* item_src = reinterpret_cast<uint32_t*>(part + 6 * max_items);
     k_item_sources<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(item_off, nsrc, item_src);
-    k_item_sums<R><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
-        pos, u, t, ncells, nsrc, vals, beg, end, item_off, item_src, part);
+    k_item_sums_rec<R><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
+        pos, u, t, ncells, nsrc, srec, recE, nrec, rbeg, beg, end, item_off, item_src, part);
     k_item_reduce<R><<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(t, ncells, nsrc, item_off,
                                                                        part, G, Q);
     counted(4);
@@ -470,10 +606,11 @@ void sum_z(const vec4<R>* v, int64_t n, double* tmp, double* out, cudaStream_t s
     template void sum_z<R>(const vec4<R>*, int64_t, double*, double*, cudaStream_t);              \
     template void grad_from_field<R>(const vec4<R>*, const vec4<R>*, int64_t, vec4<R>*, vec4<R>*, \
                                      cudaStream_t);                                               \
-    template void grad_source_sums<R>(const vec4<R>*, const vec4<R>*, Tree<R>, int64_t, int64_t,  \
-                                      const uint32_t*, const uint32_t*, const uint32_t*,          \
-                                      uint32_t*, uint32_t*, uint32_t*, double*, int64_t, double*, \
-                                      double*, cudaStream_t);                                    \
+    template void grad_source_sums_rec<R>(const vec4<R>*, const vec4<R>*, Tree<R>, int64_t,       \
+                                          int64_t, const uint2*, const uint32_t*, int64_t,        \
+                                          const uint32_t*, const uint32_t*, const uint32_t*,      \
+                                          uint32_t*, uint32_t*, uint32_t*, double*, int64_t,      \
+                                          double*, double*, cudaStream_t);                        \
     template void grad_finish<R>(Tree<R>, int64_t, int64_t, const double*, const double*,         \
                                  const vec4<R>*, const vec4<R>*, R, vec4<R>*, vec4<R>*,           \
                                  cudaStream_t);
