@@ -106,7 +106,13 @@ struct ff_ctx {
     int64_t s_cap = 0;           // sources the buffers hold
     double* i_part = nullptr;    // per work item: six partial sums; then each item's source
     int64_t i_cap = 0;
-    // records of the group walk (one per task and source taken by some lane of the task)
+    // every particle's sources, written by the counting walk (chunks of kPoolChunk)
+    uint32_t* p_keys = nullptr;
+    uint32_t* p_link = nullptr;
+    unsigned* p_next = nullptr;
+    int64_t p_cap = 0;           // chunks
+    uint32_t* s_src = nullptr;   // the source at each place of the depth-first order (s_cap)
+    // records (one per task and source some particle of the task has)
     uint32_t* t_cnt = nullptr;   // per task: its records (ntask)
     uint32_t* t_off = nullptr;   // their exclusive scan (ntask + 1)
     uint32_t* s_rbeg = nullptr;  // per source: its first sorted record (s_cap)
@@ -362,7 +368,8 @@ struct LaunchTally {
 // Sort the state into Morton order (the other buffer), build and aggregate
 // the tree, traverse.  h, f, esr (and counts) end in sorted order.
 template <typename R>
-ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = false)
+ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = false,
+                  const ffk::EntryPool* pool = nullptr)
 {
     const int64_t n = c->n;
     cudaStream_t s = c->stream;
@@ -403,15 +410,21 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = f
     }
     {
         StageTimer st(c, S_FIELD);
-        ffk::bh_field<R>(V<R>(b.pos), V<R>(b.u), n, t, field_params<R>(c, theta, include_sr),
-                         V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr),
-                         (c->p.count_interactions || force_counts) ? c->counts : nullptr,
-                         c->dflags, c->work,
-                         traverse_group(c), c->sched, c->off, segs_of(c), s);
+        if (pool)
+            ffk::bh_field_record<R>(V<R>(b.pos), V<R>(b.u), n, t,
+                                    field_params<R>(c, theta, include_sr), V<R>(c->h), V<R>(c->f),
+                                    static_cast<R*>(c->esr), c->counts, c->dflags, c->work, c->off,
+                                    segs_of(c), *pool, s);
+        else
+            ffk::bh_field<R>(V<R>(b.pos), V<R>(b.u), n, t, field_params<R>(c, theta, include_sr),
+                             V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr),
+                             (c->p.count_interactions || force_counts) ? c->counts : nullptr,
+                             c->dflags, c->work, traverse_group(c), c->sched, c->off, segs_of(c),
+                             s);
     }
     FF_LAUNCHED(c);
     c->tree_valid = true;
-    c->counts_valid = c->p.count_interactions != 0 || force_counts;
+    c->counts_valid = c->p.count_interactions != 0 || force_counts || pool;
     return FF_OK;
 }
 
@@ -501,7 +514,7 @@ void free_all(ff_ctx* c)
                     c->e_keys[0], c->e_keys[1], c->e_vals[0], c->e_vals[1], c->e_tmp, c->s_beg,
                     c->s_end, c->s_G, c->s_Q, c->s_items, c->s_item_off, c->s_scan, c->i_part,
                     c->t_cnt, c->t_off, c->s_rbeg, c->r_key, c->r_idx, c->r_rec, c->r_srec,
-                    c->r_cnt, c->r_E, c->r_scan};
+                    c->r_cnt, c->r_E, c->r_scan, c->p_keys, c->p_link, c->p_next, c->s_src};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int k = 0; k < 2; ++k) {
@@ -792,7 +805,8 @@ ff_status grow(ff_ctx* c, T** p, size_t count)
 
 // After a counted Barnes-Hut evaluation: scans the per-particle interaction
 // counts into entry slots and sizes every buffer the recorded entries need.
-ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64_t* max_items_out)
+ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64_t* max_items_out,
+                          int64_t* pool_used = nullptr)
 {
     const int64_t n = c->n;
     cudaStream_t s = c->stream;
@@ -810,7 +824,11 @@ ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64
     unsigned long long total = 0;
     FF_CUDA(c, cudaMemcpyAsync(&total, c->e_total, sizeof(total), cudaMemcpyDeviceToHost, s));
     FF_CUDA(c, cudaMemcpyAsync(&ncells_h, c->off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    unsigned taken = 0;
+    if (pool_used)
+        FF_CUDA(c, cudaMemcpyAsync(&taken, c->p_next, sizeof(taken), cudaMemcpyDeviceToHost, s));
     if ((st = sync_and_check(c)) != FF_OK) return st;
+    if (pool_used) *pool_used = n + (int64_t)taken;
     // entry positions are 32-bit, with room for the recording walk's 16-byte groups
     if (total >= 0xfffffff0ull)
         return fail(c, FF_EINVAL, "too many interactions (%llu) for one gradient pass", total);
@@ -836,6 +854,7 @@ ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64
         if ((st = grow(c, &c->s_item_off, cap + 1)) != FF_OK) return st;
         if ((st = grow(c, &c->s_scan, ffk::scan_tmp_words(cap))) != FF_OK) return st;
         if ((st = grow(c, &c->s_rbeg, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->s_src, cap)) != FF_OK) return st;
         c->s_cap = cap;
     }
     const int64_t max_items = nsrc + ne / ffk::kGradItemEntries + 1;
@@ -865,13 +884,40 @@ void sort_entries(ff_ctx* c, int64_t ne, int64_t nsrc, const uint32_t** keys,
     *vals = c->e_vals[in1 ? 1 : 0];
 }
 
-// After prepare_entries: the group walk's records, packed, sorted by source and
-// scanned into entry offsets (k_field.cu group_record_task, k_grad.cu).  Waits
-// for the walk to read the number of records.
+// The entry pool of the recording walk: at least `chunks` chunks.
+ff_status grow_pool(ff_ctx* c, int64_t chunks)
+{
+    ff_status st;
+    if (chunks <= c->p_cap) return FF_OK;
+    if (chunks > 0xffffffffll)
+        return fail(c, FF_EINVAL, "too many interactions (%lld chunks) for one gradient pass",
+                    (long long)chunks);
+    if ((st = grow(c, &c->p_keys, (size_t)chunks * ffk::kPoolChunk)) != FF_OK) return st;
+    if ((st = grow(c, &c->p_link, chunks)) != FF_OK) return st;
+    if (!c->p_next && (st = grow(c, &c->p_next, 1)) != FF_OK) return st;
+    c->p_cap = chunks;
+    return FF_OK;
+}
+
+ffk::EntryPool pool_of(ff_ctx* c)
+{
+    ffk::EntryPool p;
+    p.keys = c->p_keys;
+    p.link = c->p_link;
+    p.next = c->p_next;
+    p.cap = (uint32_t)c->p_cap;
+    p.first = (uint32_t)c->n;
+    return p;
+}
+
+// After the recording walk and prepare_entries: each task's sources merged into
+// records, packed, sorted by their place in the depth-first order and scanned
+// into entry offsets (k_grad.cu).  Waits to read the number of records.
 template <typename R>
-ff_status record_sources(ff_ctx* c, double theta, int64_t nsrc, int64_t* nrec_out)
+ff_status record_sources(ff_ctx* c, int64_t ncells, int64_t* nrec_out)
 {
     const int64_t n = c->n;
+    const int64_t nsrc = ncells + n;
     const int64_t ntask = (n + 31) / 32;
     cudaStream_t s = c->stream;
     ff_status st;
@@ -879,12 +925,11 @@ ff_status record_sources(ff_ctx* c, double theta, int64_t nsrc, int64_t* nrec_ou
         if ((st = grow(c, &c->t_cnt, ntask)) != FF_OK) return st;
         if ((st = grow(c, &c->t_off, ntask + 1)) != FF_OK) return st;
     }
-    Buffers& a = c->st[c->cur];
     // the records of task T go to the slots of its particles (e_keys[0], e_vals[0])
-    ffk::bh_group_record<R>(V<R>(a.pos), n, tree_of<R>(c), field_params<R>(c, theta, 0), c->e_base,
-                            c->e_keys[0], c->e_vals[0], c->t_cnt, c->dflags, c->work, c->off,
-                            segs_of(c), s);
+    ffk::grad_merge_records(c->e_cnt, n, pool_of(c), c->e_base, c->e_keys[0], c->e_vals[0],
+                            c->t_cnt, c->dflags, s);
     ffk::scan_exclusive(c->t_cnt, c->t_off, ntask, c->scan_tmp, s);
+    ffk::grad_source_map<R>(tree_of<R>(c), ncells, c->s_src, s);
     FF_LAUNCHED(c);
     uint32_t total = 0;
     FF_CUDA(c, cudaMemcpyAsync(&total, c->t_off + ntask, sizeof(total), cudaMemcpyDeviceToHost, s));
@@ -912,8 +957,8 @@ ff_status record_sources(ff_ctx* c, double theta, int64_t nsrc, int64_t* nrec_ou
         nullptr, 0);
     const uint32_t* skey = in1 ? c->e_keys[0] : c->r_key;
     const uint32_t* sidx = in1 ? c->e_vals[0] : c->r_idx;
-    ffk::grad_record_sources(skey, sidx, nrec, c->r_rec, nsrc, c->r_srec, c->r_cnt, c->r_E,
-                             c->r_scan, c->s_rbeg, c->s_beg, c->s_end, s);
+    ffk::grad_record_sources(skey, sidx, nrec, c->r_rec, c->s_src, nsrc, c->r_srec, c->r_cnt,
+                             c->r_E, c->r_scan, c->s_rbeg, c->s_beg, c->s_end, s);
     FF_LAUNCHED(c);
     *nrec_out = nrec;
     return FF_OK;
@@ -940,14 +985,26 @@ ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy, boo
         ffk::grad_from_field<R>(V<R>(c->h), V<R>(c->f), n, V<R>(c->g_pos), V<R>(c->g_u), s);
         FF_LAUNCHED(c);
     } else {
-        if ((st = eval_bh<R>(c, theta, 0, true)) != FF_OK) return st;
-        int64_t ne = 0, ncells = 0, max_items = 0;
-        if ((st = prepare_entries(c, &ne, &ncells, &max_items)) != FF_OK) return st;
-        const int64_t nsrc = ncells + n;
+        // the field, the counts and every particle's sources in one walk; a pool
+        // that ran out is grown to what the walk took and the walk redone
+        if (c->p_cap < n + 1024 && (st = grow_pool(c, 9 * n + 1024)) != FF_OK) return st;
+        FF_CUDA(c, cudaMemsetAsync(c->p_next, 0, sizeof(unsigned), s));
+        ffk::EntryPool pool = pool_of(c);
+        if ((st = eval_bh<R>(c, theta, 0, true, &pool)) != FF_OK) return st;
+        int64_t ne = 0, ncells = 0, max_items = 0, used = 0;
+        if ((st = prepare_entries(c, &ne, &ncells, &max_items, &used)) != FF_OK) return st;
         Buffers& a = c->st[c->cur];
         ffk::Tree<R> t = tree_of<R>(c);
+        if (used > c->p_cap) {
+            if ((st = grow_pool(c, used + used / 8 + 1024)) != FF_OK) return st;
+            FF_CUDA(c, cudaMemsetAsync(c->p_next, 0, sizeof(unsigned), s));
+            ffk::bh_field_record<R>(V<R>(a.pos), V<R>(a.u), n, t, field_params<R>(c, theta, 0),
+                                    V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr), c->counts,
+                                    c->dflags, c->work, c->off, segs_of(c), pool_of(c), s);
+            FF_LAUNCHED(c);
+        }
         int64_t nrec = 0;
-        if ((st = record_sources<R>(c, theta, nsrc, &nrec)) != FF_OK) return st;
+        if ((st = record_sources<R>(c, ncells, &nrec)) != FF_OK) return st;
         ffk::grad_source_sums_rec<R>(V<R>(a.pos), V<R>(a.u), t, ncells, n, c->r_srec, c->r_E,
                                      nrec, c->s_rbeg, c->s_beg, c->s_end, c->s_items,
                                      c->s_item_off, c->s_scan, c->i_part, max_items, c->s_G,

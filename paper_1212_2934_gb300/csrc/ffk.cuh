@@ -238,14 +238,28 @@ void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
                    const uint32_t* base, uint32_t* keys, int* flags, int* work,
                    const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s);
 
-// Source records of the gradient pass (see k_field.cu): one warp per task of 32
-// particles walks the union of their cell lists; every source some lane takes
-// is written once, with the mask of those lanes, to rkeys/rmask from
-// base[32 task] on, and the task's number of records to tcount[task].
+// Source lists written by the counting traversal of the gradient pass: the
+// sources of particle k, in the order of its walk, fill chunk k of kPoolChunk
+// keys and then chunks first + 0, first + 1, .. in the order *next (zeroed
+// before the walk) hands them out; link[c] is the chunk after c.  A source is
+// named by its place in the depth-first order of cells and particles (cell c:
+// c + first particle of c; particle p of leaf L: L + 1 + p), so each list
+// rises strictly.  Chunks at or past cap are not written: first + *next then
+// ends above cap and the walk must be redone with more chunks.
+constexpr int kPoolChunk = 128;
+struct EntryPool {
+    uint32_t* keys = nullptr;  // cap x kPoolChunk
+    uint32_t* link = nullptr;  // cap
+    unsigned* next = nullptr;
+    uint32_t cap = 0;
+    uint32_t first = 0;        // the first chunk handed out (n)
+};
+// bh_field of the one-lane walk with counts, also writing every particle's
+// sources to the pool.
 template <typename R>
-void bh_group_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp,
-                     const uint32_t* base, uint32_t* rkeys, uint32_t* rmask, uint32_t* tcount,
-                     int* flags, int* work, const uint32_t* off, Segs sg, cudaStream_t s);
+void bh_field_record(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
+                     vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work,
+                     const uint32_t* off, Segs sg, EntryPool pool, cudaStream_t s);
 
 // ------------------------------------------------ energy gradient (k_grad.cu)
 // entries per particle (accepted cells + exact pairs) as uint32; *total64
@@ -256,20 +270,32 @@ void grad_entry_counts(const int4* counts, int64_t n, uint32_t* out,
 // nsrc, zeroed here)
 void grad_segments(const uint32_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg, uint32_t* end,
                    cudaStream_t s);
-// Records of the group walk: the ntask tasks' records (tcount each, from
-// base[32 task] in rkeys/rmask; toff = exclusive scan of tcount) packed in task
-// order: ckey (the source), cidx[r] = r, crec[r] = (task, lane mask).
+// One warp per task of 32 particles merges their source lists (cnt[k] sources
+// of particle k in the pool): each source some lane has is written once, with
+// the mask of those lanes, to rkeys/rmask from base[32 task] on (base: scan of
+// cnt), in rising order, and the task's number of records to tcount[task].
+void grad_merge_records(const uint32_t* cnt, int64_t n, EntryPool pool, const uint32_t* base,
+                        uint32_t* rkeys, uint32_t* rmask, uint32_t* tcount, int* flags,
+                        cudaStream_t s);
+// The source named by each place of the depth-first order (cells: the cell,
+// particles of multi-particle leaves: ncells + the particle): src_of[ncells + n].
+template <typename R>
+void grad_source_map(Tree<R> t, int64_t ncells, uint32_t* src_of, cudaStream_t s);
+// Records packed in task order: the ntask tasks' records (tcount each, from
+// base[32 task] in rkeys/rmask; toff = exclusive scan of tcount) to ckey (the
+// key), cidx[r] = r, crec[r] = (task, lane mask).
 void grad_pack_records(const uint32_t* tcount, const uint32_t* toff, int64_t ntask,
                        const uint32_t* base, const uint32_t* rkeys, const uint32_t* rmask,
                        uint32_t* ckey, uint32_t* cidx, uint2* crec, cudaStream_t s);
-// After the records are sorted by source (skey, sidx = their packed index):
+// After the records are sorted by key (skey, sidx = their packed index):
 // srec[i] = crec[sidx[i]], recE[i] = entries before record i (recE[nrec] =
-// entries), and per source its first record rbeg, and the entry range beg, end
-// (nsrc each, zeroed here).  cnt: nrec words of scratch, scan_tmp for nrec.
+// entries), and per source s = src_of[key] its first record rbeg, and the
+// entry range beg, end (nsrc each, zeroed here).  cnt: nrec words of scratch,
+// scan_tmp for nrec.
 void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
-                         const uint2* crec, int64_t nsrc, uint2* srec, uint32_t* cnt,
-                         uint32_t* recE, uint32_t* scan_tmp, uint32_t* rbeg, uint32_t* beg,
-                         uint32_t* end, cudaStream_t s);
+                         const uint2* crec, const uint32_t* src_of, int64_t nsrc, uint2* srec,
+                         uint32_t* cnt, uint32_t* recE, uint32_t* scan_tmp, uint32_t* rbeg,
+                         uint32_t* beg, uint32_t* end, cudaStream_t s);
 // per source s: G_s = sum over its entries of T(r) u_m and Q_s = sum of
 // grad phi(r; w_s, u_m) / n_s, r = rho_m - x_s (FP64 results, 3 per source).
 // Entry e of source s (beg[s] <= e < end[s]) is particle 32 task + lane of the

@@ -362,19 +362,74 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
     if (COUNT) counts[k] = make_int4(nacc, npair, nopen, 0);
 }
 
+// A particle's source list in the entry pool: chunk k first, then chunks taken
+// from *next.  Sources are kept four at a time and stored as one 16-byte word
+// (a chunk holds a multiple of four); the chunk after a full one is taken at
+// once.  Nothing is written to chunks at or past cap.
+struct ChunkWriter {
+    uint32_t* keys;
+    uint32_t* link;
+    unsigned* next;
+    uint32_t cap, first;
+    uint32_t ck, f;       // current chunk, sources so far
+    uint32_t s0, s1, s2;  // the current group of four so far
+
+    __device__ __forceinline__ ChunkWriter(const EntryPool& p, uint32_t own)
+        : keys(p.keys), link(p.link), next(p.next), cap(p.cap), first(p.first), ck(own), f(0),
+          s0(0), s1(0), s2(0)
+    {
+    }
+    __device__ __forceinline__ void put(uint32_t key)
+    {
+        const uint32_t q = f & 3u;
+        if (q == 0u) {
+            s0 = key;
+        } else if (q == 1u) {
+            s1 = key;
+        } else if (q == 2u) {
+            s2 = key;
+        } else {
+            const uint32_t o = f & (uint32_t)(kPoolChunk - 1);
+            if (ck < cap)
+                *reinterpret_cast<uint4*>(keys + (size_t)ck * kPoolChunk + (o - 3u)) =
+                    make_uint4(s0, s1, s2, key);
+            if (o == (uint32_t)(kPoolChunk - 1)) {
+                const uint32_t nk = first + atomicAdd(next, 1u);
+                if (ck < cap) link[ck] = nk;
+                ck = nk;
+            }
+        }
+        ++f;
+    }
+    // the last, incomplete group
+    __device__ __forceinline__ void flush()
+    {
+        const uint32_t r = f & 3u;
+        if (r == 0u || ck >= cap) return;
+        uint32_t* p = keys + (size_t)ck * kPoolChunk + ((f - r) & (uint32_t)(kPoolChunk - 1));
+        p[0] = s0;
+        if (r > 1u) p[1] = s1;
+        if (r > 2u) p[2] = s2;
+    }
+};
+
 // Independent per-lane walk (group size 1): each lane follows its own path
-// through the cell list; no vote or shuffle per visited cell.
-template <typename R, bool COUNT, bool QUAD>
+// through the cell list; no vote or shuffle per visited cell.  With REC (and
+// COUNT) each source also goes to the particle's list in the entry pool.
+template <typename R, bool COUNT, bool QUAD, bool REC = false>
 __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ pos,
                                          const vec4<R>* __restrict__ u, int n, const Tree<R>& t,
                                          const FieldParams<R>& fp, unsigned ncells,
                                          vec4<R>* __restrict__ h, vec4<R>* __restrict__ f,
                                          R* __restrict__ esr, int4* __restrict__ counts, int* flags,
-                                         const uint32_t* __restrict__ off, const Segs& sg)
+                                         const uint32_t* __restrict__ off, const Segs& sg,
+                                         const EntryPool& ep = EntryPool())
 {
+    static_assert(!REC || (COUNT && !QUAD), "sources are recorded by the counting walk");
     const int lane = threadIdx.x & 31;
     const int k = task * 32 + lane;
     if (k >= n) return;
+    ChunkWriter cw(ep, (uint32_t)k);
     const vec4<R> xk = pos[k], uk = u[k];
     R hx = 0, hy = 0, hz = 0, fx = 0, fy = 0, fz = 0, sx = 0, sy = 0, sz = 0, es = 0, ck = 0;
     int nacc = 0, npair = 0, nopen = 0;
@@ -417,6 +472,7 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
             // particle itself (centre and moment sum of one term are exact)
             walk_pair(rx, ry, rz, r2, uk.x, uk.y, uk.z, m.x, m.y, m.z, hx, hy, hz, fx, fy, fz,
                           ck);
+            if (REC) cw.put(i + (uint32_t)nd.x);
             if (QUAD && acc && r2 > R(0))
                 quad_term<R>(rx, ry, rz, r2, t.q1[i], t.q2[i], uk.x, uk.y, uk.z, hx, hy, hz, fx,
                              fy, fz);
@@ -431,6 +487,7 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
             if (!single) {
                 for (int s = nd.x; s < nd.y; ++s) {
                     if (s == k) continue;
+                    if (REC) cw.put(i + 1u + (uint32_t)s);
                     const vec4<R> xj = pos[s], uj = u[s];
                     const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
                     const R r2 = rx * rx + ry * ry + rz * rz;
@@ -452,6 +509,7 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
         }
         i = nxt;
     }
+    if (REC) cw.flush();
     vec4<R> ho, fo;
     ho.x = fp.dip_scale * hx;
     ho.y = fp.dip_scale * hy;
@@ -669,128 +727,6 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
     }
 }
 
-// Source records for the energy gradient, one warp per 32-particle task: the
-// lanes walk the union of their cell lists in order (the lane-group walk with
-// G = 32), each lane deciding its own cells exactly as record_task does, and
-// each source that at least one lane takes is written once, with the mask of
-// the lanes that take it.  Sources are numbered as in record_task; within a
-// task each source occurs once.  The records of a task go to rkeys/rmask from
-// base[32 task] on (a task has at most as many records as entries, so they fit
-// in the task's slots) and their number to tcount[task].  Expanding the records
-// lane by lane gives every entry of the task, so after a stable sort on the
-// source the entries come out in the order of the per-lane slots.
-template <typename R>
-__device__ __forceinline__ void group_record_task(int task, const vec4<R>* __restrict__ pos, int n,
-                                                  const Tree<R>& t, const FieldParams<R>& fp,
-                                                  unsigned ncells,
-                                                  const uint32_t* __restrict__ base,
-                                                  uint32_t* __restrict__ rkeys,
-                                                  uint32_t* __restrict__ rmask,
-                                                  uint32_t* __restrict__ tcount, int* flags,
-                                                  const uint32_t* __restrict__ off, const Segs& sg)
-{
-    const int lane = threadIdx.x & 31;
-    const int k0 = task * 32;
-    const int k = k0 + lane;
-    const bool active = k < n;
-    vec4<R> xk;
-    if (active) {
-        xk = pos[k];
-    } else {
-        xk.x = xk.y = xk.z = xk.w = R(0);
-    }
-    unsigned first = 0, end = ncells;
-    if (sg.of_pos && active) {
-        const int sys = (int)sg.of_pos[k];
-        first = off[sg.start[sys]];
-        end = off[sg.start[sys + 1]];
-    }
-    unsigned nxt = active && first < end ? first : 0xffffffffu;
-    const uint32_t w0 = base[k0];
-    const uint32_t wend = base[min(k0 + 32, n)];
-    uint32_t w = w0;
-    for (;;) {
-        const unsigned i = __reduce_min_sync(kFull, nxt);
-        if (i >= ncells) break;
-        // one address for the whole warp: a single transaction
-        const Cell<R> cl = t.cell[i];
-        const int4 nd = cl.node;
-        bool take = false, pairs = false;
-        if (nxt == i) {
-            const bool inside = nd.x <= k && k < nd.y;
-            const bool leaf = (nd.w >> 8) != 0;
-            const bool single = (nd.w >> 9) != 0;  // a one-particle leaf
-            // a one-particle leaf outside is recorded as the cell whether accepted
-            // or summed as a pair (the same entry)
-            take = (single && !inside) ||
-                   (!inside && accept<R>(fp, xk, cl.cen, t.lo, (int)i, t.mom[i].w));
-            pairs = !take && leaf && !single;
-            unsigned nx = (take || leaf) ? (unsigned)nd.z : i + 1;
-            if (nx <= i) {  // skip pointers must move forward
-                atomicOr(flags, FLAG_TRAVERSE);
-                nx = 0xffffffffu;
-            }
-            nxt = nx >= end ? 0xffffffffu : nx;
-        }
-        const uint32_t mt = __ballot_sync(kFull, take);
-        if (mt) {
-            if (lane == 0 && w < wend) {
-                rkeys[w] = i;
-                rmask[w] = mt;
-            }
-            ++w;
-        }
-        const uint32_t mp = __ballot_sync(kFull, pairs);
-        if (mp) {
-            // the particles of an opened multi-particle leaf, each but the lane's own
-            for (int s = nd.x; s < nd.y; ++s) {
-                const uint32_t m = (s >= k0 && s < k0 + 32) ? mp & ~(1u << (s - k0)) : mp;
-                if (m) {
-                    if (lane == 0 && w < wend) {
-                        rkeys[w] = ncells + (uint32_t)s;
-                        rmask[w] = m;
-                    }
-                    ++w;
-                }
-            }
-        }
-    }
-    if (lane == 0) {
-        tcount[task] = w - w0;
-        if (w > wend) atomicOr(flags, FLAG_TRAVERSE);
-    }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_group_record(
-    const vec4<R>* __restrict__ pos, int n, Tree<R> t, FieldParams<R> fp,
-    const uint32_t* __restrict__ base, uint32_t* __restrict__ rkeys, uint32_t* __restrict__ rmask,
-    uint32_t* __restrict__ tcount, int* flags, int* __restrict__ work, int nseg,
-    const uint32_t* __restrict__ off, Segs sg)
-{
-    if (*flags & FLAG_CAPACITY) return;
-    const unsigned ncells = (unsigned)*t.ncells;
-    const int ntask = (n + 31) / 32;
-    unsigned smid;
-    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-    const int home = (int)(smid % (unsigned)nseg);
-    const int lane = threadIdx.x & 31;
-    for (int probe = 0; probe < nseg; ++probe) {
-        const int ws = (home + probe) % nseg;
-        const int t0 = (int)((int64_t)ntask * ws / nseg);
-        const int t1 = (int)((int64_t)ntask * (ws + 1) / nseg);
-        for (;;) {
-            int got = 0;
-            if (lane == 0) got = atomicAdd(&work[ws], 1);
-            got = __shfl_sync(kFull, got, 0);
-            const int task = t0 + got;
-            if (task >= t1) break;
-            group_record_task<R>(task, pos, n, t, fp, ncells, base, rkeys, rmask, tcount, flags,
-                                 off, sg);
-        }
-    }
-}
-
 // Persistent traversal: the key order is cut into nseg contiguous segments of
 // 32-particle tasks; a warp takes tasks from the segment of the SM it runs on
 // (so warps sharing an L1 cache walk neighbouring parts of the tree) and then
@@ -829,6 +765,48 @@ __global__ void __launch_bounds__(THREADS, MINB) k_bh(const vec4<R>* __restrict_
             else
                 bh_task<R, COUNT, G>(task, pos, u, n, t, fp, ncells, h, f, esr, counts, flags, off,
                                      sg);
+        }
+    }
+}
+
+// The counting walk that also records every particle's sources (energy
+// gradient), on the schedule of k_bh.  Its list writer needs a few more
+// registers than the counting walk: 8 blocks of 128 (64 registers) in FP32.
+#ifndef FFK_BH_MIN_BLOCKS_REC
+#define FFK_BH_MIN_BLOCKS_REC 8
+#endif
+template <typename R>
+constexpr int bh_rec_min_blocks()
+{
+    return sizeof(R) == 8 ? FFK_BH_MIN_BLOCKS_FP64 : FFK_BH_MIN_BLOCKS_REC;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBhThreads, (bh_rec_min_blocks<R>())) k_bh_rec(
+    const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u, int n, Tree<R> t,
+    FieldParams<R> fp, vec4<R>* __restrict__ h, vec4<R>* __restrict__ f, R* __restrict__ esr,
+    int4* __restrict__ counts, int* flags, int* __restrict__ work, int nseg,
+    const uint32_t* __restrict__ off, Segs sg, EntryPool ep)
+{
+    if (*flags & FLAG_CAPACITY) return;
+    const unsigned ncells = (unsigned)*t.ncells;
+    const int ntask = (n + 31) / 32;
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    const int home = (int)(smid % (unsigned)nseg);
+    const int lane = threadIdx.x & 31;
+    for (int probe = 0; probe < nseg; ++probe) {
+        const int ws = (home + probe) % nseg;
+        const int t0 = (int)((int64_t)ntask * ws / nseg);
+        const int t1 = (int)((int64_t)ntask * (ws + 1) / nseg);
+        for (;;) {
+            int got = 0;
+            if (lane == 0) got = atomicAdd(&work[ws], 1);
+            got = __shfl_sync(kFull, got, 0);
+            const int task = t0 + got;
+            if (task >= t1) break;
+            bh_task1<R, true, false, true>(task, pos, u, n, t, fp, ncells, h, f, esr, counts,
+                                           flags, off, sg, ep);
         }
     }
 }
@@ -1015,6 +993,27 @@ void bh_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldP
 }
 
 template <typename R>
+void bh_field_record(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t, FieldParams<R> fp,
+                     vec4<R>* h, vec4<R>* f, R* esr, int4* counts, int* flags, int* work,
+                     const uint32_t* off, Segs sg, EntryPool pool, cudaStream_t s)
+{
+    if (n <= 0) return;
+    static std::mutex mu;
+    static PersistentGrid cache[kMaxDevices];
+    const PersistentGrid g = persistent_grid(cache, mu, [] {
+        cudaFuncSetAttribute(k_bh_rec<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             kTraverseCarveout);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_rec<R>, kBhThreads, 0);
+        return per_sm;
+    });
+    cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
+    k_bh_rec<R><<<g.blocks, kBhThreads, 0, s>>>(pos, u, (int)n, t, fp, h, f, esr, counts, flags,
+                                                work, g.nseg, off, sg, pool);
+    counted();
+}
+
+template <typename R>
 void ap_field(const vec4<R>* pos, const vec4<R>* u, int64_t n, FieldParams<R> fp, vec4<R>* h,
               vec4<R>* f, R* esr, cudaStream_t s)
 {
@@ -1029,6 +1028,12 @@ template void bh_field<float>(const float4*, const float4*, int64_t, Tree<float>
 template void bh_field<double>(const dvec4*, const dvec4*, int64_t, Tree<double>,
                                FieldParams<double>, dvec4*, dvec4*, double*, int4*, int*, int*,
                                int, int, const uint32_t*, Segs, cudaStream_t);
+template void bh_field_record<float>(const float4*, const float4*, int64_t, Tree<float>,
+                                     FieldParams<float>, float4*, float4*, float*, int4*, int*,
+                                     int*, const uint32_t*, Segs, EntryPool, cudaStream_t);
+template void bh_field_record<double>(const dvec4*, const dvec4*, int64_t, Tree<double>,
+                                      FieldParams<double>, dvec4*, dvec4*, double*, int4*, int*,
+                                      int*, const uint32_t*, Segs, EntryPool, cudaStream_t);
 template void ap_field<float>(const float4*, const float4*, int64_t, FieldParams<float>, float4*,
                               float4*, float*, cudaStream_t);
 template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<double>, dvec4*,
@@ -1071,34 +1076,6 @@ void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
     bh_record_g<R, true>(pos, n, t, fp, base, keys, flags, work, off, sg, vj, s);
 }
 
-template <typename R>
-void bh_group_record(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp,
-                     const uint32_t* base, uint32_t* rkeys, uint32_t* rmask, uint32_t* tcount,
-                     int* flags, int* work, const uint32_t* off, Segs sg, cudaStream_t s)
-{
-    if (n <= 0) return;
-    static std::mutex mu;
-    static PersistentGrid cache[kMaxDevices];
-    const PersistentGrid g = persistent_grid(cache, mu, [] {
-        cudaFuncSetAttribute(k_bh_group_record<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             kTraverseCarveout);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_group_record<R>, kBhThreads,
-                                                      0);
-        return per_sm;
-    });
-    cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
-    k_bh_group_record<R><<<g.blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, rkeys, rmask,
-                                                         tcount, flags, work, g.nseg, off, sg);
-    counted();
-}
-
-template void bh_group_record<float>(const float4*, int64_t, Tree<float>, FieldParams<float>,
-                                     const uint32_t*, uint32_t*, uint32_t*, uint32_t*, int*, int*,
-                                     const uint32_t*, Segs, cudaStream_t);
-template void bh_group_record<double>(const dvec4*, int64_t, Tree<double>, FieldParams<double>,
-                                      const uint32_t*, uint32_t*, uint32_t*, uint32_t*, int*,
-                                      int*, const uint32_t*, Segs, cudaStream_t);
 template void bh_record_vjp<float>(const float4*, const float4*, const float4*, const float4*,
                                    int64_t, Tree<float>, FieldParams<float>, const uint32_t*,
                                    uint32_t*, int*, int*, const uint32_t*, Segs, float4*, float4*,

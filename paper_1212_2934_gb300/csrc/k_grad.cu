@@ -99,7 +99,81 @@ __global__ void k_item_sources(const uint32_t* __restrict__ item_off, int64_t ns
     for (uint32_t it = item_off[s]; it < item_off[s + 1]; ++it) item_src[it] = (uint32_t)s;
 }
 
-// ------------------------------------------------- records of the group walk
+// ------------------------------------------------------- source records
+// One warp per task of 32 particles: the lanes' source lists (each rising) are
+// merged; each step takes the smallest head, writes it once with the mask of
+// the lanes holding it, and advances those lanes.  A lane reads its list four
+// sources at a time, following the chunk links.
+__global__ void __launch_bounds__(kGradThreads) k_merge_records(
+    const uint32_t* __restrict__ cnt, int64_t n, EntryPool pool, const uint32_t* __restrict__ base,
+    uint32_t* __restrict__ rkeys, uint32_t* __restrict__ rmask, uint32_t* __restrict__ tcount,
+    int* flags)
+{
+    const int64_t task = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t ntask = (n + 31) / 32;
+    if (task >= ntask) return;
+    const int64_t k = task * 32 + lane;
+    const uint32_t c = k < n ? cnt[k] : 0u;
+    constexpr uint32_t kNone = 0xffffffffu;
+    uint32_t ck = (uint32_t)k, pos = 0, head = kNone;
+    uint4 buf = make_uint4(0u, 0u, 0u, 0u);
+    if (c > 0u) {
+        buf = *reinterpret_cast<const uint4*>(pool.keys + (size_t)ck * kPoolChunk);
+        head = buf.x;
+    }
+    const uint32_t w0 = base[task * 32];
+    const uint32_t wend = base[min(task * 32 + 32, n)];
+    uint32_t w = w0;
+    for (;;) {
+        const uint32_t key = __reduce_min_sync(kFull, head);
+        if (key == kNone) break;
+        const bool mine = head == key;
+        const uint32_t m = __ballot_sync(kFull, mine);
+        if (lane == 0 && w < wend) {
+            rkeys[w] = key;
+            rmask[w] = m;
+        }
+        ++w;
+        if (mine) {
+            ++pos;
+            if (pos == c) {
+                head = kNone;
+            } else {
+                const uint32_t o = pos & (uint32_t)(kPoolChunk - 1);
+                if (o == 0u) {
+                    ck = pool.link[ck];
+                    if (ck >= pool.cap) {  // a pool that ran out: the caller redoes the walk
+                        atomicOr(flags, FLAG_TRAVERSE);
+                        head = kNone;
+                        continue;
+                    }
+                }
+                if ((o & 3u) == 0u)
+                    buf = *reinterpret_cast<const uint4*>(pool.keys + (size_t)ck * kPoolChunk + o);
+                const uint32_t q = o & 3u;
+                head = q == 0u ? buf.x : q == 1u ? buf.y : q == 2u ? buf.z : buf.w;
+            }
+        }
+    }
+    if (lane == 0) {
+        tcount[task] = w - w0;
+        if (w > wend) atomicOr(flags, FLAG_TRAVERSE);
+    }
+}
+
+// The source at each place of the depth-first order of cells and particles.
+template <typename R>
+__global__ void k_source_map(Tree<R> t, int64_t ncells, uint32_t* __restrict__ src_of)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const int4 nd = t.cell[c].node;
+    src_of[c + nd.x] = (uint32_t)c;
+    if ((nd.w >> 8) != 0)
+        for (int p = nd.x; p < nd.y; ++p) src_of[c + 1 + p] = (uint32_t)(ncells + p);
+}
+
 // One block per task: its records, packed in task order.
 __global__ void k_pack_records(const uint32_t* __restrict__ tcount,
                                const uint32_t* __restrict__ toff, int64_t ntask,
@@ -133,6 +207,7 @@ __global__ void k_record_gather(const uint32_t* __restrict__ sidx, int64_t nrec,
 // Per source: its first sorted record and its entry range (keys outside
 // 0 .. nsrc - 1 can only come from a walk that raised its flag; skipped).
 __global__ void k_record_segments(const uint32_t* __restrict__ keys, int64_t nrec, int64_t nsrc,
+                                  const uint32_t* __restrict__ src_of,
                                   const uint32_t* __restrict__ recE, uint32_t* __restrict__ rbeg,
                                   uint32_t* __restrict__ beg, uint32_t* __restrict__ end)
 {
@@ -140,11 +215,12 @@ __global__ void k_record_segments(const uint32_t* __restrict__ keys, int64_t nre
     if (i >= nrec) return;
     const uint32_t kk = keys[i];
     if ((int64_t)kk >= nsrc) return;
+    const uint32_t src = src_of[kk];
     if (i == 0 || keys[i - 1] != kk) {
-        rbeg[kk] = (uint32_t)i;
-        beg[kk] = recE[i];
+        rbeg[src] = (uint32_t)i;
+        beg[src] = recE[i];
     }
-    if (i == nrec - 1 || keys[i + 1] != kk) end[kk] = recE[i + 1];
+    if (i == nrec - 1 || keys[i + 1] != kk) end[src] = recE[i + 1];
 }
 
 // Position of the set bit of m that has j set bits below it (m has more than j).
@@ -163,13 +239,14 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t j)
     return p;
 }
 
-// k_item_sums with the entries read from the sorted records: the item's
-// entries are taken 32 at a time, lane j holding entry c0 + j, so each lane
-// sums the same entries in the same order as there.  The records overlapping
-// a group of 32 entries are at most 32 consecutive ones (each holds at least
-// one entry): lane l reads record r + l, the lanes whose record starts inside
-// the group mark its offset, and lane j's record is the last marked one at or
-// before j.
+// One warp per item: the terms of its entries summed in single precision (lane
+// j takes entries c0 + j for c0 = the item's first entry + 32 q, q = 0, 1, ..),
+// then across the warp, written as six FP64 partials.  The entries come from
+// the sorted records: those overlapping a group of 32 entries are at most 32
+// consecutive ones (each holds at least one entry); lane l reads record r + l,
+// the lanes whose record starts inside the group mark its offset, lane j's
+// record is the last marked one at or before j, and its particle is that
+// record's set lane of the right rank.
 template <typename R>
 __global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
     const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u, Tree<R> t, int64_t ncells,
@@ -204,6 +281,7 @@ __global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
         else hi = mid;
     }
     uint32_t r = lo;
+    const uint32_t le = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;  // lanes 0 .. lane
     R gx = 0, gy = 0, gz = 0, qx = 0, qy = 0, qz = 0;
     for (uint32_t c0 = b; c0 < e; c0 += 32u) {
         const uint32_t rr = r + (uint32_t)lane;
@@ -213,8 +291,7 @@ __global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
         const uint32_t d = E - c0;  // where record rr starts in the group
         const uint32_t mark = lane == 0 ? 1u : (have && d < 32u ? 1u << d : 0u);
         const uint32_t starts = __reduce_or_sync(kFull, mark);
-        const uint32_t upto = lane == 31 ? starts : starts & ((2u << lane) - 1u);
-        const int q = __popc(upto) - 1;
+        const int q = __popc(starts & le) - 1;
         const uint32_t Eq = __shfl_sync(kFull, E, q);
         const uint32_t mq = __shfl_sync(kFull, rec.y, q);
         const uint32_t tq = __shfl_sync(kFull, rec.x, q);
@@ -486,10 +563,29 @@ void grad_pack_records(const uint32_t* tcount, const uint32_t* toff, int64_t nta
     counted();
 }
 
+void grad_merge_records(const uint32_t* cnt, int64_t n, EntryPool pool, const uint32_t* base,
+                        uint32_t* rkeys, uint32_t* rmask, uint32_t* tcount, int* flags,
+                        cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int64_t ntask = (n + 31) / 32;
+    k_merge_records<<<blocks(ntask * 32, kGradThreads), kGradThreads, 0, s>>>(
+        cnt, n, pool, base, rkeys, rmask, tcount, flags);
+    counted();
+}
+
+template <typename R>
+void grad_source_map(Tree<R> t, int64_t ncells, uint32_t* src_of, cudaStream_t s)
+{
+    if (ncells <= 0) return;
+    k_source_map<R><<<blocks(ncells, kGradThreads), kGradThreads, 0, s>>>(t, ncells, src_of);
+    counted();
+}
+
 void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
-                         const uint2* crec, int64_t nsrc, uint2* srec, uint32_t* cnt,
-                         uint32_t* recE, uint32_t* scan_tmp, uint32_t* rbeg, uint32_t* beg,
-                         uint32_t* end, cudaStream_t s)
+                         const uint2* crec, const uint32_t* src_of, int64_t nsrc, uint2* srec,
+                         uint32_t* cnt, uint32_t* recE, uint32_t* scan_tmp, uint32_t* rbeg,
+                         uint32_t* beg, uint32_t* end, cudaStream_t s)
 {
     cudaMemsetAsync(beg, 0, sizeof(uint32_t) * nsrc, s);
     cudaMemsetAsync(end, 0, sizeof(uint32_t) * nsrc, s);
@@ -497,8 +593,8 @@ void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nre
     k_record_gather<<<blocks(nrec, kGradThreads), kGradThreads, 0, s>>>(sidx, nrec, crec, srec,
                                                                        cnt);
     scan_exclusive(cnt, recE, nrec, scan_tmp, s);
-    k_record_segments<<<blocks(nrec, kGradThreads), kGradThreads, 0, s>>>(skey, nrec, nsrc, recE,
-                                                                         rbeg, beg, end);
+    k_record_segments<<<blocks(nrec, kGradThreads), kGradThreads, 0, s>>>(skey, nrec, nsrc, src_of,
+                                                                         recE, rbeg, beg, end);
     counted(2);
 }
 
@@ -606,6 +702,7 @@ void sum_z(const vec4<R>* v, int64_t n, double* tmp, double* out, cudaStream_t s
     template void sum_z<R>(const vec4<R>*, int64_t, double*, double*, cudaStream_t);              \
     template void grad_from_field<R>(const vec4<R>*, const vec4<R>*, int64_t, vec4<R>*, vec4<R>*, \
                                      cudaStream_t);                                               \
+    template void grad_source_map<R>(Tree<R>, int64_t, uint32_t*, cudaStream_t);                 \
     template void grad_source_sums_rec<R>(const vec4<R>*, const vec4<R>*, Tree<R>, int64_t,       \
                                           int64_t, const uint2*, const uint32_t*, int64_t,        \
                                           const uint32_t*, const uint32_t*, const uint32_t*,      \
