@@ -294,10 +294,12 @@ ff_status ff_tune_schedule(ff_ctx *ctx, int32_t reps, int32_t *best_schedule, fl
  * order); *energy (may be NULL) receives E in FP64; grad_pos and grad_u (may
  * be NULL) receive n x 3 values in the caller's order, dtype/loc as in
  * ff_get_particles.  With both NULL only the field and E are computed (the
- * cost of one field evaluation).  The Barnes-Hut gradient records one entry per
- * interaction (8 bytes x 2 buffers; about 1000 interactions per particle
- * at theta = 0.5), allocated on first use and grown as needed; 2^32 - 16
- * interactions or more is FF_EINVAL.  Waits.
+ * cost of one field evaluation).  The Barnes-Hut gradient keeps every
+ * particle's list of sources (4 bytes per interaction, in chunks of 128;
+ * about 900 interactions per particle at theta = 0.5) and 8 bytes per
+ * interaction of record space, allocated on first use and grown as needed
+ * (about 11 KB per particle in all at theta = 0.5); 2^32 - 16 interactions
+ * or more (about 4.5 million particles at theta = 0.5) is FF_EINVAL.  Waits.
  */
 ff_status ff_energy_grad(ff_ctx *ctx, int32_t algo, double theta, double *energy, void *grad_pos,
                          void *grad_u, int32_t dtype, int32_t loc);

@@ -95,7 +95,8 @@ struct ff_ctx {
     uint32_t* e_keys[2] = {nullptr, nullptr};
     uint32_t* e_vals[2] = {nullptr, nullptr};
     uint32_t* e_tmp = nullptr;
-    int64_t e_cap = 0;           // entries the buffers hold
+    int64_t e_cap = 0;           // entries e_keys[0], e_vals[0] hold
+    int64_t e_cap2 = 0;          // entries e_keys[1], e_vals[1] hold (the per-entry sort only)
     uint32_t* s_beg = nullptr;   // per source: entry range
     uint32_t* s_end = nullptr;
     double* s_G = nullptr;       // per source: 3 + 3 sums
@@ -806,7 +807,7 @@ ff_status grow(ff_ctx* c, T** p, size_t count)
 // After a counted Barnes-Hut evaluation: scans the per-particle interaction
 // counts into entry slots and sizes every buffer the recorded entries need.
 ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64_t* max_items_out,
-                          int64_t* pool_used = nullptr)
+                          int64_t* pool_used = nullptr, bool second_pair = false)
 {
     const int64_t n = c->n;
     cudaStream_t s = c->stream;
@@ -837,12 +838,16 @@ ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64
     const int64_t nsrc = ncells + n;
     if (ne > c->e_cap) {
         const int64_t cap = ne + ne / 8 + 1024;
-        for (int k = 0; k < 2; ++k) {
-            if ((st = grow(c, &c->e_keys[k], cap)) != FF_OK) return st;
-            if ((st = grow(c, &c->e_vals[k], cap)) != FF_OK) return st;
-        }
+        if ((st = grow(c, &c->e_keys[0], cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->e_vals[0], cap)) != FF_OK) return st;
         if ((st = grow(c, &c->e_tmp, ffk::radix_tmp_words(cap))) != FF_OK) return st;
         c->e_cap = cap;
+    }
+    if (second_pair && ne > c->e_cap2) {
+        const int64_t cap = ne + ne / 8 + 1024;
+        if ((st = grow(c, &c->e_keys[1], cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->e_vals[1], cap)) != FF_OK) return st;
+        c->e_cap2 = cap;
     }
     if (nsrc > c->s_cap) {
         const int64_t cap = nsrc + nsrc / 8 + 1024;
@@ -1209,7 +1214,8 @@ ff_status mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz_ou
             FF_CUDA(c, cudaMemcpyAsync(hp_host, hpart, sizeof(double) * 3 * nb,
                                        cudaMemcpyDeviceToHost, s));
             int64_t ne = 0, ncells = 0, max_items = 0;
-            if ((st = prepare_entries(c, &ne, &ncells, &max_items)) != FF_OK) return st;
+            st = prepare_entries(c, &ne, &ncells, &max_items, nullptr, true);
+            if (st != FF_OK) return st;
             for (int b = 0; b < nb; ++b)
                 for (int q = 0; q < 3; ++q) hsum[q] += hp_host[3 * b + q];
             const int64_t nsrc = ncells + n;

@@ -106,6 +106,32 @@ def test_bh_gradient_batched_systems(ff, ora):
     assert e == pytest.approx(etot, rel=1e-12)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_bh_gradient_regrows_its_source_lists(ff, ora, prec):
+    """A small opening angle makes nearly every source an exact pair (about n per
+    particle), more than the source lists' first allocation (9 chunks of 128 per
+    particle) holds: the walk is redone with room for what it took.  The result
+    must match the oracle, and a second call (room from the start) must give
+    the same bits."""
+    pos, u = _gas(2500, 9, phi=0.2)
+    pos = pos.astype(np.float32).astype(np.float64)
+    u = u.astype(np.float32).astype(np.float64)
+    dt = np.float64 if prec == "f64" else np.float32
+    ctx = ff.ff_create(ff.ff_params_default(n=len(pos), precision=prec, leaf_max=1))
+    ff.ff_set_particles(ctx, pos.astype(dt), u.astype(dt))
+    e, gp, gu = ff.ff_energy_grad(ctx, ff.FF_ALGO_BH, 0.05)
+    e2, gp2, gu2 = ff.ff_energy_grad(ctx, ff.FF_ALGO_BH, 0.05)
+    assert e == e2 and np.array_equal(gp, gp2) and np.array_equal(gu, gu2)
+    e0, gp0, gu0 = ora.bh_energy_grad(pos, u, 0.05, 1, prec, lj_eps=1.0, tree_centres=True)
+    tol = 1e-10 if prec == "f64" else 1e-5
+    scale = None
+    if prec != "f64":
+        scale = ora.bh(pos, u, 0.05, 1, prec, 1.0, 1.0, 1.0, 2.5, False)["fabs"]
+    assert rel_err(gu, gu0).max() <= tol, rel_err(gu, gu0).max()
+    assert rel_err(gp, gp0, scale=scale).max() <= tol, rel_err(gp, gp0, scale=scale).max()
+    assert _energy_ok(e, e0, gu0, tol)
+
+
 @pytest.mark.parametrize("n", [2, 3])
 def test_bh_gradient_fewest_entries(ff, ora, n):
     """Two and three particles: the smallest entry lists the source sort sees."""
