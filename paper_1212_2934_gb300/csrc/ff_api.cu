@@ -92,11 +92,10 @@ struct ff_ctx {
     unsigned long long* e_total = nullptr;
     void* g_pos = nullptr;       // gradients in sorted order (records)
     void* g_u = nullptr;
-    uint32_t* e_keys[2] = {nullptr, nullptr};
-    uint32_t* e_vals[2] = {nullptr, nullptr};
+    uint32_t* rs_key = nullptr;  // record space in each task's slots: source (e_cap)
+    uint32_t* rs_mask = nullptr; //   lane mask; both also the record sort's second buffers
     uint32_t* e_tmp = nullptr;
-    int64_t e_cap = 0;           // entries e_keys[0], e_vals[0] hold
-    int64_t e_cap2 = 0;          // entries e_keys[1], e_vals[1] hold (the per-entry sort only)
+    int64_t e_cap = 0;           // entries rs_key, rs_mask hold
     uint32_t* s_beg = nullptr;   // per source: entry range
     uint32_t* s_end = nullptr;
     double* s_G = nullptr;       // per source: 3 + 3 sums
@@ -512,7 +511,7 @@ void free_all(ff_ctx* c)
                     c->arrive, c->h, c->f, c->esr, c->counts, c->work, c->partials, c->obs, c->obs_step, c->dstep, c->sys_of_pos, c->sys_start, c->sys_h, c->sys_lo,
                     c->sys_hi, c->sys_acc,
                     c->dflags, c->staging, c->e_cnt, c->e_base, c->e_total, c->g_pos, c->g_u,
-                    c->e_keys[0], c->e_keys[1], c->e_vals[0], c->e_vals[1], c->e_tmp, c->s_beg,
+                    c->rs_key, c->rs_mask, c->e_tmp, c->s_beg,
                     c->s_end, c->s_G, c->s_Q, c->s_items, c->s_item_off, c->s_scan, c->i_part,
                     c->t_cnt, c->t_off, c->s_rbeg, c->r_key, c->r_idx, c->r_rec, c->r_srec,
                     c->r_cnt, c->r_E, c->r_scan, c->p_keys, c->p_link, c->p_next, c->s_src};
@@ -807,7 +806,7 @@ ff_status grow(ff_ctx* c, T** p, size_t count)
 // After a counted Barnes-Hut evaluation: scans the per-particle interaction
 // counts into entry slots and sizes every buffer the recorded entries need.
 ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64_t* max_items_out,
-                          int64_t* pool_used = nullptr, bool second_pair = false)
+                          int64_t* pool_used)
 {
     const int64_t n = c->n;
     cudaStream_t s = c->stream;
@@ -826,10 +825,9 @@ ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64
     FF_CUDA(c, cudaMemcpyAsync(&total, c->e_total, sizeof(total), cudaMemcpyDeviceToHost, s));
     FF_CUDA(c, cudaMemcpyAsync(&ncells_h, c->off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     unsigned taken = 0;
-    if (pool_used)
-        FF_CUDA(c, cudaMemcpyAsync(&taken, c->p_next, sizeof(taken), cudaMemcpyDeviceToHost, s));
+    FF_CUDA(c, cudaMemcpyAsync(&taken, c->p_next, sizeof(taken), cudaMemcpyDeviceToHost, s));
     if ((st = sync_and_check(c)) != FF_OK) return st;
-    if (pool_used) *pool_used = n + (int64_t)taken;
+    *pool_used = n + (int64_t)taken;
     // entry positions are 32-bit, with room for the recording walk's 16-byte groups
     if (total >= 0xfffffff0ull)
         return fail(c, FF_EINVAL, "too many interactions (%llu) for one gradient pass", total);
@@ -838,16 +836,10 @@ ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64
     const int64_t nsrc = ncells + n;
     if (ne > c->e_cap) {
         const int64_t cap = ne + ne / 8 + 1024;
-        if ((st = grow(c, &c->e_keys[0], cap)) != FF_OK) return st;
-        if ((st = grow(c, &c->e_vals[0], cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->rs_key, cap)) != FF_OK) return st;
+        if ((st = grow(c, &c->rs_mask, cap)) != FF_OK) return st;
         if ((st = grow(c, &c->e_tmp, ffk::radix_tmp_words(cap))) != FF_OK) return st;
         c->e_cap = cap;
-    }
-    if (second_pair && ne > c->e_cap2) {
-        const int64_t cap = ne + ne / 8 + 1024;
-        if ((st = grow(c, &c->e_keys[1], cap)) != FF_OK) return st;
-        if ((st = grow(c, &c->e_vals[1], cap)) != FF_OK) return st;
-        c->e_cap2 = cap;
     }
     if (nsrc > c->s_cap) {
         const int64_t cap = nsrc + nsrc / 8 + 1024;
@@ -873,20 +865,6 @@ ff_status prepare_entries(ff_ctx* c, int64_t* ne_out, int64_t* ncells_out, int64
     *ncells_out = ncells;
     *max_items_out = max_items;
     return FF_OK;
-}
-
-// Sorts the recorded entries by source; returns the sorted arrays.
-void sort_entries(ff_ctx* c, int64_t ne, int64_t nsrc, const uint32_t** keys,
-                  const uint32_t** vals)
-{
-    int passes = 1;
-    while (passes < 4 && ((uint64_t)nsrc >> (8 * passes)) != 0) ++passes;
-    // the particle of each entry comes from the slot offsets e_base
-    const bool in1 = ffk::radix_sort_pairs_passes<uint32_t>(
-        c->e_keys[0], c->e_vals[0], c->e_keys[1], c->e_vals[1], ne, c->e_tmp, passes, c->dflags,
-        c->stream, c->e_base, c->n);
-    *keys = c->e_keys[in1 ? 1 : 0];
-    *vals = c->e_vals[in1 ? 1 : 0];
 }
 
 // The entry pool of the recording walk: at least `chunks` chunks.
@@ -915,6 +893,35 @@ ffk::EntryPool pool_of(ff_ctx* c)
     return p;
 }
 
+// The pool ready for a recording walk: room for at least n + 1024 chunks (9 per
+// particle at first), its counter cleared.
+ff_status pool_prepare(ff_ctx* c)
+{
+    ff_status st;
+    if (c->p_cap < c->n + 1024 && (st = grow_pool(c, 9 * c->n + 1024)) != FF_OK) return st;
+    FF_CUDA(c, cudaMemsetAsync(c->p_next, 0, sizeof(unsigned), c->stream));
+    return FF_OK;
+}
+
+// After the recording walk and prepare_entries (which read the chunks it took):
+// a pool that ran out is grown to what the walk took and the walk redone (the
+// same field, force, counts and lists).
+template <typename R>
+ff_status pool_settle(ff_ctx* c, double theta, int include_sr, int64_t used)
+{
+    if (used <= c->p_cap) return FF_OK;
+    ff_status st;
+    if ((st = grow_pool(c, used + used / 8 + 1024)) != FF_OK) return st;
+    FF_CUDA(c, cudaMemsetAsync(c->p_next, 0, sizeof(unsigned), c->stream));
+    Buffers& a = c->st[c->cur];
+    ffk::bh_field_record<R>(V<R>(a.pos), V<R>(a.u), c->n, tree_of<R>(c),
+                            field_params<R>(c, theta, include_sr), V<R>(c->h), V<R>(c->f),
+                            static_cast<R*>(c->esr), c->counts, c->dflags, c->work, c->off,
+                            segs_of(c), pool_of(c), c->stream);
+    FF_LAUNCHED(c);
+    return FF_OK;
+}
+
 // After the recording walk and prepare_entries: each task's sources merged into
 // records, packed, sorted by their place in the depth-first order and scanned
 // into entry offsets (k_grad.cu).  Waits to read the number of records.
@@ -930,8 +937,8 @@ ff_status record_sources(ff_ctx* c, int64_t ncells, int64_t* nrec_out)
         if ((st = grow(c, &c->t_cnt, ntask)) != FF_OK) return st;
         if ((st = grow(c, &c->t_off, ntask + 1)) != FF_OK) return st;
     }
-    // the records of task T go to the slots of its particles (e_keys[0], e_vals[0])
-    ffk::grad_merge_records(c->e_cnt, n, pool_of(c), c->e_base, c->e_keys[0], c->e_vals[0],
+    // the records of task T go to the slots of its particles (rs_key, rs_mask)
+    ffk::grad_merge_records(c->e_cnt, n, pool_of(c), c->e_base, c->rs_key, c->rs_mask,
                             c->t_cnt, c->dflags, s);
     ffk::scan_exclusive(c->t_cnt, c->t_off, ntask, c->scan_tmp, s);
     ffk::grad_source_map<R>(tree_of<R>(c), ncells, c->s_src, s);
@@ -951,17 +958,16 @@ ff_status record_sources(ff_ctx* c, int64_t ncells, int64_t* nrec_out)
         if ((st = grow(c, &c->r_scan, ffk::scan_tmp_words(cap))) != FF_OK) return st;
         c->r_cap = cap;
     }
-    ffk::grad_pack_records(c->t_cnt, c->t_off, ntask, c->e_base, c->e_keys[0], c->e_vals[0],
+    ffk::grad_pack_records(c->t_cnt, c->t_off, ntask, c->e_base, c->rs_key, c->rs_mask,
                            c->r_key, c->r_idx, c->r_rec, s);
     int passes = 1;
     while (passes < 4 && ((uint64_t)nsrc >> (8 * passes)) != 0) ++passes;
-    // the records, in task order, sorted stably by source (e_keys[0], e_vals[0]
+    // the records, in task order, sorted stably by source (rs_key, rs_mask
     // are free again and serve as the other buffer pair)
     const bool in1 = ffk::radix_sort_pairs_passes<uint32_t>(
-        c->r_key, c->r_idx, c->e_keys[0], c->e_vals[0], nrec, c->e_tmp, passes, c->dflags, s,
-        nullptr, 0);
-    const uint32_t* skey = in1 ? c->e_keys[0] : c->r_key;
-    const uint32_t* sidx = in1 ? c->e_vals[0] : c->r_idx;
+        c->r_key, c->r_idx, c->rs_key, c->rs_mask, nrec, c->e_tmp, passes, c->dflags, s);
+    const uint32_t* skey = in1 ? c->rs_key : c->r_key;
+    const uint32_t* sidx = in1 ? c->rs_mask : c->r_idx;
     ffk::grad_record_sources(skey, sidx, nrec, c->r_rec, c->s_src, nsrc, c->r_srec, c->r_cnt,
                              c->r_E, c->r_scan, c->s_rbeg, c->s_beg, c->s_end, s);
     FF_LAUNCHED(c);
@@ -990,24 +996,15 @@ ff_status energy_grad(ff_ctx* c, int32_t algo, double theta, double* energy, boo
         ffk::grad_from_field<R>(V<R>(c->h), V<R>(c->f), n, V<R>(c->g_pos), V<R>(c->g_u), s);
         FF_LAUNCHED(c);
     } else {
-        // the field, the counts and every particle's sources in one walk; a pool
-        // that ran out is grown to what the walk took and the walk redone
-        if (c->p_cap < n + 1024 && (st = grow_pool(c, 9 * n + 1024)) != FF_OK) return st;
-        FF_CUDA(c, cudaMemsetAsync(c->p_next, 0, sizeof(unsigned), s));
-        ffk::EntryPool pool = pool_of(c);
+        // the field, the counts and every particle's sources in one walk
+        if ((st = pool_prepare(c)) != FF_OK) return st;
+        const ffk::EntryPool pool = pool_of(c);
         if ((st = eval_bh<R>(c, theta, 0, true, &pool)) != FF_OK) return st;
         int64_t ne = 0, ncells = 0, max_items = 0, used = 0;
         if ((st = prepare_entries(c, &ne, &ncells, &max_items, &used)) != FF_OK) return st;
+        if ((st = pool_settle<R>(c, theta, 0, used)) != FF_OK) return st;
         Buffers& a = c->st[c->cur];
         ffk::Tree<R> t = tree_of<R>(c);
-        if (used > c->p_cap) {
-            if ((st = grow_pool(c, used + used / 8 + 1024)) != FF_OK) return st;
-            FF_CUDA(c, cudaMemsetAsync(c->p_next, 0, sizeof(unsigned), s));
-            ffk::bh_field_record<R>(V<R>(a.pos), V<R>(a.u), n, t, field_params<R>(c, theta, 0),
-                                    V<R>(c->h), V<R>(c->f), static_cast<R*>(c->esr), c->counts,
-                                    c->dflags, c->work, c->off, segs_of(c), pool_of(c), s);
-            FF_LAUNCHED(c);
-        }
         int64_t nrec = 0;
         if ((st = record_sources<R>(c, ncells, &nrec)) != FF_OK) return st;
         ffk::grad_source_sums_rec<R>(V<R>(a.pos), V<R>(a.u), t, ncells, n, c->r_srec, c->r_E,
@@ -1203,8 +1200,10 @@ ff_status mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz_ou
         }
         for (int64_t t = t1 - 1; t >= t0; --t) {
             if ((st = load(seg[(size_t)(t - t0)])) != FF_OK) return st;
-            // the step's tree, decisions, field and force (the state is sorted)
-            if ((st = eval_bh<R>(c, theta, 1, true)) != FF_OK) return st;
+            // the step's tree, decisions, field, force and source lists (the state is sorted)
+            if ((st = pool_prepare(c)) != FF_OK) return st;
+            const ffk::EntryPool pool = pool_of(c);
+            if ((st = eval_bh<R>(c, theta, 1, true, &pool)) != FF_OK) return st;
             Buffers& a = c->st[c->cur];
             const uint32_t* perm = c->vals[0];
             ffk::em_adjoint<R>(n, V<R>(a.pos), V<R>(a.u), V<R>(a.om), V<R>(c->h), dyn_params<R>(c),
@@ -1213,24 +1212,21 @@ ff_status mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz_ou
             FF_LAUNCHED(c);
             FF_CUDA(c, cudaMemcpyAsync(hp_host, hpart, sizeof(double) * 3 * nb,
                                        cudaMemcpyDeviceToHost, s));
-            int64_t ne = 0, ncells = 0, max_items = 0;
-            st = prepare_entries(c, &ne, &ncells, &max_items, nullptr, true);
-            if (st != FF_OK) return st;
+            int64_t ne = 0, ncells = 0, max_items = 0, used = 0;
+            if ((st = prepare_entries(c, &ne, &ncells, &max_items, &used)) != FF_OK) return st;
             for (int b = 0; b < nb; ++b)
                 for (int q = 0; q < 3; ++q) hsum[q] += hp_host[3 * b + q];
-            const int64_t nsrc = ncells + n;
+            if ((st = pool_settle<R>(c, theta, 1, used)) != FF_OK) return st;
             ffk::Tree<R> tr = tree_of<R>(c);
-            ffk::bh_record_vjp<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar), n, tr,
-                                  field_params<R>(c, theta, 1), c->e_base, c->e_keys[0],
-                                  c->dflags, c->work, c->off, segs_of(c), V<R>(dxt), V<R>(dut), s);
-            const uint32_t* keys = nullptr;
-            const uint32_t* vals = nullptr;
-            sort_entries(c, ne, nsrc, &keys, &vals);
-            ffk::grad_segments(keys, ne, nsrc, c->s_beg, c->s_end, s);
-            ffk::vjp_source_sums<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar),
-                                    (R)c->p.dip_scale, tr, ncells, n, vals, c->s_beg, c->s_end,
-                                    c->s_items, c->s_item_off, c->s_scan, c->i_part, max_items,
-                                    c->s_G, c->s_Q, s);
+            ffk::bh_vjp_target<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar), n, tr,
+                                  field_params<R>(c, theta, 1), c->dflags, c->work, c->off,
+                                  segs_of(c), V<R>(dxt), V<R>(dut), s);
+            int64_t nrec = 0;
+            if ((st = record_sources<R>(c, ncells, &nrec)) != FF_OK) return st;
+            ffk::vjp_source_sums_rec<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar),
+                                        (R)c->p.dip_scale, tr, ncells, n, c->r_srec, c->r_E, nrec,
+                                        c->s_rbeg, c->s_beg, c->s_end, c->s_items, c->s_item_off,
+                                        c->s_scan, c->i_part, max_items, c->s_G, c->s_Q, s);
             ffk::vjp_finish<R>(tr, ncells, n, c->s_G, c->s_Q, V<R>(dxt), V<R>(dut), V<R>(adj[0]),
                                V<R>(adj[2]), s);
             // carry the adjoints back through the step's gather into the state's order

@@ -66,9 +66,8 @@ constexpr int kOsMaxPasses = 8;
 constexpr int64_t os_tiles(int64_t n) { return (n + kOsTile - 1) / kOsTile; }
 constexpr size_t os_tmp_words(int64_t n)
 {
-    // ... plus, when values come from segment offsets, each tile's first segment
     return (size_t)kOsMaxPasses * kRadixBins + 4 * (size_t)kRadixBins * (size_t)os_tiles(n) +
-           kOsMaxPasses + (size_t)os_tiles(n);
+           kOsMaxPasses;
 }
 
 // Root cube, written by the bbox kernels and read by the key kernel.
@@ -184,13 +183,10 @@ void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, in
                       uint32_t* tmp, int* flags, cudaStream_t s);
 // The same on the low 8 * passes bits only (K = uint64_t or uint32_t keys,
 // passes 1 .. 8); returns true when the sorted data ended in (k1, v1) (an odd
-// number of passes).  With vseg (nseg + 1 nondecreasing offsets, vseg[0] = 0,
-// vseg[nseg] = n) the values are not read from v0: element i enters the sort
-// with the value k of the segment vseg[k] <= i < vseg[k + 1].
+// number of passes).
 template <typename K>
 bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
-                             int passes, int* flags, cudaStream_t s,
-                             const uint32_t* vseg = nullptr, int64_t nseg = 0);
+                             int passes, int* flags, cudaStream_t s);
 
 // One pass of the 64-bit key sort in which tile 0 withholds its digit counts
 // and every look-back word is polled once: the bounded wait of tile 1 runs out
@@ -228,14 +224,12 @@ void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint3
                     const uint32_t* off, Tree<R> t, vec4<A>* ssum, vec4<A>* smom, int* flags,
                     cudaStream_t s);
 
-// Source lists of a vector-Jacobian product of h and f with cotangents abar,
-// bbar (see k_field.cu): per particle k, entries base[k] .. base[k + 1] hold
-// its sources in the order of its walk (the particle of an entry is implied by
-// its slot); each particle's target-side terms go to dxt, dut.
+// Target-side terms of a vector-Jacobian product of h and f with cotangents
+// abar, bbar (see k_field.cu), on the traversal's decisions: each particle's
+// dL/dx and dL/du from its own sources, to dxt, dut.
 template <typename R>
-void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
-                   const vec4<R>* bbar, int64_t n, Tree<R> t, FieldParams<R> fp,
-                   const uint32_t* base, uint32_t* keys, int* flags, int* work,
+void bh_vjp_target(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar, const vec4<R>* bbar,
+                   int64_t n, Tree<R> t, FieldParams<R> fp, int* flags, int* work,
                    const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s);
 
 // Source lists written by the counting traversal of the gradient pass: the
@@ -266,10 +260,6 @@ void bh_field_record(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t,
 // (zeroed by the caller) receives their sum in 64 bits
 void grad_entry_counts(const int4* counts, int64_t n, uint32_t* out,
                        unsigned long long* total64, cudaStream_t s);
-// first and one-past-last entry of every source in the sorted keys (arrays of
-// nsrc, zeroed here)
-void grad_segments(const uint32_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg, uint32_t* end,
-                   cudaStream_t s);
 // One warp per task of 32 particles merges their source lists (cnt[k] sources
 // of particle k in the pool): each source some lane has is written once, with
 // the mask of those lanes, to rkeys/rmask from base[32 task] on (base: scan of
@@ -321,14 +311,15 @@ void grad_finish(Tree<R> t, int64_t ncells, int64_t n, const double* G, const do
 // Vector-Jacobian product of h and f, source side: per source s,
 // G_s = ds sum [T(r) abar_m + grad phi(r; bbar_m, u_m)] (dL/dw_s) and
 // Q_s = -ds sum [grad phi(r; abar_m, w_s) + H phi(r; u_m, w_s) bbar_m] / n_s
-// (dL/dx_s per member), from the sorted entries vals (targets), beg and end
-// (grad_segments); same items, order and scratch as grad_source_sums_rec.
+// (dL/dx_s per member), over the entries of the sorted records; same items,
+// order and scratch as grad_source_sums_rec.
 template <typename R>
-void vjp_source_sums(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
-                     const vec4<R>* bbar, R ds, Tree<R> t, int64_t ncells, int64_t n,
-                     const uint32_t* vals, const uint32_t* beg, const uint32_t* end,
-                     uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
-                     int64_t max_items, double* G, double* Q, cudaStream_t s);
+void vjp_source_sums_rec(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
+                         const vec4<R>* bbar, R ds, Tree<R> t, int64_t ncells, int64_t n,
+                         const uint2* srec, const uint32_t* recE, int64_t nrec,
+                         const uint32_t* rbeg, const uint32_t* beg, const uint32_t* end,
+                         uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
+                         int64_t max_items, double* G, double* Q, cudaStream_t s);
 // dx_p += dxt_p + sum of Q over the cells holding p (and p's own particle
 // source), du_p += dut_p + the same for G (accumulated into dx, du).
 template <typename R>

@@ -525,19 +525,12 @@ __device__ __forceinline__ void bh_task1(int task, const vec4<R>* __restrict__ p
     if (COUNT) counts[k] = make_int4(nacc, npair, nopen, 0);
 }
 
-// Source lists for the energy gradient: the walk of bh_task1, making the same
-// decisions in the same order, writes one entry per source instead of
-// summing: the source, a cell (accepted, or a one-particle leaf summed
-// exactly) or ncells + the position of a particle of an opened multi-particle
-// leaf.  base[k] .. base[k + 1] is the particle's slot, sized from the counted
-// walk (accepted cells + exact pairs), so the slot names the particle and only
-// the source is stored; a walk that does not fill its slot exactly raises the
-// traversal flag.
-// With VJP, the walk also sums the target-side terms of a vector-Jacobian
-// product of h and f (cotangents abar, bbar) for L = sum abar . h + bbar . f:
+// Target-side terms of a vector-Jacobian product of h and f (cotangents abar,
+// bbar) for L = sum abar . h + bbar . f, on the walk of bh_task1 (the same
+// decisions in the same order):
 //   dL/du_k   += ds grad phi(r; bbar_k, w_s)
 //   dL/drho_k += ds [grad phi(r; abar_k, w_s) + H phi(r; u_k, w_s) bbar_k] + LJ terms
-// written to dxt, dut (the source-side terms come from the recorded entries).
+// written to dxt, dut; the source-side terms come from the source records.
 template <typename R>
 struct VjpIn {
     const vec4<R>* u;
@@ -564,72 +557,24 @@ __device__ __forceinline__ void vjp_target(const FieldParams<R>& fp, const vec4<
     hess_phi_add<R>(g, uk.x, uk.y, uk.z, ws.x, ws.y, ws.z, bk.x, bk.y, bk.z, ds, dx, dy, dz);
 }
 
-// The entries of one particle's slot [w, wend), written four at a time (one
-// 16-byte store) from the first 16-byte boundary of the slot on, the entries
-// before it and after the last full group one by one.  Positions at or past
-// wend are never written (a walk that overfills its slot raises the flag).
-struct SlotWriter {
-    uint32_t* keys;
-    uint32_t w, wend, a;  // next position, slot end, first aligned position
-    uint32_t s0, s1, s2;  // the entries of the current group of four so far
-
-    __device__ __forceinline__ SlotWriter(uint32_t* k, uint32_t begin, uint32_t stop)
-        : keys(k), w(begin), wend(stop), a((begin + 3u) & ~3u), s0(0), s1(0), s2(0)
-    {
-    }
-    __device__ __forceinline__ void put(uint32_t key)
-    {
-        const uint32_t q = w & 3u;
-        if (w < a) {
-            if (w < wend) keys[w] = key;
-        } else if (q == 0u) {
-            s0 = key;
-        } else if (q == 1u) {
-            s1 = key;
-        } else if (q == 2u) {
-            s2 = key;
-        } else if (w < wend) {
-            *reinterpret_cast<uint4*>(keys + (w - 3u)) = make_uint4(s0, s1, s2, key);
-        }
-        ++w;
-    }
-    // The entries of the last, incomplete group: positions g .. w - 1.
-    __device__ __forceinline__ void flush()
-    {
-        if (w <= a) return;
-        const uint32_t r = (w - a) & 3u;
-        const uint32_t g = w - r;
-        if (r > 0u && g < wend) keys[g] = s0;
-        if (r > 1u && g + 1u < wend) keys[g + 1u] = s1;
-        if (r > 2u && g + 2u < wend) keys[g + 2u] = s2;
-    }
-};
-
-template <typename R, bool VJP>
-__device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict__ pos, int n,
-                                            const Tree<R>& t, const FieldParams<R>& fp,
-                                            unsigned ncells, const uint32_t* __restrict__ base,
-                                            uint32_t* __restrict__ keys, int* flags,
-                                            const uint32_t* __restrict__ off, const Segs& sg,
-                                            const VjpIn<R>& vj)
+template <typename R>
+__device__ __forceinline__ void vjp_task(int task, const vec4<R>* __restrict__ pos, int n,
+                                         const Tree<R>& t, const FieldParams<R>& fp,
+                                         unsigned ncells, int* flags,
+                                         const uint32_t* __restrict__ off, const Segs& sg,
+                                         const VjpIn<R>& vj)
 {
     const int k = task * 32 + (threadIdx.x & 31);
     if (k >= n) return;
     const vec4<R> xk = pos[k];
-    vec4<R> uk, ak, bk;
+    const vec4<R> uk = vj.u[k], ak = vj.abar[k], bk = vj.bbar[k];
     R dx = 0, dy = 0, dz = 0, ux = 0, uy = 0, uz = 0;
-    if (VJP) {
-        uk = vj.u[k];
-        ak = vj.abar[k];
-        bk = vj.bbar[k];
-    }
     unsigned i = 0, end = ncells;
     if (sg.of_pos) {
         const int sys = (int)sg.of_pos[k];
         i = off[sg.start[sys]];
         end = off[sg.start[sys + 1]];
     }
-    SlotWriter sw(keys, base[k], base[k + 1]);
     while (i < end) {
         const Cell<R> cl = t.cell[i];
         const int4 nd = cl.node;
@@ -640,40 +585,33 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         const bool out1 = single && !inside;
         const R rx = rsub(xk.x, cl.cen.x), ry = rsub(xk.y, cl.cen.y), rz = rsub(xk.z, cl.cen.z);
         const R r2 = rx * rx + ry * ry + rz * rz;
-        // A one-particle leaf gives the same entry whether accepted or summed as a
-        // pair; only the LJ term of the product differs, and it vanishes outside
+        // A one-particle leaf gives the same dipole terms whether accepted or
+        // summed as a pair; only the LJ term differs, and it vanishes outside
         // [lj_rcut2_lo, lj_rcut2_hi) (see bh_task1), so it is decided only there.
         const bool acc =
-            out1 ? (VJP && fp.include_sr && r2 < fp.lj_rcut2_hi && r2 >= fp.lj_rcut2_lo &&
+            out1 ? (fp.include_sr && r2 < fp.lj_rcut2_hi && r2 >= fp.lj_rcut2_lo &&
                     accept<R>(fp, rx, ry, rz, xk, cl.cen, t.lo, (int)i, ws.w))
                  : (!inside && accept<R>(fp, rx, ry, rz, xk, cl.cen, t.lo, (int)i, ws.w));
         unsigned nxt = i + 1;
         if (acc || out1) {
-            sw.put(i);
-            if (VJP) {
-                vjp_target<R>(fp, xk, uk, ak, bk, cl.cen, ws, dx, dy, dz, ux, uy, uz);
-                if (!acc && fp.include_sr) {
-                    const vec4<R> bj = vj.bbar[nd.x];
-                    lj_vjp<R>(fp, rx, ry, rz, r2, bk.x - bj.x, bk.y - bj.y, bk.z - bj.z, dx, dy,
-                              dz);
-                }
+            vjp_target<R>(fp, xk, uk, ak, bk, cl.cen, ws, dx, dy, dz, ux, uy, uz);
+            if (!acc && fp.include_sr) {
+                const vec4<R> bj = vj.bbar[nd.x];
+                lj_vjp<R>(fp, rx, ry, rz, r2, bk.x - bj.x, bk.y - bj.y, bk.z - bj.z, dx, dy, dz);
             }
             nxt = (unsigned)nd.z;
         } else if (leaf) {
             if (!single) {
                 for (int s = nd.x; s < nd.y; ++s) {
                     if (s == k) continue;
-                    sw.put(ncells + (uint32_t)s);
-                    if (VJP) {
-                        const vec4<R> xj = pos[s], uj = vj.u[s], bj = vj.bbar[s];
-                        vjp_target<R>(fp, xk, uk, ak, bk, xj, uj, dx, dy, dz, ux, uy, uz);
-                        if (fp.include_sr) {
-                            const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
-                            const R r2 = rx * rx + ry * ry + rz * rz;
-                            if (r2 > R(0))
-                                lj_vjp<R>(fp, rx, ry, rz, r2, bk.x - bj.x, bk.y - bj.y,
-                                          bk.z - bj.z, dx, dy, dz);
-                        }
+                    const vec4<R> xj = pos[s], uj = vj.u[s], bj = vj.bbar[s];
+                    vjp_target<R>(fp, xk, uk, ak, bk, xj, uj, dx, dy, dz, ux, uy, uz);
+                    if (fp.include_sr) {
+                        const R rx = xk.x - xj.x, ry = xk.y - xj.y, rz = xk.z - xj.z;
+                        const R r2 = rx * rx + ry * ry + rz * rz;
+                        if (r2 > R(0))
+                            lj_vjp<R>(fp, rx, ry, rz, r2, bk.x - bj.x, bk.y - bj.y, bk.z - bj.z,
+                                      dx, dy, dz);
                     }
                 }
             }
@@ -685,24 +623,19 @@ __device__ __forceinline__ void record_task(int task, const vec4<R>* __restrict_
         }
         i = nxt;
     }
-    sw.flush();
-    if (sw.w != sw.wend) atomicOr(flags, FLAG_TRAVERSE);
-    if (VJP) {
-        vec4<R> o;
-        o.x = dx; o.y = dy; o.z = dz; o.w = R(0);
-        vj.dxt[k] = o;
-        o.x = ux; o.y = uy; o.z = uz;
-        vj.dut[k] = o;
-    }
+    vec4<R> o;
+    o.x = dx; o.y = dy; o.z = dz; o.w = R(0);
+    vj.dxt[k] = o;
+    o.x = ux; o.y = uy; o.z = uz;
+    vj.dut[k] = o;
 }
 
-// The recording walk on the traversal's schedule: warps take 32-particle tasks
-// from their SM's Morton segment first (see k_bh).
-template <typename R, bool VJP>
-__global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
-    const vec4<R>* __restrict__ pos, int n, Tree<R> t, FieldParams<R> fp,
-    const uint32_t* __restrict__ base, uint32_t* __restrict__ keys, int* flags, int* __restrict__ work, int nseg, const uint32_t* __restrict__ off, Segs sg,
-    VjpIn<R> vj)
+// The target-side walk on the traversal's schedule: warps take 32-particle
+// tasks from their SM's Morton segment first (see k_bh).
+template <typename R>
+__global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_vjp(
+    const vec4<R>* __restrict__ pos, int n, Tree<R> t, FieldParams<R> fp, int* flags,
+    int* __restrict__ work, int nseg, const uint32_t* __restrict__ off, Segs sg, VjpIn<R> vj)
 {
     if (*flags & FLAG_CAPACITY) return;
     const unsigned ncells = (unsigned)*t.ncells;
@@ -721,8 +654,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_record(
             got = __shfl_sync(kFull, got, 0);
             const int task = t0 + got;
             if (task >= t1) break;
-            record_task<R, VJP>(task, pos, n, t, fp, ncells, base, keys, flags, off, sg,
-                                vj);
+            vjp_task<R>(task, pos, n, t, fp, ncells, flags, off, sg, vj);
         }
     }
 }
@@ -1040,30 +972,9 @@ template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<
                                dvec4*, double*, cudaStream_t);
 
 
-template <typename R, bool VJP>
-void bh_record_g(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, const uint32_t* base,
-                 uint32_t* keys, int* flags, int* work, const uint32_t* off, Segs sg, VjpIn<R> vj,
-                 cudaStream_t s)
-{
-    static std::mutex mu;
-    static PersistentGrid cache[kMaxDevices];
-    const PersistentGrid g = persistent_grid(cache, mu, [] {
-        cudaFuncSetAttribute(k_bh_record<R, VJP>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             kTraverseCarveout);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_record<R, VJP>, kBhThreads, 0);
-        return per_sm;
-    });
-    cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
-    k_bh_record<R, VJP><<<g.blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, base, keys, flags,
-                                                        work, g.nseg, off, sg, vj);
-    counted();
-}
-
 template <typename R>
-void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
-                   const vec4<R>* bbar, int64_t n, Tree<R> t, FieldParams<R> fp,
-                   const uint32_t* base, uint32_t* keys, int* flags, int* work,
+void bh_vjp_target(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar, const vec4<R>* bbar,
+                   int64_t n, Tree<R> t, FieldParams<R> fp, int* flags, int* work,
                    const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s)
 {
     if (n <= 0) return;
@@ -1073,16 +984,26 @@ void bh_record_vjp(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
     vj.bbar = bbar;
     vj.dxt = dxt;
     vj.dut = dut;
-    bh_record_g<R, true>(pos, n, t, fp, base, keys, flags, work, off, sg, vj, s);
+    static std::mutex mu;
+    static PersistentGrid cache[kMaxDevices];
+    const PersistentGrid g = persistent_grid(cache, mu, [] {
+        cudaFuncSetAttribute(k_bh_vjp<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             kTraverseCarveout);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_vjp<R>, kBhThreads, 0);
+        return per_sm;
+    });
+    cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
+    k_bh_vjp<R><<<g.blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, flags, work, g.nseg, off, sg,
+                                                vj);
+    counted();
 }
 
-template void bh_record_vjp<float>(const float4*, const float4*, const float4*, const float4*,
-                                   int64_t, Tree<float>, FieldParams<float>, const uint32_t*,
-                                   uint32_t*, int*, int*, const uint32_t*, Segs, float4*, float4*,
-                                   cudaStream_t);
-template void bh_record_vjp<double>(const dvec4*, const dvec4*, const dvec4*, const dvec4*,
-                                    int64_t, Tree<double>, FieldParams<double>, const uint32_t*,
-                                    uint32_t*, int*, int*, const uint32_t*, Segs, dvec4*, dvec4*,
-                                    cudaStream_t);
+template void bh_vjp_target<float>(const float4*, const float4*, const float4*, const float4*,
+                                   int64_t, Tree<float>, FieldParams<float>, int*, int*,
+                                   const uint32_t*, Segs, float4*, float4*, cudaStream_t);
+template void bh_vjp_target<double>(const dvec4*, const dvec4*, const dvec4*, const dvec4*,
+                                    int64_t, Tree<double>, FieldParams<double>, int*, int*,
+                                    const uint32_t*, Segs, dvec4*, dvec4*, cudaStream_t);
 
 }  // namespace ffk

@@ -41,37 +41,6 @@ __global__ void k_entry_counts(const int4* __restrict__ counts, int64_t n,
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
 }
 
-// (keys outside 0 .. nsrc - 1 can only come from a recording walk that
-// raised its flag; they are skipped)
-__global__ void k_segments(const uint32_t* __restrict__ keys, int64_t ne, int64_t nsrc,
-                           uint32_t* beg, uint32_t* end)
-{
-    // four consecutive keys per thread (one 16-byte load; keys is 16-byte
-    // aligned), their neighbours across the group from plain loads
-    const int64_t i0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-    if (i0 >= ne) return;
-    uint32_t k[4];
-    if (i0 + 4 <= ne) {
-        const uint4 q = *reinterpret_cast<const uint4*>(keys + i0);
-        k[0] = q.x; k[1] = q.y; k[2] = q.z; k[3] = q.w;
-    } else {
-        for (int j = 0; j < 4; ++j) k[j] = i0 + j < ne ? keys[i0 + j] : 0u;
-    }
-    uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int64_t i = i0 + j;
-        if (i >= ne) break;
-        const uint32_t kk = k[j];
-        const uint32_t next = i + 1 < ne ? (j < 3 ? k[j + 1] : keys[i + 1]) : 0u;
-        if ((int64_t)kk < nsrc) {
-            if (i == 0 || prev != kk) beg[kk] = (uint32_t)i;
-            if (i == ne - 1 || next != kk) end[kk] = (uint32_t)(i + 1);
-        }
-        prev = kk;
-    }
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {
@@ -247,11 +216,12 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t j)
 // the lanes whose record starts inside the group mark its offset, lane j's
 // record is the last marked one at or before j, and its particle is that
 // record's set lane of the right rank.
-template <typename R>
+template <typename R, bool VJP>
 __global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
-    const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u, Tree<R> t, int64_t ncells,
-    int64_t nsrc, const uint2* __restrict__ srec, const uint32_t* __restrict__ recE, int64_t nrec,
-    const uint32_t* __restrict__ rbeg, const uint32_t* __restrict__ beg,
+    const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u,
+    const vec4<R>* __restrict__ abar, const vec4<R>* __restrict__ bbar, R ds, Tree<R> t,
+    int64_t ncells, int64_t nsrc, const uint2* __restrict__ srec, const uint32_t* __restrict__ recE,
+    int64_t nrec, const uint32_t* __restrict__ rbeg, const uint32_t* __restrict__ beg,
     const uint32_t* __restrict__ end, const uint32_t* __restrict__ item_off,
     const uint32_t* __restrict__ item_src, double* __restrict__ part)
 {
@@ -302,10 +272,22 @@ __global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
                 const vec4<R> xm = pos[m], um = u[m];
                 const R rx = xm.x - x.x, ry = xm.y - x.y, rz = xm.z - x.z;
                 const R r2 = rx * rx + ry * ry + rz * rz;
-                // T(r) u_m (field of u_m) and grad phi(r; w_s, u_m) (force on w_s)
-                if (r2 > R(0))
-                    dipole<R>(rx, ry, rz, r2, w.x, w.y, w.z, um.x, um.y, um.z, gx, gy, gz, qx,
-                              qy, qz);
+                if (!VJP) {
+                    // T(r) u_m (field of u_m) and grad phi(r; w_s, u_m) (force on w_s)
+                    if (r2 > R(0))
+                        dipole<R>(rx, ry, rz, r2, w.x, w.y, w.z, um.x, um.y, um.z, gx, gy, gz,
+                                  qx, qy, qz);
+                } else if (r2 > R(0)) {
+                    const vec4<R> am = abar[m], bm = bbar[m];
+                    const PairGeo<R> g = pair_geo<R>(rx, ry, rz, r2);
+                    // dL/dw_s: T(r) abar_m + grad phi(r; bbar_m, u_m)
+                    t_apply_add<R>(g, am.x, am.y, am.z, R(1), gx, gy, gz);
+                    grad_phi_add<R>(g, bm.x, bm.y, bm.z, um.x, um.y, um.z, R(1), gx, gy, gz);
+                    // dL/dx_s: -(grad phi(r; abar_m, w_s) + H phi(r; u_m, w_s) bbar_m)
+                    grad_phi_add<R>(g, am.x, am.y, am.z, w.x, w.y, w.z, R(-1), qx, qy, qz);
+                    hess_phi_add<R>(g, um.x, um.y, um.z, w.x, w.y, w.z, bm.x, bm.y, bm.z, R(-1),
+                                    qx, qy, qz);
+                }
             }
         }
         // the record holding entry c0 + 32: the group's last record, or the next
@@ -318,8 +300,9 @@ __global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
     qx = warp_sum(qx); qy = warp_sum(qy); qz = warp_sum(qz);
     if (lane == 0) {
         double* o = part + 6 * it;
-        o[0] = gx; o[1] = gy; o[2] = gz;
-        o[3] = qx; o[4] = qy; o[5] = qz;
+        const double sc = VJP ? (double)ds : 1.0;
+        o[0] = (double)gx * sc; o[1] = (double)gy * sc; o[2] = (double)gz * sc;
+        o[3] = (double)qx * sc; o[4] = (double)qy * sc; o[5] = (double)qz * sc;
     }
 }
 
@@ -346,57 +329,6 @@ __global__ void k_item_reduce(Tree<R> t, int64_t ncells, int64_t nsrc,
     for (int a = 0; a < 3; ++a) {
         G[3 * s + a] = g[a];
         Q[3 * s + a] = q[a] / ns;
-    }
-}
-
-// One warp per item of the general vector-Jacobian product (see
-// vjp_source_sums): six single-precision sums per item, written in FP64.
-template <typename R>
-__global__ void __launch_bounds__(kGradThreads) k_vjp_item_sums(
-    const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u,
-    const vec4<R>* __restrict__ abar, const vec4<R>* __restrict__ bbar, R ds, Tree<R> t,
-    int64_t ncells, int64_t nsrc, const uint32_t* __restrict__ vals,
-    const uint32_t* __restrict__ beg, const uint32_t* __restrict__ end,
-    const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ item_src,
-    double* __restrict__ part)
-{
-    const int64_t it = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (it >= (int64_t)item_off[nsrc]) return;
-    const int64_t s = item_src[it];  // the source owning this item
-    vec4<R> x, w;
-    if (s < ncells) {
-        x = t.cell[s].cen;
-        w = t.mom[s];
-    } else {
-        x = pos[s - ncells];
-        w = u[s - ncells];
-    }
-    const uint32_t b = beg[s] + (uint32_t)(it - item_off[s]) * (uint32_t)kGradItemEntries;
-    const uint32_t e = min(end[s], b + (uint32_t)kGradItemEntries);
-    const uint32_t np = (uint32_t)(nsrc - ncells);
-    R gx = 0, gy = 0, gz = 0, qx = 0, qy = 0, qz = 0;
-    for (uint32_t k = b + lane; k < e; k += 32) {
-        const uint32_t m = vals[k];
-        if (m >= np) continue;  // only after a flagged recording walk
-        const vec4<R> xm = pos[m], um = u[m], am = abar[m], bm = bbar[m];
-        const R rx = xm.x - x.x, ry = xm.y - x.y, rz = xm.z - x.z;
-        const R r2 = rx * rx + ry * ry + rz * rz;
-        if (!(r2 > R(0))) continue;
-        const PairGeo<R> g = pair_geo<R>(rx, ry, rz, r2);
-        // dL/dw_s: T(r) abar_m + grad phi(r; bbar_m, u_m)
-        t_apply_add<R>(g, am.x, am.y, am.z, R(1), gx, gy, gz);
-        grad_phi_add<R>(g, bm.x, bm.y, bm.z, um.x, um.y, um.z, R(1), gx, gy, gz);
-        // dL/dx_s: -(grad phi(r; abar_m, w_s) + H phi(r; u_m, w_s) bbar_m)
-        grad_phi_add<R>(g, am.x, am.y, am.z, w.x, w.y, w.z, R(-1), qx, qy, qz);
-        hess_phi_add<R>(g, um.x, um.y, um.z, w.x, w.y, w.z, bm.x, bm.y, bm.z, R(-1), qx, qy, qz);
-    }
-    gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz);
-    qx = warp_sum(qx); qy = warp_sum(qy); qz = warp_sum(qz);
-    if (lane == 0) {
-        double* o = part + 6 * it;
-        o[0] = (double)gx * (double)ds; o[1] = (double)gy * (double)ds; o[2] = (double)gz * (double)ds;
-        o[3] = (double)qx * (double)ds; o[4] = (double)qy * (double)ds; o[5] = (double)qz * (double)ds;
     }
 }
 
@@ -541,17 +473,6 @@ void grad_entry_counts(const int4* counts, int64_t n, uint32_t* out, unsigned lo
     counted();
 }
 
-void grad_segments(const uint32_t* keys, int64_t ne, int64_t nsrc, uint32_t* beg, uint32_t* end,
-                   cudaStream_t s)
-{
-    cudaMemsetAsync(beg, 0, sizeof(uint32_t) * nsrc, s);
-    cudaMemsetAsync(end, 0, sizeof(uint32_t) * nsrc, s);
-    if (ne <= 0) return;
-    k_segments<<<blocks((ne + 3) / 4, kGradThreads), kGradThreads, 0, s>>>(keys, ne, nsrc, beg,
-                                                                          end);
-    counted();
-}
-
 void grad_pack_records(const uint32_t* tcount, const uint32_t* toff, int64_t ntask,
                        const uint32_t* base, const uint32_t* rkeys, const uint32_t* rmask,
                        uint32_t* ckey, uint32_t* cidx, uint2* crec, cudaStream_t s)
@@ -598,6 +519,35 @@ void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nre
     counted(2);
 }
 
+namespace {
+
+// Both kinds of source sums: item counts, their scan, the item -> source map,
+// the item sums and the per-source reduction.
+template <typename R, bool VJP>
+void record_source_sums(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
+                        const vec4<R>* bbar, R ds, Tree<R> t, int64_t ncells, int64_t n,
+                        const uint2* srec, const uint32_t* recE, int64_t nrec,
+                        const uint32_t* rbeg, const uint32_t* beg, const uint32_t* end,
+                        uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
+                        int64_t max_items, double* G, double* Q, cudaStream_t s)
+{
+    const int64_t nsrc = ncells + n;
+    if (nsrc <= 0) return;
+    k_item_counts<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(beg, end, nsrc, items);
+    scan_exclusive(items, item_off, nsrc, scan_tmp, s);
+    // part holds 6 partial sums per item, then the item -> source map
+    uint32_t* item_src = reinterpret_cast<uint32_t*>(part + 6 * max_items);
+    k_item_sources<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(item_off, nsrc, item_src);
+    k_item_sums_rec<R, VJP><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
+        pos, u, abar, bbar, ds, t, ncells, nsrc, srec, recE, nrec, rbeg, beg, end, item_off,
+        item_src, part);
+    k_item_reduce<R><<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(t, ncells, nsrc, item_off,
+                                                                       part, G, Q);
+    counted(4);
+}
+
+}  // namespace
+
 template <typename R>
 void grad_source_sums_rec(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64_t ncells,
                           int64_t n, const uint2* srec, const uint32_t* recE, int64_t nrec,
@@ -605,17 +555,21 @@ void grad_source_sums_rec(const vec4<R>* pos, const vec4<R>* u, Tree<R> t, int64
                           uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
                           int64_t max_items, double* G, double* Q, cudaStream_t s)
 {
-    const int64_t nsrc = ncells + n;
-    if (nsrc <= 0) return;
-    k_item_counts<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(beg, end, nsrc, items);
-    scan_exclusive(items, item_off, nsrc, scan_tmp, s);
-    uint32_t* item_src = reinterpret_cast<uint32_t*>(part + 6 * max_items);
-    k_item_sources<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(item_off, nsrc, item_src);
-    k_item_sums_rec<R><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
-        pos, u, t, ncells, nsrc, srec, recE, nrec, rbeg, beg, end, item_off, item_src, part);
-    k_item_reduce<R><<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(t, ncells, nsrc, item_off,
-                                                                       part, G, Q);
-    counted(4);
+    record_source_sums<R, false>(pos, u, nullptr, nullptr, R(1), t, ncells, n, srec, recE, nrec,
+                                 rbeg, beg, end, items, item_off, scan_tmp, part, max_items, G, Q,
+                                 s);
+}
+
+template <typename R>
+void vjp_source_sums_rec(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
+                         const vec4<R>* bbar, R ds, Tree<R> t, int64_t ncells, int64_t n,
+                         const uint2* srec, const uint32_t* recE, int64_t nrec,
+                         const uint32_t* rbeg, const uint32_t* beg, const uint32_t* end,
+                         uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
+                         int64_t max_items, double* G, double* Q, cudaStream_t s)
+{
+    record_source_sums<R, true>(pos, u, abar, bbar, ds, t, ncells, n, srec, recE, nrec, rbeg, beg,
+                                end, items, item_off, scan_tmp, part, max_items, G, Q, s);
 }
 
 template <typename R>
@@ -637,26 +591,6 @@ void grad_from_field(const vec4<R>* h, const vec4<R>* f, int64_t n, vec4<R>* gra
     k_grad_from_field<R><<<blocks(n, kGradThreads), kGradThreads, 0, s>>>(h, f, n, grad_pos,
                                                                           grad_u);
     counted();
-}
-
-template <typename R>
-void vjp_source_sums(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar,
-                     const vec4<R>* bbar, R ds, Tree<R> t, int64_t ncells, int64_t n,
-                     const uint32_t* vals, const uint32_t* beg, const uint32_t* end,
-                     uint32_t* items, uint32_t* item_off, uint32_t* scan_tmp, double* part,
-                     int64_t max_items, double* G, double* Q, cudaStream_t s)
-{
-    const int64_t nsrc = ncells + n;
-    if (nsrc <= 0) return;
-    k_item_counts<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(beg, end, nsrc, items);
-    scan_exclusive(items, item_off, nsrc, scan_tmp, s);
-    uint32_t* item_src = reinterpret_cast<uint32_t*>(part + 6 * max_items);
-    k_item_sources<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(item_off, nsrc, item_src);
-    k_vjp_item_sums<R><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
-        pos, u, abar, bbar, ds, t, ncells, nsrc, vals, beg, end, item_off, item_src, part);
-    k_item_reduce<R><<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(t, ncells, nsrc, item_off,
-                                                                       part, G, Q);
-    counted(4);
 }
 
 template <typename R>
@@ -690,11 +624,12 @@ void sum_z(const vec4<R>* v, int64_t n, double* tmp, double* out, cudaStream_t s
 }
 
 #define FFK_GRAD_INST(R)                                                                          \
-    template void vjp_source_sums<R>(const vec4<R>*, const vec4<R>*, const vec4<R>*,              \
-                                     const vec4<R>*, R, Tree<R>, int64_t, int64_t,               \
-                                     const uint32_t*, const uint32_t*, const uint32_t*,           \
-                                     uint32_t*, uint32_t*, uint32_t*, double*, int64_t, double*,  \
-                                     double*, cudaStream_t);                                     \
+    template void vjp_source_sums_rec<R>(const vec4<R>*, const vec4<R>*, const vec4<R>*,          \
+                                         const vec4<R>*, R, Tree<R>, int64_t, int64_t,           \
+                                         const uint2*, const uint32_t*, int64_t, const uint32_t*, \
+                                         const uint32_t*, const uint32_t*, uint32_t*, uint32_t*,  \
+                                         uint32_t*, double*, int64_t, double*, double*,          \
+                                         cudaStream_t);                                          \
     template void vjp_finish<R>(Tree<R>, int64_t, int64_t, const double*, const double*,          \
                                 const vec4<R>*, const vec4<R>*, vec4<R>*, vec4<R>*, cudaStream_t);\
     template void scatter_records<R>(const uint32_t*, int64_t, const vec4<R>*, vec4<R>*,          \

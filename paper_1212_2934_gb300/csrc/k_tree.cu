@@ -182,9 +182,7 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
     unsigned long long* status, unsigned long long* __restrict__ status_next,
-    uint32_t* ticket, int* flags, const uint32_t* __restrict__ vseg,
-    const uint32_t* __restrict__ tile_seg,
-    const uint32_t* __restrict__ sysd, int withhold)
+    uint32_t* ticket, int* flags, const uint32_t* __restrict__ sysd, int withhold)
 {
     constexpr int kWarps = kOsThreads / 32;
     constexpr int kItems = os_items<K>();
@@ -198,7 +196,6 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     __shared__ uint32_t s_dstart[kRadixBins];        // where each digit starts in the tile
     __shared__ uint32_t s_gstart[kRadixBins];        // where this tile's run of it goes
     __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_k0;  // with vseg: the segment of the tile's first element
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     if (t == 0) s_tile = atomicAdd(ticket, 1u);
@@ -210,26 +207,15 @@ __global__ void __launch_bounds__(kOsThreads, os_min_blocks<K>()) k_os_scatter(
     const int tile_n = (int)min((int64_t)kTile, n - base);
     // the words of this tile in the array the next pass uses
     status_next[tile * kRadixBins + t] = 0ull;
-    if (vseg) {
-        if (t == 0) s_k0 = tile_seg[tile];
-        __syncthreads();
-    }
 
     K key[kItems];
     uint32_t val[kItems], rank[kItems];
-    uint32_t seg = vseg ? s_k0 : 0u;
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const int e = w * kWarpItems + r * 32 + lane;
         if (e < tile_n) {
             key[r] = kin[base + e];
-            if (vseg) {
-                // this thread's elements rise with r: the segment only moves on
-                while ((int64_t)vseg[seg + 1] <= base + e) ++seg;
-                val[r] = seg;
-            } else {
-                val[r] = vin[base + e];
-            }
+            val[r] = vin[base + e];
         }
     }
 #pragma unroll
@@ -892,18 +878,6 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
     counted(nb > 0 ? 3 : 1);
 }
 
-// With values from segment offsets: the segment of each tile's first element,
-// tile_seg[t] = the k with vseg[k] <= t * tile < vseg[k + 1] (thread k writes
-// the tiles that start inside its segment).
-__global__ void k_tile_segments(const uint32_t* __restrict__ vseg, int64_t nseg, int tile,
-                                int64_t tiles, uint32_t* __restrict__ tile_seg)
-{
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nseg) return;
-    const int64_t lo = vseg[k], hi = vseg[k + 1];
-    for (int64_t t = (lo + tile - 1) / tile; t * tile < hi && t < tiles; ++t) tile_seg[t] = (uint32_t)k;
-}
-
 // The scatter's tile needs more dynamic shared memory than the default limit;
 // the limit is raised once per device.
 template <typename K>
@@ -926,11 +900,9 @@ size_t radix_tmp_words(int64_t n) { return os_tmp_words(n); }
 // with sysd, of the system of each element's value.
 template <typename K>
 bool os_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp, int passes,
-             int* flags, cudaStream_t s, const uint32_t* vseg, int64_t nseg, const uint32_t* sysd,
-             int withhold = 0)
+             int* flags, cudaStream_t s, const uint32_t* sysd, int withhold = 0)
 {
-    // one element is sorted already, unless its value still has to be formed
-    if (n < 1 || passes < 1 || (n == 1 && !vseg)) return false;
+    if (n <= 1 || passes < 1) return false;
     if (passes > kOsMaxPasses) passes = kOsMaxPasses;
     if (!sysd && passes * kRadixBits > (int)(8 * sizeof(K))) passes = (int)(8 * sizeof(K)) / kRadixBits;
     const int64_t tiles = (n + kOsThreads * os_items<K>() - 1) / (kOsThreads * os_items<K>());
@@ -939,10 +911,6 @@ bool os_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
     status[0] = reinterpret_cast<unsigned long long*>(tmp + kOsMaxPasses * kRadixBins);
     status[1] = status[0] + kRadixBins * tiles;
     uint32_t* tickets = reinterpret_cast<uint32_t*>(status[1] + kRadixBins * tiles);
-    uint32_t* tile_seg = tickets + kOsMaxPasses;
-    if (vseg)
-        k_tile_segments<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(
-            vseg, nseg, kOsThreads * os_items<K>(), tiles, tile_seg);
     // counts and the first pass's status words start at zero; the second
     // array is cleared tile by tile during the first pass, and so on
     cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kOsMaxPasses * kRadixBins, s);
@@ -959,40 +927,36 @@ bool os_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
     for (int p = 0; p < passes; ++p) {
         k_os_scatter<K><<<(unsigned)tiles, kOsThreads, os_dyn_smem<K>(), s>>>(
             ka, va, kb, vb, n, p * kRadixBits, hist + p * kRadixBins, status[p & 1],
-            status[(p + 1) & 1], tickets + p, flags, p == 0 ? vseg : nullptr, tile_seg, sysd,
-            withhold);
+            status[(p + 1) & 1], tickets + p, flags, sysd, withhold);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
-    counted(1 + passes + (vseg ? 1 : 0));
+    counted(1 + passes);
     return (passes & 1) != 0;
 }
 
 template <typename K>
 bool radix_sort_pairs_passes(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, uint32_t* tmp,
-                             int passes, int* flags, cudaStream_t s, const uint32_t* vseg,
-                             int64_t nseg)
+                             int passes, int* flags, cudaStream_t s)
 {
-    return os_sort<K>(k0, v0, k1, v1, n, tmp, passes, flags, s, vseg, nseg, nullptr);
+    return os_sort<K>(k0, v0, k1, v1, n, tmp, passes, flags, s, nullptr);
 }
 template bool radix_sort_pairs_passes<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, int64_t,
-                                                uint32_t*, int, int*, cudaStream_t,
-                                                const uint32_t*, int64_t);
+                                                uint32_t*, int, int*, cudaStream_t);
 template bool radix_sort_pairs_passes<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t,
-                                                uint32_t*, int, int*, cudaStream_t,
-                                                const uint32_t*, int64_t);
+                                                uint32_t*, int, int*, cudaStream_t);
 
 void radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
                       uint32_t* tmp, int* flags, cudaStream_t s)
 {
     // eight passes: the sorted data are back in (k0, v0)
-    os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, 8, flags, s, nullptr, 0, nullptr);
+    os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, 8, flags, s, nullptr);
 }
 
 void radix_sort_wait_selftest(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
                               uint32_t* tmp, int* flags, cudaStream_t s)
 {
-    os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, 1, flags, s, nullptr, 0, nullptr, 1);
+    os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, 1, flags, s, nullptr, 1);
 }
 
 void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
@@ -1004,7 +968,7 @@ void radix_sort_systems(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, 
     int passes = 0;
     for (int b = 0; (1 << b) < sg.nseg; b += kRadixBits) ++passes;
     if (passes & 1) ++passes;
-    os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, passes, flags, s, nullptr, 0, sg.of_pos);
+    os_sort<uint64_t>(k0, v0, k1, v1, n, tmp, passes, flags, s, sg.of_pos);
 }
 
 template <typename R>
