@@ -285,20 +285,21 @@ class Clocks:
 
 
 def traffic_for(kernel_src, n, workload, theta, leaf_max, schedule):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source,
-    this workload and this traversal launch schedule."""
+    """DRAM bytes per launch from the committed ncu summaries (one record per launch
+    schedule), if one was taken on this source, this workload and this schedule."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        d = json.load(open(path))
+        recs = json.load(open(path))
         sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-        same = (d.get("source_sha256") == sha and d.get("n") == n and
-                d.get("workload_name") == workload and d.get("theta") == theta and
-                d.get("leaf_max") == leaf_max and d.get("schedule") == schedule)
-        if same:
-            return d.get("dram_bytes_per_launch")
-    except (OSError, ValueError):
+        for d in recs if isinstance(recs, list) else [recs]:
+            same = (d.get("source_sha256") == sha and d.get("n") == n and
+                    d.get("workload_name") == workload and d.get("theta") == theta and
+                    d.get("leaf_max") == leaf_max and d.get("schedule") == schedule)
+            if same:
+                return d.get("dram_bytes_per_launch")
+    except (OSError, ValueError, AttributeError):
         pass
     return None
 

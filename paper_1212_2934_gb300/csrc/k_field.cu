@@ -367,16 +367,12 @@ __device__ __forceinline__ void bh_task(int task, const vec4<R>* __restrict__ po
 // (a chunk holds a multiple of four); the chunk after a full one is taken at
 // once.  Nothing is written to chunks at or past cap.
 struct ChunkWriter {
-    uint32_t* keys;
-    uint32_t* link;
-    unsigned* next;
-    uint32_t cap, first;
+    const EntryPool& p;   // the kernel's parameter: read where used, not held
     uint32_t ck, f;       // current chunk, sources so far
     uint32_t s0, s1, s2;  // the current group of four so far
 
-    __device__ __forceinline__ ChunkWriter(const EntryPool& p, uint32_t own)
-        : keys(p.keys), link(p.link), next(p.next), cap(p.cap), first(p.first), ck(own), f(0),
-          s0(0), s1(0), s2(0)
+    __device__ __forceinline__ ChunkWriter(const EntryPool& pool, uint32_t own)
+        : p(pool), ck(own), f(0), s0(0), s1(0), s2(0)
     {
     }
     __device__ __forceinline__ void put(uint32_t key)
@@ -390,12 +386,12 @@ struct ChunkWriter {
             s2 = key;
         } else {
             const uint32_t o = f & (uint32_t)(kPoolChunk - 1);
-            if (ck < cap)
-                *reinterpret_cast<uint4*>(keys + (size_t)ck * kPoolChunk + (o - 3u)) =
+            if (ck < p.cap)
+                *reinterpret_cast<uint4*>(p.keys + (size_t)ck * kPoolChunk + (o - 3u)) =
                     make_uint4(s0, s1, s2, key);
             if (o == (uint32_t)(kPoolChunk - 1)) {
-                const uint32_t nk = first + atomicAdd(next, 1u);
-                if (ck < cap) link[ck] = nk;
+                const uint32_t nk = p.first + atomicAdd(p.next, 1u);
+                if (ck < p.cap) p.link[ck] = nk;
                 ck = nk;
             }
         }
@@ -405,11 +401,11 @@ struct ChunkWriter {
     __device__ __forceinline__ void flush()
     {
         const uint32_t r = f & 3u;
-        if (r == 0u || ck >= cap) return;
-        uint32_t* p = keys + (size_t)ck * kPoolChunk + ((f - r) & (uint32_t)(kPoolChunk - 1));
-        p[0] = s0;
-        if (r > 1u) p[1] = s1;
-        if (r > 2u) p[2] = s2;
+        if (r == 0u || ck >= p.cap) return;
+        uint32_t* q = p.keys + (size_t)ck * kPoolChunk + ((f - r) & (uint32_t)(kPoolChunk - 1));
+        q[0] = s0;
+        if (r > 1u) q[1] = s1;
+        if (r > 2u) q[2] = s2;
     }
 };
 
