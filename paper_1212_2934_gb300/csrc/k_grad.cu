@@ -26,6 +26,13 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGradThreads = 256;
+// record building by hash table (k_hash_records): block size, table slots (32 KB
+// of keys and masks), most sources a task may have there; a task with more is
+// marked kHashOverflow and merged by k_merge_records instead
+constexpr int kHashThreads = 256;
+constexpr int kHashSlots = 4096;
+constexpr int kHashLimit = 3072;
+constexpr uint32_t kHashOverflow = 0xffffffffu;
 
 __global__ void k_entry_counts(const int4* __restrict__ counts, int64_t n,
                                uint32_t* __restrict__ out, unsigned long long* total)
@@ -81,7 +88,7 @@ __global__ void __launch_bounds__(kGradThreads) k_merge_records(
     const int64_t task = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t ntask = (n + 31) / 32;
-    if (task >= ntask) return;
+    if (task >= ntask || tcount[task] != kHashOverflow) return;
     const int64_t k = task * 32 + lane;
     const uint32_t c = k < n ? cnt[k] : 0u;
     constexpr uint32_t kNone = 0xffffffffu;
@@ -125,10 +132,99 @@ __global__ void __launch_bounds__(kGradThreads) k_merge_records(
             }
         }
     }
+    __syncwarp();
     if (lane == 0) {
         tcount[task] = w - w0;
         if (w > wend) atomicOr(flags, FLAG_TRAVERSE);
     }
+}
+
+// Records by a hash table in shared memory, one block per task: the 32 source
+// lists are read chunk by chunk (a warp reads 128 sources with one 16-byte load
+// per lane) and every source is entered with its lane's bit; the table then
+// holds each source of the task once with the mask of the lanes that have it,
+// and is written out.  The records of a task come out in no particular order
+// (each source occurs once in a task, so after the stable sort by source every
+// source's records are in task order all the same).  A task with more than
+// kHashLimit sources is left to the warp merge (tcount = kHashOverflow).
+__device__ __forceinline__ bool seen(const uint32_t& flag)
+{
+    return *reinterpret_cast<const volatile uint32_t*>(&flag) != 0u;
+}
+
+__global__ void __launch_bounds__(kHashThreads) k_hash_records(
+    const uint32_t* __restrict__ cnt, int64_t n, EntryPool pool, const uint32_t* __restrict__ base,
+    uint32_t* __restrict__ rkeys, uint32_t* __restrict__ rmask, uint32_t* __restrict__ tcount)
+{
+    constexpr uint32_t kEmpty = 0xffffffffu;
+    __shared__ uint32_t hk[kHashSlots];
+    __shared__ uint32_t hm[kHashSlots];
+    __shared__ uint32_t used, over, wout;
+    const int64_t task = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int i = t; i < kHashSlots; i += kHashThreads) {
+        hk[i] = kEmpty;
+        hm[i] = 0u;
+    }
+    if (t == 0) {
+        used = 0u;
+        over = 0u;
+        wout = 0u;
+    }
+    __syncthreads();
+    for (int j = w; j < 32; j += kHashThreads / 32) {
+        const int64_t k = task * 32 + j;
+        const uint32_t c = k < n ? cnt[k] : 0u;
+        const uint32_t bit = 1u << j;
+        uint32_t ck = (uint32_t)k;
+        for (uint32_t e0 = 0; e0 < c; e0 += (uint32_t)kPoolChunk) {
+            if (e0 > 0u) {
+                ck = pool.link[ck];
+                if (ck >= pool.cap) {  // a pool that ran out: the caller redoes the walk
+                    over = 1u;
+                    break;
+                }
+            }
+            if (seen(over)) break;
+            const uint32_t e = e0 + 4u * (uint32_t)lane;
+            if (e >= c) continue;
+            const uint4 g = *reinterpret_cast<const uint4*>(pool.keys + (size_t)ck * kPoolChunk +
+                                                            4u * (uint32_t)lane);
+            const uint32_t key4[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (e + (uint32_t)q >= c || seen(over)) break;
+                const uint32_t key = key4[q];
+                uint32_t h = (key * 2654435761u) >> (32 - 12);  // 12 = log2(kHashSlots)
+                for (int probe = 0; probe < kHashSlots; ++probe) {
+                    const uint32_t prev = atomicCAS(&hk[h], kEmpty, key);
+                    if (prev == kEmpty || prev == key) {
+                        atomicOr(&hm[h], bit);
+                        if (prev == kEmpty && atomicAdd(&used, 1u) >= (uint32_t)kHashLimit)
+                            over = 1u;
+                        break;
+                    }
+                    h = (h + 1u) & (uint32_t)(kHashSlots - 1);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (over) {
+        if (t == 0) tcount[task] = kHashOverflow;
+        return;
+    }
+    const uint32_t w0 = base[task * 32];
+    for (int i = t; i < kHashSlots; i += kHashThreads) {
+        const uint32_t key = hk[i];
+        if (key != kEmpty) {
+            const uint32_t r = atomicAdd(&wout, 1u);
+            rkeys[w0 + r] = key;
+            rmask[w0 + r] = hm[i];
+        }
+    }
+    __syncthreads();
+    if (t == 0) tcount[task] = wout;
 }
 
 // The source at each place of the depth-first order of cells and particles.
@@ -490,9 +586,11 @@ void grad_merge_records(const uint32_t* cnt, int64_t n, EntryPool pool, const ui
 {
     if (n <= 0) return;
     const int64_t ntask = (n + 31) / 32;
+    k_hash_records<<<(unsigned)ntask, kHashThreads, 0, s>>>(cnt, n, pool, base, rkeys, rmask,
+                                                           tcount);
     k_merge_records<<<blocks(ntask * 32, kGradThreads), kGradThreads, 0, s>>>(
         cnt, n, pool, base, rkeys, rmask, tcount, flags);
-    counted();
+    counted(2);
 }
 
 template <typename R>

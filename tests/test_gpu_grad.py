@@ -132,6 +132,18 @@ def test_bh_gradient_regrows_its_source_lists(ff, ora, prec):
     assert _energy_ok(e, e0, gu0, tol)
 
 
+def test_bh_gradient_tasks_with_many_sources(ff, ora):
+    """5000 particles at theta = 0.05: every 32-particle task has about 5000 distinct
+    sources, more than the shared-memory table that collects a task's sources holds, so
+    the tasks' source lists are merged warp by warp instead; the result must still match."""
+    pos, u = _gas(5000, 13, phi=0.2)
+    e, gp, gu = _grad(ff, "f64", pos, u, ff.FF_ALGO_BH, 0.05)
+    e0, gp0, gu0 = ora.bh_energy_grad(pos, u, 0.05, 1, "f64", lj_eps=1.0, tree_centres=True)
+    assert rel_err(gu, gu0).max() <= 1e-10
+    assert rel_err(gp, gp0).max() <= 1e-10
+    assert _energy_ok(e, e0, gu0, 1e-10)
+
+
 @pytest.mark.parametrize("n", [2, 3])
 def test_bh_gradient_fewest_entries(ff, ora, n):
     """Two and three particles: the smallest entry lists the source sort sees."""
