@@ -284,7 +284,7 @@ class Clocks:
                 "power_w_median": float(np.median(power)) if power else None}
 
 
-def traffic_for(kernel_src, n, workload, theta, leaf_max, schedule):
+def traffic_for(kernel_src, n, workload, theta, leaf_max, schedule, kernel="k_bh"):
     """DRAM bytes per launch from the committed ncu summaries (one record per launch
     schedule), if one was taken on this source, this workload and this schedule."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -294,7 +294,8 @@ def traffic_for(kernel_src, n, workload, theta, leaf_max, schedule):
         recs = json.load(open(path))
         sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
         for d in recs if isinstance(recs, list) else [recs]:
-            same = (d.get("source_sha256") == sha and d.get("n") == n and
+            same = (d.get("kernel", "k_bh") == kernel and
+                    d.get("source_sha256") == sha and d.get("n") == n and
                     d.get("workload_name") == workload and d.get("theta") == theta and
                     d.get("leaf_max") == leaf_max and d.get("schedule") == schedule)
             if same:
@@ -1046,6 +1047,34 @@ def run_grad(args):
     f1.record(stream)
     barrier()
     field_ms = f0.elapsed_time(f1) / K
+    # roofline of the largest kernel, the counting walk that also writes the source lists
+    # (k_bh_rec): its launch time from the library's stage events over K more gradients,
+    # its work from the interaction counts of the same walk
+    ff.ff_profile(ctx, True)
+    for _ in range(K):
+        grad_once()
+        flush.zero_()
+    barrier()
+    prof = ff.ff_profile_read(ctx)
+    ff.ff_profile(ctx, False)
+    rec_ms = prof["ms"]["field"] / max(prof["calls"]["field"], 1)
+    nacc, npair, _ = ff.ff_get_counts(ctx)
+    inter = float(np.sum(nacc, dtype=np.int64) + np.sum(npair, dtype=np.int64))
+    peaks = simt_peaks(dev)
+    rec_flops = inter * FLOPS_PER_INTERACTION
+    achieved = rec_flops / (rec_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / peaks["fp32_tflops"],
+                "traffic": traffic_for(os.path.join(ROOT, "paper_1212_2934_gb300", "csrc",
+                                                    "k_field.cu"), n, "grad", args.theta,
+                                       args.leaf_max, 0, kernel="k_bh_rec"),
+                "kernel": "k_bh_rec (counting walk writing every particle's source list)",
+                "peak_note": peak_note(peaks, "fp32"), "peaks_measured": peaks,
+                "algorithmic_flops_per_launch": rec_flops,
+                "list_bytes_per_launch": 4.0 * inter,
+                "avg_launch_ms": rec_ms,
+                "timing": "CUDA events around the walk's launch on the library's stream, %d "
+                          "gradients right after the timed region" % K}
     # end to end: host state in, gradients out to pinned host memory
     host_p = torch.from_numpy(pos.astype(np.float32)).pin_memory().numpy()
     host_u = torch.from_numpy(u.astype(np.float32)).pin_memory().numpy()
@@ -1111,6 +1140,7 @@ def run_grad(args):
                    "leaf_max": args.leaf_max, "precision": "fp32",
                    "l2": "flushed between timed evaluations (256 MB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
+        "roofline": roofline,
         "gpu_launches": int(launches),
         "clocks": clk,
         "paths": {"field_only_ms": field_ms, "gradient_over_field": (max_ms / K) / field_ms,

@@ -296,10 +296,10 @@ ff_status ff_tune_schedule(ff_ctx *ctx, int32_t reps, int32_t *best_schedule, fl
  * ff_get_particles.  With both NULL only the field and E are computed (the
  * cost of one field evaluation).  The Barnes-Hut gradient keeps every
  * particle's list of sources (4 bytes per interaction, in chunks of 128;
- * about 900 interactions per particle at theta = 0.5) and 8 bytes per
+ * 700 to 900 interactions per particle at theta = 0.5) and 8 bytes per
  * interaction of record space, allocated on first use and grown as needed
- * (about 11 KB per particle in all at theta = 0.5); 2^32 - 16 interactions
- * or more (about 4.5 million particles at theta = 0.5) is FF_EINVAL.  Waits.
+ * (about 10 KB per particle in all at theta = 0.5); 2^32 - 16 interactions
+ * or more (about 5 million particles at theta = 0.5) is FF_EINVAL.  Waits.
  */
 ff_status ff_energy_grad(ff_ctx *ctx, int32_t algo, double theta, double *energy, void *grad_pos,
                          void *grad_u, int32_t dtype, int32_t loc);
