@@ -922,7 +922,7 @@ ff_status pool_settle(ff_ctx* c, double theta, int include_sr, int64_t used)
     return FF_OK;
 }
 
-// After the recording walk and prepare_entries: each task's sources merged into
+// After the recording walk and prepare_entries: each task's sources gathered into
 // records, packed, sorted by their place in the depth-first order and scanned
 // into entry offsets (k_grad.cu).  Waits to read the number of records.
 template <typename R>

@@ -260,10 +260,13 @@ void bh_field_record(const vec4<R>* pos, const vec4<R>* u, int64_t n, Tree<R> t,
 // (zeroed by the caller) receives their sum in 64 bits
 void grad_entry_counts(const int4* counts, int64_t n, uint32_t* out,
                        unsigned long long* total64, cudaStream_t s);
-// One warp per task of 32 particles merges their source lists (cnt[k] sources
-// of particle k in the pool): each source some lane has is written once, with
-// the mask of those lanes, to rkeys/rmask from base[32 task] on (base: scan of
-// cnt), in rising order, and the task's number of records to tcount[task].
+// The records of every task of 32 particles from their source lists (cnt[k]
+// sources of particle k in the pool): each source some particle of the task has
+// is written once, with the mask of the lanes that have it, to rkeys/rmask from
+// base[32 task] on (base: scan of cnt), and the task's number of records to
+// tcount[task].  A block per task collects them in a shared-memory hash table
+// (in no particular order); a task with too many sources for it is merged by
+// one warp from its rising lists instead (in rising order).
 void grad_merge_records(const uint32_t* cnt, int64_t n, EntryPool pool, const uint32_t* base,
                         uint32_t* rkeys, uint32_t* rmask, uint32_t* tcount, int* flags,
                         cudaStream_t s);
