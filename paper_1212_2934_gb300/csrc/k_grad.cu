@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_records(
             const uint32_t key4[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (e + (uint32_t)q >= c || seen(over)) break;
+                if (e + (uint32_t)q >= c) break;
                 const uint32_t key = key4[q];
                 uint32_t h = (key * 2654435761u) >> (32 - 12);  // 12 = log2(kHashSlots)
                 for (int probe = 0; probe < kHashSlots; ++probe) {
