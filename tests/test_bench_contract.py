@@ -30,22 +30,27 @@ def test_reference_arm_line():
 
 
 def test_traffic_records_match_kernel_and_schedule(tmp_path, monkeypatch):
+    """bench.traffic_for returns a record's DRAM bytes only for the same kernel, source
+    (by hash), workload and launch schedule."""
+    import hashlib
+
     import bench
 
-    recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    src = os.path.join(ROOT, "paper_1212_2934_gb300", "csrc", "k_field.cu")
-    for d in recs:
-        got = bench.traffic_for(src, d["n"], d["workload_name"], d["theta"], d["leaf_max"],
-                                d["schedule"], kernel=d.get("kernel", "k_bh"))
-        assert got == d["dram_bytes_per_launch"]
-    # another schedule, workload or kernel has no record
-    d = recs[0]
-    assert bench.traffic_for(src, d["n"], d["workload_name"], d["theta"], d["leaf_max"], 99,
-                             kernel=d.get("kernel", "k_bh")) is None
-    assert bench.traffic_for(src, d["n"], "chains", d["theta"], d["leaf_max"], d["schedule"],
-                             kernel=d.get("kernel", "k_bh")) is None
-    # a changed source has no record
-    changed = tmp_path / "k_field.cu"
-    changed.write_bytes(open(src, "rb").read() + b"\n")
-    assert bench.traffic_for(str(changed), d["n"], d["workload_name"], d["theta"],
-                             d["leaf_max"], d["schedule"], kernel=d.get("kernel", "k_bh")) is None
+    src = tmp_path / "k_field.cu"
+    src.write_bytes(b"// a kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    recs = [dict(kernel="k_bh", source_sha256=sha, n=1024, workload_name="phi05", theta=0.5,
+                 leaf_max=1, schedule=2, dram_bytes_per_launch=111),
+            dict(kernel="k_bh_rec", source_sha256=sha, n=1024, workload_name="grad", theta=0.5,
+                 leaf_max=1, schedule=0, dram_bytes_per_launch=222)]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(recs))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for(str(src), 1024, "phi05", 0.5, 1, 2) == 111
+    assert bench.traffic_for(str(src), 1024, "grad", 0.5, 1, 0, kernel="k_bh_rec") == 222
+    assert bench.traffic_for(str(src), 1024, "phi05", 0.5, 1, 1) is None        # schedule
+    assert bench.traffic_for(str(src), 1024, "chains", 0.5, 1, 2) is None       # workload
+    assert bench.traffic_for(str(src), 2048, "phi05", 0.5, 1, 2) is None        # size
+    assert bench.traffic_for(str(src), 1024, "grad", 0.5, 1, 0) is None         # kernel
+    src.write_bytes(b"// the kernel source, changed\n")
+    assert bench.traffic_for(str(src), 1024, "phi05", 0.5, 1, 2) is None        # source
