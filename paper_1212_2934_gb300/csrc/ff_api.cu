@@ -369,7 +369,7 @@ struct LaunchTally {
 // the tree, traverse.  h, f, esr (and counts) end in sorted order.
 template <typename R>
 ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = false,
-                  const ffk::EntryPool* pool = nullptr)
+                  const ffk::EntryPool* pool = nullptr, bool field = true)
 {
     const int64_t n = c->n;
     cudaStream_t s = c->stream;
@@ -408,7 +408,7 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = f
             ffk::aggregate_tree<R, R>(V<R>(b.pos), V<R>(b.u), n, c->cnt, c->off, t, t.sum, t.mom,
                                       c->dflags, s);
     }
-    {
+    if (field) {
         StageTimer st(c, S_FIELD);
         if (pool)
             ffk::bh_field_record<R>(V<R>(b.pos), V<R>(b.u), n, t,
@@ -424,7 +424,7 @@ ff_status eval_bh(ff_ctx* c, double theta, int include_sr, bool force_counts = f
     }
     FF_LAUNCHED(c);
     c->tree_valid = true;
-    c->counts_valid = c->p.count_interactions != 0 || force_counts || pool;
+    c->counts_valid = field && (c->p.count_interactions != 0 || force_counts || pool);
     return FF_OK;
 }
 
@@ -1130,6 +1130,9 @@ ff_status mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz_ou
     for (auto& d : cps) new_snap(d);
     for (auto& d : seg) new_snap(d);
     new_snap(fin);
+    // the field of each recomputed step (its particles' sorted order), for its adjoint
+    std::vector<void*> hseg(seg.size());
+    for (auto& q : hseg) q = alloc(rb);
     R* adj[4];
     R* tmp[4];
     for (int q = 0; q < 4; ++q) {
@@ -1197,13 +1200,17 @@ ff_status mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz_ou
         for (int64_t t = t0; t < t1; ++t) {
             if ((st = save(seg[(size_t)(t - t0)])) != FF_OK) return st;
             if ((st = do_step<R>(c)) != FF_OK) return st;
+            FF_CUDA(c, cudaMemcpyAsync(hseg[(size_t)(t - t0)], c->h, rb, cudaMemcpyDeviceToDevice,
+                                       s));
         }
         for (int64_t t = t1 - 1; t >= t0; --t) {
             if ((st = load(seg[(size_t)(t - t0)])) != FF_OK) return st;
-            // the step's tree, decisions, field, force and source lists (the state is sorted)
-            if ((st = pool_prepare(c)) != FF_OK) return st;
-            const ffk::EntryPool pool = pool_of(c);
-            if ((st = eval_bh<R>(c, theta, 1, true, &pool)) != FF_OK) return st;
+            // the step's tree and decisions (the state is sorted), its field as the
+            // recomputed step left it, the cotangents of the field and force, then one
+            // walk for the target-side terms that also writes the source lists
+            if ((st = eval_bh<R>(c, theta, 1, false, nullptr, false)) != FF_OK) return st;
+            FF_CUDA(c, cudaMemcpyAsync(c->h, hseg[(size_t)(t - t0)], rb, cudaMemcpyDeviceToDevice,
+                                       s));
             Buffers& a = c->st[c->cur];
             const uint32_t* perm = c->vals[0];
             ffk::em_adjoint<R>(n, V<R>(a.pos), V<R>(a.u), V<R>(a.om), V<R>(c->h), dyn_params<R>(c),
@@ -1212,15 +1219,28 @@ ff_status mz_sensitivity(ff_ctx* c, int64_t nsteps, int64_t every, double* mz_ou
             FF_LAUNCHED(c);
             FF_CUDA(c, cudaMemcpyAsync(hp_host, hpart, sizeof(double) * 3 * nb,
                                        cudaMemcpyDeviceToHost, s));
+            ffk::Tree<R> tr = tree_of<R>(c);
+            auto vjp_walk = [&]() -> ff_status {
+                const ffk::EntryPool pool = pool_of(c);
+                ffk::bh_vjp_target<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar), n, tr,
+                                      field_params<R>(c, theta, 1), c->dflags, c->work, c->off,
+                                      segs_of(c), V<R>(dxt), V<R>(dut), s, c->counts, &pool);
+                FF_LAUNCHED(c);
+                return FF_OK;
+            };
+            if ((st = pool_prepare(c)) != FF_OK) return st;
+            if ((st = vjp_walk()) != FF_OK) return st;
             int64_t ne = 0, ncells = 0, max_items = 0, used = 0;
             if ((st = prepare_entries(c, &ne, &ncells, &max_items, &used)) != FF_OK) return st;
             for (int b = 0; b < nb; ++b)
                 for (int q = 0; q < 3; ++q) hsum[q] += hp_host[3 * b + q];
-            if ((st = pool_settle<R>(c, theta, 1, used)) != FF_OK) return st;
-            ffk::Tree<R> tr = tree_of<R>(c);
-            ffk::bh_vjp_target<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar), n, tr,
-                                  field_params<R>(c, theta, 1), c->dflags, c->work, c->off,
-                                  segs_of(c), V<R>(dxt), V<R>(dut), s);
+            if (used > c->p_cap) {
+                // a pool that ran out: grown to what the walk took, the walk redone
+                if ((st = grow_pool(c, used + used / 8 + 1024)) != FF_OK) return st;
+                FF_CUDA(c, cudaMemsetAsync(c->p_next, 0, sizeof(unsigned), s));
+                if ((st = vjp_walk()) != FF_OK) return st;
+            }
+            c->counts_valid = false;  // entries per particle, not the counting walk's split
             int64_t nrec = 0;
             if ((st = record_sources<R>(c, ncells, &nrec)) != FF_OK) return st;
             ffk::vjp_source_sums_rec<R>(V<R>(a.pos), V<R>(a.u), V<R>(abar), V<R>(bbar),

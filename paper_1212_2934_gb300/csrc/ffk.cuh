@@ -226,11 +226,15 @@ void aggregate_tree(const vec4<R>* pos, const vec4<R>* u, int64_t n, const uint3
 
 // Target-side terms of a vector-Jacobian product of h and f with cotangents
 // abar, bbar (see k_field.cu), on the traversal's decisions: each particle's
-// dL/dx and dL/du from its own sources, to dxt, dut.
+// dL/dx and dL/du from its own sources, to dxt, dut.  With a pool (declared
+// below) the same walk also writes every particle's sources there and their
+// number to counts[k].x (counts[k].y = 0).
+struct EntryPool;
 template <typename R>
 void bh_vjp_target(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar, const vec4<R>* bbar,
                    int64_t n, Tree<R> t, FieldParams<R> fp, int* flags, int* work,
-                   const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s);
+                   const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s,
+                   int4* counts = nullptr, const EntryPool* pool = nullptr);
 
 // Source lists written by the counting traversal of the gradient pass: the
 // sources of particle k, in the order of its walk, fill chunk k of kPoolChunk

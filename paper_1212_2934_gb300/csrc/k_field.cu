@@ -247,6 +247,17 @@ constexpr int bh_min_blocks()
 }
 static_assert(kBhThreads % 32 == 0, "whole warps");
 
+// The walks that also write the source lists need a few more registers than
+// the counting walk: 8 blocks of 128 (64 registers) in FP32.
+#ifndef FFK_BH_MIN_BLOCKS_REC
+#define FFK_BH_MIN_BLOCKS_REC 8
+#endif
+template <typename R>
+constexpr int bh_rec_min_blocks()
+{
+    return sizeof(R) == 8 ? FFK_BH_MIN_BLOCKS_FP64 : FFK_BH_MIN_BLOCKS_REC;
+}
+
 // Minimum of v over each aligned group of G lanes.
 template <int G>
 __device__ __forceinline__ unsigned group_min(unsigned v)
@@ -553,15 +564,20 @@ __device__ __forceinline__ void vjp_target(const FieldParams<R>& fp, const vec4<
     hess_phi_add<R>(g, uk.x, uk.y, uk.z, ws.x, ws.y, ws.z, bk.x, bk.y, bk.z, ds, dx, dy, dz);
 }
 
-template <typename R>
+// With REC the walk also writes each particle's sources to the entry pool and
+// their number to counts[k].x (as the counting walk of the gradient pass does).
+template <typename R, bool REC = false>
 __device__ __forceinline__ void vjp_task(int task, const vec4<R>* __restrict__ pos, int n,
                                          const Tree<R>& t, const FieldParams<R>& fp,
                                          unsigned ncells, int* flags,
                                          const uint32_t* __restrict__ off, const Segs& sg,
-                                         const VjpIn<R>& vj)
+                                         const VjpIn<R>& vj, int4* __restrict__ counts = nullptr,
+                                         const EntryPool& ep = EntryPool())
 {
     const int k = task * 32 + (threadIdx.x & 31);
     if (k >= n) return;
+    ChunkWriter cw(ep, (uint32_t)k);
+    int nent = 0;
     const vec4<R> xk = pos[k];
     const vec4<R> uk = vj.u[k], ak = vj.abar[k], bk = vj.bbar[k];
     R dx = 0, dy = 0, dz = 0, ux = 0, uy = 0, uz = 0;
@@ -590,6 +606,10 @@ __device__ __forceinline__ void vjp_task(int task, const vec4<R>* __restrict__ p
                  : (!inside && accept<R>(fp, rx, ry, rz, xk, cl.cen, t.lo, (int)i, ws.w));
         unsigned nxt = i + 1;
         if (acc || out1) {
+            if (REC) {
+                cw.put(i + (uint32_t)nd.x);
+                ++nent;
+            }
             vjp_target<R>(fp, xk, uk, ak, bk, cl.cen, ws, dx, dy, dz, ux, uy, uz);
             if (!acc && fp.include_sr) {
                 const vec4<R> bj = vj.bbar[nd.x];
@@ -600,6 +620,10 @@ __device__ __forceinline__ void vjp_task(int task, const vec4<R>* __restrict__ p
             if (!single) {
                 for (int s = nd.x; s < nd.y; ++s) {
                     if (s == k) continue;
+                    if (REC) {
+                        cw.put(i + 1u + (uint32_t)s);
+                        ++nent;
+                    }
                     const vec4<R> xj = pos[s], uj = vj.u[s], bj = vj.bbar[s];
                     vjp_target<R>(fp, xk, uk, ak, bk, xj, uj, dx, dy, dz, ux, uy, uz);
                     if (fp.include_sr) {
@@ -624,14 +648,19 @@ __device__ __forceinline__ void vjp_task(int task, const vec4<R>* __restrict__ p
     vj.dxt[k] = o;
     o.x = ux; o.y = uy; o.z = uz;
     vj.dut[k] = o;
+    if (REC) {
+        cw.flush();
+        counts[k] = make_int4(nent, 0, 0, 0);
+    }
 }
 
 // The target-side walk on the traversal's schedule: warps take 32-particle
 // tasks from their SM's Morton segment first (see k_bh).
-template <typename R>
-__global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_vjp(
+template <typename R, bool REC>
+__global__ void __launch_bounds__(kBhThreads, (REC ? bh_rec_min_blocks<R>() : kBhMinBlocks)) k_bh_vjp(
     const vec4<R>* __restrict__ pos, int n, Tree<R> t, FieldParams<R> fp, int* flags,
-    int* __restrict__ work, int nseg, const uint32_t* __restrict__ off, Segs sg, VjpIn<R> vj)
+    int* __restrict__ work, int nseg, const uint32_t* __restrict__ off, Segs sg, VjpIn<R> vj,
+    int4* __restrict__ counts, EntryPool ep)
 {
     if (*flags & FLAG_CAPACITY) return;
     const unsigned ncells = (unsigned)*t.ncells;
@@ -650,7 +679,7 @@ __global__ void __launch_bounds__(kBhThreads, kBhMinBlocks) k_bh_vjp(
             got = __shfl_sync(kFull, got, 0);
             const int task = t0 + got;
             if (task >= t1) break;
-            vjp_task<R>(task, pos, n, t, fp, ncells, flags, off, sg, vj);
+            vjp_task<R, REC>(task, pos, n, t, fp, ncells, flags, off, sg, vj, counts, ep);
         }
     }
 }
@@ -698,16 +727,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_bh(const vec4<R>* __restrict_
 }
 
 // The counting walk that also records every particle's sources (energy
-// gradient), on the schedule of k_bh.  Its list writer needs a few more
-// registers than the counting walk: 8 blocks of 128 (64 registers) in FP32.
-#ifndef FFK_BH_MIN_BLOCKS_REC
-#define FFK_BH_MIN_BLOCKS_REC 8
-#endif
-template <typename R>
-constexpr int bh_rec_min_blocks()
-{
-    return sizeof(R) == 8 ? FFK_BH_MIN_BLOCKS_FP64 : FFK_BH_MIN_BLOCKS_REC;
-}
+// gradient), on the schedule of k_bh.
 
 template <typename R>
 __global__ void __launch_bounds__(kBhThreads, (bh_rec_min_blocks<R>())) k_bh_rec(
@@ -968,10 +988,31 @@ template void ap_field<double>(const dvec4*, const dvec4*, int64_t, FieldParams<
                                dvec4*, double*, cudaStream_t);
 
 
+template <typename R, bool REC>
+void bh_vjp_launch(const vec4<R>* pos, int64_t n, Tree<R> t, FieldParams<R> fp, int* flags,
+                   int* work, const uint32_t* off, Segs sg, VjpIn<R> vj, int4* counts,
+                   EntryPool ep, cudaStream_t s)
+{
+    static std::mutex mu;
+    static PersistentGrid cache[kMaxDevices];
+    const PersistentGrid g = persistent_grid(cache, mu, [] {
+        cudaFuncSetAttribute(k_bh_vjp<R, REC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             kTraverseCarveout);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_vjp<R, REC>, kBhThreads, 0);
+        return per_sm;
+    });
+    cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
+    k_bh_vjp<R, REC><<<g.blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, flags, work, g.nseg, off,
+                                                     sg, vj, counts, ep);
+    counted();
+}
+
 template <typename R>
 void bh_vjp_target(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar, const vec4<R>* bbar,
                    int64_t n, Tree<R> t, FieldParams<R> fp, int* flags, int* work,
-                   const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s)
+                   const uint32_t* off, Segs sg, vec4<R>* dxt, vec4<R>* dut, cudaStream_t s,
+                   int4* counts, const EntryPool* pool)
 {
     if (n <= 0) return;
     VjpIn<R> vj;
@@ -980,26 +1021,19 @@ void bh_vjp_target(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* abar, co
     vj.bbar = bbar;
     vj.dxt = dxt;
     vj.dut = dut;
-    static std::mutex mu;
-    static PersistentGrid cache[kMaxDevices];
-    const PersistentGrid g = persistent_grid(cache, mu, [] {
-        cudaFuncSetAttribute(k_bh_vjp<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             kTraverseCarveout);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bh_vjp<R>, kBhThreads, 0);
-        return per_sm;
-    });
-    cudaMemsetAsync(work, 0, sizeof(int) * g.nseg, s);
-    k_bh_vjp<R><<<g.blocks, kBhThreads, 0, s>>>(pos, (int)n, t, fp, flags, work, g.nseg, off, sg,
-                                                vj);
-    counted();
+    if (pool)
+        bh_vjp_launch<R, true>(pos, n, t, fp, flags, work, off, sg, vj, counts, *pool, s);
+    else
+        bh_vjp_launch<R, false>(pos, n, t, fp, flags, work, off, sg, vj, nullptr, EntryPool(), s);
 }
 
 template void bh_vjp_target<float>(const float4*, const float4*, const float4*, const float4*,
                                    int64_t, Tree<float>, FieldParams<float>, int*, int*,
-                                   const uint32_t*, Segs, float4*, float4*, cudaStream_t);
+                                   const uint32_t*, Segs, float4*, float4*, cudaStream_t, int4*,
+                                   const EntryPool*);
 template void bh_vjp_target<double>(const dvec4*, const dvec4*, const dvec4*, const dvec4*,
                                     int64_t, Tree<double>, FieldParams<double>, int*, int*,
-                                    const uint32_t*, Segs, dvec4*, dvec4*, cudaStream_t);
+                                    const uint32_t*, Segs, dvec4*, dvec4*, cudaStream_t, int4*,
+                                    const EntryPool*);
 
 }  // namespace ffk
