@@ -120,9 +120,8 @@ struct ff_ctx {
     uint32_t* r_idx = nullptr;   //   the packed index (sort value)
     uint2* r_rec = nullptr;      //   (task, lane mask)
     uint2* r_srec = nullptr;     // sorted by source
-    uint32_t* r_cnt = nullptr;   //   entries of each sorted record
-    uint32_t* r_E = nullptr;     //   their exclusive scan (+1)
-    uint32_t* r_scan = nullptr;
+    uint32_t* r_E = nullptr;     //   entries before each sorted record (+1)
+    unsigned long long* r_scan = nullptr;  // the one-pass scan's status words
     int64_t r_cap = 0;
     bool tree_valid = false;     // a Barnes-Hut tree of some state exists
     bool counts_valid = false;
@@ -514,7 +513,7 @@ void free_all(ff_ctx* c)
                     c->rs_key, c->rs_mask, c->e_tmp, c->s_beg,
                     c->s_end, c->s_G, c->s_Q, c->s_items, c->s_item_off, c->s_scan, c->i_part,
                     c->t_cnt, c->t_off, c->s_rbeg, c->r_key, c->r_idx, c->r_rec, c->r_srec,
-                    c->r_cnt, c->r_E, c->r_scan, c->p_keys, c->p_link, c->p_next, c->s_src};
+                    c->r_E, c->r_scan, c->p_keys, c->p_link, c->p_next, c->s_src};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int k = 0; k < 2; ++k) {
@@ -953,9 +952,8 @@ ff_status record_sources(ff_ctx* c, int64_t ncells, int64_t* nrec_out)
         if ((st = grow(c, &c->r_idx, cap)) != FF_OK) return st;
         if ((st = grow(c, &c->r_rec, cap)) != FF_OK) return st;
         if ((st = grow(c, &c->r_srec, cap)) != FF_OK) return st;
-        if ((st = grow(c, &c->r_cnt, cap)) != FF_OK) return st;
         if ((st = grow(c, &c->r_E, cap + 1)) != FF_OK) return st;
-        if ((st = grow(c, &c->r_scan, ffk::scan_tmp_words(cap))) != FF_OK) return st;
+        if ((st = grow(c, &c->r_scan, ffk::record_scan_words(cap))) != FF_OK) return st;
         c->r_cap = cap;
     }
     ffk::grad_pack_records(c->t_cnt, c->t_off, ntask, c->e_base, c->rs_key, c->rs_mask,
@@ -968,8 +966,8 @@ ff_status record_sources(ff_ctx* c, int64_t ncells, int64_t* nrec_out)
         c->r_key, c->r_idx, c->rs_key, c->rs_mask, nrec, c->e_tmp, passes, c->dflags, s);
     const uint32_t* skey = in1 ? c->rs_key : c->r_key;
     const uint32_t* sidx = in1 ? c->rs_mask : c->r_idx;
-    ffk::grad_record_sources(skey, sidx, nrec, c->r_rec, c->s_src, nsrc, c->r_srec, c->r_cnt,
-                             c->r_E, c->r_scan, c->s_rbeg, c->s_beg, c->s_end, s);
+    ffk::grad_record_sources(skey, sidx, nrec, c->r_rec, c->s_src, nsrc, c->r_srec, c->r_E,
+                             c->r_scan, c->s_rbeg, c->s_beg, c->s_end, c->dflags, s);
     FF_LAUNCHED(c);
     *nrec_out = nrec;
     return FF_OK;

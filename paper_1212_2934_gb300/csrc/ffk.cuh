@@ -287,12 +287,14 @@ void grad_pack_records(const uint32_t* tcount, const uint32_t* toff, int64_t nta
 // After the records are sorted by key (skey, sidx = their packed index):
 // srec[i] = crec[sidx[i]], recE[i] = entries before record i (recE[nrec] =
 // entries), and per source s = src_of[key] its first record rbeg, and the
-// entry range beg, end (nsrc each, zeroed here).  cnt: nrec words of scratch,
-// scan_tmp for nrec.
+// entry range beg, end (nsrc each, zeroed here), in one pass.  scan_words:
+// record_scan_words(nrec) words of scratch.  A tile that waits too long for an
+// earlier one raises FLAG_SORT in flags.
+size_t record_scan_words(int64_t nrec);
 void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
                          const uint2* crec, const uint32_t* src_of, int64_t nsrc, uint2* srec,
-                         uint32_t* cnt, uint32_t* recE, uint32_t* scan_tmp, uint32_t* rbeg,
-                         uint32_t* beg, uint32_t* end, cudaStream_t s);
+                         uint32_t* recE, unsigned long long* scan_words, uint32_t* rbeg,
+                         uint32_t* beg, uint32_t* end, int* flags, cudaStream_t s);
 // per source s: G_s = sum over its entries of T(r) u_m and Q_s = sum of
 // grad phi(r; w_s, u_m) / n_s, r = rho_m - x_s (FP64 results, 3 per source).
 // Entry e of source s (beg[s] <= e < end[s]) is particle 32 task + lane of the

@@ -7,9 +7,10 @@
 //   dE/drho_k = -1/2 [ f_k - ds sum over (m, s), k in s, of
 //                      grad phi(rho_m - x_s; w_s, u_m) / n_s ]
 // h and f are the dipolar field and force of the same traversal (ds
-// included).  The reverse sums are formed without atomics.  One warp per task
-// of 32 consecutive particles walks the union of their cell lists and writes,
-// per source some lane takes, one record (source, task, lane mask); the records
+// included).  The reverse sums are formed without atomics.  The counting walk
+// writes every particle's sources (in depth-first order) to an entry pool; one
+// block per task of 32 consecutive particles gathers its 32 lists into records
+// (source, task, lane mask), one per source some lane takes; the records
 // (about a tenth as many as the (source, target) entries) are packed in task
 // order and sorted stably by source, so each source's entries, expanded lane
 // by lane, come out in target order.  Each source's entries are summed in a
@@ -191,6 +192,7 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_records(
             const uint4 g = *reinterpret_cast<const uint4*>(pool.keys + (size_t)ck * kPoolChunk +
                                                             4u * (uint32_t)lane);
             const uint32_t key4[4] = {g.x, g.y, g.z, g.w};
+            uint32_t fresh = 0u;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (e + (uint32_t)q >= c) break;
@@ -200,13 +202,20 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_records(
                     const uint32_t prev = atomicCAS(&hk[h], kEmpty, key);
                     if (prev == kEmpty || prev == key) {
                         atomicOr(&hm[h], bit);
-                        if (prev == kEmpty && atomicAdd(&used, 1u) >= (uint32_t)kHashLimit)
-                            over = 1u;
+                        fresh += prev == kEmpty ? 1u : 0u;
                         break;
                     }
                     h = (h + 1u) & (uint32_t)(kHashSlots - 1);
                 }
             }
+            // the new sources, counted once per group of lanes that arrive here
+            // together (at most 8 x 128 beyond the limit before every warp sees
+            // `over`: the table never fills)
+            const unsigned am = __activemask();
+            const uint32_t tot = __reduce_add_sync(am, fresh);
+            if (lane == __ffs(am) - 1 && tot != 0u &&
+                atomicAdd(&used, tot) + tot > (uint32_t)kHashLimit)
+                over = 1u;
         }
     }
     __syncthreads();
@@ -257,35 +266,130 @@ __global__ void k_pack_records(const uint32_t* __restrict__ tcount,
     }
 }
 
-// The sorted records and their entry counts.
-__global__ void k_record_gather(const uint32_t* __restrict__ sidx, int64_t nrec,
-                                const uint2* __restrict__ crec, uint2* __restrict__ srec,
-                                uint32_t* __restrict__ cnt)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrec) return;
-    const uint2 r = crec[sidx[i]];
-    srec[i] = r;
-    cnt[i] = (uint32_t)__popc(r.y);
-}
+// The sorted records in one pass: srec[i] = crec[sidx[i]], recE[i] = the
+// entries (set mask bits) of the records before i, and per source s = src_of[key]
+// its first record rbeg[s] and entry range [beg[s], end[s]) (keys outside
+// 0 .. nsrc - 1 can only come from a walk that raised its flag; skipped).  Tiles
+// of kRsTile records take tickets in the order they start; a tile publishes its
+// own entry count, then adds up the counts of the tiles before it, back to the
+// first whose running total is out (the status words: a flag in the high half,
+// the count in the low half), and publishes its running total.  A wait on an
+// earlier tile is bounded: when it runs out, FLAG_SORT is raised.
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;
+constexpr unsigned long long kRsAggregate = 1ull << 32;  // this tile alone
+constexpr unsigned long long kRsPrefix = 2ull << 32;     // this tile and all before it
+constexpr int kRsSpinLimit = 1 << 22;
 
-// Per source: its first sorted record and its entry range (keys outside
-// 0 .. nsrc - 1 can only come from a walk that raised its flag; skipped).
-__global__ void k_record_segments(const uint32_t* __restrict__ keys, int64_t nrec, int64_t nsrc,
-                                  const uint32_t* __restrict__ src_of,
-                                  const uint32_t* __restrict__ recE, uint32_t* __restrict__ rbeg,
-                                  uint32_t* __restrict__ beg, uint32_t* __restrict__ end)
+__global__ void __launch_bounds__(kRsThreads) k_record_scan(
+    const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx, int64_t nrec,
+    const uint2* __restrict__ crec, const uint32_t* __restrict__ src_of, int64_t nsrc,
+    uint2* __restrict__ srec, uint32_t* __restrict__ recE, uint32_t* __restrict__ rbeg,
+    uint32_t* __restrict__ beg, uint32_t* __restrict__ end, unsigned long long* status,
+    uint32_t* ticket, int* flags)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrec) return;
-    const uint32_t kk = keys[i];
-    if ((int64_t)kk >= nsrc) return;
-    const uint32_t src = src_of[kk];
-    if (i == 0 || keys[i - 1] != kk) {
-        rbeg[src] = (uint32_t)i;
-        beg[src] = recE[i];
+    __shared__ uint32_t s_tile, s_excl;
+    __shared__ uint32_t s_warp[kRsThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    // warp w takes records tile * kRsTile + 256 w + [0, 256), a row of 32
+    // consecutive ones per step (lane l: 32 q + l); `incl` the running
+    // inclusive count of the warp's records up to this lane's in row q
+    const int64_t wbase = tile * kRsTile + (int64_t)w * (32 * kRsItems);
+    uint32_t cnt[kRsItems], incl[kRsItems];
+    uint32_t run = 0;
+    // every gather in flight at once, then the row scans
+    uint32_t ix[kRsItems];
+#pragma unroll
+    for (int q = 0; q < kRsItems; ++q) {
+        const int64_t i = wbase + 32 * q + lane;
+        ix[q] = i < nrec ? sidx[i] : 0xffffffffu;
     }
-    if (i == nrec - 1 || keys[i + 1] != kk) end[src] = recE[i + 1];
+#pragma unroll
+    for (int q = 0; q < kRsItems; ++q) {
+        cnt[q] = 0u;
+        if (ix[q] != 0xffffffffu) {
+            const uint2 r = crec[ix[q]];
+            srec[wbase + 32 * q + lane] = r;
+            cnt[q] = (uint32_t)__popc(r.y);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kRsItems; ++q) {
+        const uint32_t c = cnt[q];
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        incl[q] = run + x;
+        run += __shfl_sync(kFull, x, 31);
+    }
+    if (lane == 0) s_warp[w] = run;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < kRsThreads / 32; ++k) {
+        const uint32_t v = s_warp[k];
+        if (k < w) before += v;
+        total += v;
+    }
+    if (w == 0) {
+        // the first warp looks back 32 tiles a round trip: lane k reads tile
+        // j0 - k; once every tile up to the nearest running total has published,
+        // their counts are added (a full window of tile counts moves it back)
+        volatile unsigned long long* st = status;
+        if (lane == 0) st[tile] = (tile == 0 ? kRsPrefix : kRsAggregate) | total;
+        uint32_t excl = 0;
+        int64_t j0 = tile - 1;
+        for (int spins = 0; j0 >= 0;) {
+            const int64_t j = j0 - lane;
+            unsigned long long v = kRsPrefix;  // before the first tile: a total of 0
+            if (j >= 0) v = st[j];
+            const uint32_t pub = __ballot_sync(kFull, (v >> 32) != 0);
+            const uint32_t pre = __ballot_sync(kFull, (v & kRsPrefix) != 0);
+            const uint32_t upto = pre != 0u ? (2u << (__ffs(pre) - 1)) - 1u : kFull;
+            if ((pub & upto) == upto) {
+                excl += warp_sum((upto >> lane) & 1u ? (uint32_t)v : 0u);
+                if (pre != 0u) break;
+                j0 -= 32;
+                continue;
+            }
+            if (++spins >= kRsSpinLimit) {
+                if (lane == 0) atomicOr(flags, FLAG_SORT);
+                break;
+            }
+            __nanosleep(32);
+        }
+        if (lane == 0) {
+            if (tile > 0) st[tile] = kRsPrefix | (unsigned long long)(excl + total);
+            s_excl = excl;
+        }
+    }
+    __syncthreads();
+    const uint32_t E0 = s_excl + before;
+#pragma unroll
+    for (int q = 0; q < kRsItems; ++q) {
+        const int64_t i = wbase + 32 * q + lane;
+        if (i < nrec) {
+            const uint32_t E = E0 + incl[q] - cnt[q];
+            recE[i] = E;
+            const uint32_t kk = skey[i];
+            if ((int64_t)kk < nsrc) {
+                const uint32_t src = src_of[kk];
+                if (i == 0 || skey[i - 1] != kk) {
+                    rbeg[src] = (uint32_t)i;
+                    beg[src] = E;
+                }
+                if (i == nrec - 1 || skey[i + 1] != kk) end[src] = E + cnt[q];
+            }
+            if (i == nrec - 1) recE[nrec] = E + cnt[q];
+        }
+    }
 }
 
 // Position of the set bit of m that has j set bits below it (m has more than j).
@@ -312,8 +416,17 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t j)
 // the lanes whose record starts inside the group mark its offset, lane j's
 // record is the last marked one at or before j, and its particle is that
 // record's set lane of the right rank.
+// (blocks of 4 warps: a block's warps wait less for its longest item; ten such
+// blocks an SM in single precision, where the terms fit 48 registers)
+constexpr int kItemThreads = 128;
+template <typename R>
+constexpr int item_min_blocks()
+{
+    return sizeof(R) == 8 ? 1 : 10;
+}
+
 template <typename R, bool VJP>
-__global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
+__global__ void __launch_bounds__(kItemThreads, item_min_blocks<R>()) k_item_sums_rec(
     const vec4<R>* __restrict__ pos, const vec4<R>* __restrict__ u,
     const vec4<R>* __restrict__ abar, const vec4<R>* __restrict__ bbar, R ds, Tree<R> t,
     int64_t ncells, int64_t nsrc, const uint2* __restrict__ srec, const uint32_t* __restrict__ recE,
@@ -321,7 +434,7 @@ __global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
     const uint32_t* __restrict__ end, const uint32_t* __restrict__ item_off,
     const uint32_t* __restrict__ item_src, double* __restrict__ part)
 {
-    const int64_t it = ((int64_t)blockIdx.x * kGradThreads + threadIdx.x) >> 5;
+    const int64_t it = ((int64_t)blockIdx.x * kItemThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (it >= (int64_t)item_off[nsrc]) return;
     const int64_t s = item_src[it];  // the source owning this item
@@ -402,29 +515,102 @@ __global__ void __launch_bounds__(kGradThreads) k_item_sums_rec(
     }
 }
 
-// One thread per source: its items' partials added in order in FP64.
+// Each source's items' partials added in item order in FP64, starting from
+// zero.  Lane l of a warp owns source 32 w + l and adds up a short list itself;
+// a long one (a cell that a large part of the particles accept has up to
+// n / 1024 items) is added by six lanes of the warp, one such source after
+// another, each lane one of the six sums in item order with its loads issued
+// ahead (the one-by-one sums, without one lane waiting on the loads of every
+// item in turn, and with no FP64 addition repeated: FP64 is scarce on this
+// part).  A cell's position terms are then divided by its particle count (its
+// centre is their mean).  FP64 division is a long instruction sequence here,
+// and most sources (particles, one-particle leaves) hold one particle (x / 1 is
+// x): the quotients a warp does need are gathered, ten sources (30 quotients)
+// to one pass of the division over the warp's lanes, and handed back.
+constexpr uint32_t kReduceShort = 4;
+
 template <typename R>
-__global__ void k_item_reduce(Tree<R> t, int64_t ncells, int64_t nsrc,
-                              const uint32_t* __restrict__ item_off,
-                              const double* __restrict__ part, double* __restrict__ G,
-                              double* __restrict__ Q)
+__global__ void __launch_bounds__(kGradThreads) k_item_reduce(
+    Tree<R> t, int64_t ncells, int64_t nsrc, const uint32_t* __restrict__ item_off,
+    const double* __restrict__ part, double* __restrict__ G, double* __restrict__ Q)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nsrc) return;
+    const int lane = threadIdx.x & 31;
+    const bool have = s < nsrc;
     double g[3] = {0.0, 0.0, 0.0}, q[3] = {0.0, 0.0, 0.0};
-    for (uint32_t it = item_off[s]; it < item_off[s + 1]; ++it) {
-        const double* o = part + 6 * (int64_t)it;
-        g[0] += o[0]; g[1] += o[1]; g[2] += o[2];
-        q[0] += o[3]; q[1] += o[4]; q[2] += o[5];
+    int ns = 1;
+    uint32_t i0 = 0, i1 = 0;
+    if (have) {
+        i0 = item_off[s];
+        i1 = item_off[s + 1];
+        if (s < ncells) {
+            const int4 nd = t.cell[s].node;
+            ns = nd.y - nd.x;
+        }
     }
-    double ns = 1.0;
-    if (s < ncells) {
-        const int4 nd = t.cell[s].node;
-        ns = (double)(nd.y - nd.x);
+    const bool longer = i1 - i0 > kReduceShort;
+    if (!longer) {
+        for (uint32_t it = i0; it < i1; ++it) {
+            const double* o = part + 6 * (int64_t)it;
+            g[0] += o[0]; g[1] += o[1]; g[2] += o[2];
+            q[0] += o[3]; q[1] += o[4]; q[2] += o[5];
+        }
     }
+    for (uint32_t lm = __ballot_sync(kFull, longer); lm != 0u; lm &= lm - 1u) {
+        const int l = __ffs(lm) - 1;
+        const uint32_t a = __shfl_sync(kFull, i0, l), b = __shfl_sync(kFull, i1, l);
+        double x = 0.0;
+        if (lane < 6) {
+            // lane e adds up component e, loads issued eight items ahead
+            const double* o = part + 6 * (int64_t)a + lane;
+            const uint32_t m = b - a;
+            uint32_t j = 0;
+            for (; j + 8u <= m; j += 8u) {
+                double v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = o[6 * (int64_t)(j + k)];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) x += v[k];
+            }
+            for (; j < m; ++j) x += o[6 * (int64_t)j];
+        }
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            const double y = __shfl_sync(kFull, x, e);
+            if (lane == l) {
+                if (e < 3) g[e] = y;
+                else q[e - 3] = y;
+            }
+        }
+    }
+    double qo[3] = {q[0], q[1], q[2]};
+    // lane 3 r + c (r < 10) divides component c of the pass's r-th source
+    const int r = lane / 3, c = lane - 3 * r;
+    const uint32_t below = (1u << lane) - 1u;
+    for (uint32_t m = __ballot_sync(kFull, ns != 1); m != 0u;) {
+        const int cnt = min(__popc(m), 10);
+        const int from = r < cnt ? (int)nth_set_bit(m, (uint32_t)r) : lane;
+        const double n0 = __shfl_sync(kFull, q[0], from);
+        const double n1 = __shfl_sync(kFull, q[1], from);
+        const double n2 = __shfl_sync(kFull, q[2], from);
+        const int d = __shfl_sync(kFull, ns, from);
+        // every lane divides (idle lanes by their own count, results unused)
+        const double quo = (c == 0 ? n0 : c == 1 ? n1 : n2) / (double)d;
+        const int k = __popc(m & below);  // this lane's rank in the pass
+        const bool mine = ((m >> lane) & 1u) != 0u && k < cnt;
+        const int at = mine ? 3 * k : 0;
+        const double a0 = __shfl_sync(kFull, quo, at);
+        const double a1 = __shfl_sync(kFull, quo, at + 1);
+        const double a2 = __shfl_sync(kFull, quo, at + 2);
+        if (mine) {
+            qo[0] = a0; qo[1] = a1; qo[2] = a2;
+        }
+        for (int j = 0; j < cnt; ++j) m &= m - 1u;
+    }
+    if (!have) return;
     for (int a = 0; a < 3; ++a) {
         G[3 * s + a] = g[a];
-        Q[3 * s + a] = q[a] / ns;
+        Q[3 * s + a] = qo[a];
     }
 }
 
@@ -601,20 +787,26 @@ void grad_source_map(Tree<R> t, int64_t ncells, uint32_t* src_of, cudaStream_t s
     counted();
 }
 
+size_t record_scan_words(int64_t nrec)
+{
+    return (size_t)((nrec + kRsTile - 1) / kRsTile) + 1;
+}
+
 void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
                          const uint2* crec, const uint32_t* src_of, int64_t nsrc, uint2* srec,
-                         uint32_t* cnt, uint32_t* recE, uint32_t* scan_tmp, uint32_t* rbeg,
-                         uint32_t* beg, uint32_t* end, cudaStream_t s)
+                         uint32_t* recE, unsigned long long* scan_words, uint32_t* rbeg,
+                         uint32_t* beg, uint32_t* end, int* flags, cudaStream_t s)
 {
     cudaMemsetAsync(beg, 0, sizeof(uint32_t) * nsrc, s);
     cudaMemsetAsync(end, 0, sizeof(uint32_t) * nsrc, s);
     if (nrec <= 0) return;
-    k_record_gather<<<blocks(nrec, kGradThreads), kGradThreads, 0, s>>>(sidx, nrec, crec, srec,
-                                                                       cnt);
-    scan_exclusive(cnt, recE, nrec, scan_tmp, s);
-    k_record_segments<<<blocks(nrec, kGradThreads), kGradThreads, 0, s>>>(skey, nrec, nsrc, src_of,
-                                                                         recE, rbeg, beg, end);
-    counted(2);
+    const int64_t ntile = (nrec + kRsTile - 1) / kRsTile;
+    // the tiles' status words, then the ticket counter
+    cudaMemsetAsync(scan_words, 0, sizeof(unsigned long long) * (size_t)(ntile + 1), s);
+    k_record_scan<<<(unsigned)ntile, kRsThreads, 0, s>>>(
+        skey, sidx, nrec, crec, src_of, nsrc, srec, recE, rbeg, beg, end, scan_words,
+        reinterpret_cast<uint32_t*>(scan_words + ntile), flags);
+    counted(1);
 }
 
 namespace {
@@ -636,7 +828,7 @@ void record_source_sums(const vec4<R>* pos, const vec4<R>* u, const vec4<R>* aba
     // part holds 6 partial sums per item, then the item -> source map
     uint32_t* item_src = reinterpret_cast<uint32_t*>(part + 6 * max_items);
     k_item_sources<<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(item_off, nsrc, item_src);
-    k_item_sums_rec<R, VJP><<<blocks(max_items * 32, kGradThreads), kGradThreads, 0, s>>>(
+    k_item_sums_rec<R, VJP><<<blocks(max_items * 32, kItemThreads), kItemThreads, 0, s>>>(
         pos, u, abar, bbar, ds, t, ncells, nsrc, srec, recE, nrec, rbeg, beg, end, item_off,
         item_src, part);
     k_item_reduce<R><<<blocks(nsrc, kGradThreads), kGradThreads, 0, s>>>(t, ncells, nsrc, item_off,
