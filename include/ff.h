@@ -427,6 +427,24 @@ ff_status ff_morton_order_noalloc(const float *pos, int64_t n, uint64_t *keys_ou
  */
 ff_status ff_selftest_sort_wait(int64_t n, void *stream);
 
+/*
+ * Self-test of the other wait on other thread blocks (no counterpart in the
+ * paper): the energy gradient's record pass scans the sorted records' entry
+ * counts in one pass, each tile adding up the counts that earlier tiles
+ * publish, polling a bounded number of times and raising the same device
+ * error flag when the polls run out.  This call runs that pass on nrec
+ * synthetic records in buffers it allocates and frees, with the first tile
+ * withholding its count and every look-back window read once, so the second
+ * tile's wait must run out.
+ *
+ * nrec: 4096 .. 2^24 (at least two tiles).  stream: a cudaStream_t, NULL for
+ * the default stream.  Waits before returning.  FF_OK: the wait ran out and
+ * its flag reached the host.  FF_EDEVICE: it did not.  FF_EINVAL: nrec out of
+ * range.  FF_ECUDA: a CUDA call failed.  The reason is given by
+ * ff_last_error(NULL).
+ */
+ff_status ff_selftest_record_wait(int64_t nrec, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -185,4 +185,61 @@ ff_status ff_selftest_sort_wait(int64_t n, void* stream)
     return FF_OK;
 }
 
+// Synthetic sorted records: record i has key i / 4, index i and one entry.
+__global__ void k_selftest_records(uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
+                                   uint2* __restrict__ rec, int64_t nrec,
+                                   uint32_t* __restrict__ src_of, int64_t nsrc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nrec) {
+        key[i] = (uint32_t)(i / 4);
+        idx[i] = (uint32_t)i;
+        rec[i] = make_uint2((uint32_t)i, 1u);
+    }
+    if (i < nsrc) src_of[i] = (uint32_t)i;
+}
+
+ff_status ff_selftest_record_wait(int64_t nrec, void* stream)
+{
+    const int64_t tile = ffk::record_scan_tile();
+    if (nrec < 2 * tile || nrec > (int64_t)1 << 24)
+        return noalloc_fail(FF_EINVAL, "nrec must span at least two scan tiles (4096 .. 2^24)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t nsrc = nrec / 4 + 1;
+    uint32_t *key = nullptr, *idx = nullptr, *src_of = nullptr, *recE = nullptr;
+    uint32_t *rbeg = nullptr, *beg = nullptr, *end = nullptr;
+    uint2 *rec = nullptr, *srec = nullptr;
+    unsigned long long* words = nullptr;
+    int* flags = nullptr;
+    cudaError_t e = cudaMalloc(&key, sizeof(uint32_t) * nrec);
+    if (e == cudaSuccess) e = cudaMalloc(&idx, sizeof(uint32_t) * nrec);
+    if (e == cudaSuccess) e = cudaMalloc(&rec, sizeof(uint2) * nrec);
+    if (e == cudaSuccess) e = cudaMalloc(&srec, sizeof(uint2) * nrec);
+    if (e == cudaSuccess) e = cudaMalloc(&recE, sizeof(uint32_t) * (nrec + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&src_of, sizeof(uint32_t) * nsrc);
+    if (e == cudaSuccess) e = cudaMalloc(&rbeg, sizeof(uint32_t) * nsrc);
+    if (e == cudaSuccess) e = cudaMalloc(&beg, sizeof(uint32_t) * nsrc);
+    if (e == cudaSuccess) e = cudaMalloc(&end, sizeof(uint32_t) * nsrc);
+    if (e == cudaSuccess) e = cudaMalloc(&words, sizeof(unsigned long long) * ffk::record_scan_words(nrec));
+    if (e == cudaSuccess) e = cudaMalloc(&flags, sizeof(int));
+    int hflag = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_selftest_records<<<(unsigned)((nrec + 255) / 256), 256, 0, s>>>(key, idx, rec, nrec,
+                                                                          src_of, nsrc);
+        ffk::record_scan_wait_selftest(key, idx, nrec, rec, src_of, nsrc, srec, recE, words, rbeg,
+                                       beg, end, flags, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const cudaError_t e_run = e;
+    void* bufs[] = {key, idx, rec, srec, recE, src_of, rbeg, beg, end, words, flags};
+    for (void* b : bufs) cudaFree(b);
+    if (e_run != cudaSuccess) return noalloc_fail(FF_ECUDA, "record scan wait self-test", e_run);
+    if (!(hflag & ffk::FLAG_SORT))
+        return noalloc_fail(FF_EDEVICE, "the record scan's look-back wait did not run out with a tile withheld");
+    return FF_OK;
+}
+
 }  // extern "C"

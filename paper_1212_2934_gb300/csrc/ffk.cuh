@@ -291,10 +291,20 @@ void grad_pack_records(const uint32_t* tcount, const uint32_t* toff, int64_t nta
 // record_scan_words(nrec) words of scratch.  A tile that waits too long for an
 // earlier one raises FLAG_SORT in flags.
 size_t record_scan_words(int64_t nrec);
+int64_t record_scan_tile();  // records per tile of that pass
 void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
                          const uint2* crec, const uint32_t* src_of, int64_t nsrc, uint2* srec,
                          uint32_t* recE, unsigned long long* scan_words, uint32_t* rbeg,
                          uint32_t* beg, uint32_t* end, int* flags, cudaStream_t s);
+// The same pass with tile 0 withholding its count and every look-back window
+// read once: the bounded wait of tile 1 runs out and raises FLAG_SORT (the
+// offsets are then wrong; every write stays in bounds).  Only the self-test
+// calls it, and nothing reads its output.
+void record_scan_wait_selftest(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
+                               const uint2* crec, const uint32_t* src_of, int64_t nsrc,
+                               uint2* srec, uint32_t* recE, unsigned long long* scan_words,
+                               uint32_t* rbeg, uint32_t* beg, uint32_t* end, int* flags,
+                               cudaStream_t s);
 // per source s: G_s = sum over its entries of T(r) u_m and Q_s = sum of
 // grad phi(r; w_s, u_m) / n_s, r = rho_m - x_s (FP64 results, 3 per source).
 // Entry e of source s (beg[s] <= e < end[s]) is particle 32 task + lane of the

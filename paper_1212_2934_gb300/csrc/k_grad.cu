@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kRsThreads) k_record_scan(
     const uint2* __restrict__ crec, const uint32_t* __restrict__ src_of, int64_t nsrc,
     uint2* __restrict__ srec, uint32_t* __restrict__ recE, uint32_t* __restrict__ rbeg,
     uint32_t* __restrict__ beg, uint32_t* __restrict__ end, unsigned long long* status,
-    uint32_t* ticket, int* flags)
+    uint32_t* ticket, int* flags, int withhold)
 {
     __shared__ uint32_t s_tile, s_excl;
     __shared__ uint32_t s_warp[kRsThreads / 32];
@@ -343,7 +343,11 @@ __global__ void __launch_bounds__(kRsThreads) k_record_scan(
         // j0 - k; once every tile up to the nearest running total has published,
         // their counts are added (a full window of tile counts moves it back)
         volatile unsigned long long* st = status;
-        if (lane == 0) st[tile] = (tile == 0 ? kRsPrefix : kRsAggregate) | total;
+        // withhold (a self-test of the bounded wait): tile 0 never publishes and
+        // each window is read once, so the wait of tile 1 runs out
+        if (lane == 0 && !(withhold && tile == 0))
+            st[tile] = (tile == 0 ? kRsPrefix : kRsAggregate) | total;
+        const int spin_limit = withhold ? 1 : kRsSpinLimit;
         uint32_t excl = 0;
         int64_t j0 = tile - 1;
         for (int spins = 0; j0 >= 0;) {
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(kRsThreads) k_record_scan(
                 j0 -= 32;
                 continue;
             }
-            if (++spins >= kRsSpinLimit) {
+            if (++spins >= spin_limit) {
                 if (lane == 0) atomicOr(flags, FLAG_SORT);
                 break;
             }
@@ -792,10 +796,12 @@ size_t record_scan_words(int64_t nrec)
     return (size_t)((nrec + kRsTile - 1) / kRsTile) + 1;
 }
 
-void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
-                         const uint2* crec, const uint32_t* src_of, int64_t nsrc, uint2* srec,
-                         uint32_t* recE, unsigned long long* scan_words, uint32_t* rbeg,
-                         uint32_t* beg, uint32_t* end, int* flags, cudaStream_t s)
+namespace {
+
+void record_scan(const uint32_t* skey, const uint32_t* sidx, int64_t nrec, const uint2* crec,
+                 const uint32_t* src_of, int64_t nsrc, uint2* srec, uint32_t* recE,
+                 unsigned long long* scan_words, uint32_t* rbeg, uint32_t* beg, uint32_t* end,
+                 int* flags, int withhold, cudaStream_t s)
 {
     cudaMemsetAsync(beg, 0, sizeof(uint32_t) * nsrc, s);
     cudaMemsetAsync(end, 0, sizeof(uint32_t) * nsrc, s);
@@ -805,8 +811,31 @@ void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nre
     cudaMemsetAsync(scan_words, 0, sizeof(unsigned long long) * (size_t)(ntile + 1), s);
     k_record_scan<<<(unsigned)ntile, kRsThreads, 0, s>>>(
         skey, sidx, nrec, crec, src_of, nsrc, srec, recE, rbeg, beg, end, scan_words,
-        reinterpret_cast<uint32_t*>(scan_words + ntile), flags);
+        reinterpret_cast<uint32_t*>(scan_words + ntile), flags, withhold);
     counted(1);
+}
+
+}  // namespace
+
+int64_t record_scan_tile() { return kRsTile; }
+
+void grad_record_sources(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
+                         const uint2* crec, const uint32_t* src_of, int64_t nsrc, uint2* srec,
+                         uint32_t* recE, unsigned long long* scan_words, uint32_t* rbeg,
+                         uint32_t* beg, uint32_t* end, int* flags, cudaStream_t s)
+{
+    record_scan(skey, sidx, nrec, crec, src_of, nsrc, srec, recE, scan_words, rbeg, beg, end,
+                flags, 0, s);
+}
+
+void record_scan_wait_selftest(const uint32_t* skey, const uint32_t* sidx, int64_t nrec,
+                               const uint2* crec, const uint32_t* src_of, int64_t nsrc,
+                               uint2* srec, uint32_t* recE, unsigned long long* scan_words,
+                               uint32_t* rbeg, uint32_t* beg, uint32_t* end, int* flags,
+                               cudaStream_t s)
+{
+    record_scan(skey, sidx, nrec, crec, src_of, nsrc, srec, recE, scan_words, rbeg, beg, end,
+                flags, 1, s);
 }
 
 namespace {

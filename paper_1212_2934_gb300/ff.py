@@ -97,6 +97,7 @@ _SIGS = {
     "ff_profile_read": (_st, [_vp, C.POINTER(ff_profile_t)]),
     "ff_morton_order_noalloc": (_st, [_vp, C.c_int64, _vp, _vp, _vp]),
     "ff_selftest_sort_wait": (_st, [C.c_int64, _vp]),
+    "ff_selftest_record_wait": (_st, [C.c_int64, _vp]),
     "ff_schedule_count": (C.c_int32, []),
     "ff_schedule_info": (_st, [C.c_int32, _vp, _vp, _vp]),
     "ff_set_schedule": (_st, [_vp, C.c_int32]),
@@ -518,6 +519,13 @@ def ff_selftest_sort_wait(n=20000, stream=None):
     unless the bounded wait ran out and reported its flag."""
     sp = None if stream is None else C.c_void_p(stream.cuda_stream)
     _check(None, lib().ff_selftest_sort_wait(int(n), sp))
+
+
+def ff_selftest_record_wait(nrec=20000, stream=None):
+    """Runs the gradient's one-pass record scan with its first tile withholding its count
+    (include/ff.h); raises FFError unless the bounded wait ran out and reported its flag."""
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(None, lib().ff_selftest_record_wait(int(nrec), sp))
 
 
 def ff_last_error(ctx=None):
