@@ -494,7 +494,7 @@ ff_status sync_and_check(ff_ctx* c)
     if (fl & ffk::FLAG_NONFINITE) return fail(c, FF_ENONFINITE, "a particle position is NaN or infinite");
     if (fl & ffk::FLAG_TRAVERSE) return fail(c, FF_EDEVICE, "traversal guard tripped");
     if (fl & ffk::FLAG_AGGREGATE) return fail(c, FF_EDEVICE, "aggregation guard tripped");
-    if (fl & ffk::FLAG_SORT) return fail(c, FF_EDEVICE, "sort tile timed out waiting for an earlier tile");
+    if (fl & ffk::FLAG_SORT) return fail(c, FF_EDEVICE, "a sort or record-scan tile timed out waiting for an earlier tile");
     if (fl & ffk::FLAG_CAPACITY) {
         const ff_status s = recover_cells(c);
         return s == FF_OK ? kRetry : s;

@@ -32,7 +32,7 @@ enum : int {
     FLAG_TRAVERSE = 2,    // traversal guard tripped (corrupt skip pointers)
     FLAG_CAPACITY = 4,    // more cells than allocated
     FLAG_AGGREGATE = 8,   // aggregation walk exceeded the level bound
-    FLAG_SORT = 16,       // a sort tile waited too long for an earlier tile's counts
+    FLAG_SORT = 16,       // a sort (or record-scan) tile waited too long for an earlier tile's counts
 };
 
 constexpr int kMaxLevel = 21;        // 21 bits per axis -> 63-bit Morton keys
